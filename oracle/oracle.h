@@ -1,0 +1,190 @@
+/*
+ * FP64 CPU oracle for the parametric detector response (TEST INFRASTRUCTURE).
+ *
+ * This is the plain, slow, obviously-correct reference that the CUDA path is
+ * checked against.  Only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no code, header, table
+ * or constant generator with the CUDA library: it expands the detector card
+ * itself, implements its own Philox4x32-10, and computes every step in double
+ * precision in the order the method defines.
+ *
+ * The method is the paper's parametric backend (TorchDelphes, Sec. 2.2 and
+ * App. C.1): particle propagation in the solenoid field, tracking efficiency,
+ * momentum smearing, calorimeter response (towers), energy-flow merging, and
+ * the lepton isolation of Sec. 2.3 (Eq. 1).  The paper prints no formulas for
+ * the TorchDelphes modules; the readings used here (helix geometry, log-normal
+ * smearing, tower centres, thresholds, counter-based random numbers) are the
+ * project's and are listed in the design notes.
+ *
+ * Decisions taken on floating-point values (a tower index, a threshold, a cone
+ * edge) are taken in float32, the CUDA kernel's precision: the double value is
+ * rounded to float and compared with the float32 threshold or edge.  Every such
+ * decision whose double value lies within a relative band g of its threshold is
+ * reported as "marginal", and a caller may ask the oracle to take the other
+ * branch of a marginal decision (a "flip").  The oracle refuses flips of
+ * decisions that are not marginal.  This lets a test accept either outcome of a
+ * decision that float32 rounding can legitimately change, and still check
+ * everything downstream of it exactly.
+ */
+#ifndef PDR_ORACLE_H
+#define PDR_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAXSEG 4      /* eta segments per calorimeter (per side)        */
+#define OR_MAXEDGE 8     /* edges per piecewise-constant table axis         */
+#define OR_MAXRING 512   /* eta rings per calorimeter (both sides)          */
+
+/* Particle classes (from |pdg| and charge). */
+enum { OR_CLS_E = 0, OR_CLS_MU = 1, OR_CLS_GAMMA = 2, OR_CLS_CHAD = 3,
+       OR_CLS_NHAD = 4, OR_CLS_INVIS = 5 };
+/* Calorimeters. */
+enum { OR_ECAL = 0, OR_HCAL = 1 };
+/* Resolution components. */
+enum { OR_RES_TRACK = 0, OR_RES_MUON = 1, OR_RES_ECAL = 2, OR_RES_HCAL = 3 };
+/* Random-number purposes (third Philox counter word). */
+enum { OR_PURPOSE_TRACK = 1, OR_PURPOSE_ID = 2, OR_PURPOSE_TOWER_ECAL = 3,
+       OR_PURPOSE_TOWER_HCAL = 4 };
+
+/* Decision kinds (for marginal reports and flips). */
+enum {
+  OR_K_BARREL = 1,    /* id = particle: |z at barrel| <= L                    */
+  OR_K_LOOP = 2,      /* id = particle: endcap turning angle psi < 2 pi         */
+  OR_K_ETA = 3,       /* id = particle, aux = calo: eta-ring lookup           */
+  OR_K_PHI = 4,       /* id = particle, aux = calo: phi-bin lookup            */
+  OR_K_TWR_E = 5,     /* id = tower key: E' > E_min                           */
+  OR_K_TWR_S = 6,     /* id = tower key: E'/sigma(E') > S_min                 */
+  OR_K_EF_E = 7,      /* id = tower key: dE > E_min                           */
+  OR_K_EF_S = 8,      /* id = tower key: dE/sigma(E') > S_min                 */
+  OR_K_ISO_PT = 9,    /* id = object (track: particle, neutral: key), aux = 0 track / 1 neutral */
+  OR_K_ISO_DR = 10,   /* id = candidate particle, aux = object id, aux2 = object type: dR^2 < dR_max^2 */
+  OR_K_ISO_DRMIN = 11,/* same ids: dR^2 >= dR_min^2                            */
+  OR_K_ISOLATED = 12  /* id = candidate particle: I < I_max                    */
+};
+
+/* Particle flag bits (per-particle debug record). */
+#define OR_F_REACH   0x01u  /* reached the calorimeter surface                */
+#define OR_F_BARREL  0x02u  /* hit the barrel (else endcap)                     */
+#define OR_F_TRACKED 0x04u  /* accepted by the tracking efficiency              */
+#define OR_F_CAND    0x08u  /* e/mu/gamma candidate accepted by its ID efficiency */
+#define OR_F_ECAL    0x10u  /* deposited in ECAL                                */
+#define OR_F_HCAL    0x20u  /* deposited in HCAL                                */
+
+#define OR_NO_KEY 0xFFFFFFFFu
+
+/* Raw detector card (the JSON card's numbers; units GeV, m, T). */
+typedef struct {
+  double B, R, L;
+  int32_t nseg[2];
+  double seg_eta_hi[2][OR_MAXSEG];
+  int32_t seg_neta[2][OR_MAXSEG];
+  int32_t seg_nphi[2][OR_MAXSEG];
+  int32_t trk_npt, trk_neta;
+  double trk_pt_edges[OR_MAXEDGE];
+  double trk_eta_edges[OR_MAXEDGE];
+  double trk_eff[3][OR_MAXEDGE][OR_MAXEDGE];  /* [hadron, electron, muon][pt bin][|eta| bin] */
+  int32_t res_n[4];
+  double res_edges[4][OR_MAXEDGE];
+  double res_abcd[4][OR_MAXEDGE][4];         /* [component][|eta| bin][a, b, c, d] */
+  int32_t id_n;
+  double id_edges[OR_MAXEDGE];
+  double id_eff[3][OR_MAXEDGE];              /* [electron, muon, photon][|eta| bin] */
+  double e_min[2], s_min[2];
+  double cand_ptmin, iso_dr, iso_drmin, iso_ptmin, iso_imax;
+} oracle_card;
+
+/* Per-particle record. */
+typedef struct {
+  double eta_pos, phi_pos;   /* position on the calorimeter surface (if reached) */
+  double e;                  /* truth energy                                   */
+  uint32_t key;              /* tower key deposited into, or OR_NO_KEY          */
+  uint32_t flags;            /* OR_F_* bits                                    */
+  uint32_t cls;              /* OR_CLS_*                                       */
+  uint32_t pad;
+} or_particle;
+
+typedef struct {
+  double pt, eta, phi, e;    /* smeared pT, momentum direction, track energy  */
+  uint32_t idx, pad;         /* particle index in the event                    */
+} or_track;
+
+typedef struct {
+  double esum, etrk;         /* pre-smearing deposit sum, sum of track energies */
+  double e, et, sigma;       /* smeared energy, E'/cosh(eta_c), sigma(E')       */
+  double eflow_e, eflow_et;  /* dE = E' - etrk and dE/cosh(eta_c)               */
+  double eta_c, phi_c;       /* tower centre                                    */
+  uint32_t key, owner;       /* tower key; lowest depositing particle index     */
+  uint32_t kept, eflow_kept;
+} or_tower;
+
+typedef struct {
+  double pt, eta, phi;       /* smeared pT, momentum direction                 */
+  double iso_sum, iso_rel;   /* cone sum and I = sum / pT                       */
+  uint32_t idx, cls;         /* particle index, 0 e / 1 mu / 2 gamma            */
+  uint32_t isolated, pad;
+} or_cand;
+
+typedef struct {
+  uint32_t kind, id, aux, aux2;
+  double v, t;               /* decision value and threshold (double)          */
+  double w;                  /* pair decisions: the object's pT contribution   */
+  int32_t taken, alt;        /* branch taken; alternative (lookups: other bin) */
+} or_marginal;
+
+typedef struct { uint32_t kind, id, aux, aux2; } or_flip;
+
+typedef struct {
+  int32_t n_trk, n_twr, n_twr_kept, n_eflow, n_cand, n_marg, err, pad;
+} or_counts;
+
+/* ---- building blocks (exposed for the pin tests) ---- */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double oracle_u01(uint32_t w);
+double oracle_normal(uint32_t wa, uint32_t wb);
+double oracle_lognormal(double x, double rel, double z);
+double oracle_rel_resolution(const oracle_card* c, int comp, double abseta, double x);
+uint64_t oracle_eff_threshold(double eff);
+int oracle_classify(int32_t pdg, int32_t charge);
+/* Propagation of one particle; returns reach (0/1).  barrel/eta_pos/phi_pos out. */
+int oracle_propagate(const oracle_card* c, double pt, double eta, double phi, int32_t q,
+                     double vz, int32_t* barrel, double* eta_pos, double* phi_pos);
+/* Tower key of a position in a calorimeter, or OR_NO_KEY if outside coverage. */
+uint32_t oracle_tower_key(const oracle_card* c, int calo, double eta_pos, double phi_pos);
+/* Centre of a tower; returns 0 on success. */
+int oracle_tower_centre(const oracle_card* c, uint32_t key, double* eta_c, double* phi_c,
+                        int32_t* ring, int32_t* iphi);
+int oracle_n_towers(const oracle_card* c, int calo);
+/* Array forms for the statistical pins (element-wise, n elements). */
+void oracle_philox_n(int64_t n, const uint32_t* ctr4, const uint32_t key[2], uint32_t* out4);
+void oracle_normal_n(int64_t n, const uint32_t* wa, const uint32_t* wb, double* out);
+void oracle_lognormal_n(int64_t n, double x, double rel, const double* z, double* out);
+
+/* ---- one event, with decision reports and flips ----
+ * Outputs are caller-allocated with room for n records each (marg: marg_cap).
+ * Towers are returned in ascending key order, all of them (kept or not).
+ * Returns 0, or a negative code: -1 bad argument, -2 a flip named a decision
+ * that is not marginal, -3 marginal list overflow. */
+int oracle_run_event(const oracle_card* c, int64_t n, const float* pt, const float* eta,
+                     const float* phi, const float* mass, const int32_t* pdg,
+                     const int8_t* charge, const float* vz, uint64_t seed, uint32_t event,
+                     double g, const or_flip* flips, int32_t n_flips,
+                     or_particle* part, or_track* trk, or_tower* twr, or_cand* cand,
+                     or_marginal* marg, int32_t marg_cap, or_counts* counts);
+
+/* ---- a whole CSR batch on nthreads host threads (CPU baseline) ----
+ * counts_out[e*4 + {0,1,2,3}] = tracks, kept towers, EFlow neutrals, candidates.
+ * Returns 0 or a negative code. */
+int oracle_run_batch(const oracle_card* c, int64_t n_events, const uint64_t* offsets,
+                     const float* pt, const float* eta, const float* phi, const float* mass,
+                     const int32_t* pdg, const int8_t* charge, const float* vz,
+                     uint64_t seed, uint32_t event_base, int32_t nthreads,
+                     uint32_t* counts_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
