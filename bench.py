@@ -1,0 +1,378 @@
+"""Benchmark: particles/s through the detector response on one B300.
+
+A step is one pass of the whole response (propagation, efficiencies,
+smearing, towers, energy flow, isolation, counts) over one batch of synthetic
+events already resident in HBM: a single fused persistent launch.  The default
+workload is the batched CMS-like configuration (100k events, Poisson(400) + 4
+hard objects, ~40.4M particles).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batched|ee|pileup|tiny]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (events are independent; no data-path collective) and the
+slowest rank's time counts; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s through detector response at 1 B300 (% HBM roofline) vs per-event; p99 latency"
+WORKLOAD_DESC = {
+    "batched": "batched CMS-like: 100k events x (Poisson(400) + 4 hard objects), one ragged CSR launch",
+    "ee": "e+e- ALEPH-like: 1M events x Poisson(35), sum E = 91.2 GeV",
+    "pileup": "pileup CMS-like: 10k events x (Poisson(400) + 170 x Poisson(30)), vertex z spread",
+    "tiny": "tiny CMS-like: 100 events x Poisson(50)",
+}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            backend = os.environ.get("PDR_DIST_BACKEND", "nccl")
+            dist.init_process_group(backend)
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_from_profile(workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the kernel source."""
+    path = os.path.join(ROOT, "profiles", f"fused_kernel_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = open(os.path.join(ROOT, "paper_2606_26089_b300", "csrc", "pdr_kernel.cu"), "rb").read()
+    sha = hashlib.sha1(src).hexdigest()[:12]
+    m_sha = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_t or m_sha.group(1) != sha:
+        return None
+    return float(m_t.group(1))
+
+
+def bench_ours(args, dist, rank, ws):
+    import torch
+
+    from paper_2606_26089_b300 import binding as B
+    from paper_2606_26089_b300 import build as pdr_build
+    from paper_2606_26089_b300 import synth
+
+    pdr_build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    batch = synth.make(args.workload, args.events)
+    card_name = synth.card_for(args.workload)
+    n_ev, n_p = batch.n_events, batch.n_particles
+    ctx = B.Context(local, pool_bytes=int(args.pool_gb * (1 << 30)))
+    cid = ctx.card_load(card_name)
+    dev = B.batch_to_device(batch)
+    out = B.alloc_outputs(n_ev, n_p)
+    ob = B.make_outputs(out)
+    base = rank * n_ev  # replicas process different events
+    bt = B.make_batch(dev, cid, args.seed, event_base=base)
+    best = ctx.autotune(bt, ob)
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident throughput: K fused launches, per-launch CUDA events
+    for _ in range(args.warmup):
+        ctx.run(bt, ob)
+    torch.cuda.synchronize()
+    ctx.check()
+    counts = out["counts"].cpu().numpy().view(np.uint32)[:n_ev].astype(np.int64)
+    tot = counts.sum(axis=0)
+    in_bytes = batch.nbytes_input()
+    out_bytes = 16 * tot[0] + 12 * tot[1] + 12 * tot[2] + (16 + 8) * tot[3] + 16 * n_ev
+    alg_bytes = int(in_bytes + out_bytes)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        ctx.run(bt, ob)
+        stops[k].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ctx.check()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n_p * args.steps / (total_ms / 1e3)
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = alg_bytes / avg_launch_s / 1e9
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    traffic = _traffic_from_profile(args.workload)
+
+    # ---- end to end through the host-buffer call: H2D inputs, run, D2H results
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_in = {k: (None if getattr(batch, k) is None else pin(getattr(batch, k)))
+                for k in ("offsets", "pt", "eta", "phi", "mass", "pdg", "charge", "vz")}
+        hb = B.pdr_batch()
+        hb.n_events = n_ev
+        for k, v in h_in.items():
+            setattr(hb, k, None if v is None else v.ctypes.data)
+        hb.seed, hb.event_index_base, hb.card_id, hb.max_event_size, hb.flags = args.seed, base, cid, 0, 0
+        hb.max_event_size = int(batch.multiplicities().max())
+        h_out = {k: torch.empty(shape, dtype=dt).pin_memory().numpy() for k, shape, dt in (
+            ("tracks", (n_p, 4), torch.float32), ("towers", (n_p, 3), torch.float32),
+            ("eflow", (n_p, 3), torch.float32), ("cands", (n_p, 4), torch.float32),
+            ("iso", (n_p, 2), torch.float32), ("counts", (n_ev, 4), torch.int32))}
+        ho = B.pdr_outputs()
+        for k, v in h_out.items():
+            setattr(ho, k, v.ctypes.data)
+        for _ in range(max(1, min(args.warmup, 2))):
+            ctx.run_host(hb, ho, launch=best)
+        if dist:
+            dist.barrier()
+        times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.run_host(hb, ho, launch=best)
+            times.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(times)
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        c2 = h_out["counts"].view(np.uint32).astype(np.int64).sum(axis=0)
+        d2h = int(16 * c2[0] + 12 * c2[1] + 12 * c2[2] + (16 + 8) * c2[3] + 16 * n_ev)
+        e2e = {"value": ws * n_p / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": int(in_bytes),
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+
+    # ---- the plain per-event form (one launch per event) on a prefix
+    per_event = None
+    if not args.no_per_event and n_ev > 0:
+        npre = min(args.per_event_events, n_ev)
+        pre = batch.slice_events(0, npre)
+        pdev = B.batch_to_device(pre)
+        pout = B.alloc_outputs(npre, pre.n_particles)
+        pb = B.make_batch(pdev, cid, args.seed, event_base=base)
+        ctx.run_per_event(pb, B.make_outputs(pout))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.run_per_event(pb, B.make_outputs(pout))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        per_event = {"value": pre.n_particles / s, "unit": "particles/s", "events": npre,
+                     "events_per_s": npre / s, "speedup_batched_over_per_event": (n_p / avg_launch_s) / (pre.n_particles / s)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "events_per_s": ws * n_ev * args.steps / (total_ms / 1e3),
+        "config": {"workload": WORKLOAD_DESC[args.workload], "card": card_name, "n_events": n_ev,
+                   "n_particles": n_p, "seed": args.seed, "launch": best.as_dict(),
+                   "l2": f"inputs {in_bytes / 1e6:.0f} MB per step > 126 MB L2; no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.4 TB/s",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_s * 1e3,
+                     "kernel": "pdr::fused_kernel"},
+        "e2e": e2e,
+        "per_event_form": per_event,
+        "clocks": clk,
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch, card_name, args.seed, args.cpu_seconds)
+    ctx.close()
+    return line
+
+
+def cpu_baseline(batch, card_name, seed, target_s):
+    """The oracle as it stands, on the host cores, on a bounded prefix of the workload."""
+    import oracle
+
+    oracle.build()
+    card = oracle.load_card(card_name)
+    cores = os.cpu_count() or 1
+    n = min(batch.n_events, 200)
+    t0 = time.perf_counter()
+    oracle.run_batch(card, batch.slice_events(0, n), seed, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n_sample = int(min(batch.n_events, max(n, n * target_s / dt)))
+    sample = batch.slice_events(0, n_sample)
+    t0 = time.perf_counter()
+    oracle.run_batch(card, sample, seed, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample.n_particles / dt, "unit": "particles/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample} of {batch.n_events} events ({sample.n_particles} particles), "
+                      f"{dt:.1f} s on {cores} threads"}
+
+
+def bench_reference(args, rank):
+    """The reference arm: the FP64 oracle on the host cores, bounded samples."""
+    from paper_2606_26089_b300 import synth
+    import oracle
+
+    if rank != 0:
+        return None
+    oracle.build()
+    batch = synth.make(args.workload, args.events)
+    card = oracle.load_card(synth.card_for(args.workload))
+    cores = os.cpu_count() or 1
+    n = min(batch.n_events, 200)
+    t0 = time.perf_counter()
+    oracle.run_batch(card, batch.slice_events(0, n), args.seed, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_step = min(10.0, 150.0 / max(args.steps + args.warmup, 1))
+    n_sample = int(min(batch.n_events, max(n, n * per_step / dt)))
+    sample = batch.slice_events(0, n_sample)
+    for _ in range(args.warmup):
+        oracle.run_batch(card, sample, args.seed, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_batch(card, sample, args.seed, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    s = statistics.mean(times)
+    value = sample.n_particles / s
+    desc = f"first {n_sample} of {batch.n_events} events ({sample.n_particles} particles) per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "card": synth.card_for(args.workload),
+                       "n_events": batch.n_events, "n_particles": batch.n_particles, "seed": args.seed,
+                       "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_DESC), default="batched")
+    ap.add_argument("--events", type=int, default=None, help="override the workload's event count")
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--pool-gb", type=float, default=8.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--per-event-events", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-event", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.seed is None:
+        args.seed = {"tiny": 0, "batched": 1, "ee": 2, "pileup": 3}[args.workload]
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        # rank 0 alone times the oracle; other ranks exit without work
+        rank = int(os.environ.get("RANK", "0"))
+        line = bench_reference(args, rank)
+        if rank == 0 and line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    dist, rank, ws = _dist()
+    line = bench_ours(args, dist, rank, ws)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,270 @@
+/*
+ * pdr.h - parametric detector response on one GPU: the C ABI.
+ *
+ * The library applies a Delphes-style parametric detector response to every
+ * truth particle of every event in a batch: the TorchDelphes module chain of
+ * the paper (Sec. 2.2 "parametric backend"; App. C.1): particle propagation in
+ * the solenoid field, tracking / lepton / photon efficiencies, momentum and
+ * energy smearing, ECAL/HCAL eta-phi towers with smearing and thresholds,
+ * energy-flow track subtraction (Towers and EFlowObjects), and the cone
+ * isolation of electrons, muons and photons (Sec. 2.3, Eq. 1).
+ *
+ * Everything on the data path runs in the library's CUDA kernels.  All entry
+ * points are plain C: pointers, sizes and status codes; no C++ types and no
+ * PyTorch types cross this boundary.  Pointers are DEVICE pointers unless an
+ * entry point says HOST.  Streams are passed as `void*` holding a
+ * `cudaStream_t` (NULL = the legacy default stream).
+ *
+ * Errors: every entry point returns a pdr_status.  Nothing is thrown across
+ * the ABI.  On failure `pdr_last_error(ctx)` gives a message for the calling
+ * thread.  A device-side error (an overflowed table, a bounded wait that ran
+ * out) is recorded in a device error word that `pdr_check` / `pdr_wait` read.
+ *
+ * Randomness: counter-based Philox4x32-10 keyed by (seed low, seed high) with
+ * counter (slot, event, purpose, 0), where event = event_index_base + e for
+ * the e-th event of a batch, slot = the particle's index inside its event
+ * (purposes 1 tracking, 2 identification) or the tower id (purposes 3 ECAL,
+ * 4 HCAL tower smearing).  A result therefore depends only on the event's
+ * particles, the card, the seed and the event's index - not on batching,
+ * launch shape or which other events share the batch.
+ */
+#ifndef PDR_H
+#define PDR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDR_ABI_VERSION 1
+
+typedef enum {
+  PDR_OK = 0,
+  PDR_EINVAL = -1,     /* bad argument (null pointer, malformed CSR, bad size)      */
+  PDR_ENOMEM = -2,     /* device or pool memory exhausted                           */
+  PDR_ECARD = -3,      /* malformed card (non-monotone edges, efficiency outside [0,1]) */
+  PDR_ETIMEDOUT = -4,  /* a bounded wait ran out                                    */
+  PDR_EDEVICE = -5,    /* CUDA error, or a device-side error word was set           */
+  PDR_EBUSY = -6,      /* too many tickets in flight / serving loop busy            */
+  PDR_ENOTFOUND = -7,  /* unknown card id or ticket                                 */
+  PDR_EOVERFLOW = -8   /* an event exceeds the size the launch configuration allows */
+} pdr_status;
+
+/* ---------------------------------------------------------------- cards -- */
+#define PDR_MAXSEG 4   /* eta segments per calorimeter side           */
+#define PDR_MAXEDGE 8  /* edges per axis of a piecewise-constant table */
+
+/* Calorimeters and classes (also used in output keys and flags). */
+#define PDR_ECAL 0
+#define PDR_HCAL 1
+#define PDR_CAND_E 0
+#define PDR_CAND_MU 1
+#define PDR_CAND_GAMMA 2
+
+/*
+ * Detector card: raw parameters (GeV, m, T), as the paper's cards give the
+ * per-module parameters (App. C.1).  The library expands them into device
+ * tables at pdr_card_load; the caller keeps ownership of the struct.
+ *
+ * Calorimeter grids: each side of eta = 0 is cut into nseg segments; segment
+ * s spans [eta_hi[s-1], eta_hi[s]] (eta_hi[-1] = 0) in neta[s] rings of
+ * nphi[s] towers.  Ring edges inside a segment are lo + ((hi - lo) * k) / n
+ * (double precision), segment ends exact; phi edges are -pi + (2 pi k) / nphi.
+ * Tower id = (rings below) + phi bin; tower key = calo << 24 | id.
+ * Piecewise-constant tables use bins [edge_k, edge_k+1) with an open last bin.
+ */
+typedef struct pdr_card {
+  double B, R, L;                        /* field (T), calorimeter radius and half-length (m) */
+  int32_t nseg[2];
+  double seg_eta_hi[2][PDR_MAXSEG];
+  int32_t seg_neta[2][PDR_MAXSEG];
+  int32_t seg_nphi[2][PDR_MAXSEG];
+  int32_t trk_npt, trk_neta;             /* tracking efficiency table axes       */
+  double trk_pt_edges[PDR_MAXEDGE];
+  double trk_eta_edges[PDR_MAXEDGE];     /* |eta| edges                          */
+  double trk_eff[3][PDR_MAXEDGE][PDR_MAXEDGE]; /* [hadron, electron, muon][pT bin][|eta| bin] */
+  int32_t res_n[4];                      /* resolution tables: track, muon, ECAL, HCAL */
+  double res_edges[4][PDR_MAXEDGE];      /* |eta| edges                          */
+  double res_abcd[4][PDR_MAXEDGE][4];    /* sigma/x = sqrt(a^2/x + b^2/x^2 + c^2 + d^2 x^2) */
+  int32_t id_n;                          /* identification efficiency table      */
+  double id_edges[PDR_MAXEDGE];          /* |eta| edges                          */
+  double id_eff[3][PDR_MAXEDGE];         /* [electron, muon, photon][|eta| bin]  */
+  double e_min[2], s_min[2];             /* tower / EFlow thresholds: E > e_min, E/sigma > s_min */
+  double cand_ptmin;                     /* e/mu/gamma candidates need truth pT > cand_ptmin */
+  double iso_dr, iso_drmin, iso_ptmin, iso_imax; /* isolation cone, inner cone, object pT floor, I_max */
+} pdr_card;
+
+/* ---------------------------------------------------------- output records -- */
+/* All output collections are written per event into slots starting at the
+ * event's INPUT offset (offsets[e]); event e's k-th record of a collection is
+ * at [offsets[e] + k], and counts[4 e + c] says how many there are (c = 0
+ * tracks, 1 towers, 2 EFlow neutrals, 3 candidates).  Every collection has at
+ * most as many records as the event has particles, so buffers of n_particles
+ * records always suffice.  Records within an event are ordered by particle
+ * index (towers and EFlow neutrals: by the lowest index depositing in them). */
+typedef struct { float pt, eta, phi; uint32_t idx; } pdr_track;     /* smeared pT, momentum direction, particle index */
+typedef struct { uint32_t key; float e, et; } pdr_tower;            /* key = calo << 24 | tower id; E', E'/cosh(eta_c) */
+typedef struct { uint32_t key; float e, et; } pdr_eflow;            /* EFlow neutral at the tower centre: dE, dE/cosh(eta_c) */
+typedef struct { float pt, eta, phi; uint32_t info; } pdr_cand;     /* info = idx | class << 28 | isolated << 31 */
+typedef struct { float sum, rel; } pdr_iso;                         /* cone pT sum and sum / pT */
+typedef struct { uint32_t key; float eta_pos, phi_pos; uint32_t flags; } pdr_debug; /* per particle */
+
+#define PDR_CAND_IDX(info) ((info) & 0x0FFFFFFFu)
+#define PDR_CAND_CLASS(info) (((info) >> 28) & 0x3u)
+#define PDR_CAND_ISOLATED(info) ((info) >> 31)
+
+/* pdr_debug.flags bits */
+#define PDR_F_REACH 0x01u    /* reached the calorimeter surface     */
+#define PDR_F_BARREL 0x02u   /* hit the barrel (else the endcap)      */
+#define PDR_F_TRACKED 0x04u  /* accepted by the tracking efficiency   */
+#define PDR_F_CAND 0x08u     /* accepted e/mu/gamma candidate         */
+#define PDR_F_ECAL 0x10u     /* deposited in ECAL                     */
+#define PDR_F_HCAL 0x20u     /* deposited in HCAL                     */
+#define PDR_NO_KEY 0xFFFFFFFFu
+
+/* ---------------------------------------------------------------- batches -- */
+/* A ragged CSR batch in SoA layout (DEVICE pointers unless PDR_BATCH_HOST).
+ * offsets[n_events + 1] is non-decreasing with offsets[0] = 0; particle
+ * arrays hold offsets[n_events] entries; vz may be NULL (all vertices at 0). */
+#define PDR_BATCH_DEBUG 0x1u      /* also write pdr_debug records             */
+typedef struct pdr_batch {
+  uint64_t n_events;
+  const uint64_t* offsets;
+  const float* pt;            /* GeV                          */
+  const float* eta;           /* momentum pseudorapidity      */
+  const float* phi;           /* momentum azimuth, [-pi, pi)  */
+  const float* mass;          /* GeV                          */
+  const int32_t* pdg;         /* PDG id                       */
+  const int8_t* charge;       /* units of e                   */
+  const float* vz;            /* vertex z (m) or NULL         */
+  uint64_t seed;
+  uint32_t event_index_base;
+  uint32_t card_id;
+  uint32_t max_event_size;    /* largest event (particles); 0 = let the library find it */
+  uint32_t flags;             /* PDR_BATCH_* */
+} pdr_batch;
+
+/* Caller-owned DEVICE output buffers, each with room for offsets[n_events]
+ * records (counts: 4 * n_events words; debug may be NULL). */
+typedef struct pdr_outputs {
+  pdr_track* tracks;
+  pdr_tower* towers;
+  pdr_eflow* eflow;
+  pdr_cand* cands;
+  pdr_iso* iso;
+  uint32_t* counts;
+  pdr_debug* debug;
+} pdr_outputs;
+
+/* Launch shape of the fused kernel: `team` threads work on one event (32 =
+ * warp per event ... 1024 = block per event), `block` threads per CTA (a
+ * multiple of team), `table_slots` shared-memory tower-table slots per team
+ * (power of two; events larger than about 0.85 x table_slots particles use a
+ * global-memory table), `grid` CTAs (0 = fill the GPU, persistent). */
+typedef struct pdr_launch {
+  uint32_t team, block, table_slots, grid;
+} pdr_launch;
+
+/* ---------------------------------------------------------------- context -- */
+typedef struct pdr_ctx pdr_ctx;
+
+typedef struct pdr_options {
+  uint64_t pool_bytes;    /* device pool for submit() results and scratch (0: 1 GiB) */
+  uint32_t max_tickets;   /* outstanding submit() tickets (0: 64)                    */
+  uint32_t flags;         /* reserved, 0                                             */
+} pdr_options;
+
+/* Create a context on CUDA device `cuda_device` (made current by the call).
+ * opt may be NULL.  On success *out owns device memory until pdr_destroy. */
+int pdr_create(pdr_ctx** out, int cuda_device, const pdr_options* opt);
+/* Destroy a context after synchronising its work.  Frees every card, ticket,
+ * graph and pool it owns.  NULL is accepted. */
+int pdr_destroy(pdr_ctx* ctx);
+/* Thread-local message for the calling thread's last failure in ctx. */
+const char* pdr_last_error(pdr_ctx* ctx);
+/* Version of this ABI (PDR_ABI_VERSION). */
+int pdr_abi_version(void);
+
+/* Validate a card (monotone edges, efficiencies in [0, 1], positive R, L,
+ * table sizes in range), expand it and copy the tables to the device.  The
+ * struct is HOST memory and stays the caller's.  *card_id names it. */
+int pdr_card_load(pdr_ctx* ctx, const pdr_card* card, uint32_t* card_id);
+/* Free a card's device tables (after synchronising). */
+int pdr_card_unload(pdr_ctx* ctx, uint32_t card_id);
+/* Number of towers of a card's calorimeter (PDR_ECAL / PDR_HCAL) via *n. */
+int pdr_card_towers(pdr_ctx* ctx, uint32_t card_id, int calo, uint32_t* n);
+
+/* ------------------------------------------------------------ batched path -- */
+/* Enqueue the whole detector response for a batch on `stream` (one persistent
+ * fused launch), writing into caller-owned device buffers.  Asynchronous: the
+ * caller must keep inputs and outputs alive until the stream has finished.
+ * launch may be NULL (the context's tuned or default shape is used).  Events
+ * larger than the launch's shared-memory table use a global-memory table from
+ * the context pool (allocated on first need, outside any stream capture).
+ * Returns PDR_EINVAL for malformed arguments (checked on the host: non-null
+ * pointers, n_events < 2^31; the CSR itself is checked on the device and a bad
+ * one sets the device error word). */
+int pdr_run(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,
+            const pdr_launch* launch, void* stream);
+
+/* The plain per-event form: one launch per event (team = block per event),
+ * for comparison with pdr_run.  Same outputs, same bits. */
+int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,
+                      void* stream);
+
+/* End-to-end call with HOST buffers: copies the batch (HOST pointers, ideally
+ * pinned) to device memory from the context pool, runs it, and copies every
+ * output back into HOST buffers laid out as pdr_outputs (HOST pointers, same
+ * sizes), then synchronises `stream`.  Blocking. */
+int pdr_run_host(pdr_ctx* ctx, const pdr_batch* host_batch, const pdr_outputs* host_out,
+                 const pdr_launch* launch, void* stream);
+
+/* Time the candidate launch shapes on this batch (each once after a warm-up)
+ * and remember the fastest for batches of this card and size class; *best
+ * (may be NULL) receives it.  The outputs are scratch for the trial runs.
+ * Synchronises the stream. */
+int pdr_autotune(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* scratch_out,
+                 void* stream, pdr_launch* best);
+
+/* Largest event (particles) of a batch, computed on the device (synchronous
+ * on `stream`). */
+int pdr_max_event_size(pdr_ctx* ctx, const pdr_batch* batch, void* stream, uint32_t* out);
+
+/* Read and clear the device error word after synchronising `stream`.
+ * PDR_OK, or PDR_EDEVICE with the reason in pdr_last_error. */
+int pdr_check(pdr_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------- library-owned results -- */
+/* Result view returned by pdr_fetch: DEVICE pointers owned by the library
+ * until pdr_release(ticket); layouts as pdr_outputs. */
+typedef struct pdr_result {
+  uint64_t n_events, n_particles;
+  const uint64_t* offsets;    /* = the batch's offsets (slot bases), copied into the pool */
+  const uint32_t* counts;
+  const pdr_track* tracks;
+  const pdr_tower* towers;
+  const pdr_eflow* eflow;
+  const pdr_cand* cands;
+  const pdr_iso* iso;
+  const pdr_debug* debug;     /* NULL unless PDR_BATCH_DEBUG */
+} pdr_result;
+
+/* Allocate result buffers from the pool, enqueue the batch on `stream` and
+ * return a ticket.  The caller keeps the batch's inputs alive until pdr_wait
+ * returns PDR_OK.  PDR_ENOMEM when the pool has no room (admission by free
+ * device memory); PDR_EBUSY when max_tickets are outstanding. */
+int pdr_submit(pdr_ctx* ctx, const pdr_batch* batch, void* stream, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a ticket; PDR_ETIMEDOUT if it is
+ * still running (the wait never hangs), PDR_EDEVICE on a device error. */
+int pdr_wait(pdr_ctx* ctx, uint64_t ticket, int timeout_ms);
+/* Result view of a finished ticket. */
+int pdr_fetch(pdr_ctx* ctx, uint64_t ticket, pdr_result* r);
+/* Return a ticket's buffers to the pool. */
+int pdr_release(pdr_ctx* ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDR_H */

@@ -1,0 +1,373 @@
+"""Thin ctypes binding of the CUDA library (include/pdr.h).
+
+Argument marshalling only: every step of the detector response runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  If the
+built library is missing or cannot be loaded this module raises - there is no
+CPU fallback.
+
+The functions keep the C names (``pdr_create``, ``pdr_run``, ...); ``Context``
+wraps them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpdr.so")
+CARD_DIR = os.path.join(HERE, "cards")
+
+MAXSEG, MAXEDGE = 4, 8
+ECAL, HCAL = 0, 1
+BATCH_DEBUG = 0x1
+F_REACH, F_BARREL, F_TRACKED, F_CAND, F_ECAL, F_HCAL = 0x01, 0x02, 0x04, 0x08, 0x10, 0x20
+NO_KEY = 0xFFFFFFFF
+STATUS = {0: "PDR_OK", -1: "PDR_EINVAL", -2: "PDR_ENOMEM", -3: "PDR_ECARD", -4: "PDR_ETIMEDOUT",
+          -5: "PDR_EDEVICE", -6: "PDR_EBUSY", -7: "PDR_ENOTFOUND", -8: "PDR_EOVERFLOW"}
+
+
+class PdrError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pdr_card(C.Structure):
+    _fields_ = [
+        ("B", C.c_double), ("R", C.c_double), ("L", C.c_double),
+        ("nseg", C.c_int32 * 2),
+        ("seg_eta_hi", (C.c_double * MAXSEG) * 2),
+        ("seg_neta", (C.c_int32 * MAXSEG) * 2),
+        ("seg_nphi", (C.c_int32 * MAXSEG) * 2),
+        ("trk_npt", C.c_int32), ("trk_neta", C.c_int32),
+        ("trk_pt_edges", C.c_double * MAXEDGE),
+        ("trk_eta_edges", C.c_double * MAXEDGE),
+        ("trk_eff", ((C.c_double * MAXEDGE) * MAXEDGE) * 3),
+        ("res_n", C.c_int32 * 4),
+        ("res_edges", (C.c_double * MAXEDGE) * 4),
+        ("res_abcd", ((C.c_double * 4) * MAXEDGE) * 4),
+        ("id_n", C.c_int32),
+        ("id_edges", C.c_double * MAXEDGE),
+        ("id_eff", (C.c_double * MAXEDGE) * 3),
+        ("e_min", C.c_double * 2), ("s_min", C.c_double * 2),
+        ("cand_ptmin", C.c_double),
+        ("iso_dr", C.c_double), ("iso_drmin", C.c_double), ("iso_ptmin", C.c_double),
+        ("iso_imax", C.c_double),
+    ]
+
+
+class pdr_batch(C.Structure):
+    _fields_ = [
+        ("n_events", C.c_uint64), ("offsets", C.c_void_p),
+        ("pt", C.c_void_p), ("eta", C.c_void_p), ("phi", C.c_void_p), ("mass", C.c_void_p),
+        ("pdg", C.c_void_p), ("charge", C.c_void_p), ("vz", C.c_void_p),
+        ("seed", C.c_uint64), ("event_index_base", C.c_uint32), ("card_id", C.c_uint32),
+        ("max_event_size", C.c_uint32), ("flags", C.c_uint32),
+    ]
+
+
+class pdr_outputs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("tracks", "towers", "eflow", "cands", "iso", "counts", "debug")]
+
+
+class pdr_launch(C.Structure):
+    _fields_ = [("team", C.c_uint32), ("block", C.c_uint32), ("table_slots", C.c_uint32),
+                ("grid", C.c_uint32)]
+
+    def as_dict(self):
+        return dict(team=self.team, block=self.block, table_slots=self.table_slots, grid=self.grid)
+
+
+class pdr_options(C.Structure):
+    _fields_ = [("pool_bytes", C.c_uint64), ("max_tickets", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class pdr_result(C.Structure):
+    _fields_ = [("n_events", C.c_uint64), ("n_particles", C.c_uint64)] + [
+        (n, C.c_void_p) for n in ("offsets", "counts", "tracks", "towers", "eflow", "cands", "iso", "debug")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpdr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run python -m paper_2606_26089_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        P, I = C.c_void_p, C.c_int
+        sig = {
+            "pdr_abi_version": ([], I),
+            "pdr_create": ([C.POINTER(P), I, C.POINTER(pdr_options)], I),
+            "pdr_destroy": ([P], I),
+            "pdr_last_error": ([P], C.c_char_p),
+            "pdr_card_load": ([P, C.POINTER(pdr_card), C.POINTER(C.c_uint32)], I),
+            "pdr_card_unload": ([P, C.c_uint32], I),
+            "pdr_card_towers": ([P, C.c_uint32, I, C.POINTER(C.c_uint32)], I),
+            "pdr_run": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_launch), P], I),
+            "pdr_run_per_event": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P], I),
+            "pdr_run_host": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_launch), P], I),
+            "pdr_autotune": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P, C.POINTER(pdr_launch)], I),
+            "pdr_max_event_size": ([P, C.POINTER(pdr_batch), P, C.POINTER(C.c_uint32)], I),
+            "pdr_check": ([P, P], I),
+            "pdr_submit": ([P, C.POINTER(pdr_batch), P, C.POINTER(C.c_uint64)], I),
+            "pdr_wait": ([P, C.c_uint64, I], I),
+            "pdr_fetch": ([P, C.c_uint64, C.POINTER(pdr_result)], I),
+            "pdr_release": ([P, C.c_uint64], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [n for n in dir(lib()) if n.startswith("pdr_")]
+
+
+def card_path(name: str) -> str:
+    return name if name.endswith(".json") else os.path.join(CARD_DIR, name + ".json")
+
+
+def card_from_json(name_or_dict) -> pdr_card:
+    """Fill a pdr_card from the card JSON (raw detector parameters)."""
+    d = name_or_dict if isinstance(name_or_dict, dict) else json.load(open(card_path(name_or_dict)))
+    c = pdr_card()
+    c.B, c.R, c.L = d["B"], d["R"], d["L"]
+    for calo, cname in ((ECAL, "ecal"), (HCAL, "hcal")):
+        segs = d[cname]["segments"]
+        c.nseg[calo] = len(segs)
+        for s, seg in enumerate(segs):
+            c.seg_eta_hi[calo][s] = seg["eta_hi"]
+            c.seg_neta[calo][s] = seg["n_eta"]
+            c.seg_nphi[calo][s] = seg["n_phi"]
+    te = d["track_eff"]
+    c.trk_npt, c.trk_neta = len(te["pt_edges"]), len(te["abseta_edges"])
+    for k, v in enumerate(te["pt_edges"]):
+        c.trk_pt_edges[k] = v
+    for k, v in enumerate(te["abseta_edges"]):
+        c.trk_eta_edges[k] = v
+    for t, name in enumerate(("hadron", "electron", "muon")):
+        for i, row in enumerate(te[name]):
+            for j, v in enumerate(row):
+                c.trk_eff[t][i][j] = v
+    for comp, name in enumerate(("track", "muon", "ecal", "hcal")):
+        r = d["resolution"][name]
+        c.res_n[comp] = len(r["abseta_edges"])
+        for k, v in enumerate(r["abseta_edges"]):
+            c.res_edges[comp][k] = v
+        for k, abcd in enumerate(r["abcd"]):
+            for j in range(4):
+                c.res_abcd[comp][k][j] = abcd[j]
+    ie = d["id_eff"]
+    c.id_n = len(ie["abseta_edges"])
+    for k, v in enumerate(ie["abseta_edges"]):
+        c.id_edges[k] = v
+    for t, name in enumerate(("electron", "muon", "photon")):
+        for k, v in enumerate(ie[name]):
+            c.id_eff[t][k] = v
+    th = d["thresholds"]
+    c.e_min[ECAL], c.s_min[ECAL] = th["ecal"]["e_min"], th["ecal"]["s_min"]
+    c.e_min[HCAL], c.s_min[HCAL] = th["hcal"]["e_min"], th["hcal"]["s_min"]
+    iso = d["isolation"]
+    c.cand_ptmin = iso["cand_ptmin"]
+    c.iso_dr, c.iso_drmin, c.iso_ptmin, c.iso_imax = iso["dr"], iso["dr_min"], iso["pt_min"], iso["i_max"]
+    return c
+
+
+# ---------------------------------------------------------------------------
+# torch marshalling helpers
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def batch_to_device(batch, device="cuda"):
+    """Copy a synth.EventBatch (numpy) to device tensors."""
+    torch = _torch()
+    out = {}
+    for k in ("offsets", "pt", "eta", "phi", "mass", "pdg", "charge", "vz"):
+        v = getattr(batch, k)
+        if v is None:
+            out[k] = None
+            continue
+        a = np.ascontiguousarray(v)
+        if k == "offsets":
+            a = a.astype(np.int64)
+        out[k] = torch.from_numpy(a).to(device)
+    out["n_events"] = batch.n_events
+    out["n_particles"] = batch.n_particles
+    out["max_event_size"] = int(batch.multiplicities().max()) if batch.n_events else 0
+    return out
+
+
+def alloc_outputs(n_events: int, n_particles: int, debug: bool = False, device="cuda"):
+    """Device output buffers in the slot layout of pdr_outputs (torch tensors)."""
+    torch = _torch()
+    cap = max(n_particles, 1)
+    f = dict(dtype=torch.float32, device=device)
+    o = dict(tracks=torch.empty((cap, 4), **f), towers=torch.empty((cap, 3), **f),
+             eflow=torch.empty((cap, 3), **f), cands=torch.empty((cap, 4), **f),
+             iso=torch.empty((cap, 2), **f),
+             counts=torch.zeros((max(n_events, 1), 4), dtype=torch.int32, device=device),
+             debug=torch.empty((cap, 4), **f) if debug else None)
+    return o
+
+
+def make_batch(dev, card_id: int, seed: int, event_base: int = 0, debug: bool = False,
+               max_event_size: Optional[int] = None) -> pdr_batch:
+    b = pdr_batch()
+    b.n_events = dev["n_events"]
+    for k in ("offsets", "pt", "eta", "phi", "mass", "pdg", "charge", "vz"):
+        setattr(b, k, _ptr(dev[k]))
+    b.seed = seed & (2**64 - 1)
+    b.event_index_base = event_base & 0xFFFFFFFF
+    b.card_id = card_id
+    b.max_event_size = dev.get("max_event_size", 0) if max_event_size is None else max_event_size
+    b.flags = BATCH_DEBUG if debug else 0
+    return b
+
+
+def make_outputs(o) -> pdr_outputs:
+    r = pdr_outputs()
+    for k in ("tracks", "towers", "eflow", "cands", "iso", "counts", "debug"):
+        setattr(r, k, _ptr(o.get(k)))
+    return r
+
+
+class Context:
+    """A pdr_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0, pool_bytes: int = 0, max_tickets: int = 0):
+        self.L = lib()
+        opt = pdr_options(pool_bytes, max_tickets, 0)
+        h = C.c_void_p()
+        self._check(self.L.pdr_create(C.byref(h), device, C.byref(opt)), "pdr_create", None)
+        self.h = h
+        self.device = device
+
+    def _check(self, rc, where, h="self"):
+        if rc != 0:
+            handle = self.h if h == "self" else h
+            msg = self.L.pdr_last_error(handle)
+            raise PdrError(rc, where, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pdr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        if stream is None:
+            return _torch().cuda.current_stream().cuda_stream
+        return stream if isinstance(stream, int) else stream.cuda_stream
+
+    def card_load(self, card) -> int:
+        c = card if isinstance(card, pdr_card) else card_from_json(card)
+        cid = C.c_uint32()
+        self._check(self.L.pdr_card_load(self.h, C.byref(c), C.byref(cid)), "pdr_card_load")
+        return cid.value
+
+    def card_unload(self, card_id: int):
+        self._check(self.L.pdr_card_unload(self.h, card_id), "pdr_card_unload")
+
+    def card_towers(self, card_id: int, calo: int) -> int:
+        n = C.c_uint32()
+        self._check(self.L.pdr_card_towers(self.h, card_id, calo, C.byref(n)), "pdr_card_towers")
+        return n.value
+
+    def run(self, batch: pdr_batch, out: pdr_outputs, launch: Optional[pdr_launch] = None, stream=None):
+        self._check(self.L.pdr_run(self.h, C.byref(batch), C.byref(out),
+                                   C.byref(launch) if launch is not None else None,
+                                   self._stream(stream)), "pdr_run")
+
+    def run_per_event(self, batch: pdr_batch, out: pdr_outputs, stream=None):
+        self._check(self.L.pdr_run_per_event(self.h, C.byref(batch), C.byref(out), self._stream(stream)),
+                    "pdr_run_per_event")
+
+    def run_host(self, batch: pdr_batch, out: pdr_outputs, launch: Optional[pdr_launch] = None, stream=None):
+        self._check(self.L.pdr_run_host(self.h, C.byref(batch), C.byref(out),
+                                        C.byref(launch) if launch is not None else None,
+                                        self._stream(stream)), "pdr_run_host")
+
+    def autotune(self, batch: pdr_batch, out: pdr_outputs, stream=None) -> pdr_launch:
+        best = pdr_launch()
+        self._check(self.L.pdr_autotune(self.h, C.byref(batch), C.byref(out), self._stream(stream),
+                                        C.byref(best)), "pdr_autotune")
+        return best
+
+    def max_event_size(self, batch: pdr_batch, stream=None) -> int:
+        n = C.c_uint32()
+        self._check(self.L.pdr_max_event_size(self.h, C.byref(batch), self._stream(stream), C.byref(n)),
+                    "pdr_max_event_size")
+        return n.value
+
+    def check(self, stream=None):
+        self._check(self.L.pdr_check(self.h, self._stream(stream)), "pdr_check")
+
+    def submit(self, batch: pdr_batch, stream=None) -> int:
+        t = C.c_uint64()
+        self._check(self.L.pdr_submit(self.h, C.byref(batch), self._stream(stream), C.byref(t)), "pdr_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        return self.L.pdr_wait(self.h, ticket, timeout_ms)
+
+    def fetch(self, ticket: int) -> pdr_result:
+        r = pdr_result()
+        self._check(self.L.pdr_fetch(self.h, ticket, C.byref(r)), "pdr_fetch")
+        return r
+
+    def release(self, ticket: int):
+        self._check(self.L.pdr_release(self.h, ticket), "pdr_release")
+
+
+# ---------------------------------------------------------------------------
+# views of the output records
+# ---------------------------------------------------------------------------
+def event_records(out_host: dict, counts: np.ndarray, offsets: np.ndarray, e: int) -> dict:
+    """Slot-layout host copies -> the records of event e (numpy, typed)."""
+    a = int(offsets[e])
+    nt, nw, nf, nc = (int(x) for x in counts[e])
+    tr = out_host["tracks"][a:a + nt]
+    tw = out_host["towers"][a:a + nw]
+    ef = out_host["eflow"][a:a + nf]
+    cd = out_host["cands"][a:a + nc]
+    iso = out_host["iso"][a:a + nc]
+    r = dict(
+        tracks=dict(pt=tr[:, 0], eta=tr[:, 1], phi=tr[:, 2], idx=tr[:, 3].view(np.uint32)),
+        towers=dict(key=tw[:, 0].view(np.uint32), e=tw[:, 1], et=tw[:, 2]),
+        eflow=dict(key=ef[:, 0].view(np.uint32), e=ef[:, 1], et=ef[:, 2]),
+        cands=dict(pt=cd[:, 0], eta=cd[:, 1], phi=cd[:, 2], info=cd[:, 3].view(np.uint32),
+                   iso_sum=iso[:, 0], iso_rel=iso[:, 1]),
+    )
+    if out_host.get("debug") is not None:
+        d = out_host["debug"][a:int(offsets[e + 1])]
+        r["debug"] = dict(key=d[:, 0].view(np.uint32), eta_pos=d[:, 1], phi_pos=d[:, 2],
+                          flags=d[:, 3].view(np.uint32))
+    return r

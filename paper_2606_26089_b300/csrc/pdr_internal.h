@@ -1,0 +1,117 @@
+// Internal layouts of the CUDA library: the expanded device card and the
+// kernel parameter block.  Shared by the kernels and the host runtime of the
+// library only.
+#pragma once
+
+#include <stdint.h>
+
+#include "pdr.h"
+
+#define PDR_MAXRING 512      // eta rings per calorimeter (both sides)
+#define PDR_MAXPHI 1024      // phi bins per ring
+#define PDR_PHIPOOL (2 * PDR_MAXSEG * (2 * PDR_MAXPHI + 1))
+#define PDR_FP_SCALE 68719476736.0f   // 2^36: fixed-point quantum of energy sums (GeV)
+#define PDR_FP_INV 1.4551915228366852e-11f  // 2^-36
+#define PDR_MAXQ 8           // |charge| handled by the precomputed reach constants
+#define PDR_CMAX 32          // isolation candidates held in shared memory at once
+#define PDR_EMPTY 0xFFFFFFFFu
+
+#ifdef __CUDACC__
+#define PDR_HD __host__ __device__
+#else
+#define PDR_HD
+#endif
+
+namespace pdr {
+
+enum { CLS_E = 0, CLS_MU = 1, CLS_GAMMA = 2, CLS_CHAD = 3, CLS_NHAD = 4, CLS_INVIS = 5 };
+enum { RES_TRACK = 0, RES_MUON = 1, RES_ECAL = 2, RES_HCAL = 3 };
+
+// One calorimeter's tower grid, float32 where a decision is taken on it.
+struct DevCalo {
+  int32_t nring, ntowers, nseg, pad;
+  float seg_lo[PDR_MAXSEG], seg_hi[PDR_MAXSEG], seg_scale[PDR_MAXSEG];  // |eta| segments (guess only)
+  int32_t seg_n[PDR_MAXSEG], seg_first[PDR_MAXSEG];
+  float edge[PDR_MAXRING + 1];   // signed ring edges, float32 (decisions)
+  int32_t base[PDR_MAXRING];     // first tower id of each ring
+  int32_t nphi[PDR_MAXRING];
+  int32_t phioff[PDR_MAXRING];   // offset of the ring's phi table in DevCard::phi_pool
+  float phi_scale[PDR_MAXRING];  // nphi / (2 pi), guess only
+  float eta_c[PDR_MAXRING];      // ring centre (float32 of the double midpoint)
+  float cosh_c[PDR_MAXRING];     // cosh(eta_c) (float32 of the double value)
+  int32_t resbin[PDR_MAXRING];   // resolution row of |eta_c|
+};
+
+struct DevCard {
+  DevCalo calo[2];
+  // phi tables: for each distinct ring layout, nphi + 1 edges then nphi centres
+  float phi_pool[PDR_PHIPOOL];
+  // propagation
+  float R, L;                    // float32 of the card values
+  float kB;                      // 0.299792458 |B|
+  int32_t Bsign, has_field, pad0;
+  float cR_hi[PDR_MAXQ + 1], cR_lo[PDR_MAXQ + 1];  // c = 0.299792458 |q| |B| R, split hi + lo
+  // tracking efficiency: pass iff (u64) w < T
+  int32_t trk_npt, trk_neta;
+  float trk_pt_edges[PDR_MAXEDGE], trk_eta_edges[PDR_MAXEDGE];
+  unsigned long long trk_T[3][PDR_MAXEDGE][PDR_MAXEDGE];
+  // resolutions, squared coefficients
+  int32_t res_n[4];
+  float res_edges[4][PDR_MAXEDGE];
+  float res_a2[4][PDR_MAXEDGE], res_b2[4][PDR_MAXEDGE], res_c2[4][PDR_MAXEDGE], res_d2[4][PDR_MAXEDGE];
+  // identification efficiency
+  int32_t id_n, pad1;
+  float id_edges[PDR_MAXEDGE];
+  unsigned long long id_T[3][PDR_MAXEDGE];
+  // thresholds and isolation (float32 of the card values; dr2 = float32(dr * dr))
+  float e_min[2], s_min[2];
+  float cand_ptmin, dr2max, dr2min, iso_ptmin, imax, pad2;
+};
+
+// Kernel parameter block (passed by value).
+struct KParams {
+  const DevCard* card;
+  uint64_t n_events;
+  const uint64_t* offsets;
+  const float *pt, *eta, *phi, *mass, *vz;
+  const int32_t* pdg;
+  const int8_t* charge;
+  uint32_t seed_lo, seed_hi, event_base, flags;
+  pdr_track* tracks;
+  pdr_tower* towers;
+  pdr_eflow* eflow;
+  pdr_cand* cands;
+  pdr_iso* iso;
+  uint32_t* counts;
+  pdr_debug* debug;
+  uint32_t table_slots, log2_slots;  // shared-memory table per team
+  uint32_t nmax_smem;                // largest event handled in shared memory
+  uint32_t g_slots, g_log2, g_nmax;  // global-memory table per team for larger events
+  unsigned char* gscratch;           // g_team_bytes per team, or null
+  uint64_t g_team_bytes;
+  uint32_t* err;                     // device error word (bit flags below)
+  uint32_t* next_event;              // dynamic event counter (null: static schedule)
+};
+
+enum : uint32_t {
+  ERR_CSR = 1u,        // offsets not monotone
+  ERR_OVERSIZE = 2u,   // event larger than any table available to the launch
+  ERR_TABLE = 4u,      // tower table full (cannot happen when sized as documented)
+};
+
+// Shared-memory bytes needed by one team of a launch shape.
+PDR_HD inline uint64_t team_smem_bytes(uint32_t team, uint32_t slots, uint32_t nmax) {
+  uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8);  // keys, owner, esum, etrk
+  b += (uint64_t)nmax * 4;                          // per-particle slot | ring
+  b = (b + 15) & ~15ull;
+  b += 2 * 32 * 4;                                  // scan buffers
+  b += PDR_CMAX * (16 + 4 + 4 + 8);                 // isolation candidates (eta, phi, pt, idx; key; pad) and sums
+  return (b + 15) & ~15ull;
+}
+
+PDR_HD inline uint64_t global_team_bytes(uint32_t slots, uint32_t nmax) {
+  uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * 4;
+  return (b + 255) & ~255ull;
+}
+
+}  // namespace pdr

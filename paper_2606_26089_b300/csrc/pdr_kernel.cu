@@ -1,0 +1,750 @@
+// The fused detector-response kernel (sm_103a).
+//
+// One persistent launch walks a ragged CSR batch.  A "team" of TEAM threads
+// (a warp ... a whole CTA) owns one event at a time and runs the TorchDelphes
+// chain of the paper (Sec. 2.2, App. C.1) plus the isolation of Sec. 2.3:
+//
+//   phase 1, per particle (chunks of TEAM particles, coalesced SoA loads):
+//     S0 classify, S1 propagate to the calorimeter surface, S2 tracking
+//     efficiency, S3 momentum smearing, S4 e/mu/gamma identification and
+//     smearing, S5 tower lookup and deposit into the event's tower table;
+//     tracks and candidates are compacted in particle order (warp ballot +
+//     team scan) straight into their output slots.
+//   phase 2, per tower (each tower is processed by its lowest-index
+//     depositing particle, so towers come out in a deterministic order):
+//     S6 tower smearing and thresholds, S7 energy-flow subtraction.
+//   phase 3, per candidate: S8 cone isolation over the event's energy-flow
+//     tracks and neutrals.
+//   S9: per-event counts.
+//
+// Tower sums are exact 64-bit fixed-point integer sums (quantum 2^-36 GeV)
+// accumulated with shared-memory integer atomics: integer addition is
+// associative, so the sums are bitwise deterministic without any float atomics
+// and independent of the launch shape.  Random numbers are counter-based
+// (Philox4x32-10 keyed by seed, counter (slot, event, purpose, 0)), so every
+// draw is reproducible and independent of scheduling.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdr_internal.h"
+
+namespace pdr {
+
+#define PDR_FULL 0xFFFFFFFFu
+
+static constexpr float PI_F = 3.14159265358979323846f;
+static constexpr float TWO_PI_F = 6.28318530717958647692f;
+static constexpr float PIO2_HI = 1.57079637050628662109375f;  // float32(pi/2)
+static constexpr float PIO2_LO = -4.37113900018624283e-8f;     // pi/2 - PIO2_HI
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten multiply/xor rounds on a 128-bit
+// counter under a 64-bit key bumped by the Weyl constants.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// (2k + 1) / 2^24 for the top 23 bits k of w: exact in float32.
+__device__ __forceinline__ float u01(uint32_t w) {
+  return (__uint2float_rn(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
+}
+
+// Box-Muller, cosine branch.
+__device__ __forceinline__ float normal(uint32_t wa, uint32_t wb) {
+  return sqrtf(-2.0f * logf(u01(wa))) * cospif(2.0f * u01(wb));
+}
+
+// Log-normal with mean x and relative variance rel2 = (sigma/x)^2.
+__device__ __forceinline__ float lognormal(float x, float rel2, float z) {
+  const float s2 = log1pf(rel2);
+  const float s = sqrtf(s2);
+  return x * expf(fmaf(s, z, -0.5f * s2));
+}
+
+// (sigma/x)^2 = a^2/x + b^2/x^2 + c^2 + d^2 x^2.
+__device__ __forceinline__ float rel2_of(float a2, float b2, float c2, float d2, float x) {
+  const float ix = 1.0f / x;
+  return fmaf(fmaf(b2, ix, a2), ix, fmaf(d2 * x, x, c2));
+}
+
+// Largest k < n with edges[k] <= x (-1 if none): piecewise-constant tables.
+__device__ __forceinline__ int small_lookup(const float* edges, int n, float x) {
+  int k = -1;
+#pragma unroll
+  for (int j = 0; j < PDR_MAXEDGE; ++j)
+    if (j < n && edges[j] <= x) k = j;
+  return k;
+}
+
+__device__ __forceinline__ unsigned long long to_fp(float v) {
+  return (unsigned long long)__float2ll_rn(v * PDR_FP_SCALE);
+}
+
+__device__ __forceinline__ float from_fp(unsigned long long v) {
+  return __ull2float_rn(v) * PDR_FP_INV;
+}
+
+__device__ __forceinline__ int classify(int32_t pdg, int q) {
+  const int a = pdg < 0 ? -pdg : pdg;
+  if (a == 11) return CLS_E;
+  if (a == 13) return CLS_MU;
+  if (a == 22) return CLS_GAMMA;
+  if (a == 12 || a == 14 || a == 16) return CLS_INVIS;
+  return q != 0 ? CLS_CHAD : CLS_NHAD;
+}
+
+// ------------------------------------------------------------- propagation
+struct Prop {
+  int reach, barrel;
+  float eta_pos, phi_pos;
+};
+
+// S1: straight line (neutral, or B = 0) or helix from (0, 0, vz) to the
+// cylinder R, +-L.  Helix radius r = pT / (0.299792458 |q| |B|); the barrel is
+// reached iff 2 pT >= c = 0.299792458 |q| |B| R, at turning angle
+// 2 asin(c / 2pT); otherwise the endcap after psi = s_z / r < 2 pi.
+__device__ __forceinline__ Prop propagate(const DevCard& K, float pt, float eta, float phi,
+                                          int q, float vz) {
+  Prop P;
+  P.reach = 0; P.barrel = 0; P.eta_pos = 0.0f; P.phi_pos = 0.0f;
+  if (!(fabsf(vz) <= K.L)) return P;
+  const float sh = sinhf(eta);
+  if (q == 0 || !K.has_field) {
+    P.reach = 1;
+    P.phi_pos = phi;
+    if (vz == 0.0f) {  // from the axis origin a straight line keeps its direction
+      P.barrel = fabsf(K.R * sh) <= K.L;
+      P.eta_pos = eta;
+      return P;
+    }
+    const float z = fmaf(K.R, sh, vz);
+    P.barrel = fabsf(z) <= K.L;
+    if (P.barrel) {
+      P.eta_pos = asinhf(z / K.R);
+    } else {
+      const float ze = sh > 0.0f ? K.L : -K.L;
+      const float rho = (ze - vz) / sh;
+      P.eta_pos = asinhf(ze / rho);
+    }
+    return P;
+  }
+  const int aq = q < 0 ? -q : q;
+  const float kq = K.kB * (float)aq;
+  const float r = pt / kq;
+  const float h = ((q > 0) == (K.Bsign > 0)) ? 1.0f : -1.0f;
+  float cR, cRl;
+  if (aq <= PDR_MAXQ) { cR = K.cR_hi[aq]; cRl = K.cR_lo[aq]; }
+  else { cR = kq * K.R; cRl = 0.0f; }
+  const float twopt = 2.0f * pt;
+  float a = 0.0f, z = 0.0f;
+  if (twopt >= cR) {
+    const float x = cR / twopt;
+    if (x <= 0.5f) {
+      a = asinf(x);
+    } else {
+      // near the tangent point use asin(x) = pi/2 - 2 asin(sqrt((1 - x)/2)) with
+      // 1 - x = (2pT - c) / 2pT; 2pT - c_hi is exact (Sterbenz) for x > 1/2.
+      const float d = (twopt - cR) - cRl;
+      const float omx = fmaxf(d / twopt, 0.0f);
+      a = (PIO2_HI - 2.0f * asinf(sqrtf(0.5f * omx))) + PIO2_LO;
+    }
+    z = fmaf(2.0f * r * a, sh, vz);
+    P.barrel = fabsf(z) <= K.L;
+  }
+  float pphi;
+  if (P.barrel) {
+    P.eta_pos = asinhf(z / K.R);
+    pphi = phi - h * a;
+  } else {
+    if (sh == 0.0f) return P;  // pz = 0 and the barrel out of reach
+    const float ze = sh > 0.0f ? K.L : -K.L;
+    const float sz = (ze - vz) / sh;
+    const float psi = sz / r;
+    if (!(psi < TWO_PI_F)) return P;  // looper
+    const float rho = 2.0f * r * fabsf(sinf(0.5f * psi));
+    P.eta_pos = asinhf(ze / rho);
+    pphi = phi - h * (0.5f * psi);
+  }
+  if (pphi < -PI_F) pphi += TWO_PI_F;
+  else if (pphi >= PI_F) pphi -= TWO_PI_F;
+  P.phi_pos = pphi;
+  P.reach = 1;
+  return P;
+}
+
+// Ring containing v: largest r with edge[r] <= v, or -1 outside coverage.
+__device__ __forceinline__ int ring_of(const DevCalo& C, float v) {
+  const int nr = C.nring;
+  if (!(v >= C.edge[0]) || !(v < C.edge[nr])) return -1;
+  const float av = fabsf(v);
+  int s = 0;
+  while (s < C.nseg - 1 && av >= C.seg_hi[s]) ++s;
+  int j = (int)((av - C.seg_lo[s]) * C.seg_scale[s]);
+  j = min(max(j, 0), C.seg_n[s] - 1) + C.seg_first[s];
+  const int m = nr >> 1;
+  int r = v >= 0.0f ? m + j : m - 1 - j;
+  r = min(max(r, 0), nr - 1);
+  while (r > 0 && v < C.edge[r]) --r;
+  while (r < nr - 1 && v >= C.edge[r + 1]) ++r;
+  return r;
+}
+
+// Phi bin of v in a ring: largest k with edge[k] <= v, clamped to [0, nphi - 1].
+__device__ __forceinline__ int phi_bin(const float* pe, int nphi, float scale, float v) {
+  int k = (int)((v + PI_F) * scale);
+  k = min(max(k, 0), nphi - 1);
+  while (k > 0 && v < pe[k]) --k;
+  while (k < nphi - 1 && v >= pe[k + 1]) ++k;
+  return k;
+}
+
+// ------------------------------------------------------------------ teams
+template <int TEAM>
+struct TeamCtx {
+  int tid, tix;
+  __device__ __forceinline__ void sync() const {
+    if (TEAM == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(tix + 1), "r"(TEAM) : "memory");
+  }
+};
+
+// Exclusive team prefix of two flags packed as (a | b << 16); total via ref.
+template <int TEAM>
+__device__ __forceinline__ uint32_t team_scan2(bool fa, bool fb, uint32_t* wbuf, uint32_t& total,
+                                               const TeamCtx<TEAM>& t) {
+  const uint32_t ma = __ballot_sync(PDR_FULL, fa), mb = __ballot_sync(PDR_FULL, fb);
+  const int lane = t.tid & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t lane_pre = __popc(ma & lt) | ((uint32_t)__popc(mb & lt) << 16);
+  const uint32_t wtot = __popc(ma) | ((uint32_t)__popc(mb) << 16);
+  if (TEAM == 32) {
+    total = wtot;
+    return lane_pre;
+  }
+  constexpr int NW = TEAM / 32;
+  const int w = t.tid >> 5;
+  if (lane == 0) wbuf[w] = wtot;
+  t.sync();
+  uint32_t v = lane < NW ? wbuf[lane] : 0u;
+#pragma unroll
+  for (int o = 1; o < NW; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(PDR_FULL, v, o);
+    if (lane >= o) v += u;
+  }
+  total = __shfl_sync(PDR_FULL, v, NW - 1);
+  const uint32_t incl_w = __shfl_sync(PDR_FULL, v, w);
+  return incl_w - wtot + lane_pre;
+}
+
+// ------------------------------------------------------------ tower table
+struct Tbl {
+  uint32_t* keys;
+  uint32_t* owner;
+  unsigned long long* esum;
+  unsigned long long* etrk;
+  uint32_t* pinfo;
+  uint32_t mask, shift;
+};
+
+__device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t log2) {
+  Tbl t;
+  t.keys = (uint32_t*)base;
+  t.owner = t.keys + slots;
+  t.esum = (unsigned long long*)(t.owner + slots);
+  t.etrk = t.esum + slots;
+  t.pinfo = (uint32_t*)(t.etrk + slots);
+  t.mask = slots - 1;
+  t.shift = 32 - log2;
+  return t;
+}
+
+// Insert key; the thread that claims a slot initialises it.  Returns the slot.
+__device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uint32_t* err) {
+  uint32_t h = (key * 0x9E3779B1u) >> T.shift;
+  for (uint32_t probe = 0; probe <= T.mask; ++probe) {
+    const uint32_t prev = atomicCAS(&T.keys[h], PDR_EMPTY, key);
+    if (prev == PDR_EMPTY) {
+      T.owner[h] = PDR_EMPTY;
+      T.esum[h] = 0ull;
+      T.etrk[h] = 0ull;
+      return h;
+    }
+    if (prev == key) return h;
+    h = (h + 1) & T.mask;
+  }
+  atomicOr(err, ERR_TABLE);
+  return PDR_EMPTY;
+}
+
+// ------------------------------------------------------- per-particle stage
+struct PartOut {
+  uint32_t key, ring, flags;
+  float E, etrk, ptp, cpt, eta_pos, phi_pos;
+  int cc;
+  bool tracked, cand;
+};
+
+__device__ __forceinline__ void particle_stage(const KParams& p, const DevCard& K, uint64_t g,
+                                               uint32_t i, uint32_t event, PartOut& o) {
+  const float PT = __ldg(p.pt + g), ETA = __ldg(p.eta + g), PHI = __ldg(p.phi + g);
+  const float M = __ldg(p.mass + g);
+  const int32_t PDG = __ldg(p.pdg + g);
+  const int Q = (int)__ldg(p.charge + g);
+  const float VZ = p.vz ? __ldg(p.vz + g) : 0.0f;
+  o.key = PDR_NO_KEY; o.ring = 0; o.flags = 0;
+  o.etrk = 0.0f; o.ptp = 0.0f; o.cpt = 0.0f; o.eta_pos = 0.0f; o.phi_pos = 0.0f;
+  o.cc = -1; o.tracked = false; o.cand = false;
+  const int cls = classify(PDG, Q);
+  const float ch = coshf(ETA);
+  const float pc = PT * ch;
+  o.E = sqrtf(fmaf(pc, pc, M * M));
+  if (cls == CLS_INVIS) return;
+  // S1
+  const Prop P = propagate(K, PT, ETA, PHI, Q, VZ);
+  if (!P.reach) return;
+  o.flags = PDR_F_REACH | (P.barrel ? PDR_F_BARREL : 0u);
+  o.eta_pos = P.eta_pos;
+  o.phi_pos = P.phi_pos;
+  // S5 tower placement: e/gamma to ECAL (or HCAL beyond ECAL), hadrons to HCAL
+  int calo = -1, ring = -1;
+  if (cls == CLS_E || cls == CLS_GAMMA) {
+    ring = ring_of(K.calo[0], P.eta_pos);
+    if (ring >= 0) calo = 0;
+    else {
+      ring = ring_of(K.calo[1], P.eta_pos);
+      if (ring >= 0) calo = 1;
+    }
+  } else if (cls == CLS_CHAD || cls == CLS_NHAD) {
+    ring = ring_of(K.calo[1], P.eta_pos);
+    if (ring >= 0) calo = 1;
+  }
+  if (calo >= 0) {
+    const DevCalo& C = K.calo[calo];
+    const int nphi = C.nphi[ring];
+    const int k = phi_bin(K.phi_pool + C.phioff[ring], nphi, C.phi_scale[ring], P.phi_pos);
+    o.key = ((uint32_t)calo << 24) | (uint32_t)(C.base[ring] + k);
+    o.ring = (uint32_t)ring;
+    o.flags |= calo == 0 ? PDR_F_ECAL : PDR_F_HCAL;
+  }
+  const float aeta = fabsf(ETA);
+  // S2, S3 tracking efficiency and momentum smearing
+  if (Q != 0) {
+    const int tc = cls == CLS_E ? 1 : (cls == CLS_MU ? 2 : 0);
+    const int kp = small_lookup(K.trk_pt_edges, K.trk_npt, PT);
+    const int ke = small_lookup(K.trk_eta_edges, K.trk_neta, aeta);
+    const unsigned long long T = (kp >= 0 && ke >= 0) ? K.trk_T[tc][kp][ke] : 0ull;
+    const uint4 w = philox(i, event, 1u, 0u, p.seed_lo, p.seed_hi);
+    if ((unsigned long long)w.x < T) {
+      o.tracked = true;
+      o.flags |= PDR_F_TRACKED;
+      const float z = normal(w.y, w.z);
+      const int rb = max(small_lookup(K.res_edges[RES_TRACK], K.res_n[RES_TRACK], aeta), 0);
+      const float r2 = rel2_of(K.res_a2[RES_TRACK][rb], K.res_b2[RES_TRACK][rb],
+                               K.res_c2[RES_TRACK][rb], K.res_d2[RES_TRACK][rb], PT);
+      o.ptp = lognormal(PT, r2, z);
+      const float pcp = o.ptp * ch;
+      o.etrk = sqrtf(fmaf(pcp, pcp, M * M));
+    }
+  }
+  // S4 e/mu/gamma identification and smearing
+  int cc = -1;
+  if (cls == CLS_E && o.tracked) cc = 0;
+  else if (cls == CLS_MU && o.tracked) cc = 1;
+  else if (cls == CLS_GAMMA && calo == 0) cc = 2;
+  if (cc >= 0 && PT > K.cand_ptmin) {
+    const int ke = small_lookup(K.id_edges, K.id_n, aeta);
+    const unsigned long long T = ke >= 0 ? K.id_T[cc][ke] : 0ull;
+    const uint4 w = philox(i, event, 2u, 0u, p.seed_lo, p.seed_hi);
+    if ((unsigned long long)w.x < T) {
+      const float z = normal(w.y, w.z);
+      if (cc != 1) {
+        const int rb = max(small_lookup(K.res_edges[RES_ECAL], K.res_n[RES_ECAL], aeta), 0);
+        const float r2 = rel2_of(K.res_a2[RES_ECAL][rb], K.res_b2[RES_ECAL][rb],
+                                 K.res_c2[RES_ECAL][rb], K.res_d2[RES_ECAL][rb], o.E);
+        o.cpt = lognormal(o.E, r2, z) / ch;
+      } else {
+        const int rb = max(small_lookup(K.res_edges[RES_MUON], K.res_n[RES_MUON], aeta), 0);
+        const float r2 = rel2_of(K.res_a2[RES_MUON][rb], K.res_b2[RES_MUON][rb],
+                                 K.res_c2[RES_MUON][rb], K.res_d2[RES_MUON][rb], PT);
+        o.cpt = lognormal(PT, r2, z);
+      }
+      o.cand = true;
+      o.cc = cc;
+      o.flags |= PDR_F_CAND;
+    }
+  }
+  // the track energy is subtracted from the particle's own tower (e, hadrons)
+  if (o.key == PDR_NO_KEY) o.etrk = 0.0f;
+}
+
+// ---------------------------------------------------------- per-tower stage
+struct TowerOut {
+  float e, et, de, det;
+  bool kept, ef;
+};
+
+__device__ __forceinline__ void tower_stage(const DevCard& K, uint32_t key, uint32_t ring,
+                                            unsigned long long es, unsigned long long et,
+                                            uint32_t event, uint32_t s0, uint32_t s1,
+                                            TowerOut& o) {
+  const int calo = (int)(key >> 24);
+  const uint32_t id = key & 0xFFFFFFu;
+  const DevCalo& C = K.calo[calo];
+  const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
+  const int rb = C.resbin[ring];
+  const float a2 = K.res_a2[comp][rb], b2 = K.res_b2[comp][rb];
+  const float c2 = K.res_c2[comp][rb], d2 = K.res_d2[comp][rb];
+  const float Es = from_fp(es);
+  const float Et = from_fp(et);
+  const uint4 w = philox(id, event, 3u + (uint32_t)calo, 0u, s0, s1);
+  const float z = normal(w.x, w.y);
+  const float E1 = lognormal(Es, rel2_of(a2, b2, c2, d2, Es), z);
+  const float sig = E1 * sqrtf(rel2_of(a2, b2, c2, d2, E1));
+  const float emin = K.e_min[calo], smin = K.s_min[calo];
+  o.kept = (E1 > emin) & (E1 / sig > smin);
+  const float chc = C.cosh_c[ring];
+  o.e = E1;
+  o.et = E1 / chc;
+  const float dE = E1 - Et;
+  o.ef = (dE > emin) & (dE / sig > smin);
+  o.de = dE;
+  o.det = dE / chc;
+}
+
+// Ring of a tower id (largest r with base[r] <= id).
+__device__ __forceinline__ int ring_of_id(const DevCalo& C, uint32_t id) {
+  int lo = 0, hi = C.nring - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((uint32_t)C.base[mid] <= id) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------- one event
+template <int TEAM>
+__device__ __forceinline__ void process_event(const KParams& p, const DevCard& K, const Tbl& T,
+                                              uint32_t* wbuf, float4* cf, uint32_t* ckey,
+                                              unsigned long long* csum, const TeamCtx<TEAM>& tc,
+                                              uint64_t e, uint64_t a, uint32_t n) {
+  const uint32_t event = p.event_base + (uint32_t)e;
+  const bool dbg = p.debug != nullptr;
+  uint32_t n_trk = 0, n_cand = 0, flip = 0;
+
+  // ---- phase 1: particles
+  for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
+    const uint32_t i = c0 + (uint32_t)tc.tid;
+    const bool valid = i < n;
+    PartOut o;
+    o.tracked = false; o.cand = false; o.key = PDR_NO_KEY;
+    if (valid) particle_stage(p, K, a + i, i, event, o);
+    uint32_t slot = PDR_EMPTY;
+    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, p.err);
+    if (valid) T.pinfo[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
+    uint32_t tot;
+    const uint32_t pre = team_scan2<TEAM>(o.tracked, o.cand, wbuf + 32 * flip, tot, tc);
+    flip ^= 1u;
+    if (slot != PDR_EMPTY) {
+      atomicAdd(&T.esum[slot], to_fp(o.E));
+      if (o.etrk > 0.0f) atomicAdd(&T.etrk[slot], to_fp(o.etrk));
+      atomicMin(&T.owner[slot], i);
+    }
+    if (o.tracked) {
+      const uint64_t j = a + n_trk + (pre & 0xFFFFu);
+      reinterpret_cast<float4*>(p.tracks)[j] =
+          make_float4(o.ptp, __ldg(p.eta + a + i), __ldg(p.phi + a + i), __uint_as_float(i));
+    }
+    if (o.cand) {
+      const uint64_t j = a + n_cand + (pre >> 16);
+      reinterpret_cast<float4*>(p.cands)[j] =
+          make_float4(o.cpt, __ldg(p.eta + a + i), __ldg(p.phi + a + i),
+                      __uint_as_float(i | ((uint32_t)o.cc << 28)));
+      // the candidate's own tower key, read back by the isolation phase
+      reinterpret_cast<float2*>(p.iso)[j] = make_float2(__uint_as_float(o.key), 0.0f);
+    }
+    if (dbg && valid)
+      reinterpret_cast<float4*>(p.debug)[a + i] =
+          make_float4(__uint_as_float(o.key), o.eta_pos, o.phi_pos, __uint_as_float(o.flags));
+    n_trk += tot & 0xFFFFu;
+    n_cand += tot >> 16;
+  }
+  tc.sync();
+
+  // ---- phase 2: towers, each by its lowest-index depositing particle
+  uint32_t n_twr = 0, n_ef = 0;
+  for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
+    const uint32_t i = c0 + (uint32_t)tc.tid;
+    TowerOut to;
+    to.kept = false; to.ef = false;
+    uint32_t key = PDR_NO_KEY;
+    if (i < n) {
+      const uint32_t pi = T.pinfo[i];
+      if (pi != PDR_EMPTY) {
+        const uint32_t slot = pi & 0xFFFFu;
+        if (T.owner[slot] == i) {
+          key = T.keys[slot];
+          tower_stage(K, key, pi >> 16, T.esum[slot], T.etrk[slot], event, p.seed_lo, p.seed_hi, to);
+          T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
+        }
+      }
+    }
+    uint32_t tot;
+    const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, wbuf + 32 * flip, tot, tc);
+    flip ^= 1u;
+    if (to.kept) {
+      pdr_tower* r = p.towers + a + n_twr + (pre & 0xFFFFu);
+      r->key = key; r->e = to.e; r->et = to.et;
+    }
+    if (to.ef) {
+      pdr_eflow* r = p.eflow + a + n_ef + (pre >> 16);
+      r->key = key; r->e = to.de; r->et = to.det;
+    }
+    n_twr += tot & 0xFFFFu;
+    n_ef += tot >> 16;
+  }
+
+  // ---- phase 3: isolation of the event's candidates
+  if (n_cand > 0) {
+    tc.sync();
+    const uint32_t n_obj = n_trk + n_ef;
+    for (uint32_t g0 = 0; g0 < n_cand; g0 += PDR_CMAX) {
+      const uint32_t gn = min((uint32_t)PDR_CMAX, n_cand - g0);
+      if ((uint32_t)tc.tid < gn) {
+        const uint64_t j = a + g0 + tc.tid;
+        const float4 c = reinterpret_cast<const float4*>(p.cands)[j];
+        cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
+        ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(p.iso)[j].x);
+        csum[tc.tid] = 0ull;
+      }
+      tc.sync();
+      for (uint32_t j = tc.tid; j < n_obj; j += TEAM) {
+        float oe, op, opt;
+        uint32_t oid;
+        bool is_trk;
+        if (j < n_trk) {
+          const float4 t = reinterpret_cast<const float4*>(p.tracks)[a + j];
+          opt = t.x; oe = t.y; op = t.z; oid = __float_as_uint(t.w); is_trk = true;
+        } else {
+          const pdr_eflow f = p.eflow[a + (j - n_trk)];
+          const int calo = (int)(f.key >> 24);
+          const DevCalo& C = K.calo[calo];
+          const uint32_t id = f.key & 0xFFFFFFu;
+          const int r = ring_of_id(C, id);
+          oe = C.eta_c[r];
+          op = K.phi_pool[C.phioff[r] + C.nphi[r] + 1 + (id - (uint32_t)C.base[r])];
+          opt = f.et; oid = f.key; is_trk = false;
+        }
+        if (!(opt > K.iso_ptmin)) continue;
+        const unsigned long long wgt = to_fp(opt);
+        for (uint32_t c = 0; c < gn; ++c) {
+          const float4 cv = cf[c];
+          if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == ckey[c])) continue;
+          const float de = oe - cv.x;
+          float dp = op - cv.y;
+          if (dp >= PI_F) dp -= TWO_PI_F;
+          else if (dp < -PI_F) dp += TWO_PI_F;
+          const float dr2 = fmaf(de, de, dp * dp);
+          if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
+        }
+      }
+      tc.sync();
+      if ((uint32_t)tc.tid < gn) {
+        const uint64_t j = a + g0 + tc.tid;
+        const float s = from_fp(csum[tc.tid]);
+        const float rel = s / cf[tc.tid].z;
+        reinterpret_cast<float2*>(p.iso)[j] = make_float2(s, rel);
+        if (rel < K.imax) {
+          uint32_t* info = reinterpret_cast<uint32_t*>(p.cands + j) + 3;
+          *info |= 0x80000000u;
+        }
+      }
+      tc.sync();
+    }
+  }
+  tc.sync();
+  if (tc.tid == 0)
+    reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
+}
+
+// ------------------------------------------------------------------ kernel
+template <int TEAM, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fused_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NT = BLOCK / TEAM;
+  TeamCtx<TEAM> tc;
+  tc.tix = (int)threadIdx.x / TEAM;
+  tc.tid = (int)threadIdx.x % TEAM;
+  const uint64_t tbytes = team_smem_bytes(TEAM, p.table_slots, p.nmax_smem);
+  unsigned char* mine = smem + (uint64_t)tc.tix * tbytes;
+  const Tbl st = carve(mine, p.table_slots, p.log2_slots);
+  unsigned char* tail = mine + ((((uint64_t)p.table_slots * 24 + (uint64_t)p.nmax_smem * 4) + 15) & ~15ull);
+  uint32_t* wbuf = (uint32_t*)tail;
+  float4* cf = (float4*)(tail + 2 * 32 * 4);
+  uint32_t* ckey = (uint32_t*)(cf + PDR_CMAX);
+  unsigned long long* csum = (unsigned long long*)(ckey + 2 * PDR_CMAX);
+  for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys[s] = PDR_EMPTY;
+  tc.sync();
+  const DevCard& K = *p.card;
+  const uint64_t gteam = (uint64_t)blockIdx.x * NT + tc.tix;
+  const uint64_t nteams = (uint64_t)gridDim.x * NT;
+  for (uint64_t e = gteam; e < p.n_events; e += nteams) {
+    const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
+    if (b < a || b - a >= (1ull << 28)) {
+      if (tc.tid == 0) {
+        atomicOr(p.err, ERR_CSR);
+        reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(0, 0, 0, 0);
+      }
+      continue;
+    }
+    const uint32_t n = (uint32_t)(b - a);
+    if (n <= p.nmax_smem) {
+      process_event<TEAM>(p, K, st, wbuf, cf, ckey, csum, tc, e, a, n);
+    } else if (p.gscratch != nullptr && n <= p.g_nmax) {
+      const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_log2);
+      for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys[s] = PDR_EMPTY;
+      tc.sync();
+      process_event<TEAM>(p, K, gt, wbuf, cf, ckey, csum, tc, e, a, n);
+    } else {
+      if (tc.tid == 0) {
+        atomicOr(p.err, ERR_OVERSIZE);
+        reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(0, 0, 0, 0);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- auxiliary kernels
+__global__ void max_event_kernel(const uint64_t* __restrict__ offsets, uint64_t n_events,
+                                 uint32_t* out, uint32_t* err) {
+  uint32_t m = 0;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_events;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = offsets[e], b = offsets[e + 1];
+    if (b < a) atomicOr(err, ERR_CSR);
+    else m = max(m, (uint32_t)min(b - a, (uint64_t)0xFFFFFFFFu));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(PDR_FULL, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Dense compaction for host delivery: exclusive scan of per-event counts per
+// collection (single block per collection, chunked), then a gather.
+__global__ void scan_counts_kernel(const uint32_t* __restrict__ counts, uint64_t n_events,
+                                   uint64_t* __restrict__ dense_off /* [4][n_events + 1] */) {
+  const int c = blockIdx.x;  // collection
+  __shared__ unsigned long long part[1024];
+  uint64_t* out = dense_off + (uint64_t)c * (n_events + 1);
+  unsigned long long carry = 0;
+  for (uint64_t base = 0; base < n_events; base += blockDim.x) {
+    const uint64_t e = base + threadIdx.x;
+    const unsigned long long v = e < n_events ? counts[4 * e + c] : 0ull;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (unsigned o = 1; o < blockDim.x; o <<= 1) {
+      const unsigned long long u = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      part[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (e < n_events) out[e] = carry + part[threadIdx.x] - v;
+    const unsigned long long blk = part[blockDim.x - 1];
+    __syncthreads();
+    carry += blk;
+  }
+  if (threadIdx.x == 0) out[n_events] = carry;
+}
+
+__global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64_t n_events,
+                                    const uint32_t* __restrict__ counts,
+                                    const uint64_t* __restrict__ dense_off, pdr_outputs src,
+                                    pdr_outputs dst) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t e = warp; e < n_events; e += nwarps) {
+    const uint64_t a = offsets[e];
+    const uint32_t nt = counts[4 * e], nw = counts[4 * e + 1], nf = counts[4 * e + 2], nc = counts[4 * e + 3];
+    const uint64_t dt = dense_off[e], dw = dense_off[(n_events + 1) + e];
+    const uint64_t df = dense_off[2 * (n_events + 1) + e], dc = dense_off[3 * (n_events + 1) + e];
+    for (uint32_t k = lane; k < nt; k += 32) dst.tracks[dt + k] = src.tracks[a + k];
+    for (uint32_t k = lane; k < nw; k += 32) dst.towers[dw + k] = src.towers[a + k];
+    for (uint32_t k = lane; k < nf; k += 32) dst.eflow[df + k] = src.eflow[a + k];
+    for (uint32_t k = lane; k < nc; k += 32) {
+      dst.cands[dc + k] = src.cands[a + k];
+      dst.iso[dc + k] = src.iso[a + k];
+    }
+  }
+}
+
+// ------------------------------------------------------- launch helpers
+template <int TEAM, int BLOCK>
+static cudaError_t launch_t(const KParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
+  auto fn = fused_kernel<TEAM, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, BLOCK, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int TEAM, int BLOCK>
+static cudaError_t occupancy_t(int* blocks, size_t smem) {
+  auto fn = fused_kernel<TEAM, BLOCK>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, BLOCK, smem);
+}
+
+#define PDR_SHAPES(X) X(32, 128) X(32, 256) X(64, 256) X(128, 128) X(128, 256) X(256, 256) X(512, 512) X(1024, 1024)
+
+bool shape_supported(uint32_t team, uint32_t block) {
+#define PDR_SUP(T, B) if (team == T && block == B) return true;
+  PDR_SHAPES(PDR_SUP)
+#undef PDR_SUP
+  return false;
+}
+
+cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
+                         cudaStream_t s) {
+#define PDR_L(T, B) if (team == T && block == B) return launch_t<T, B>(p, grid, smem, s);
+  PDR_SHAPES(PDR_L)
+#undef PDR_L
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks) {
+#define PDR_O(T, B) if (team == T && block == B) return occupancy_t<T, B>(blocks, smem);
+  PDR_SHAPES(PDR_O)
+#undef PDR_O
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
+                             cudaStream_t s) {
+  const uint64_t blocks = n_events / 256 + 1;
+  max_event_kernel<<<(unsigned)(blocks < 1184 ? blocks : 1184), 256, 0, s>>>(offsets, n_events, out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
+                         uint64_t* dense_off, const pdr_outputs& src, const pdr_outputs& dst,
+                         int n_sms, cudaStream_t s) {
+  scan_counts_kernel<<<4, 1024, 0, s>>>(counts, n_events, dense_off);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gather_dense_kernel<<<n_sms * 8, 256, 0, s>>>(offsets, n_events, counts, dense_off, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace pdr

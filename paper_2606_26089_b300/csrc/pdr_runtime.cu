@@ -1,0 +1,924 @@
+// Host runtime of the CUDA library behind include/pdr.h: contexts, detector
+// cards, launch shapes and autotuning, scratch and the result pool, the
+// batched / per-event / host-buffer entry points and tickets.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "pdr.h"
+#include "pdr_internal.h"
+
+namespace pdr {
+bool shape_supported(uint32_t team, uint32_t block);
+cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
+                         cudaStream_t s);
+cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks);
+cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
+                             cudaStream_t s);
+cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
+                         uint64_t* dense_off, const pdr_outputs& src, const pdr_outputs& dst, int n_sms,
+                         cudaStream_t s);
+}  // namespace pdr
+
+using namespace pdr;
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const std::string& msg) {
+  t_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(PDR_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PDR_CUDA(call, what)                       \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) return cuda_fail(_e, what); \
+  } while (0)
+
+uint32_t next_pow2(uint64_t v) {
+  uint32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+uint32_t ilog2(uint32_t v) {
+  uint32_t l = 0;
+  while ((1u << l) < v) ++l;
+  return l;
+}
+
+// ---------------------------------------------------------------- pool
+// First-fit allocator over one device region (results of submit(), staging
+// of the host-buffer path, scratch).  256-byte granularity.
+struct Pool {
+  unsigned char* base = nullptr;
+  uint64_t size = 0;
+  std::map<uint64_t, uint64_t> free_;  // offset -> length
+  std::map<uint64_t, uint64_t> used_;
+
+  int init(uint64_t bytes) {
+    size = (bytes + 255) & ~255ull;
+    if (cudaMalloc((void**)&base, size) != cudaSuccess) {
+      base = nullptr;
+      return PDR_ENOMEM;
+    }
+    free_[0] = size;
+    return PDR_OK;
+  }
+  void destroy() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    free_.clear();
+    used_.clear();
+  }
+  void* alloc(uint64_t bytes) {
+    bytes = (bytes + 255) & ~255ull;
+    if (bytes == 0) bytes = 256;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const uint64_t off = it->first, len = it->second;
+        free_.erase(it);
+        if (len > bytes) free_[off + bytes] = len - bytes;
+        used_[off] = bytes;
+        return base + off;
+      }
+    }
+    return nullptr;
+  }
+  void release(void* p) {
+    if (!p) return;
+    const uint64_t off = (uint64_t)((unsigned char*)p - base);
+    auto it = used_.find(off);
+    if (it == used_.end()) return;
+    uint64_t len = it->second;
+    used_.erase(it);
+    uint64_t o = off;
+    auto nx = free_.lower_bound(o);
+    if (nx != free_.end() && nx->first == o + len) {
+      len += nx->second;
+      free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(o);
+    if (pv != free_.begin()) {
+      --pv;
+      if (pv->first + pv->second == o) {
+        o = pv->first;
+        len += pv->second;
+        free_.erase(pv);
+      }
+    }
+    free_[o] = len;
+  }
+  uint64_t free_bytes() const {
+    uint64_t s = 0;
+    for (auto& kv : free_) s += kv.second;
+    return s;
+  }
+};
+
+struct CardEntry {
+  DevCard* dev = nullptr;
+  uint32_t ntowers[2] = {0, 0};
+};
+
+struct Ticket {
+  cudaEvent_t done = nullptr;
+  void* mem = nullptr;
+  pdr_result res{};
+};
+
+}  // namespace
+
+struct pdr_ctx {
+  int device = 0;
+  int n_sms = 0;
+  size_t smem_optin = 0;
+  uint32_t* d_err = nullptr;      // device error word
+  uint32_t* d_word = nullptr;     // small device word for reductions
+  uint32_t* h_word = nullptr;     // pinned host word
+  std::map<uint32_t, CardEntry> cards;
+  uint32_t next_card = 1;
+  Pool pool;
+  uint32_t max_tickets = 64;
+  std::map<uint64_t, Ticket> tickets;
+  uint64_t next_ticket = 1;
+  std::map<uint64_t, pdr_launch> tuned;  // (card, size class) -> shape
+  unsigned char* gscratch = nullptr;      // global tower tables for large events
+  uint64_t gscratch_bytes = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+// ------------------------------------------------------------ card expansion
+int expand_calo(const pdr_card* c, int calo, DevCalo& D, float* pool, int& pool_used,
+                std::vector<std::pair<int, int>>& phi_tables) {
+  const int nseg = c->nseg[calo];
+  if (nseg < 1 || nseg > PDR_MAXSEG) return fail(PDR_ECARD, "calorimeter needs 1..4 eta segments");
+  std::vector<double> p(1, 0.0);
+  std::vector<int> pn;
+  double lo = 0.0;
+  std::memset(&D, 0, sizeof D);
+  D.nseg = nseg;
+  for (int s = 0; s < nseg; ++s) {
+    const double hi = c->seg_eta_hi[calo][s];
+    const int n = c->seg_neta[calo][s];
+    const int nphi = c->seg_nphi[calo][s];
+    if (!(hi > lo) || n < 1 || nphi < 1 || nphi > PDR_MAXPHI)
+      return fail(PDR_ECARD, "bad calorimeter segment (eta_hi must increase, n_eta >= 1, 1 <= n_phi <= 1024)");
+    D.seg_lo[s] = (float)lo;
+    D.seg_hi[s] = (float)hi;
+    D.seg_scale[s] = (float)(n / (hi - lo));
+    D.seg_n[s] = n;
+    D.seg_first[s] = (int)pn.size();
+    for (int k = 1; k <= n; ++k) {
+      p.push_back(k == n ? hi : lo + ((hi - lo) * (double)k) / (double)n);
+      pn.push_back(nphi);
+    }
+    lo = hi;
+  }
+  const int m = (int)pn.size();
+  if (2 * m > PDR_MAXRING) return fail(PDR_ECARD, "too many eta rings (max 512)");
+  D.nring = 2 * m;
+  std::vector<double> edge(2 * m + 1);
+  for (int j = 0; j <= m; ++j) {
+    edge[m + j] = p[j];
+    edge[m - j] = -p[j];
+  }
+  edge[m] = 0.0;
+  std::vector<int> nphi(2 * m);
+  for (int r = 0; r < m; ++r) {
+    nphi[m + r] = pn[r];
+    nphi[m - 1 - r] = pn[r];
+  }
+  for (int j = 0; j <= 2 * m; ++j) D.edge[j] = (float)edge[j];
+  for (int j = 0; j < 2 * m; ++j)
+    if (!(D.edge[j] < D.edge[j + 1])) return fail(PDR_ECARD, "eta ring edges not increasing in float32");
+  int base = 0;
+  for (int r = 0; r < 2 * m; ++r) {
+    D.base[r] = base;
+    D.nphi[r] = nphi[r];
+    base += nphi[r];
+    // phi table shared by rings with the same number of bins
+    int off = -1;
+    for (auto& t : phi_tables)
+      if (t.first == nphi[r]) off = t.second;
+    if (off < 0) {
+      const int np = nphi[r];
+      if (pool_used + 2 * np + 1 > PDR_PHIPOOL) return fail(PDR_ECARD, "phi table pool exhausted");
+      off = pool_used;
+      for (int k = 0; k <= np; ++k) {
+        const double e = k == 0 ? -M_PI : (k == np ? M_PI : -M_PI + (2.0 * M_PI * (double)k) / (double)np);
+        pool[off + k] = (float)e;
+      }
+      for (int k = 0; k < np; ++k) {
+        const double e0 = k == 0 ? -M_PI : -M_PI + (2.0 * M_PI * (double)k) / (double)np;
+        const double e1 = k + 1 == np ? M_PI : -M_PI + (2.0 * M_PI * (double)(k + 1)) / (double)np;
+        pool[off + np + 1 + k] = (float)(0.5 * (e0 + e1));
+      }
+      pool_used += 2 * np + 1;
+      phi_tables.push_back({np, off});
+    }
+    D.phioff[r] = off;
+    D.phi_scale[r] = (float)(nphi[r] / (2.0 * M_PI));
+    const double ec = 0.5 * (edge[r] + edge[r + 1]);
+    D.eta_c[r] = (float)ec;
+    D.cosh_c[r] = (float)std::cosh(ec);
+  }
+  D.ntowers = base;
+  if (base >= (1 << 24)) return fail(PDR_ECARD, "too many towers (max 2^24 per calorimeter)");
+  return PDR_OK;
+}
+
+int lookup_res_bin(const pdr_card* c, int comp, float x) {
+  int k = -1;
+  for (int j = 0; j < c->res_n[comp]; ++j)
+    if ((float)c->res_edges[comp][j] <= x) k = j;
+  return k < 0 ? 0 : k;
+}
+
+unsigned long long eff_threshold(double eff) {
+  if (eff >= 1.0) return 4294967296ull;
+  if (!(eff > 0.0)) return 0ull;
+  return (unsigned long long)std::floor(eff * 4294967296.0);
+}
+
+bool increasing(const double* v, int n) {
+  for (int i = 0; i + 1 < n; ++i)
+    if (!((float)v[i] < (float)v[i + 1])) return false;
+  return true;
+}
+
+int expand_card(const pdr_card* c, DevCard& D) {
+  std::memset(&D, 0, sizeof D);
+  if (!(c->R > 0.0) || !(c->L > 0.0) || !std::isfinite(c->B)) return fail(PDR_ECARD, "need R > 0, L > 0, finite B");
+  int pool_used = 0;
+  std::vector<std::pair<int, int>> tables;
+  for (int calo = 0; calo < 2; ++calo) {
+    std::vector<std::pair<int, int>> t;  // phi tables are per calorimeter
+    int rc = expand_calo(c, calo, D.calo[calo], D.phi_pool, pool_used, t);
+    if (rc) return rc;
+  }
+  D.R = (float)c->R;
+  D.L = (float)c->L;
+  D.kB = (float)(0.299792458 * std::fabs(c->B));
+  D.Bsign = c->B > 0.0 ? 1 : -1;
+  D.has_field = c->B != 0.0;
+  for (int q = 1; q <= PDR_MAXQ; ++q) {
+    const double kq = 0.299792458 * std::fabs((double)q) * std::fabs(c->B);
+    const double cR = kq * c->R;
+    D.cR_hi[q] = (float)cR;
+    D.cR_lo[q] = (float)(cR - (double)D.cR_hi[q]);
+  }
+  // efficiencies
+  if (c->trk_npt < 1 || c->trk_npt > PDR_MAXEDGE || c->trk_neta < 1 || c->trk_neta > PDR_MAXEDGE ||
+      c->id_n < 1 || c->id_n > PDR_MAXEDGE)
+    return fail(PDR_ECARD, "efficiency tables need 1..8 edges per axis");
+  if (!increasing(c->trk_pt_edges, c->trk_npt) || !increasing(c->trk_eta_edges, c->trk_neta) ||
+      !increasing(c->id_edges, c->id_n))
+    return fail(PDR_ECARD, "efficiency table edges must increase");
+  D.trk_npt = c->trk_npt;
+  D.trk_neta = c->trk_neta;
+  for (int k = 0; k < c->trk_npt; ++k) D.trk_pt_edges[k] = (float)c->trk_pt_edges[k];
+  for (int k = 0; k < c->trk_neta; ++k) D.trk_eta_edges[k] = (float)c->trk_eta_edges[k];
+  for (int t = 0; t < 3; ++t)
+    for (int i = 0; i < c->trk_npt; ++i)
+      for (int j = 0; j < c->trk_neta; ++j) {
+        const double e = c->trk_eff[t][i][j];
+        if (!(e >= 0.0 && e <= 1.0)) return fail(PDR_ECARD, "tracking efficiency outside [0, 1]");
+        D.trk_T[t][i][j] = eff_threshold(e);
+      }
+  D.id_n = c->id_n;
+  for (int k = 0; k < c->id_n; ++k) D.id_edges[k] = (float)c->id_edges[k];
+  for (int t = 0; t < 3; ++t)
+    for (int k = 0; k < c->id_n; ++k) {
+      const double e = c->id_eff[t][k];
+      if (!(e >= 0.0 && e <= 1.0)) return fail(PDR_ECARD, "identification efficiency outside [0, 1]");
+      D.id_T[t][k] = eff_threshold(e);
+    }
+  // resolutions
+  for (int comp = 0; comp < 4; ++comp) {
+    const int n = c->res_n[comp];
+    if (n < 1 || n > PDR_MAXEDGE || !increasing(c->res_edges[comp], n))
+      return fail(PDR_ECARD, "resolution tables need 1..8 increasing |eta| edges");
+    D.res_n[comp] = n;
+    for (int k = 0; k < n; ++k) {
+      D.res_edges[comp][k] = (float)c->res_edges[comp][k];
+      const double a = c->res_abcd[comp][k][0], b = c->res_abcd[comp][k][1];
+      const double cc = c->res_abcd[comp][k][2], d = c->res_abcd[comp][k][3];
+      if (!(a >= 0 && b >= 0 && cc >= 0 && d >= 0)) return fail(PDR_ECARD, "negative resolution coefficient");
+      D.res_a2[comp][k] = (float)(a * a);
+      D.res_b2[comp][k] = (float)(b * b);
+      D.res_c2[comp][k] = (float)(cc * cc);
+      D.res_d2[comp][k] = (float)(d * d);
+    }
+  }
+  for (int calo = 0; calo < 2; ++calo) {
+    DevCalo& C = D.calo[calo];
+    const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
+    for (int r = 0; r < C.nring; ++r) C.resbin[r] = lookup_res_bin(c, comp, std::fabs(C.eta_c[r]));
+    D.e_min[calo] = (float)c->e_min[calo];
+    D.s_min[calo] = (float)c->s_min[calo];
+  }
+  D.cand_ptmin = (float)c->cand_ptmin;
+  D.dr2max = (float)(c->iso_dr * c->iso_dr);
+  D.dr2min = (float)(c->iso_drmin * c->iso_drmin);
+  D.iso_ptmin = (float)c->iso_ptmin;
+  D.imax = (float)c->iso_imax;
+  return PDR_OK;
+}
+
+// ------------------------------------------------------------ launch shapes
+struct Shape {
+  uint32_t team, block, slots, nmax, grid;
+  size_t smem;
+};
+
+const uint32_t kTeams[] = {32, 64, 128, 256, 512, 1024};
+
+uint32_t slots_for(uint32_t max_n) {
+  // load factor <= 3/4
+  return std::max<uint32_t>(64, next_pow2((uint64_t)max_n * 4 / 3 + 1));
+}
+
+// Build a concrete shape for (team, block) handling events up to max_n in shared
+// memory where possible.
+int make_shape(pdr_ctx* ctx, uint32_t team, uint32_t block, uint32_t want_slots, uint32_t grid, Shape& S) {
+  if (!shape_supported(team, block)) return fail(PDR_EINVAL, "unsupported launch shape (team, block)");
+  const uint32_t nt = block / team;
+  uint32_t slots = std::max<uint32_t>(64, next_pow2(want_slots));
+  // shrink until the CTA fits in shared memory
+  while (slots > 64 && nt * team_smem_bytes(team, slots, slots * 3 / 4) > ctx->smem_optin) slots >>= 1;
+  S.team = team;
+  S.block = block;
+  S.slots = slots;
+  S.nmax = slots * 3 / 4;
+  S.smem = (size_t)(nt * team_smem_bytes(team, slots, S.nmax));
+  if (S.smem > ctx->smem_optin) return fail(PDR_EINVAL, "launch shape does not fit in shared memory");
+  int per_sm = 0;
+  cudaError_t e = occupancy_fused(team, block, S.smem, &per_sm);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (per_sm < 1) return fail(PDR_EINVAL, "launch shape cannot be resident");
+  S.grid = grid ? grid : (uint32_t)(per_sm * ctx->n_sms);
+  return PDR_OK;
+}
+
+pdr_launch default_launch(uint32_t max_n) {
+  pdr_launch l{};
+  if (max_n <= 128) { l.team = 32; l.block = 256; }
+  else if (max_n <= 640) { l.team = 128; l.block = 256; }
+  else if (max_n <= 1500) { l.team = 256; l.block = 256; }
+  else if (max_n <= 3000) { l.team = 512; l.block = 512; }
+  else { l.team = 1024; l.block = 1024; }
+  l.table_slots = slots_for(max_n);
+  l.grid = 0;
+  return l;
+}
+
+uint64_t tune_key(uint32_t card_id, uint32_t max_n) {
+  return ((uint64_t)card_id << 32) | (uint64_t)next_pow2(std::max<uint32_t>(max_n, 1));
+}
+
+int ensure_gscratch(pdr_ctx* ctx, uint64_t bytes) {
+  if (ctx->gscratch_bytes >= bytes) return PDR_OK;
+  if (ctx->gscratch) cudaFree(ctx->gscratch);
+  ctx->gscratch = nullptr;
+  ctx->gscratch_bytes = 0;
+  if (cudaMalloc((void**)&ctx->gscratch, bytes) != cudaSuccess) {
+    ctx->gscratch = nullptr;
+    return fail(PDR_ENOMEM, "cannot allocate the global tower tables for large events");
+  }
+  ctx->gscratch_bytes = bytes;
+  return PDR_OK;
+}
+
+int check_batch(pdr_ctx* ctx, const pdr_batch* b) {
+  if (!ctx || !b) return fail(PDR_EINVAL, "null context or batch");
+  if (b->n_events >= (1ull << 31)) return fail(PDR_EINVAL, "n_events must be < 2^31");
+  if (b->n_events > 0 && (!b->offsets || !b->pt || !b->eta || !b->phi || !b->mass || !b->pdg || !b->charge))
+    return fail(PDR_EINVAL, "null input array");
+  if (ctx->cards.find(b->card_id) == ctx->cards.end()) return fail(PDR_ENOTFOUND, "unknown card id");
+  return PDR_OK;
+}
+
+int check_outputs(const pdr_outputs* o) {
+  if (!o || !o->tracks || !o->towers || !o->eflow || !o->cands || !o->iso || !o->counts)
+    return fail(PDR_EINVAL, "null output buffer");
+  return PDR_OK;
+}
+
+int max_event_size_impl(pdr_ctx* ctx, const pdr_batch* b, cudaStream_t s, uint32_t* out) {
+  if (b->n_events == 0) { *out = 0; return PDR_OK; }
+  PDR_CUDA(cudaMemsetAsync(ctx->d_word, 0, 4, s), "memset");
+  PDR_CUDA(launch_max_event(b->offsets, b->n_events, ctx->d_word, ctx->d_err, s), "max event kernel");
+  PDR_CUDA(cudaMemcpyAsync(ctx->h_word, ctx->d_word, 4, cudaMemcpyDeviceToHost, s), "copy max");
+  PDR_CUDA(cudaStreamSynchronize(s), "sync");
+  *out = *ctx->h_word;
+  return PDR_OK;
+}
+
+// Fill a kernel parameter block and launch one shape over a batch.
+int run_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const Shape& S, uint32_t max_n,
+              cudaStream_t s) {
+  KParams p;
+  std::memset(&p, 0, sizeof p);
+  p.card = ctx->cards[b->card_id].dev;
+  p.n_events = b->n_events;
+  p.offsets = b->offsets;
+  p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.mass = b->mass; p.vz = b->vz;
+  p.pdg = b->pdg; p.charge = b->charge;
+  p.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
+  p.seed_hi = (uint32_t)(b->seed >> 32);
+  p.event_base = b->event_index_base;
+  p.flags = b->flags;
+  p.tracks = o->tracks; p.towers = o->towers; p.eflow = o->eflow; p.cands = o->cands;
+  p.iso = o->iso; p.counts = o->counts;
+  p.debug = (b->flags & PDR_BATCH_DEBUG) ? o->debug : nullptr;
+  p.table_slots = S.slots;
+  p.log2_slots = ilog2(S.slots);
+  p.nmax_smem = S.nmax;
+  p.err = ctx->d_err;
+  if (max_n > S.nmax) {
+    const uint32_t gs = slots_for(max_n);
+    if (gs > 65536) return fail(PDR_EOVERFLOW, "event larger than 49152 particles");
+    p.g_slots = gs;
+    p.g_log2 = ilog2(gs);
+    p.g_nmax = gs * 3 / 4;
+    p.g_team_bytes = global_team_bytes(gs, p.g_nmax);
+    const uint64_t need = p.g_team_bytes * (uint64_t)S.grid * (S.block / S.team);
+    int rc = ensure_gscratch(ctx, need);
+    if (rc) return rc;
+    p.gscratch = ctx->gscratch;
+  }
+  if (b->n_events == 0) return PDR_OK;
+  PDR_CUDA(launch_fused(S.team, S.block, p, S.grid, S.smem, s), "fused kernel launch");
+  return PDR_OK;
+}
+
+int resolve_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_launch* l, cudaStream_t s, uint32_t& max_n,
+                  Shape& S) {
+  max_n = b->max_event_size;
+  if (max_n == 0 && b->n_events > 0) {
+    int rc = max_event_size_impl(ctx, b, s, &max_n);
+    if (rc) return rc;
+  }
+  pdr_launch use;
+  if (l) use = *l;
+  else {
+    auto it = ctx->tuned.find(tune_key(b->card_id, max_n));
+    use = it != ctx->tuned.end() ? it->second : default_launch(max_n);
+  }
+  const uint32_t want = use.table_slots ? use.table_slots : slots_for(max_n);
+  return make_shape(ctx, use.team, use.block, want, use.grid, S);
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+int pdr_abi_version(void) { return PDR_ABI_VERSION; }
+
+const char* pdr_last_error(pdr_ctx*) { return t_err.c_str(); }
+
+int pdr_create(pdr_ctx** out, int cuda_device, const pdr_options* opt) {
+  if (!out) return fail(PDR_EINVAL, "null out");
+  *out = nullptr;
+  PDR_CUDA(cudaSetDevice(cuda_device), "cudaSetDevice");
+  pdr_ctx* ctx = new pdr_ctx();
+  ctx->device = cuda_device;
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, cuda_device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e, "cudaGetDeviceProperties");
+  }
+  ctx->n_sms = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  if (cudaMalloc((void**)&ctx->d_err, 16) != cudaSuccess || cudaMemset(ctx->d_err, 0, 16) != cudaSuccess) {
+    delete ctx;
+    return fail(PDR_ENOMEM, "cannot allocate the device error word");
+  }
+  ctx->d_word = ctx->d_err + 2;
+  if (cudaMallocHost((void**)&ctx->h_word, 16) != cudaSuccess) {
+    cudaFree(ctx->d_err);
+    delete ctx;
+    return fail(PDR_ENOMEM, "cannot allocate pinned host word");
+  }
+  const uint64_t pool = opt && opt->pool_bytes ? opt->pool_bytes : (1ull << 30);
+  if (ctx->pool.init(pool) != PDR_OK) {
+    cudaFree(ctx->d_err);
+    cudaFreeHost(ctx->h_word);
+    delete ctx;
+    return fail(PDR_ENOMEM, "cannot allocate the device pool");
+  }
+  if (opt && opt->max_tickets) ctx->max_tickets = opt->max_tickets;
+  *out = ctx;
+  return PDR_OK;
+}
+
+int pdr_destroy(pdr_ctx* ctx) {
+  if (!ctx) return PDR_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->tickets)
+    if (kv.second.done) cudaEventDestroy(kv.second.done);
+  for (auto& kv : ctx->cards) cudaFree(kv.second.dev);
+  ctx->pool.destroy();
+  if (ctx->gscratch) cudaFree(ctx->gscratch);
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_word);
+  delete ctx;
+  return PDR_OK;
+}
+
+int pdr_card_load(pdr_ctx* ctx, const pdr_card* card, uint32_t* card_id) {
+  if (!ctx || !card || !card_id) return fail(PDR_EINVAL, "null argument");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  DevCard* host = new DevCard();
+  int rc = expand_card(card, *host);
+  if (rc) {
+    delete host;
+    return rc;
+  }
+  CardEntry ce;
+  ce.ntowers[0] = (uint32_t)host->calo[0].ntowers;
+  ce.ntowers[1] = (uint32_t)host->calo[1].ntowers;
+  cudaSetDevice(ctx->device);
+  if (cudaMalloc((void**)&ce.dev, sizeof(DevCard)) != cudaSuccess) {
+    delete host;
+    return fail(PDR_ENOMEM, "cannot allocate card tables");
+  }
+  cudaError_t e = cudaMemcpy(ce.dev, host, sizeof(DevCard), cudaMemcpyHostToDevice);
+  delete host;
+  if (e != cudaSuccess) {
+    cudaFree(ce.dev);
+    return cuda_fail(e, "card upload");
+  }
+  *card_id = ctx->next_card++;
+  ctx->cards[*card_id] = ce;
+  return PDR_OK;
+}
+
+int pdr_card_unload(pdr_ctx* ctx, uint32_t card_id) {
+  if (!ctx) return fail(PDR_EINVAL, "null context");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->cards.find(card_id);
+  if (it == ctx->cards.end()) return fail(PDR_ENOTFOUND, "unknown card id");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(it->second.dev);
+  ctx->cards.erase(it);
+  return PDR_OK;
+}
+
+int pdr_card_towers(pdr_ctx* ctx, uint32_t card_id, int calo, uint32_t* n) {
+  if (!ctx || !n || calo < 0 || calo > 1) return fail(PDR_EINVAL, "bad argument");
+  auto it = ctx->cards.find(card_id);
+  if (it == ctx->cards.end()) return fail(PDR_ENOTFOUND, "unknown card id");
+  *n = it->second.ntowers[calo];
+  return PDR_OK;
+}
+
+int pdr_max_event_size(pdr_ctx* ctx, const pdr_batch* b, void* stream, uint32_t* out) {
+  if (!ctx || !b || !out) return fail(PDR_EINVAL, "null argument");
+  if (b->n_events > 0 && !b->offsets) return fail(PDR_EINVAL, "null offsets");
+  cudaSetDevice(ctx->device);
+  return max_event_size_impl(ctx, b, (cudaStream_t)stream, out);
+}
+
+int pdr_run(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_launch* l, void* stream) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if ((rc = check_outputs(o))) return rc;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  Shape S;
+  uint32_t max_n = 0;
+  if ((rc = resolve_shape(ctx, b, l, (cudaStream_t)stream, max_n, S))) return rc;
+  return run_shape(ctx, b, o, S, max_n, (cudaStream_t)stream);
+}
+
+int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* stream) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if ((rc = check_outputs(o))) return rc;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t max_n = b->max_event_size;
+  if (max_n == 0 && b->n_events > 0 && (rc = max_event_size_impl(ctx, b, s, &max_n))) return rc;
+  Shape S;
+  if ((rc = make_shape(ctx, 256, 256, slots_for(max_n), 1, S))) return rc;
+  S.grid = 1;
+  for (uint64_t e = 0; e < b->n_events; ++e) {
+    pdr_batch one = *b;
+    one.n_events = 1;
+    one.offsets = b->offsets + e;
+    one.event_index_base = b->event_index_base + (uint32_t)e;
+    pdr_outputs oe = *o;
+    oe.counts = o->counts + 4 * e;
+    if ((rc = run_shape(ctx, &one, &oe, S, max_n, s))) return rc;
+  }
+  return PDR_OK;
+}
+
+int pdr_check(pdr_ctx* ctx, void* stream) {
+  if (!ctx) return fail(PDR_EINVAL, "null context");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  PDR_CUDA(cudaMemcpyAsync(ctx->h_word, ctx->d_err, 4, cudaMemcpyDeviceToHost, s), "read error word");
+  PDR_CUDA(cudaStreamSynchronize(s), "sync");
+  const uint32_t w = *ctx->h_word;
+  PDR_CUDA(cudaMemsetAsync(ctx->d_err, 0, 4, s), "clear error word");
+  PDR_CUDA(cudaStreamSynchronize(s), "sync");
+  if (w) {
+    std::string m = "device error:";
+    if (w & ERR_CSR) m += " malformed CSR offsets;";
+    if (w & ERR_OVERSIZE) m += " event larger than the launch allows;";
+    if (w & ERR_TABLE) m += " tower table full;";
+    return fail(PDR_EDEVICE, m);
+  }
+  return PDR_OK;
+}
+
+int pdr_autotune(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* stream, pdr_launch* best) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if ((rc = check_outputs(o))) return rc;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t max_n = b->max_event_size;
+  if (max_n == 0 && b->n_events > 0 && (rc = max_event_size_impl(ctx, b, s, &max_n))) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  pdr_launch best_l = default_launch(max_n);
+  const uint32_t blocks_for[] = {256, 256, 256, 256, 512, 1024};
+  for (int ti = 0; ti < 6; ++ti) {
+    const uint32_t team = kTeams[ti];
+    for (uint32_t block : {blocks_for[ti], team < 256 ? 128u : 0u}) {
+      if (block == 0 || block < team || !shape_supported(team, block)) continue;
+      // table sized for the largest event, or for the typical event with the
+      // largest ones spilling to the global table
+      for (uint32_t want : {slots_for(max_n), slots_for(std::max<uint32_t>(max_n / 2, 1))}) {
+        Shape S;
+        if (make_shape(ctx, team, block, want, 0, S) != PDR_OK) continue;
+        // a team must not walk a huge event alone in tiny chunks
+        if (team == 32 && max_n > 1024) continue;
+        if (run_shape(ctx, b, o, S, max_n, s) != PDR_OK) continue;  // warm-up
+        cudaEventRecord(e0, s);
+        if (run_shape(ctx, b, o, S, max_n, s) != PDR_OK) continue;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_l.team = team;
+          best_l.block = block;
+          best_l.table_slots = S.slots;
+          best_l.grid = 0;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  ctx->tuned[tune_key(b->card_id, max_n)] = best_l;
+  if (best) *best = best_l;
+  return PDR_OK;
+}
+
+int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const pdr_launch* l, void* stream) {
+  int rc = check_batch(ctx, hb);
+  if (rc) return rc;
+  if (!ho || !ho->tracks || !ho->towers || !ho->eflow || !ho->cands || !ho->iso || !ho->counts)
+    return fail(PDR_EINVAL, "null host output buffer");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t ne = hb->n_events;
+  const uint64_t np = ne ? hb->offsets[ne] : 0;
+  const uint64_t cap = np ? np : 1;
+  // device staging from the pool: inputs, slot-layout outputs, dense outputs
+  const uint64_t in_bytes = (ne + 1) * 8 + np * (4 * 4 + 4 + 1) + (hb->vz ? np * 4 : 0) + 8 * 256;
+  const uint64_t out_bytes = cap * (sizeof(pdr_track) + sizeof(pdr_tower) + sizeof(pdr_eflow) +
+                                    sizeof(pdr_cand) + sizeof(pdr_iso)) + (ne + 1) * 16 + 8 * 256;
+  const uint64_t dense_bytes = out_bytes + 4 * (ne + 1) * 8 + 256;
+  std::unique_lock<std::mutex> g(ctx->mu);
+  unsigned char* m = (unsigned char*)ctx->pool.alloc(in_bytes + out_bytes + dense_bytes);
+  g.unlock();
+  if (!m) return fail(PDR_ENOMEM, "device pool too small for this batch");
+  auto carve = [&](uint64_t bytes) {
+    unsigned char* r = m;
+    m += (bytes + 255) & ~255ull;
+    return (void*)r;
+  };
+  unsigned char* mem0 = m;
+  pdr_batch db = *hb;
+  db.offsets = (const uint64_t*)carve((ne + 1) * 8);
+  db.pt = (const float*)carve(np * 4);
+  db.eta = (const float*)carve(np * 4);
+  db.phi = (const float*)carve(np * 4);
+  db.mass = (const float*)carve(np * 4);
+  db.pdg = (const int32_t*)carve(np * 4);
+  db.charge = (const int8_t*)carve(np);
+  db.vz = hb->vz ? (const float*)carve(np * 4) : nullptr;
+  pdr_outputs so{};
+  so.tracks = (pdr_track*)carve(cap * sizeof(pdr_track));
+  so.towers = (pdr_tower*)carve(cap * sizeof(pdr_tower));
+  so.eflow = (pdr_eflow*)carve(cap * sizeof(pdr_eflow));
+  so.cands = (pdr_cand*)carve(cap * sizeof(pdr_cand));
+  so.iso = (pdr_iso*)carve(cap * sizeof(pdr_iso));
+  so.counts = (uint32_t*)carve((ne + 1) * 16);
+  pdr_outputs dd{};
+  dd.tracks = (pdr_track*)carve(cap * sizeof(pdr_track));
+  dd.towers = (pdr_tower*)carve(cap * sizeof(pdr_tower));
+  dd.eflow = (pdr_eflow*)carve(cap * sizeof(pdr_eflow));
+  dd.cands = (pdr_cand*)carve(cap * sizeof(pdr_cand));
+  dd.iso = (pdr_iso*)carve(cap * sizeof(pdr_iso));
+  uint64_t* dense_off = (uint64_t*)carve(4 * (ne + 1) * 8);
+  auto done = [&](int code) {
+    std::lock_guard<std::mutex> g2(ctx->mu);
+    ctx->pool.release(mem0);
+    return code;
+  };
+#define PDR_H2D(dst, src, bytes)                                                              \
+  if ((bytes) && cudaMemcpyAsync((void*)(dst), (src), (bytes), cudaMemcpyHostToDevice, s) != cudaSuccess) \
+    return done(fail(PDR_EDEVICE, "host-to-device copy"));
+  PDR_H2D(db.offsets, hb->offsets, (ne + 1) * 8);
+  PDR_H2D(db.pt, hb->pt, np * 4);
+  PDR_H2D(db.eta, hb->eta, np * 4);
+  PDR_H2D(db.phi, hb->phi, np * 4);
+  PDR_H2D(db.mass, hb->mass, np * 4);
+  PDR_H2D(db.pdg, hb->pdg, np * 4);
+  PDR_H2D(db.charge, hb->charge, np);
+  if (hb->vz) PDR_H2D(db.vz, hb->vz, np * 4);
+#undef PDR_H2D
+  db.flags &= ~PDR_BATCH_DEBUG;
+  {
+    std::lock_guard<std::mutex> g2(ctx->mu);
+    Shape S;
+    uint32_t max_n = 0;
+    if ((rc = resolve_shape(ctx, &db, l, s, max_n, S))) return done(rc);
+    if ((rc = run_shape(ctx, &db, &so, S, max_n, s))) return done(rc);
+  }
+  if (ne > 0) {
+    cudaError_t e = launch_dense(db.offsets, ne, so.counts, dense_off, so, dd, ctx->n_sms, s);
+    if (e != cudaSuccess) return done(cuda_fail(e, "dense compaction"));
+  }
+  // totals per collection, then copy back exactly the records produced
+  uint64_t totals[4] = {0, 0, 0, 0};
+  if (ne > 0) {
+    for (int c = 0; c < 4; ++c)
+      if (cudaMemcpyAsync(&totals[c], dense_off + (uint64_t)c * (ne + 1) + ne, 8, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess)
+        return done(fail(PDR_EDEVICE, "device-to-host copy"));
+  }
+  if (cudaMemcpyAsync(ho->counts, so.counts, ne * 16, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return done(fail(PDR_EDEVICE, "device-to-host copy"));
+  if (cudaStreamSynchronize(s) != cudaSuccess) return done(fail(PDR_EDEVICE, "stream synchronise"));
+#define PDR_D2H(dst, src, bytes)                                                               \
+  if ((bytes) && cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyDeviceToHost, s) != cudaSuccess) \
+    return done(fail(PDR_EDEVICE, "device-to-host copy"));
+  PDR_D2H(ho->tracks, dd.tracks, totals[0] * sizeof(pdr_track));
+  PDR_D2H(ho->towers, dd.towers, totals[1] * sizeof(pdr_tower));
+  PDR_D2H(ho->eflow, dd.eflow, totals[2] * sizeof(pdr_eflow));
+  PDR_D2H(ho->cands, dd.cands, totals[3] * sizeof(pdr_cand));
+  PDR_D2H(ho->iso, dd.iso, totals[3] * sizeof(pdr_iso));
+#undef PDR_D2H
+  if (cudaStreamSynchronize(s) != cudaSuccess) return done(fail(PDR_EDEVICE, "stream synchronise"));
+  return done(PDR_OK);
+}
+
+// ---------------------------------------------------------------- tickets
+int pdr_submit(pdr_ctx* ctx, const pdr_batch* b, void* stream, uint64_t* ticket) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if (!ticket) return fail(PDR_EINVAL, "null ticket");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (ctx->tickets.size() >= ctx->max_tickets) return fail(PDR_EBUSY, "too many tickets in flight");
+  uint64_t np = 0;
+  if (b->n_events > 0) {
+    PDR_CUDA(cudaMemcpyAsync(ctx->h_word, b->offsets + b->n_events, 8, cudaMemcpyDeviceToHost, s), "read size");
+    PDR_CUDA(cudaStreamSynchronize(s), "sync");
+    std::memcpy(&np, ctx->h_word, 8);
+  }
+  const uint64_t cap = np ? np : 1;
+  const bool dbg = (b->flags & PDR_BATCH_DEBUG) != 0;
+  const uint64_t rec = sizeof(pdr_track) + sizeof(pdr_tower) + sizeof(pdr_eflow) + sizeof(pdr_cand) +
+                       sizeof(pdr_iso) + (dbg ? sizeof(pdr_debug) : 0);
+  const uint64_t bytes = cap * rec + (b->n_events + 1) * (16 + 8) + 16 * 256;
+  unsigned char* m = (unsigned char*)ctx->pool.alloc(bytes);
+  if (!m) return fail(PDR_ENOMEM, "device pool has no room for this batch (admission refused)");
+  Ticket t;
+  t.mem = m;
+  auto carve = [&](uint64_t n) {
+    unsigned char* r = m;
+    m += (n + 255) & ~255ull;
+    return (void*)r;
+  };
+  pdr_outputs o{};
+  o.tracks = (pdr_track*)carve(cap * sizeof(pdr_track));
+  o.towers = (pdr_tower*)carve(cap * sizeof(pdr_tower));
+  o.eflow = (pdr_eflow*)carve(cap * sizeof(pdr_eflow));
+  o.cands = (pdr_cand*)carve(cap * sizeof(pdr_cand));
+  o.iso = (pdr_iso*)carve(cap * sizeof(pdr_iso));
+  o.counts = (uint32_t*)carve((b->n_events + 1) * 16);
+  o.debug = dbg ? (pdr_debug*)carve(cap * sizeof(pdr_debug)) : nullptr;
+  uint64_t* offs = (uint64_t*)carve((b->n_events + 1) * 8);
+  if (b->n_events > 0)
+    PDR_CUDA(cudaMemcpyAsync(offs, b->offsets, (b->n_events + 1) * 8, cudaMemcpyDeviceToDevice, s), "copy offsets");
+  Shape S;
+  uint32_t max_n = 0;
+  if ((rc = resolve_shape(ctx, b, nullptr, s, max_n, S)) || (rc = run_shape(ctx, b, &o, S, max_n, s))) {
+    ctx->pool.release(t.mem);
+    return rc;
+  }
+  if (cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(t.done, s) != cudaSuccess) {
+    ctx->pool.release(t.mem);
+    return fail(PDR_EDEVICE, "cannot record completion event");
+  }
+  t.res.n_events = b->n_events;
+  t.res.n_particles = np;
+  t.res.offsets = offs;
+  t.res.counts = o.counts;
+  t.res.tracks = o.tracks;
+  t.res.towers = o.towers;
+  t.res.eflow = o.eflow;
+  t.res.cands = o.cands;
+  t.res.iso = o.iso;
+  t.res.debug = o.debug;
+  *ticket = ctx->next_ticket++;
+  ctx->tickets[*ticket] = t;
+  return PDR_OK;
+}
+
+int pdr_wait(pdr_ctx* ctx, uint64_t ticket, int timeout_ms) {
+  if (!ctx) return fail(PDR_EINVAL, "null context");
+  cudaEvent_t ev;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
+    ev = it->second.done;
+  }
+  cudaSetDevice(ctx->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "ticket");
+    if (timeout_ms >= 0 &&
+        std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return fail(PDR_ETIMEDOUT, "ticket still running");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  return PDR_OK;
+}
+
+int pdr_fetch(pdr_ctx* ctx, uint64_t ticket, pdr_result* r) {
+  if (!ctx || !r) return fail(PDR_EINVAL, "null argument");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
+  if (cudaEventQuery(it->second.done) != cudaSuccess) return fail(PDR_EBUSY, "ticket not finished");
+  *r = it->second.res;
+  return PDR_OK;
+}
+
+int pdr_release(pdr_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return fail(PDR_EINVAL, "null context");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
+  cudaSetDevice(ctx->device);
+  cudaEventSynchronize(it->second.done);
+  cudaEventDestroy(it->second.done);
+  ctx->pool.release(it->second.mem);
+  ctx->tickets.erase(it);
+  return PDR_OK;
+}
+
+}  // extern "C"
