@@ -73,7 +73,7 @@ class Card(C.Structure):
     ]
 
 
-PARTICLE = np.dtype([("eta_pos", "f8"), ("phi_pos", "f8"), ("e", "f8"), ("key", "u4"),
+PARTICLE = np.dtype([("eta_pos", "f8"), ("phi_pos", "f8"), ("e", "f8"), ("cond", "f8"), ("key", "u4"),
                      ("flags", "u4"), ("cls", "u4"), ("pad", "u4")])
 TRACK = np.dtype([("pt", "f8"), ("eta", "f8"), ("phi", "f8"), ("e", "f8"), ("idx", "u4"),
                   ("pad", "u4")])

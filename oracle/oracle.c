@@ -253,8 +253,10 @@ static int decide(or_dctx* d, uint32_t kind, uint32_t id, uint32_t aux, uint32_t
   return res;
 }
 
-/* Eta-ring lookup with decision report: ring index, or -1 outside coverage. */
-static int ring_decide(or_dctx* d, uint32_t id, int calo, const or_grid* g, double v) {
+/* Eta-ring lookup with decision report: ring index, or -1 outside coverage.
+ * extra: an absolute widening of the marginal band (conditioning of v). */
+static int ring_decide(or_dctx* d, uint32_t id, int calo, const or_grid* g, double v,
+                       double extra) {
   int m = g->nring;
   float vf = (float)v;
   int k = -1;
@@ -269,7 +271,7 @@ static int ring_decide(or_dctx* d, uint32_t id, int calo, const or_grid* g, doub
   }
   int below = jn - 1 >= 0 ? jn - 1 : -1;
   int above = jn < m ? jn : -1;
-  int marginal = isfinite(v) && dn <= d->g * fmax(fabs(v), 1.0) &&
+  int marginal = isfinite(v) && dn <= d->g * fmax(fabs(v), 1.0) + extra &&
                  (ring == below || ring == above);
   int alt = (ring == above) ? below : above;
   if (d->nflips > 0 && find_flip(d, OR_K_ETA, id, (uint32_t)calo, 0)) {
@@ -322,11 +324,12 @@ static int phi_decide(or_dctx* d, uint32_t id, int calo, int nphi, double v) {
 /* ------------------------------------------------------------------------ */
 static int propagate_dec(const oracle_card* c, or_dctx* d, uint32_t id, double pt, double eta,
                          double phi, int q, double vz, int* barrel, double* eta_pos,
-                         double* phi_pos) {
+                         double* phi_pos, double* cond) {
   const double L = c->L, R = c->R, B = c->B;
   *barrel = 0;
   *eta_pos = 0.0;
   *phi_pos = 0.0;
+  *cond = 0.0;
   if (!((float)fabs(vz) <= (float)L)) return 0; /* produced outside the detector */
   double sh = sinh(eta);                          /* pz / pT */
   if (q == 0 || B == 0.0) {
@@ -374,6 +377,10 @@ static int propagate_dec(const oracle_card* c, or_dctx* d, uint32_t id, double p
     double rho = 2.0 * r * fabs(sin(0.5 * psi));
     *eta_pos = asinh(ze / rho);
     pphi = phi - h * 0.5 * psi;
+    /* d eta_pos / d ln psi = -(L/rho)/sqrt(1 + (L/rho)^2) * (psi/2) cot(psi/2):
+     * large when the helix has nearly closed (psi -> 2 pi, rho -> 0). */
+    double lr = fabs(ze) / rho;
+    *cond = lr / sqrt(1.0 + lr * lr) * fabs(0.5 * psi * cos(0.5 * psi) / sin(0.5 * psi));
   }
   if (pphi < -M_PI) pphi += TWO_PI;
   else if (pphi >= M_PI) pphi -= TWO_PI;
@@ -387,7 +394,8 @@ int oracle_propagate(const oracle_card* c, double pt, double eta, double phi, in
   memset(&d, 0, sizeof d);
   d.cap = -1;
   int b = 0;
-  int reach = propagate_dec(c, &d, 0, pt, eta, phi, q, vz, &b, eta_pos, phi_pos);
+  double cond = 0.0;
+  int reach = propagate_dec(c, &d, 0, pt, eta, phi, q, vz, &b, eta_pos, phi_pos, &cond);
   *barrel = b;
   return reach;
 }
@@ -398,7 +406,7 @@ uint32_t oracle_tower_key(const oracle_card* c, int calo, double eta_pos, double
   or_dctx d;
   memset(&d, 0, sizeof d);
   d.cap = -1;
-  int ring = ring_decide(&d, 0, calo, &g, eta_pos);
+  int ring = ring_decide(&d, 0, calo, &g, eta_pos, 0.0);
   if (ring < 0) return OR_NO_KEY;
   int iphi = phi_decide(&d, 0, calo, g.nphi[ring], phi_pos);
   return ((uint32_t)calo << 24) | (uint32_t)(g.base[ring] + iphi);
@@ -485,24 +493,28 @@ static int run_event_impl(const oracle_card* c, const or_grid grid[2], int64_t n
 
     /* S1: propagation */
     int barrel = 0;
-    double ep = 0.0, pp = 0.0;
-    if (!propagate_dec(c, d, i, PT, ETA, PHI, q, VZ, &barrel, &ep, &pp)) continue;
+    double ep = 0.0, pp = 0.0, cond = 0.0;
+    if (!propagate_dec(c, d, i, PT, ETA, PHI, q, VZ, &barrel, &ep, &pp, &cond)) continue;
     P->flags |= OR_F_REACH | (barrel ? OR_F_BARREL : 0u);
     P->eta_pos = ep;
     P->phi_pos = pp;
+    P->cond = cond;
+    /* float32 carries the turning angle to a few units of 2^-24 relative; the
+     * ring decisions on eta_pos are marginal within that error times cond */
+    const double cband = 16.0 * 5.9604644775390625e-8 * cond;
 
     /* S5: which calorimeter tower receives the deposit.  e/gamma go to ECAL,
      * or to HCAL where ECAL does not cover; hadrons to HCAL; mu/nu to none. */
     int calo = -1, ring = -1;
     if (cls == OR_CLS_E || cls == OR_CLS_GAMMA) {
-      ring = ring_decide(d, i, OR_ECAL, &grid[OR_ECAL], ep);
+      ring = ring_decide(d, i, OR_ECAL, &grid[OR_ECAL], ep, cband);
       if (ring >= 0) calo = OR_ECAL;
       else {
-        ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep);
+        ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep, cband);
         if (ring >= 0) calo = OR_HCAL;
       }
     } else if (cls == OR_CLS_CHAD || cls == OR_CLS_NHAD) {
-      ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep);
+      ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep, cband);
       if (ring >= 0) calo = OR_HCAL;
     }
     uint32_t key = OR_NO_KEY;

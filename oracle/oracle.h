@@ -101,6 +101,8 @@ typedef struct {
 typedef struct {
   double eta_pos, phi_pos;   /* position on the calorimeter surface (if reached) */
   double e;                  /* truth energy                                   */
+  double cond;               /* |d eta_pos / d ln(psi)|: conditioning of eta_pos
+                                on the turning angle (endcap helices; else 0)  */
   uint32_t key;              /* tower key deposited into, or OR_NO_KEY          */
   uint32_t flags;            /* OR_F_* bits                                    */
   uint32_t cls;              /* OR_CLS_*                                       */
