@@ -236,6 +236,33 @@ int pdr_max_event_size(pdr_ctx* ctx, const pdr_batch* batch, void* stream, uint3
  * PDR_OK, or PDR_EDEVICE with the reason in pdr_last_error. */
 int pdr_check(pdr_ctx* ctx, void* stream);
 
+/* ------------------------------------------------------- allocation-free run -- */
+/* The paper has no counterpart to this entry point; it exists for callers of
+ * this library that may not allocate device memory when they run the response:
+ * applications that hand out all device memory through their own fixed-budget
+ * allocator and forbid allocations after start-up, or latency-critical paths
+ * that cannot afford an allocation's implicit synchronisation.  The caller
+ * passes HOST card and DEVICE inputs/outputs exactly as for pdr_run (the
+ * batch's card_id is ignored); the library allocates nothing.  Everything else
+ * the kernel needs - the expanded card, an error word, and the global-memory
+ * tower tables for events larger than the shared-memory table - lives in one
+ * static device array of PDR_NOALLOC_SCRATCH_BYTES compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * The first call on a device looks up that array's device address (a one-time
+ * set-up with the device current); make that first call before any stream
+ * capture.  Calls share the array and it keeps the previous call's contents:
+ * each call re-stages the card, clears the error word and re-initialises the
+ * tables it uses, but calls whose work overlaps on the GPU race and must not
+ * be issued.  The call returns after the work on `stream` has finished (it
+ * synchronises the stream) and reports device-side errors directly:
+ * PDR_EDEVICE for malformed CSR offsets, PDR_EOVERFLOW when an event has more
+ * than 49152 particles or its tower tables do not fit in the static array,
+ * PDR_EINVAL / PDR_ECARD for bad arguments or cards.  No context is needed;
+ * messages go to pdr_last_error(NULL). */
+#define PDR_NOALLOC_SCRATCH_BYTES (32ull << 20)
+int pdr_run_noalloc(const pdr_card* card, const pdr_batch* batch, const pdr_outputs* out, void* stream);
+
 /* ------------------------------------------------------- library-owned results -- */
 /* Result view returned by pdr_fetch: DEVICE pointers owned by the library
  * until pdr_release(ticket); layouts as pdr_outputs. */

@@ -144,6 +144,11 @@ struct Ticket {
 
 }  // namespace
 
+namespace pdr {
+// Record a failure message for pdr_last_error from other files of the library.
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace pdr
+
 struct pdr_ctx {
   int device = 0;
   int n_sms = 0;
