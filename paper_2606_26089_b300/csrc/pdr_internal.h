@@ -40,6 +40,10 @@ struct DevCalo {
   float eta_c[PDR_MAXRING];      // ring centre (float32 of the double midpoint)
   float cosh_c[PDR_MAXRING];     // cosh(eta_c) (float32 of the double value)
   int32_t resbin[PDR_MAXRING];   // resolution row of |eta_c|
+  // ring groups: runs of rings with the same phi segmentation, in ring order
+  // (tower id -> ring without a search: ring = first + (id - base) / nphi)
+  int32_t ngroup, pad2[3];
+  int32_t grp_first[2 * PDR_MAXSEG], grp_base[2 * PDR_MAXSEG], grp_nphi[2 * PDR_MAXSEG];
 };
 
 struct DevCard {
@@ -52,25 +56,73 @@ struct DevCard {
   int32_t Bsign, has_field, pad0;
   float cR_hi[PDR_MAXQ + 1], cR_lo[PDR_MAXQ + 1];  // c = 0.299792458 |q| |B| R, split hi + lo
   // tracking efficiency: pass iff (u64) w < T
+  // small piecewise-constant tables: edges padded with +inf to PDR_MAXEDGE,
+  // 16-byte aligned so a lookup is two vector loads
   int32_t trk_npt, trk_neta;
-  float trk_pt_edges[PDR_MAXEDGE], trk_eta_edges[PDR_MAXEDGE];
+  alignas(16) float trk_pt_edges[PDR_MAXEDGE];
+  alignas(16) float trk_eta_edges[PDR_MAXEDGE];
   unsigned long long trk_T[3][PDR_MAXEDGE][PDR_MAXEDGE];
   // resolutions, squared coefficients
   int32_t res_n[4];
-  float res_edges[4][PDR_MAXEDGE];
+  alignas(16) float res_edges[4][PDR_MAXEDGE];
   float res_a2[4][PDR_MAXEDGE], res_b2[4][PDR_MAXEDGE], res_c2[4][PDR_MAXEDGE], res_d2[4][PDR_MAXEDGE];
   // identification efficiency
   int32_t id_n, pad1;
-  float id_edges[PDR_MAXEDGE];
+  alignas(16) float id_edges[PDR_MAXEDGE];
   unsigned long long id_T[3][PDR_MAXEDGE];
   // thresholds and isolation (float32 of the card values; dr2 = float32(dr * dr))
   float e_min[2], s_min[2];
   float cand_ptmin, dr2max, dr2min, iso_ptmin, imax, pad2;
 };
 
+// The part of a card the kernel touches per particle and per tower, laid out
+// compactly so each persistent CTA copies it once into shared memory.  A fixed
+// header (below) is followed by `data_floats` floats: per calorimeter the ring
+// edges (nring + 1), per-ring data (eta_c, cosh(eta_c), resolution row as int
+// bits: 3 floats a ring), and per eta segment its phi table (nphi + 1 edges,
+// then nphi centres).  Tower ids are computed from per-segment bases, so no
+// per-ring table is read to place a deposit.
+struct HotSeg {
+  float lo, hi, scale;      // |eta| range of the segment, n / (hi - lo) (guess only)
+  int32_t n, first;         // rings in the segment; first ring counting from eta = 0
+  int32_t nphi;
+  int32_t base_pos, base_neg;  // tower id of the segment's lowest-index ring on each side
+  int32_t phioff;           // offset (floats) of the phi table in the data part
+  float phi_scale;          // nphi / (2 pi), guess only
+  int32_t pad[2];
+};
+
+struct HotCalo {
+  int32_t nring, m, nseg, edge_off;  // m = nring / 2; edge_off: offset of the ring edges
+  int32_t ring_off, pad[3];          // offset of the per-ring data (3 floats a ring)
+  HotSeg seg[PDR_MAXSEG];
+};
+
+struct alignas(16) HotCard {
+  HotCalo calo[2];
+  float R, L, kB;
+  int32_t Bsign, has_field, trk_npt, trk_neta, id_n;
+  int32_t res_n[4];
+  alignas(16) float trk_pt_edges[PDR_MAXEDGE];
+  alignas(16) float trk_eta_edges[PDR_MAXEDGE];
+  alignas(16) float id_edges[PDR_MAXEDGE];
+  alignas(16) float res_edges[4][PDR_MAXEDGE];
+  float res_a2[4][PDR_MAXEDGE], res_b2[4][PDR_MAXEDGE], res_c2[4][PDR_MAXEDGE], res_d2[4][PDR_MAXEDGE];
+  float cR_hi[PDR_MAXQ + 1], cR_lo[PDR_MAXQ + 1];
+  unsigned long long trk_T[3][PDR_MAXEDGE][PDR_MAXEDGE];
+  unsigned long long id_T[3][PDR_MAXEDGE];
+  float e_min[2], s_min[2];
+  float cand_ptmin, dr2max, dr2min, iso_ptmin, imax;
+  int32_t data_floats;
+};
+
+#define PDR_HOT_MAX_BYTES (40u * 1024u)   // shared-memory card cache limit
+
 // Kernel parameter block (passed by value).
 struct KParams {
   const DevCard* card;
+  const unsigned char* hot;          // HotCard + data, hot_bytes long (multiple of 16)
+  uint32_t hot_bytes, pad_hot;
   uint64_t n_events;
   const uint64_t* offsets;
   const float *pt, *eta, *phi, *mass, *vz;
@@ -99,19 +151,24 @@ enum : uint32_t {
   ERR_TABLE = 4u,      // tower table full (cannot happen when sized as documented)
 };
 
-// Shared-memory bytes needed by one team of a launch shape.
+// Bytes of a team's tower table: keys, owner, esum, etrk per slot and one
+// info word per particle (16-byte multiple).
+PDR_HD inline uint64_t table_bytes(uint32_t slots, uint32_t nmax) {
+  const uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * 4;
+  return (b + 15) & ~15ull;
+}
+
+// Shared-memory bytes needed by one team of a launch shape (the card cache is
+// counted separately, once per CTA).
 PDR_HD inline uint64_t team_smem_bytes(uint32_t team, uint32_t slots, uint32_t nmax) {
-  uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8);  // keys, owner, esum, etrk
-  b += (uint64_t)nmax * 4;                          // per-particle slot | ring
-  b = (b + 15) & ~15ull;
-  b += 2 * 32 * 4;                                  // scan buffers
+  uint64_t b = table_bytes(slots, nmax);
+  b += 2 * 32 * 4;                                  // scan buffers (double-buffered)
   b += PDR_CMAX * (16 + 4 + 4 + 8);                 // isolation candidates (eta, phi, pt, idx; key; pad) and sums
   return (b + 15) & ~15ull;
 }
 
 PDR_HD inline uint64_t global_team_bytes(uint32_t slots, uint32_t nmax) {
-  uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * 4;
-  return (b + 255) & ~255ull;
+  return (table_bytes(slots, nmax) + 255) & ~255ull;
 }
 
 }  // namespace pdr

@@ -13,16 +13,20 @@
 //   phase 2, per tower (each tower is processed by its lowest-index
 //     depositing particle, so towers come out in a deterministic order):
 //     S6 tower smearing and thresholds, S7 energy-flow subtraction.
-//   phase 3, per candidate: S8 cone isolation over the event's energy-flow
-//     tracks and neutrals.
+//   phase 3, per event with candidates: S8 cone isolation over the event's
+//     energy-flow tracks and neutrals.
 //   S9: per-event counts.
 //
-// Tower sums are exact 64-bit fixed-point integer sums (quantum 2^-36 GeV)
-// accumulated with shared-memory integer atomics: integer addition is
-// associative, so the sums are bitwise deterministic without any float atomics
-// and independent of the launch shape.  Random numbers are counter-based
-// (Philox4x32-10 keyed by seed, counter (slot, event, purpose, 0)), so every
-// draw is reproducible and independent of scheduling.
+// Each CTA first copies the card's hot tables (ring edges, per-segment tower
+// bases and phi tables, per-ring centres, efficiency and resolution tables,
+// about 13 KB for the CMS-like card) into shared memory: placing a deposit
+// then needs no global-memory lookups.  Tower sums are exact 64-bit
+// fixed-point integer sums (quantum 2^-36 GeV): the first depositor of a tower
+// stores its value, later ones add with shared-memory integer atomics, so the
+// sums are bitwise deterministic without float atomics and independent of the
+// launch shape.  Random numbers are counter-based (Philox4x32-10 keyed by seed,
+// counter (slot, event, purpose, 0)), so every draw is reproducible and
+// independent of scheduling.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,20 +83,32 @@ __device__ __forceinline__ float rel2_of(float a2, float b2, float c2, float d2,
 }
 
 // Largest k < n with edges[k] <= x (-1 if none): piecewise-constant tables.
+// The card pads each table to PDR_MAXEDGE edges with +inf, so for sorted edges
+// the count of edges <= x is that index plus one (two vector loads).
 __device__ __forceinline__ int small_lookup(const float* edges, int n, float x) {
-  int k = -1;
-#pragma unroll
-  for (int j = 0; j < PDR_MAXEDGE; ++j)
-    if (j < n && edges[j] <= x) k = j;
-  return k;
+  const float4 a = *reinterpret_cast<const float4*>(edges);
+  const float4 b = *reinterpret_cast<const float4*>(edges + 4);
+  const int c = (int)(a.x <= x) + (int)(a.y <= x) + (int)(a.z <= x) + (int)(a.w <= x) +
+                (int)(b.x <= x) + (int)(b.y <= x) + (int)(b.z <= x) + (int)(b.w <= x);
+  return min(c, n) - 1;
 }
 
+// Fixed-point energy (quantum 2^-36 GeV) with 32-bit conversions only: the
+// integer part of 16 v in the high word, the remaining fraction times 2^32 in
+// the low word (the split is exact; only the low word is rounded).
 __device__ __forceinline__ unsigned long long to_fp(float v) {
-  return (unsigned long long)__float2ll_rn(v * PDR_FP_SCALE);
+  const float x = v * 16.0f;
+  const float hi = truncf(x);
+  const float frac = x - hi;
+  const uint32_t h = __float2uint_rz(hi);
+  const uint32_t l = __float2uint_rn(frac * 4294967296.0f);
+  return ((unsigned long long)h << 32) | l;
 }
 
 __device__ __forceinline__ float from_fp(unsigned long long v) {
-  return __ull2float_rn(v) * PDR_FP_INV;
+  const float hi = __uint2float_rn((uint32_t)(v >> 32));
+  const float lo = __uint2float_rn((uint32_t)v);
+  return fmaf(hi, 4294967296.0f, lo) * PDR_FP_INV;
 }
 
 __device__ __forceinline__ int classify(int32_t pdg, int q) {
@@ -114,7 +130,7 @@ struct Prop {
 // cylinder R, +-L.  Helix radius r = pT / (0.299792458 |q| |B|); the barrel is
 // reached iff 2 pT >= c = 0.299792458 |q| |B| R, at turning angle
 // 2 asin(c / 2pT); otherwise the endcap after psi = s_z / r < 2 pi.
-__device__ __forceinline__ Prop propagate(const DevCard& K, float pt, float eta, float phi,
+__device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta, float phi,
                                           int q, float vz) {
   Prop P;
   P.reach = 0; P.barrel = 0; P.eta_pos = 0.0f; P.phi_pos = 0.0f;
@@ -183,30 +199,70 @@ __device__ __forceinline__ Prop propagate(const DevCard& K, float pt, float eta,
   return P;
 }
 
-// Ring containing v: largest r with edge[r] <= v, or -1 outside coverage.
-__device__ __forceinline__ int ring_of(const DevCalo& C, float v) {
-  const int nr = C.nring;
-  if (!(v >= C.edge[0]) || !(v < C.edge[nr])) return -1;
-  const float av = fabsf(v);
-  int s = 0;
-  while (s < C.nseg - 1 && av >= C.seg_hi[s]) ++s;
-  int j = (int)((av - C.seg_lo[s]) * C.seg_scale[s]);
-  j = min(max(j, 0), C.seg_n[s] - 1) + C.seg_first[s];
-  const int m = nr >> 1;
-  int r = v >= 0.0f ? m + j : m - 1 - j;
-  r = min(max(r, 0), nr - 1);
-  while (r > 0 && v < C.edge[r]) --r;
-  while (r < nr - 1 && v >= C.edge[r + 1]) ++r;
-  return r;
-}
-
-// Phi bin of v in a ring: largest k with edge[k] <= v, clamped to [0, nphi - 1].
+// Phi bin of v: largest k with edge[k] <= v, clamped to [0, nphi - 1].
 __device__ __forceinline__ int phi_bin(const float* pe, int nphi, float scale, float v) {
   int k = (int)((v + PI_F) * scale);
   k = min(max(k, 0), nphi - 1);
   while (k > 0 && v < pe[k]) --k;
   while (k < nphi - 1 && v >= pe[k + 1]) ++k;
   return k;
+}
+
+// S5 tower of a surface position in one calorimeter, from the shared-memory
+// card: ring = largest r with edge[r] <= eta (guessed from the segment's
+// uniform binning, then checked against the float32 edges), phi bin likewise,
+// tower id from the segment's base.  Returns false outside coverage.
+__device__ __forceinline__ bool tower_of(const HotCard& K, const float* KD, int calo, float v, float phi,
+                                         uint32_t& id, int& ring) {
+  const HotCalo& C = K.calo[calo];
+  const float* edge = KD + C.edge_off;
+  const int nr = C.nring;
+  if (!(v >= edge[0]) || !(v < edge[nr])) return false;
+  const float av = fabsf(v);
+  int s = 0;
+  while (s < C.nseg - 1 && av >= C.seg[s].hi) ++s;
+  int j = (int)((av - C.seg[s].lo) * C.seg[s].scale);
+  j = min(max(j, 0), C.seg[s].n - 1) + C.seg[s].first;
+  const int m = C.m;
+  int r = v >= 0.0f ? m + j : m - 1 - j;
+  r = min(max(r, 0), nr - 1);
+  while (r > 0 && v < edge[r]) --r;
+  while (r < nr - 1 && v >= edge[r + 1]) ++r;
+  const int jj = r >= m ? r - m : m - 1 - r;
+  s = 0;
+  while (s < C.nseg - 1 && jj >= C.seg[s].first + C.seg[s].n) ++s;
+  const HotSeg& S = C.seg[s];
+  const int k = phi_bin(KD + S.phioff, S.nphi, S.phi_scale, phi);
+  const int base = r >= m ? S.base_pos + (jj - S.first) * S.nphi
+                          : S.base_neg + (r - (m - S.first - S.n)) * S.nphi;
+  id = (uint32_t)(base + k);
+  ring = r;
+  return true;
+}
+
+// Ring, eta_c and phi_c of a tower id.
+__device__ __forceinline__ void tower_decode(const HotCard& K, const float* KD, int calo, uint32_t id,
+                                             int& ring, float& eta_c, float& phi_c) {
+  const HotCalo& C = K.calo[calo];
+  const int m = C.m;
+  int r = 0, k = 0;
+  for (int s = 0; s < C.nseg; ++s) {
+    const HotSeg& S = C.seg[s];
+    const uint32_t span = (uint32_t)(S.n * S.nphi);
+    if (id - (uint32_t)S.base_neg < span) {
+      const uint32_t rel = id - (uint32_t)S.base_neg;
+      r = (m - S.first - S.n) + (int)(rel / (uint32_t)S.nphi);
+      k = (int)(rel % (uint32_t)S.nphi);
+      phi_c = KD[S.phioff + S.nphi + 1 + k];
+    } else if (id - (uint32_t)S.base_pos < span) {
+      const uint32_t rel = id - (uint32_t)S.base_pos;
+      r = m + S.first + (int)(rel / (uint32_t)S.nphi);
+      k = (int)(rel % (uint32_t)S.nphi);
+      phi_c = KD[S.phioff + S.nphi + 1 + k];
+    }
+  }
+  ring = r;
+  eta_c = KD[C.ring_off + 3 * r];
 }
 
 // ------------------------------------------------------------------ teams
@@ -220,6 +276,7 @@ struct TeamCtx {
 };
 
 // Exclusive team prefix of two flags packed as (a | b << 16); total via ref.
+// Includes a team barrier (a warp barrier for one-warp teams).
 template <int TEAM>
 __device__ __forceinline__ uint32_t team_scan2(bool fa, bool fb, uint32_t* wbuf, uint32_t& total,
                                                const TeamCtx<TEAM>& t) {
@@ -229,6 +286,7 @@ __device__ __forceinline__ uint32_t team_scan2(bool fa, bool fb, uint32_t* wbuf,
   const uint32_t lane_pre = __popc(ma & lt) | ((uint32_t)__popc(mb & lt) << 16);
   const uint32_t wtot = __popc(ma) | ((uint32_t)__popc(mb) << 16);
   if (TEAM == 32) {
+    __syncwarp();  // orders the lanes' shared-memory writes before what follows
     total = wtot;
     return lane_pre;
   }
@@ -247,46 +305,6 @@ __device__ __forceinline__ uint32_t team_scan2(bool fa, bool fb, uint32_t* wbuf,
   return incl_w - wtot + lane_pre;
 }
 
-// ------------------------------------------------------------ tower table
-struct Tbl {
-  uint32_t* keys;
-  uint32_t* owner;
-  unsigned long long* esum;
-  unsigned long long* etrk;
-  uint32_t* pinfo;
-  uint32_t mask, shift;
-};
-
-__device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t log2) {
-  Tbl t;
-  t.keys = (uint32_t*)base;
-  t.owner = t.keys + slots;
-  t.esum = (unsigned long long*)(t.owner + slots);
-  t.etrk = t.esum + slots;
-  t.pinfo = (uint32_t*)(t.etrk + slots);
-  t.mask = slots - 1;
-  t.shift = 32 - log2;
-  return t;
-}
-
-// Insert key; the thread that claims a slot initialises it.  Returns the slot.
-__device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uint32_t* err) {
-  uint32_t h = (key * 0x9E3779B1u) >> T.shift;
-  for (uint32_t probe = 0; probe <= T.mask; ++probe) {
-    const uint32_t prev = atomicCAS(&T.keys[h], PDR_EMPTY, key);
-    if (prev == PDR_EMPTY) {
-      T.owner[h] = PDR_EMPTY;
-      T.esum[h] = 0ull;
-      T.etrk[h] = 0ull;
-      return h;
-    }
-    if (prev == key) return h;
-    h = (h + 1) & T.mask;
-  }
-  atomicOr(err, ERR_TABLE);
-  return PDR_EMPTY;
-}
-
 // ------------------------------------------------------- per-particle stage
 struct PartOut {
   uint32_t key, ring, flags;
@@ -295,8 +313,8 @@ struct PartOut {
   bool tracked, cand;
 };
 
-__device__ __forceinline__ void particle_stage(const KParams& p, const DevCard& K, uint64_t g,
-                                               uint32_t i, uint32_t event, PartOut& o) {
+__device__ __forceinline__ void particle_stage(const KParams& p, const HotCard& K, const float* KD,
+                                               uint64_t g, uint32_t i, uint32_t event, PartOut& o) {
   const float PT = __ldg(p.pt + g), ETA = __ldg(p.eta + g), PHI = __ldg(p.phi + g);
   const float M = __ldg(p.mass + g);
   const int32_t PDG = __ldg(p.pdg + g);
@@ -318,22 +336,14 @@ __device__ __forceinline__ void particle_stage(const KParams& p, const DevCard& 
   o.phi_pos = P.phi_pos;
   // S5 tower placement: e/gamma to ECAL (or HCAL beyond ECAL), hadrons to HCAL
   int calo = -1, ring = -1;
-  if (cls == CLS_E || cls == CLS_GAMMA) {
-    ring = ring_of(K.calo[0], P.eta_pos);
-    if (ring >= 0) calo = 0;
-    else {
-      ring = ring_of(K.calo[1], P.eta_pos);
-      if (ring >= 0) calo = 1;
-    }
-  } else if (cls == CLS_CHAD || cls == CLS_NHAD) {
-    ring = ring_of(K.calo[1], P.eta_pos);
-    if (ring >= 0) calo = 1;
+  uint32_t id = 0;
+  const bool em = cls == CLS_E || cls == CLS_GAMMA;
+  if (em || cls == CLS_CHAD || cls == CLS_NHAD) {
+    if (em && tower_of(K, KD, 0, P.eta_pos, P.phi_pos, id, ring)) calo = 0;
+    else if (tower_of(K, KD, 1, P.eta_pos, P.phi_pos, id, ring)) calo = 1;
   }
   if (calo >= 0) {
-    const DevCalo& C = K.calo[calo];
-    const int nphi = C.nphi[ring];
-    const int k = phi_bin(K.phi_pool + C.phioff[ring], nphi, C.phi_scale[ring], P.phi_pos);
-    o.key = ((uint32_t)calo << 24) | (uint32_t)(C.base[ring] + k);
+    o.key = ((uint32_t)calo << 24) | id;
     o.ring = (uint32_t)ring;
     o.flags |= calo == 0 ? PDR_F_ECAL : PDR_F_HCAL;
   }
@@ -368,17 +378,13 @@ __device__ __forceinline__ void particle_stage(const KParams& p, const DevCard& 
     const uint4 w = philox(i, event, 2u, 0u, p.seed_lo, p.seed_hi);
     if ((unsigned long long)w.x < T) {
       const float z = normal(w.y, w.z);
-      if (cc != 1) {
-        const int rb = max(small_lookup(K.res_edges[RES_ECAL], K.res_n[RES_ECAL], aeta), 0);
-        const float r2 = rel2_of(K.res_a2[RES_ECAL][rb], K.res_b2[RES_ECAL][rb],
-                                 K.res_c2[RES_ECAL][rb], K.res_d2[RES_ECAL][rb], o.E);
-        o.cpt = lognormal(o.E, r2, z) / ch;
-      } else {
-        const int rb = max(small_lookup(K.res_edges[RES_MUON], K.res_n[RES_MUON], aeta), 0);
-        const float r2 = rel2_of(K.res_a2[RES_MUON][rb], K.res_b2[RES_MUON][rb],
-                                 K.res_c2[RES_MUON][rb], K.res_d2[RES_MUON][rb], PT);
-        o.cpt = lognormal(PT, r2, z);
-      }
+      const int comp = cc != 1 ? RES_ECAL : RES_MUON;
+      const float x = cc != 1 ? o.E : PT;
+      const int rb = max(small_lookup(K.res_edges[comp], K.res_n[comp], aeta), 0);
+      const float r2 = rel2_of(K.res_a2[comp][rb], K.res_b2[comp][rb], K.res_c2[comp][rb],
+                               K.res_d2[comp][rb], x);
+      const float sm = lognormal(x, r2, z);
+      o.cpt = cc != 1 ? sm / ch : sm;
       o.cand = true;
       o.cc = cc;
       o.flags |= PDR_F_CAND;
@@ -388,21 +394,76 @@ __device__ __forceinline__ void particle_stage(const KParams& p, const DevCard& 
   if (o.key == PDR_NO_KEY) o.etrk = 0.0f;
 }
 
+// ------------------------------------------------------------ tower table
+// Per-team open-addressing table (linear probing, multiplicative hash) keyed
+// by tower key, plus one info word per particle (slot | ring << 16, or empty).
+// Between events every key is empty; the other slot fields are initialised by
+// the thread that claims the slot.
+struct Tbl {
+  uint32_t* keys;
+  uint32_t* owner;
+  unsigned long long* esum;
+  unsigned long long* etrk;
+  uint32_t* pinfo;
+  uint32_t mask, shift;
+};
+
+__device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t log2) {
+  Tbl t;
+  t.keys = (uint32_t*)base;
+  t.owner = t.keys + slots;
+  t.esum = (unsigned long long*)(t.owner + slots);
+  t.etrk = t.esum + slots;
+  t.pinfo = (uint32_t*)(t.etrk + slots);
+  t.mask = slots - 1;
+  t.shift = 32 - log2;
+  return t;
+}
+
+// Find or claim the slot of key.  The thread that claims an empty slot writes
+// its own deposit, track energy and index with plain stores (before the team
+// barrier that precedes any accumulation); every other depositor adds with
+// atomics after that barrier.  Returns the slot; *claimed tells which case.
+__device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uint32_t i,
+                                                 unsigned long long e_fp, unsigned long long t_fp,
+                                                 bool* claimed, uint32_t* err) {
+  uint32_t h = (key * 0x9E3779B1u) >> T.shift;
+  *claimed = false;
+  for (uint32_t probe = 0; probe <= T.mask; ++probe) {
+    const uint32_t cur = T.keys[h];
+    if (cur == key) return h;
+    if (cur == PDR_EMPTY) {
+      const uint32_t prev = atomicCAS(&T.keys[h], PDR_EMPTY, key);
+      if (prev == PDR_EMPTY) {
+        T.owner[h] = i;
+        T.esum[h] = e_fp;
+        T.etrk[h] = t_fp;
+        *claimed = true;
+        return h;
+      }
+      if (prev == key) return h;
+    }
+    h = (h + 1) & T.mask;
+  }
+  atomicOr(err, ERR_TABLE);
+  return PDR_EMPTY;
+}
+
 // ---------------------------------------------------------- per-tower stage
 struct TowerOut {
   float e, et, de, det;
   bool kept, ef;
 };
 
-__device__ __forceinline__ void tower_stage(const DevCard& K, uint32_t key, uint32_t ring,
-                                            unsigned long long es, unsigned long long et,
-                                            uint32_t event, uint32_t s0, uint32_t s1,
-                                            TowerOut& o) {
+__device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, uint32_t key,
+                                            uint32_t ring, unsigned long long es, unsigned long long et,
+                                            uint32_t event, uint32_t s0, uint32_t s1, TowerOut& o) {
   const int calo = (int)(key >> 24);
   const uint32_t id = key & 0xFFFFFFu;
-  const DevCalo& C = K.calo[calo];
+  const float* rd = KD + K.calo[calo].ring_off + 3 * ring;
+  const float chc = rd[1];
+  const int rb = __float_as_int(rd[2]);
   const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
-  const int rb = C.resbin[ring];
   const float a2 = K.res_a2[comp][rb], b2 = K.res_b2[comp][rb];
   const float c2 = K.res_c2[comp][rb], d2 = K.res_d2[comp][rb];
   const float Es = from_fp(es);
@@ -413,7 +474,6 @@ __device__ __forceinline__ void tower_stage(const DevCard& K, uint32_t key, uint
   const float sig = E1 * sqrtf(rel2_of(a2, b2, c2, d2, E1));
   const float emin = K.e_min[calo], smin = K.s_min[calo];
   o.kept = (E1 > emin) & (E1 / sig > smin);
-  const float chc = C.cosh_c[ring];
   o.e = E1;
   o.et = E1 / chc;
   const float dE = E1 - Et;
@@ -422,57 +482,53 @@ __device__ __forceinline__ void tower_stage(const DevCard& K, uint32_t key, uint
   o.det = dE / chc;
 }
 
-// Ring of a tower id (largest r with base[r] <= id).
-__device__ __forceinline__ int ring_of_id(const DevCalo& C, uint32_t id) {
-  int lo = 0, hi = C.nring - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((uint32_t)C.base[mid] <= id) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // ------------------------------------------------------------- one event
 template <int TEAM>
-__device__ __forceinline__ void process_event(const KParams& p, const DevCard& K, const Tbl& T,
-                                              uint32_t* wbuf, float4* cf, uint32_t* ckey,
+__device__ __forceinline__ void process_event(const KParams& p, const HotCard& K, const float* KD,
+                                              const Tbl& T, uint32_t* wbuf, float4* cf, uint32_t* ckey,
                                               unsigned long long* csum, const TeamCtx<TEAM>& tc,
                                               uint64_t e, uint64_t a, uint32_t n) {
   const uint32_t event = p.event_base + (uint32_t)e;
   const bool dbg = p.debug != nullptr;
   uint32_t n_trk = 0, n_cand = 0, flip = 0;
 
-  // ---- phase 1: particles
+  // ---- phase 1: particles (S0-S5); tracks and candidates in particle order
   for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
     const uint32_t i = c0 + (uint32_t)tc.tid;
     const bool valid = i < n;
     PartOut o;
-    o.tracked = false; o.cand = false; o.key = PDR_NO_KEY;
-    if (valid) particle_stage(p, K, a + i, i, event, o);
+    o.tracked = false; o.cand = false; o.key = PDR_NO_KEY; o.E = 0.0f; o.etrk = 0.0f;
+    if (valid) particle_stage(p, K, KD, a + i, i, event, o);
     uint32_t slot = PDR_EMPTY;
-    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, p.err);
+    bool claimed = false;
+    const unsigned long long e_fp = to_fp(o.E);
+    const unsigned long long t_fp = o.etrk > 0.0f ? to_fp(o.etrk) : 0ull;
+    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, t_fp, &claimed, p.err);
     if (valid) T.pinfo[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(o.tracked, o.cand, wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
-    if (slot != PDR_EMPTY) {
-      atomicAdd(&T.esum[slot], to_fp(o.E));
-      if (o.etrk > 0.0f) atomicAdd(&T.etrk[slot], to_fp(o.etrk));
+    if (slot != PDR_EMPTY && !claimed) {
+      atomicAdd(&T.esum[slot], e_fp);
+      if (t_fp) atomicAdd(&T.etrk[slot], t_fp);
       atomicMin(&T.owner[slot], i);
     }
-    if (o.tracked) {
-      const uint64_t j = a + n_trk + (pre & 0xFFFFu);
-      reinterpret_cast<float4*>(p.tracks)[j] =
-          make_float4(o.ptp, __ldg(p.eta + a + i), __ldg(p.phi + a + i), __uint_as_float(i));
-    }
-    if (o.cand) {
-      const uint64_t j = a + n_cand + (pre >> 16);
-      reinterpret_cast<float4*>(p.cands)[j] =
-          make_float4(o.cpt, __ldg(p.eta + a + i), __ldg(p.phi + a + i),
-                      __uint_as_float(i | ((uint32_t)o.cc << 28)));
-      // the candidate's own tower key, read back by the isolation phase
-      reinterpret_cast<float2*>(p.iso)[j] = make_float2(__uint_as_float(o.key), 0.0f);
+    if (o.tracked || o.cand) {
+      const float eta = __ldg(p.eta + a + i), phi = __ldg(p.phi + a + i);
+      if (o.tracked)
+        reinterpret_cast<float4*>(p.tracks)[a + n_trk + (pre & 0xFFFFu)] =
+            make_float4(o.ptp, eta, phi, __uint_as_float(i));
+      if (o.cand) {
+        const uint32_t j = n_cand + (pre >> 16);
+        reinterpret_cast<float4*>(p.cands)[a + j] =
+            make_float4(o.cpt, eta, phi, __uint_as_float(i | ((uint32_t)o.cc << 28)));
+        // own tower key, read back by the isolation of candidates beyond the staged ones
+        reinterpret_cast<float2*>(p.iso)[a + j] = make_float2(__uint_as_float(o.key), 0.0f);
+        if (j < PDR_CMAX) {  // staged for the isolation phase
+          cf[j] = make_float4(eta, phi, o.cpt, __uint_as_float(i));
+          ckey[j] = o.key;
+        }
+      }
     }
     if (dbg && valid)
       reinterpret_cast<float4*>(p.debug)[a + i] =
@@ -482,7 +538,7 @@ __device__ __forceinline__ void process_event(const KParams& p, const DevCard& K
   }
   tc.sync();
 
-  // ---- phase 2: towers, each by its lowest-index depositing particle
+  // ---- phase 2: towers (S6, S7), each by its lowest-index depositing particle
   uint32_t n_twr = 0, n_ef = 0;
   for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
     const uint32_t i = c0 + (uint32_t)tc.tid;
@@ -495,7 +551,7 @@ __device__ __forceinline__ void process_event(const KParams& p, const DevCard& K
         const uint32_t slot = pi & 0xFFFFu;
         if (T.owner[slot] == i) {
           key = T.keys[slot];
-          tower_stage(K, key, pi >> 16, T.esum[slot], T.etrk[slot], event, p.seed_lo, p.seed_hi, to);
+          tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, p.seed_lo, p.seed_hi, to);
           T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
         }
       }
@@ -515,20 +571,20 @@ __device__ __forceinline__ void process_event(const KParams& p, const DevCard& K
     n_ef += tot >> 16;
   }
 
-  // ---- phase 3: isolation of the event's candidates
+  // ---- phase 3: isolation (S8): every EFlow object above the pT floor adds
+  // its fixed-point pT to each candidate cone holding it
   if (n_cand > 0) {
-    tc.sync();
     const uint32_t n_obj = n_trk + n_ef;
     for (uint32_t g0 = 0; g0 < n_cand; g0 += PDR_CMAX) {
       const uint32_t gn = min((uint32_t)PDR_CMAX, n_cand - g0);
-      if ((uint32_t)tc.tid < gn) {
+      tc.sync();
+      if (g0 > 0 && (uint32_t)tc.tid < gn) {  // candidates beyond the staged ones
         const uint64_t j = a + g0 + tc.tid;
         const float4 c = reinterpret_cast<const float4*>(p.cands)[j];
         cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
         ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(p.iso)[j].x);
-        csum[tc.tid] = 0ull;
       }
-      tc.sync();
+      if (g0 > 0) tc.sync();
       for (uint32_t j = tc.tid; j < n_obj; j += TEAM) {
         float oe, op, opt;
         uint32_t oid;
@@ -538,12 +594,8 @@ __device__ __forceinline__ void process_event(const KParams& p, const DevCard& K
           opt = t.x; oe = t.y; op = t.z; oid = __float_as_uint(t.w); is_trk = true;
         } else {
           const pdr_eflow f = p.eflow[a + (j - n_trk)];
-          const int calo = (int)(f.key >> 24);
-          const DevCalo& C = K.calo[calo];
-          const uint32_t id = f.key & 0xFFFFFFu;
-          const int r = ring_of_id(C, id);
-          oe = C.eta_c[r];
-          op = K.phi_pool[C.phioff[r] + C.nphi[r] + 1 + (id - (uint32_t)C.base[r])];
+          int r;
+          tower_decode(K, KD, (int)(f.key >> 24), f.key & 0xFFFFFFu, r, oe, op);
           opt = f.et; oid = f.key; is_trk = false;
         }
         if (!(opt > K.iso_ptmin)) continue;
@@ -563,40 +615,45 @@ __device__ __forceinline__ void process_event(const KParams& p, const DevCard& K
       if ((uint32_t)tc.tid < gn) {
         const uint64_t j = a + g0 + tc.tid;
         const float s = from_fp(csum[tc.tid]);
+        csum[tc.tid] = 0ull;  // clean for the next group / event
         const float rel = s / cf[tc.tid].z;
         reinterpret_cast<float2*>(p.iso)[j] = make_float2(s, rel);
-        if (rel < K.imax) {
-          uint32_t* info = reinterpret_cast<uint32_t*>(p.cands + j) + 3;
-          *info |= 0x80000000u;
-        }
+        if (rel < K.imax) reinterpret_cast<uint32_t*>(p.cands + j)[3] |= 0x80000000u;
       }
-      tc.sync();
     }
   }
+  // the next event reuses the table, the staged candidates and the scan buffers
   tc.sync();
   if (tc.tid == 0)
     reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
 }
 
 // ------------------------------------------------------------------ kernel
+// Shared memory: the card cache (hot_bytes), then per team its tower table,
+// particle records, scan buffers and isolation candidates.  Register cap: at most 64
+// registers a thread (1024 / BLOCK resident CTAs).
 template <int TEAM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) fused_kernel(const KParams p) {
+__global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1) fused_kernel(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NT = BLOCK / TEAM;
+  for (uint32_t k = threadIdx.x; k < p.hot_bytes / 16; k += BLOCK)
+    reinterpret_cast<uint4*>(smem)[k] = __ldg(reinterpret_cast<const uint4*>(p.hot) + k);
+  const HotCard& K = *reinterpret_cast<const HotCard*>(smem);
+  const float* KD = reinterpret_cast<const float*>(smem + sizeof(HotCard));
   TeamCtx<TEAM> tc;
   tc.tix = (int)threadIdx.x / TEAM;
   tc.tid = (int)threadIdx.x % TEAM;
   const uint64_t tbytes = team_smem_bytes(TEAM, p.table_slots, p.nmax_smem);
-  unsigned char* mine = smem + (uint64_t)tc.tix * tbytes;
+  unsigned char* mine = smem + p.hot_bytes + (uint64_t)tc.tix * tbytes;
   const Tbl st = carve(mine, p.table_slots, p.log2_slots);
-  unsigned char* tail = mine + ((((uint64_t)p.table_slots * 24 + (uint64_t)p.nmax_smem * 4) + 15) & ~15ull);
+  unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
   uint32_t* wbuf = (uint32_t*)tail;
   float4* cf = (float4*)(tail + 2 * 32 * 4);
   uint32_t* ckey = (uint32_t*)(cf + PDR_CMAX);
   unsigned long long* csum = (unsigned long long*)(ckey + 2 * PDR_CMAX);
   for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys[s] = PDR_EMPTY;
-  tc.sync();
-  const DevCard& K = *p.card;
+  if ((uint32_t)tc.tid < PDR_CMAX) csum[tc.tid] = 0ull;
+  __syncthreads();
   const uint64_t gteam = (uint64_t)blockIdx.x * NT + tc.tix;
   const uint64_t nteams = (uint64_t)gridDim.x * NT;
   for (uint64_t e = gteam; e < p.n_events; e += nteams) {
@@ -609,13 +666,17 @@ __global__ void __launch_bounds__(BLOCK) fused_kernel(const KParams p) {
       continue;
     }
     const uint32_t n = (uint32_t)(b - a);
+    if (n == 0) {  // nothing to do (and no team synchronisation for an empty event)
+      if (tc.tid == 0) reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(0, 0, 0, 0);
+      continue;
+    }
     if (n <= p.nmax_smem) {
-      process_event<TEAM>(p, K, st, wbuf, cf, ckey, csum, tc, e, a, n);
+      process_event<TEAM>(p, K, KD, st, wbuf, cf, ckey, csum, tc, e, a, n);
     } else if (p.gscratch != nullptr && n <= p.g_nmax) {
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_log2);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys[s] = PDR_EMPTY;
       tc.sync();
-      process_event<TEAM>(p, K, gt, wbuf, cf, ckey, csum, tc, e, a, n);
+      process_event<TEAM>(p, K, KD, gt, wbuf, cf, ckey, csum, tc, e, a, n);
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);

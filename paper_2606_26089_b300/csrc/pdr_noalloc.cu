@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "pdr.h"
+#include "pdr_hot.h"
 #include "pdr_internal.h"
 
 namespace pdr {
@@ -42,11 +43,13 @@ using namespace pdr;
 
 namespace {
 
-// Layout of the static array: [error word, max-event word | card | tower tables].
+// Layout of the static array: [error word, max-event word | card | card cache
+// image | tower tables].
 constexpr uint64_t kHeaderBytes = 256;
 constexpr uint64_t kCardOffset = kHeaderBytes;
 constexpr uint64_t kCardBytes = (sizeof(DevCard) + 255) & ~255ull;
-constexpr uint64_t kTableOffset = kCardOffset + kCardBytes;
+constexpr uint64_t kHotOffset = kCardOffset + kCardBytes;
+constexpr uint64_t kTableOffset = kHotOffset + PDR_HOT_MAX_BYTES;
 static_assert(kTableOffset < PDR_NOALLOC_SCRATCH_BYTES, "scratch too small for the card");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PDR_NOALLOC_SCRATCH_BYTES];
@@ -61,6 +64,7 @@ constexpr int kMaxDevices = 64;
 DeviceSlot g_slots[kMaxDevices];
 std::mutex g_mu;
 DevCard g_host_card;  // host staging of the expanded card (static storage, no heap)
+unsigned char g_host_hot[PDR_HOT_MAX_BYTES];  // host staging of the card cache image
 
 int err(int code, const char* msg) { return set_last_error(code, msg); }
 
@@ -161,6 +165,17 @@ int expand_calo_fixed(const pdr_card* c, int calo, DevCalo& D, float* pool, int&
     D.cosh_c[r] = (float)std::cosh(ec);
   }
   D.ntowers = base;
+  // ring groups in ring order: negative-side segments outermost first, then
+  // positive-side segments innermost first
+  D.ngroup = 2 * nseg;
+  for (int s = 0; s < nseg; ++s) {
+    const int gn = nseg - 1 - s, gp = nseg + s;
+    D.grp_first[gn] = m - D.seg_first[s] - D.seg_n[s];
+    D.grp_first[gp] = m + D.seg_first[s];
+    D.grp_nphi[gn] = D.grp_nphi[gp] = c->seg_nphi[calo][s];
+    D.grp_base[gn] = D.base[D.grp_first[gn]];
+    D.grp_base[gp] = D.base[D.grp_first[gp]];
+  }
   if (base >= (1 << 24)) return err(PDR_ECARD, "too many towers");
   return PDR_OK;
 }
@@ -201,6 +216,10 @@ int expand_card_fixed(const pdr_card* c, DevCard& D) {
     return err(PDR_ECARD, "bad efficiency table edges");
   D.trk_npt = c->trk_npt;
   D.trk_neta = c->trk_neta;
+  for (int k = 0; k < PDR_MAXEDGE; ++k) {
+    D.trk_pt_edges[k] = D.trk_eta_edges[k] = D.id_edges[k] = INFINITY;
+    for (int comp = 0; comp < 4; ++comp) D.res_edges[comp][k] = INFINITY;
+  }
   for (int k = 0; k < c->trk_npt; ++k) D.trk_pt_edges[k] = (float)c->trk_pt_edges[k];
   for (int k = 0; k < c->trk_neta; ++k) D.trk_eta_edges[k] = (float)c->trk_eta_edges[k];
   for (int t = 0; t < 3; ++t)
@@ -285,8 +304,11 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   uint32_t* d_err = (uint32_t*)base;
   uint32_t* d_max = d_err + 1;
   if ((rc = expand_card_fixed(card, g_host_card))) return rc;
+  const size_t hot_bytes = build_hot_card(g_host_card, g_host_hot, sizeof g_host_hot);
+  if (hot_bytes == 0) return err(PDR_ECARD, "card tables exceed the 40 KiB shared-memory card cache");
   if (cudaMemsetAsync(base, 0, 16, s) != cudaSuccess ||
-      cudaMemcpyAsync(base + kCardOffset, &g_host_card, sizeof(DevCard), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      cudaMemcpyAsync(base + kCardOffset, &g_host_card, sizeof(DevCard), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(base + kHotOffset, g_host_hot, hot_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return err(PDR_EDEVICE, "cannot stage the card in the static scratch");
   if (b->n_events == 0) return cudaStreamSynchronize(s) == cudaSuccess ? PDR_OK : err(PDR_EDEVICE, "sync");
   uint32_t max_n = b->max_event_size;
@@ -306,8 +328,9 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   else { team = 1024; block = 1024; }
   const uint32_t nt = block / team;
   uint32_t slots = std::max<uint32_t>(64, pow2_at_least((uint64_t)max_n * 4 / 3 + 1));
-  while (slots > 64 && nt * team_smem_bytes(team, slots, slots * 3 / 4) > (uint64_t)slot->smem_optin) slots >>= 1;
-  const size_t smem = (size_t)(nt * team_smem_bytes(team, slots, slots * 3 / 4));
+  while (slots > 64 && hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4) > (uint64_t)slot->smem_optin)
+    slots >>= 1;
+  const size_t smem = (size_t)(hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4));
   int per_sm = 0;
   if (occupancy_fused(team, block, smem, &per_sm) != cudaSuccess || per_sm < 1)
     return err(PDR_EDEVICE, "launch shape cannot be resident");
@@ -315,6 +338,8 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   KParams p;
   std::memset(&p, 0, sizeof p);
   p.card = (const DevCard*)(base + kCardOffset);
+  p.hot = base + kHotOffset;
+  p.hot_bytes = (uint32_t)hot_bytes;
   p.n_events = b->n_events;
   p.offsets = b->offsets;
   p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.mass = b->mass; p.vz = b->vz;

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "pdr.h"
+#include "pdr_hot.h"
 #include "pdr_internal.h"
 
 namespace pdr {
@@ -133,6 +134,8 @@ struct Pool {
 
 struct CardEntry {
   DevCard* dev = nullptr;
+  unsigned char* hot = nullptr;   // shared-memory card cache image (device)
+  uint32_t hot_bytes = 0;
   uint32_t ntowers[2] = {0, 0};
 };
 
@@ -246,6 +249,17 @@ int expand_calo(const pdr_card* c, int calo, DevCalo& D, float* pool, int& pool_
     D.cosh_c[r] = (float)std::cosh(ec);
   }
   D.ntowers = base;
+  // ring groups in ring order: negative-side segments outermost first, then
+  // positive-side segments innermost first
+  D.ngroup = 2 * nseg;
+  for (int s = 0; s < nseg; ++s) {
+    const int gn = nseg - 1 - s, gp = nseg + s;
+    D.grp_first[gn] = m - D.seg_first[s] - D.seg_n[s];
+    D.grp_first[gp] = m + D.seg_first[s];
+    D.grp_nphi[gn] = D.grp_nphi[gp] = c->seg_nphi[calo][s];
+    D.grp_base[gn] = D.base[D.grp_first[gn]];
+    D.grp_base[gp] = D.base[D.grp_first[gp]];
+  }
   if (base >= (1 << 24)) return fail(PDR_ECARD, "too many towers (max 2^24 per calorimeter)");
   return PDR_OK;
 }
@@ -299,6 +313,10 @@ int expand_card(const pdr_card* c, DevCard& D) {
     return fail(PDR_ECARD, "efficiency table edges must increase");
   D.trk_npt = c->trk_npt;
   D.trk_neta = c->trk_neta;
+  for (int k = 0; k < PDR_MAXEDGE; ++k) {
+    D.trk_pt_edges[k] = D.trk_eta_edges[k] = D.id_edges[k] = INFINITY;
+    for (int comp = 0; comp < 4; ++comp) D.res_edges[comp][k] = INFINITY;
+  }
   for (int k = 0; k < c->trk_npt; ++k) D.trk_pt_edges[k] = (float)c->trk_pt_edges[k];
   for (int k = 0; k < c->trk_neta; ++k) D.trk_eta_edges[k] = (float)c->trk_eta_edges[k];
   for (int t = 0; t < 3; ++t)
@@ -357,23 +375,25 @@ struct Shape {
 const uint32_t kTeams[] = {32, 64, 128, 256, 512, 1024};
 
 uint32_t slots_for(uint32_t max_n) {
-  // load factor <= 3/4
+  // at most 3/4 of the slots can be in use (an event never has more distinct
+  // towers than particles); probing stays short at that load
   return std::max<uint32_t>(64, next_pow2((uint64_t)max_n * 4 / 3 + 1));
 }
 
 // Build a concrete shape for (team, block) handling events up to max_n in shared
 // memory where possible.
-int make_shape(pdr_ctx* ctx, uint32_t team, uint32_t block, uint32_t want_slots, uint32_t grid, Shape& S) {
+int make_shape(pdr_ctx* ctx, uint32_t team, uint32_t block, uint32_t want_slots, uint32_t grid,
+               uint32_t hot_bytes, Shape& S) {
   if (!shape_supported(team, block)) return fail(PDR_EINVAL, "unsupported launch shape (team, block)");
   const uint32_t nt = block / team;
   uint32_t slots = std::max<uint32_t>(64, next_pow2(want_slots));
   // shrink until the CTA fits in shared memory
-  while (slots > 64 && nt * team_smem_bytes(team, slots, slots * 3 / 4) > ctx->smem_optin) slots >>= 1;
+  while (slots > 64 && hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4) > ctx->smem_optin) slots >>= 1;
   S.team = team;
   S.block = block;
   S.slots = slots;
   S.nmax = slots * 3 / 4;
-  S.smem = (size_t)(nt * team_smem_bytes(team, slots, S.nmax));
+  S.smem = (size_t)(hot_bytes + nt * team_smem_bytes(team, slots, S.nmax));
   if (S.smem > ctx->smem_optin) return fail(PDR_EINVAL, "launch shape does not fit in shared memory");
   int per_sm = 0;
   cudaError_t e = occupancy_fused(team, block, S.smem, &per_sm);
@@ -442,7 +462,10 @@ int run_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const Shap
               cudaStream_t s) {
   KParams p;
   std::memset(&p, 0, sizeof p);
-  p.card = ctx->cards[b->card_id].dev;
+  const CardEntry& ce = ctx->cards[b->card_id];
+  p.card = ce.dev;
+  p.hot = ce.hot;
+  p.hot_bytes = ce.hot_bytes;
   p.n_events = b->n_events;
   p.offsets = b->offsets;
   p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.mass = b->mass; p.vz = b->vz;
@@ -489,7 +512,7 @@ int resolve_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_launch* l, cudaStr
     use = it != ctx->tuned.end() ? it->second : default_launch(max_n);
   }
   const uint32_t want = use.table_slots ? use.table_slots : slots_for(max_n);
-  return make_shape(ctx, use.team, use.block, want, use.grid, S);
+  return make_shape(ctx, use.team, use.block, want, use.grid, ctx->cards[b->card_id].hot_bytes, S);
 }
 
 }  // namespace
@@ -564,12 +587,22 @@ int pdr_card_load(pdr_ctx* ctx, const pdr_card* card, uint32_t* card_id) {
   CardEntry ce;
   ce.ntowers[0] = (uint32_t)host->calo[0].ntowers;
   ce.ntowers[1] = (uint32_t)host->calo[1].ntowers;
+  std::vector<unsigned char> hot(PDR_HOT_MAX_BYTES);
+  const size_t hot_bytes = build_hot_card(*host, hot.data(), hot.size());
+  if (hot_bytes == 0) {
+    delete host;
+    return fail(PDR_ECARD, "card tables exceed the 40 KiB shared-memory card cache");
+  }
   cudaSetDevice(ctx->device);
-  if (cudaMalloc((void**)&ce.dev, sizeof(DevCard)) != cudaSuccess) {
+  const size_t hot_off = (sizeof(DevCard) + 255) & ~(size_t)255;
+  if (cudaMalloc((void**)&ce.dev, hot_off + hot_bytes) != cudaSuccess) {
     delete host;
     return fail(PDR_ENOMEM, "cannot allocate card tables");
   }
+  ce.hot = (unsigned char*)ce.dev + hot_off;
+  ce.hot_bytes = (uint32_t)hot_bytes;
   cudaError_t e = cudaMemcpy(ce.dev, host, sizeof(DevCard), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ce.hot, hot.data(), hot_bytes, cudaMemcpyHostToDevice);
   delete host;
   if (e != cudaSuccess) {
     cudaFree(ce.dev);
@@ -629,7 +662,7 @@ int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, vo
   uint32_t max_n = b->max_event_size;
   if (max_n == 0 && b->n_events > 0 && (rc = max_event_size_impl(ctx, b, s, &max_n))) return rc;
   Shape S;
-  if ((rc = make_shape(ctx, 256, 256, slots_for(max_n), 1, S))) return rc;
+  if ((rc = make_shape(ctx, 256, 256, slots_for(max_n), 1, ctx->cards[b->card_id].hot_bytes, S))) return rc;
   S.grid = 1;
   for (uint64_t e = 0; e < b->n_events; ++e) {
     pdr_batch one = *b;
@@ -683,9 +716,9 @@ int pdr_autotune(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* s
       if (block == 0 || block < team || !shape_supported(team, block)) continue;
       // table sized for the largest event, or for the typical event with the
       // largest ones spilling to the global table
-      for (uint32_t want : {slots_for(max_n), slots_for(std::max<uint32_t>(max_n / 2, 1))}) {
+      for (uint32_t want : {slots_for(max_n), 2 * slots_for(max_n), slots_for(std::max<uint32_t>(max_n / 2, 1))}) {
         Shape S;
-        if (make_shape(ctx, team, block, want, 0, S) != PDR_OK) continue;
+        if (make_shape(ctx, team, block, want, 0, ctx->cards[b->card_id].hot_bytes, S) != PDR_OK) continue;
         // a team must not walk a huge event alone in tiny chunks
         if (team == 32 && max_n > 1024) continue;
         if (run_shape(ctx, b, o, S, max_n, s) != PDR_OK) continue;  // warm-up
