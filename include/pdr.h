@@ -209,6 +209,15 @@ int pdr_card_towers(pdr_ctx* ctx, uint32_t card_id, int calo, uint32_t* n);
 int pdr_run(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,
             const pdr_launch* launch, void* stream);
 
+/* Several batches (up to 32 per launch, each with its own card among up to 4
+ * distinct cards per launch, its own seed, event-index base and outputs) in one
+ * fused persistent launch; larger sets are split into consecutive launches.
+ * Each batch's results are those pdr_run gives it alone (same bits).  The
+ * launch shape is sized for the largest event of all batches; launch may be
+ * NULL (the tuned shape of batches[0]'s card, else the default). */
+int pdr_run_multi(pdr_ctx* ctx, const pdr_batch* batches, uint32_t n, const pdr_outputs* outs,
+                  const pdr_launch* launch, void* stream);
+
 /* The plain per-event form: one launch per event (team = block per event),
  * for comparison with pdr_run.  Same outputs, same bits. */
 int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,

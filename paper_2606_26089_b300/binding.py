@@ -113,6 +113,8 @@ def lib():
             "pdr_card_towers": ([P, C.c_uint32, I, C.POINTER(C.c_uint32)], I),
             "pdr_run": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_launch), P], I),
             "pdr_run_per_event": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P], I),
+            "pdr_run_multi": ([P, C.POINTER(pdr_batch), C.c_uint32, C.POINTER(pdr_outputs),
+                               C.POINTER(pdr_launch), P], I),
             "pdr_run_host": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_launch), P], I),
             "pdr_autotune": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P, C.POINTER(pdr_launch)], I),
             "pdr_max_event_size": ([P, C.POINTER(pdr_batch), P, C.POINTER(C.c_uint32)], I),
@@ -305,6 +307,13 @@ class Context:
         self._check(self.L.pdr_run(self.h, C.byref(batch), C.byref(out),
                                    C.byref(launch) if launch is not None else None,
                                    self._stream(stream)), "pdr_run")
+
+    def run_multi(self, batches, outs, launch: Optional[pdr_launch] = None, stream=None):
+        n = len(batches)
+        ba = (pdr_batch * max(n, 1))(*batches)
+        oa = (pdr_outputs * max(n, 1))(*outs)
+        self._check(self.L.pdr_run_multi(self.h, ba, n, oa, C.byref(launch) if launch is not None else None,
+                                         self._stream(stream)), "pdr_run_multi")
 
     def run_per_event(self, batch: pdr_batch, out: pdr_outputs, stream=None):
         self._check(self.L.pdr_run_per_event(self.h, C.byref(batch), C.byref(out), self._stream(stream)),

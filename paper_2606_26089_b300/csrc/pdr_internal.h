@@ -118,31 +118,42 @@ struct alignas(16) HotCard {
 
 #define PDR_HOT_MAX_BYTES (40u * 1024u)   // shared-memory card cache limit
 
-// Kernel parameter block (passed by value).
-struct KParams {
-  const DevCard* card;
-  const unsigned char* hot;          // HotCard + data, hot_bytes long (multiple of 16)
-  uint32_t hot_bytes, pad_hot;
+#define PDR_LAUNCH_SEGS 32   // batches in one fused launch
+#define PDR_LAUNCH_CARDS 4   // distinct cards in one fused launch
+
+// One batch of a launch: its inputs, outputs, randomness and card.
+struct KSeg {
+  uint64_t event_start;              // first launch-wide event index of the batch
   uint64_t n_events;
   const uint64_t* offsets;
   const float *pt, *eta, *phi, *mass, *vz;
   const int32_t* pdg;
   const int8_t* charge;
-  uint32_t seed_lo, seed_hi, event_base, flags;
+  uint32_t seed_lo, seed_hi, event_base, card;  // card: slot of KParams::hot
   pdr_track* tracks;
   pdr_tower* towers;
   pdr_eflow* eflow;
   pdr_cand* cands;
   pdr_iso* iso;
   uint32_t* counts;
-  pdr_debug* debug;
+  pdr_debug* debug;                  // null: no debug records
+};
+
+// Kernel parameter block (passed by value, read through __grid_constant__).
+struct KParams {
+  uint64_t n_events;                 // all segments
+  uint32_t n_segs, n_cards;
+  const unsigned char* hot[PDR_LAUNCH_CARDS];   // card cache images (device)
+  uint32_t hot_bytes[PDR_LAUNCH_CARDS];         // each a multiple of 16
+  uint32_t hot_off[PDR_LAUNCH_CARDS];           // offset of each image in shared memory
+  uint32_t hot_total;                // shared memory of all card images
   uint32_t table_slots, log2_slots;  // shared-memory table per team
   uint32_t nmax_smem;                // largest event handled in shared memory
   uint32_t g_slots, g_log2, g_nmax;  // global-memory table per team for larger events
   unsigned char* gscratch;           // g_team_bytes per team, or null
   uint64_t g_team_bytes;
   uint32_t* err;                     // device error word (bit flags below)
-  uint32_t* next_event;              // dynamic event counter (null: static schedule)
+  KSeg seg[PDR_LAUNCH_SEGS];
 };
 
 enum : uint32_t {

@@ -313,13 +313,13 @@ struct PartOut {
   bool tracked, cand;
 };
 
-__device__ __forceinline__ void particle_stage(const KParams& p, const HotCard& K, const float* KD,
+__device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, const float* KD,
                                                uint64_t g, uint32_t i, uint32_t event, PartOut& o) {
-  const float PT = __ldg(p.pt + g), ETA = __ldg(p.eta + g), PHI = __ldg(p.phi + g);
-  const float M = __ldg(p.mass + g);
-  const int32_t PDG = __ldg(p.pdg + g);
-  const int Q = (int)__ldg(p.charge + g);
-  const float VZ = p.vz ? __ldg(p.vz + g) : 0.0f;
+  const float PT = __ldg(S.pt + g), ETA = __ldg(S.eta + g), PHI = __ldg(S.phi + g);
+  const float M = __ldg(S.mass + g);
+  const int32_t PDG = __ldg(S.pdg + g);
+  const int Q = (int)__ldg(S.charge + g);
+  const float VZ = S.vz ? __ldg(S.vz + g) : 0.0f;
   o.key = PDR_NO_KEY; o.ring = 0; o.flags = 0;
   o.etrk = 0.0f; o.ptp = 0.0f; o.cpt = 0.0f; o.eta_pos = 0.0f; o.phi_pos = 0.0f;
   o.cc = -1; o.tracked = false; o.cand = false;
@@ -354,7 +354,7 @@ __device__ __forceinline__ void particle_stage(const KParams& p, const HotCard& 
     const int kp = small_lookup(K.trk_pt_edges, K.trk_npt, PT);
     const int ke = small_lookup(K.trk_eta_edges, K.trk_neta, aeta);
     const unsigned long long T = (kp >= 0 && ke >= 0) ? K.trk_T[tc][kp][ke] : 0ull;
-    const uint4 w = philox(i, event, 1u, 0u, p.seed_lo, p.seed_hi);
+    const uint4 w = philox(i, event, 1u, 0u, S.seed_lo, S.seed_hi);
     if ((unsigned long long)w.x < T) {
       o.tracked = true;
       o.flags |= PDR_F_TRACKED;
@@ -375,7 +375,7 @@ __device__ __forceinline__ void particle_stage(const KParams& p, const HotCard& 
   if (cc >= 0 && PT > K.cand_ptmin) {
     const int ke = small_lookup(K.id_edges, K.id_n, aeta);
     const unsigned long long T = ke >= 0 ? K.id_T[cc][ke] : 0ull;
-    const uint4 w = philox(i, event, 2u, 0u, p.seed_lo, p.seed_hi);
+    const uint4 w = philox(i, event, 2u, 0u, S.seed_lo, S.seed_hi);
     if ((unsigned long long)w.x < T) {
       const float z = normal(w.y, w.z);
       const int comp = cc != 1 ? RES_ECAL : RES_MUON;
@@ -484,12 +484,12 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
 
 // ------------------------------------------------------------- one event
 template <int TEAM>
-__device__ __forceinline__ void process_event(const KParams& p, const HotCard& K, const float* KD,
+__device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
                                               const Tbl& T, uint32_t* wbuf, float4* cf, uint32_t* ckey,
                                               unsigned long long* csum, const TeamCtx<TEAM>& tc,
                                               uint64_t e, uint64_t a, uint32_t n) {
-  const uint32_t event = p.event_base + (uint32_t)e;
-  const bool dbg = p.debug != nullptr;
+  const uint32_t event = S.event_base + (uint32_t)e;
+  const bool dbg = S.debug != nullptr;
   uint32_t n_trk = 0, n_cand = 0, flip = 0;
 
   // ---- phase 1: particles (S0-S5); tracks and candidates in particle order
@@ -498,12 +498,12 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
     const bool valid = i < n;
     PartOut o;
     o.tracked = false; o.cand = false; o.key = PDR_NO_KEY; o.E = 0.0f; o.etrk = 0.0f;
-    if (valid) particle_stage(p, K, KD, a + i, i, event, o);
+    if (valid) particle_stage(S, K, KD, a + i, i, event, o);
     uint32_t slot = PDR_EMPTY;
     bool claimed = false;
     const unsigned long long e_fp = to_fp(o.E);
     const unsigned long long t_fp = o.etrk > 0.0f ? to_fp(o.etrk) : 0ull;
-    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, t_fp, &claimed, p.err);
+    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, t_fp, &claimed, err);
     if (valid) T.pinfo[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(o.tracked, o.cand, wbuf + 32 * flip, tot, tc);
@@ -514,16 +514,16 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
       atomicMin(&T.owner[slot], i);
     }
     if (o.tracked || o.cand) {
-      const float eta = __ldg(p.eta + a + i), phi = __ldg(p.phi + a + i);
+      const float eta = __ldg(S.eta + a + i), phi = __ldg(S.phi + a + i);
       if (o.tracked)
-        reinterpret_cast<float4*>(p.tracks)[a + n_trk + (pre & 0xFFFFu)] =
+        reinterpret_cast<float4*>(S.tracks)[a + n_trk + (pre & 0xFFFFu)] =
             make_float4(o.ptp, eta, phi, __uint_as_float(i));
       if (o.cand) {
         const uint32_t j = n_cand + (pre >> 16);
-        reinterpret_cast<float4*>(p.cands)[a + j] =
+        reinterpret_cast<float4*>(S.cands)[a + j] =
             make_float4(o.cpt, eta, phi, __uint_as_float(i | ((uint32_t)o.cc << 28)));
         // own tower key, read back by the isolation of candidates beyond the staged ones
-        reinterpret_cast<float2*>(p.iso)[a + j] = make_float2(__uint_as_float(o.key), 0.0f);
+        reinterpret_cast<float2*>(S.iso)[a + j] = make_float2(__uint_as_float(o.key), 0.0f);
         if (j < PDR_CMAX) {  // staged for the isolation phase
           cf[j] = make_float4(eta, phi, o.cpt, __uint_as_float(i));
           ckey[j] = o.key;
@@ -531,7 +531,7 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
       }
     }
     if (dbg && valid)
-      reinterpret_cast<float4*>(p.debug)[a + i] =
+      reinterpret_cast<float4*>(S.debug)[a + i] =
           make_float4(__uint_as_float(o.key), o.eta_pos, o.phi_pos, __uint_as_float(o.flags));
     n_trk += tot & 0xFFFFu;
     n_cand += tot >> 16;
@@ -551,7 +551,7 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
         const uint32_t slot = pi & 0xFFFFu;
         if (T.owner[slot] == i) {
           key = T.keys[slot];
-          tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, p.seed_lo, p.seed_hi, to);
+          tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, S.seed_lo, S.seed_hi, to);
           T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
         }
       }
@@ -560,11 +560,11 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
     const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (to.kept) {
-      pdr_tower* r = p.towers + a + n_twr + (pre & 0xFFFFu);
+      pdr_tower* r = S.towers + a + n_twr + (pre & 0xFFFFu);
       r->key = key; r->e = to.e; r->et = to.et;
     }
     if (to.ef) {
-      pdr_eflow* r = p.eflow + a + n_ef + (pre >> 16);
+      pdr_eflow* r = S.eflow + a + n_ef + (pre >> 16);
       r->key = key; r->e = to.de; r->et = to.det;
     }
     n_twr += tot & 0xFFFFu;
@@ -580,9 +580,9 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
       tc.sync();
       if (g0 > 0 && (uint32_t)tc.tid < gn) {  // candidates beyond the staged ones
         const uint64_t j = a + g0 + tc.tid;
-        const float4 c = reinterpret_cast<const float4*>(p.cands)[j];
+        const float4 c = reinterpret_cast<const float4*>(S.cands)[j];
         cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
-        ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(p.iso)[j].x);
+        ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(S.iso)[j].x);
       }
       if (g0 > 0) tc.sync();
       for (uint32_t j = tc.tid; j < n_obj; j += TEAM) {
@@ -590,10 +590,10 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
         uint32_t oid;
         bool is_trk;
         if (j < n_trk) {
-          const float4 t = reinterpret_cast<const float4*>(p.tracks)[a + j];
+          const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + j];
           opt = t.x; oe = t.y; op = t.z; oid = __float_as_uint(t.w); is_trk = true;
         } else {
-          const pdr_eflow f = p.eflow[a + (j - n_trk)];
+          const pdr_eflow f = S.eflow[a + (j - n_trk)];
           int r;
           tower_decode(K, KD, (int)(f.key >> 24), f.key & 0xFFFFFFu, r, oe, op);
           opt = f.et; oid = f.key; is_trk = false;
@@ -617,34 +617,36 @@ __device__ __forceinline__ void process_event(const KParams& p, const HotCard& K
         const float s = from_fp(csum[tc.tid]);
         csum[tc.tid] = 0ull;  // clean for the next group / event
         const float rel = s / cf[tc.tid].z;
-        reinterpret_cast<float2*>(p.iso)[j] = make_float2(s, rel);
-        if (rel < K.imax) reinterpret_cast<uint32_t*>(p.cands + j)[3] |= 0x80000000u;
+        reinterpret_cast<float2*>(S.iso)[j] = make_float2(s, rel);
+        if (rel < K.imax) reinterpret_cast<uint32_t*>(S.cands + j)[3] |= 0x80000000u;
       }
     }
   }
   // the next event reuses the table, the staged candidates and the scan buffers
   tc.sync();
   if (tc.tid == 0)
-    reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
+    reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
 }
 
 // ------------------------------------------------------------------ kernel
-// Shared memory: the card cache (hot_bytes), then per team its tower table,
-// particle records, scan buffers and isolation candidates.  Register cap: at most 64
-// registers a thread (1024 / BLOCK resident CTAs).
+// Shared memory: the card images of the launch (hot_total), then per team its
+// tower table, particle info, scan buffers and isolation candidates.
+// Register cap: at most 64 registers a thread (1024 / BLOCK resident CTAs).
+// The launch covers up to PDR_LAUNCH_SEGS batches (each with its own card,
+// inputs, outputs and seed) as one launch-wide sequence of events.
 template <int TEAM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1) fused_kernel(const KParams p) {
+__global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1)
+    fused_kernel(const __grid_constant__ KParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NT = BLOCK / TEAM;
-  for (uint32_t k = threadIdx.x; k < p.hot_bytes / 16; k += BLOCK)
-    reinterpret_cast<uint4*>(smem)[k] = __ldg(reinterpret_cast<const uint4*>(p.hot) + k);
-  const HotCard& K = *reinterpret_cast<const HotCard*>(smem);
-  const float* KD = reinterpret_cast<const float*>(smem + sizeof(HotCard));
+  for (uint32_t c = 0; c < p.n_cards; ++c)
+    for (uint32_t k = threadIdx.x; k < p.hot_bytes[c] / 16; k += BLOCK)
+      reinterpret_cast<uint4*>(smem + p.hot_off[c])[k] = __ldg(reinterpret_cast<const uint4*>(p.hot[c]) + k);
   TeamCtx<TEAM> tc;
   tc.tix = (int)threadIdx.x / TEAM;
   tc.tid = (int)threadIdx.x % TEAM;
   const uint64_t tbytes = team_smem_bytes(TEAM, p.table_slots, p.nmax_smem);
-  unsigned char* mine = smem + p.hot_bytes + (uint64_t)tc.tix * tbytes;
+  unsigned char* mine = smem + p.hot_total + (uint64_t)tc.tix * tbytes;
   const Tbl st = carve(mine, p.table_slots, p.log2_slots);
   unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
   uint32_t* wbuf = (uint32_t*)tail;
@@ -656,31 +658,37 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
   __syncthreads();
   const uint64_t gteam = (uint64_t)blockIdx.x * NT + tc.tix;
   const uint64_t nteams = (uint64_t)gridDim.x * NT;
-  for (uint64_t e = gteam; e < p.n_events; e += nteams) {
-    const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
+  uint32_t sg = 0;  // segment cursor: a team's events only move forward
+  for (uint64_t ge = gteam; ge < p.n_events; ge += nteams) {
+    while (sg + 1 < p.n_segs && ge >= p.seg[sg + 1].event_start) ++sg;
+    const KSeg& S = p.seg[sg];
+    const uint64_t e = ge - S.event_start;
+    const HotCard& K = *reinterpret_cast<const HotCard*>(smem + p.hot_off[S.card]);
+    const float* KD = reinterpret_cast<const float*>(smem + p.hot_off[S.card] + sizeof(HotCard));
+    const uint64_t a = S.offsets[e], b = S.offsets[e + 1];
     if (b < a || b - a >= (1ull << 28)) {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_CSR);
-        reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
       }
       continue;
     }
     const uint32_t n = (uint32_t)(b - a);
     if (n == 0) {  // nothing to do (and no team synchronisation for an empty event)
-      if (tc.tid == 0) reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(0, 0, 0, 0);
+      if (tc.tid == 0) reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
       continue;
     }
     if (n <= p.nmax_smem) {
-      process_event<TEAM>(p, K, KD, st, wbuf, cf, ckey, csum, tc, e, a, n);
+      process_event<TEAM>(S, p.err, K, KD, st, wbuf, cf, ckey, csum, tc, e, a, n);
     } else if (p.gscratch != nullptr && n <= p.g_nmax) {
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_log2);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys[s] = PDR_EMPTY;
       tc.sync();
-      process_event<TEAM>(p, K, KD, gt, wbuf, cf, ckey, csum, tc, e, a, n);
+      process_event<TEAM>(S, p.err, K, KD, gt, wbuf, cf, ckey, csum, tc, e, a, n);
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);
-        reinterpret_cast<uint4*>(p.counts)[e] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
       }
     }
   }

@@ -335,21 +335,28 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   if (occupancy_fused(team, block, smem, &per_sm) != cudaSuccess || per_sm < 1)
     return err(PDR_EDEVICE, "launch shape cannot be resident");
   uint32_t grid = (uint32_t)(per_sm * slot->n_sms);
-  KParams p;
+  static KParams p;  // 5 KB parameter block: static storage (calls are serialised by g_mu)
   std::memset(&p, 0, sizeof p);
-  p.card = (const DevCard*)(base + kCardOffset);
-  p.hot = base + kHotOffset;
-  p.hot_bytes = (uint32_t)hot_bytes;
+  p.n_cards = 1;
+  p.hot[0] = base + kHotOffset;
+  p.hot_bytes[0] = (uint32_t)hot_bytes;
+  p.hot_off[0] = 0;
+  p.hot_total = (uint32_t)hot_bytes;
+  p.n_segs = 1;
   p.n_events = b->n_events;
-  p.offsets = b->offsets;
-  p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.mass = b->mass; p.vz = b->vz;
-  p.pdg = b->pdg; p.charge = b->charge;
-  p.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
-  p.seed_hi = (uint32_t)(b->seed >> 32);
-  p.event_base = b->event_index_base;
-  p.tracks = o->tracks; p.towers = o->towers; p.eflow = o->eflow; p.cands = o->cands;
-  p.iso = o->iso; p.counts = o->counts;
-  p.debug = (b->flags & PDR_BATCH_DEBUG) ? o->debug : nullptr;
+  KSeg& sg = p.seg[0];
+  sg.event_start = 0;
+  sg.n_events = b->n_events;
+  sg.offsets = b->offsets;
+  sg.pt = b->pt; sg.eta = b->eta; sg.phi = b->phi; sg.mass = b->mass; sg.vz = b->vz;
+  sg.pdg = b->pdg; sg.charge = b->charge;
+  sg.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
+  sg.seed_hi = (uint32_t)(b->seed >> 32);
+  sg.event_base = b->event_index_base;
+  sg.card = 0;
+  sg.tracks = o->tracks; sg.towers = o->towers; sg.eflow = o->eflow; sg.cands = o->cands;
+  sg.iso = o->iso; sg.counts = o->counts;
+  sg.debug = (b->flags & PDR_BATCH_DEBUG) ? o->debug : nullptr;
   p.table_slots = slots;
   p.log2_slots = log2_of(slots);
   p.nmax_smem = slots * 3 / 4;

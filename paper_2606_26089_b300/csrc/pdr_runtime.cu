@@ -457,26 +457,43 @@ int max_event_size_impl(pdr_ctx* ctx, const pdr_batch* b, cudaStream_t s, uint32
   return PDR_OK;
 }
 
-// Fill a kernel parameter block and launch one shape over a batch.
-int run_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const Shape& S, uint32_t max_n,
-              cudaStream_t s) {
-  KParams p;
-  std::memset(&p, 0, sizeof p);
-  const CardEntry& ce = ctx->cards[b->card_id];
-  p.card = ce.dev;
-  p.hot = ce.hot;
-  p.hot_bytes = ce.hot_bytes;
-  p.n_events = b->n_events;
-  p.offsets = b->offsets;
-  p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.mass = b->mass; p.vz = b->vz;
-  p.pdg = b->pdg; p.charge = b->charge;
-  p.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
-  p.seed_hi = (uint32_t)(b->seed >> 32);
-  p.event_base = b->event_index_base;
-  p.flags = b->flags;
-  p.tracks = o->tracks; p.towers = o->towers; p.eflow = o->eflow; p.cands = o->cands;
-  p.iso = o->iso; p.counts = o->counts;
-  p.debug = (b->flags & PDR_BATCH_DEBUG) ? o->debug : nullptr;
+// Launch plan: the team shape before the card images of a launch are known.
+struct Plan {
+  uint32_t team, block, want_slots, grid;
+};
+
+Plan plan_launch(pdr_ctx* ctx, uint32_t card_id, uint32_t max_n, const pdr_launch* l) {
+  pdr_launch use;
+  if (l) use = *l;
+  else {
+    auto it = ctx->tuned.find(tune_key(card_id, max_n));
+    use = it != ctx->tuned.end() ? it->second : default_launch(max_n);
+  }
+  Plan P;
+  P.team = use.team;
+  P.block = use.block;
+  P.want_slots = use.table_slots ? use.table_slots : slots_for(max_n);
+  P.grid = use.grid;
+  return P;
+}
+
+void fill_seg(KSeg& g, const pdr_batch* b, const pdr_outputs* o, uint64_t start, uint32_t card) {
+  g.event_start = start;
+  g.n_events = b->n_events;
+  g.offsets = b->offsets;
+  g.pt = b->pt; g.eta = b->eta; g.phi = b->phi; g.mass = b->mass; g.vz = b->vz;
+  g.pdg = b->pdg; g.charge = b->charge;
+  g.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
+  g.seed_hi = (uint32_t)(b->seed >> 32);
+  g.event_base = b->event_index_base;
+  g.card = card;
+  g.tracks = o->tracks; g.towers = o->towers; g.eflow = o->eflow; g.cands = o->cands;
+  g.iso = o->iso; g.counts = o->counts;
+  g.debug = (b->flags & PDR_BATCH_DEBUG) ? o->debug : nullptr;
+}
+
+// Table and scratch parameters of a launch for events up to max_n.
+int set_tables(pdr_ctx* ctx, KParams& p, const Shape& S, uint32_t max_n) {
   p.table_slots = S.slots;
   p.log2_slots = ilog2(S.slots);
   p.nmax_smem = S.nmax;
@@ -493,26 +510,72 @@ int run_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const Shap
     if (rc) return rc;
     p.gscratch = ctx->gscratch;
   }
-  if (b->n_events == 0) return PDR_OK;
+  return PDR_OK;
+}
+
+// One fused launch over up to PDR_LAUNCH_SEGS batches using up to
+// PDR_LAUNCH_CARDS distinct cards (the caller groups them).
+int launch_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* const* os, uint32_t n,
+                 const Plan& P, uint32_t max_n, cudaStream_t s) {
+  static thread_local KParams p;  // 5 KB: keep it off the stack
+  std::memset(&p, 0, sizeof p);
+  uint64_t start = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const CardEntry& ce = ctx->cards[bs[k]->card_id];
+    uint32_t slot = p.n_cards;
+    for (uint32_t c = 0; c < p.n_cards; ++c)
+      if (p.hot[c] == ce.hot) slot = c;
+    if (slot == p.n_cards) {
+      if (p.n_cards == PDR_LAUNCH_CARDS) return fail(PDR_EINVAL, "too many cards in one launch group");
+      p.hot[slot] = ce.hot;
+      p.hot_bytes[slot] = ce.hot_bytes;
+      p.hot_off[slot] = p.hot_total;
+      p.hot_total += ce.hot_bytes;
+      ++p.n_cards;
+    }
+    fill_seg(p.seg[k], bs[k], os[k], start, slot);
+    start += bs[k]->n_events;
+  }
+  p.n_segs = n;
+  p.n_events = start;
+  if (p.n_events == 0) return PDR_OK;
+  Shape S;
+  int rc = make_shape(ctx, P.team, P.block, P.want_slots, P.grid, p.hot_total, S);
+  if (rc) return rc;
+  if ((rc = set_tables(ctx, p, S, max_n))) return rc;
   PDR_CUDA(launch_fused(S.team, S.block, p, S.grid, S.smem, s), "fused kernel launch");
   return PDR_OK;
 }
 
-int resolve_shape(pdr_ctx* ctx, const pdr_batch* b, const pdr_launch* l, cudaStream_t s, uint32_t& max_n,
-                  Shape& S) {
-  max_n = b->max_event_size;
-  if (max_n == 0 && b->n_events > 0) {
-    int rc = max_event_size_impl(ctx, b, s, &max_n);
-    if (rc) return rc;
+// Any number of batches: consecutive groups of at most PDR_LAUNCH_SEGS batches
+// and PDR_LAUNCH_CARDS cards, one fused launch each.
+int launch_batches(pdr_ctx* ctx, const pdr_batch* bs, const pdr_outputs* os, uint32_t n, const Plan& P,
+                   uint32_t max_n, cudaStream_t s) {
+  std::vector<const pdr_batch*> gb;
+  std::vector<const pdr_outputs*> go;
+  std::vector<uint32_t> cards;
+  auto flush = [&]() -> int {
+    int rc = gb.empty() ? PDR_OK : launch_group(ctx, gb.data(), go.data(), (uint32_t)gb.size(), P, max_n, s);
+    gb.clear(); go.clear(); cards.clear();
+    return rc;
+  };
+  for (uint32_t k = 0; k < n; ++k) {
+    const bool new_card = std::find(cards.begin(), cards.end(), bs[k].card_id) == cards.end();
+    if (gb.size() == PDR_LAUNCH_SEGS || (new_card && cards.size() == PDR_LAUNCH_CARDS)) {
+      int rc = flush();
+      if (rc) return rc;
+    }
+    if (std::find(cards.begin(), cards.end(), bs[k].card_id) == cards.end()) cards.push_back(bs[k].card_id);
+    gb.push_back(&bs[k]);
+    go.push_back(&os[k]);
   }
-  pdr_launch use;
-  if (l) use = *l;
-  else {
-    auto it = ctx->tuned.find(tune_key(b->card_id, max_n));
-    use = it != ctx->tuned.end() ? it->second : default_launch(max_n);
-  }
-  const uint32_t want = use.table_slots ? use.table_slots : slots_for(max_n);
-  return make_shape(ctx, use.team, use.block, want, use.grid, ctx->cards[b->card_id].hot_bytes, S);
+  return flush();
+}
+
+int batch_max_n(pdr_ctx* ctx, const pdr_batch* b, cudaStream_t s, uint32_t* max_n) {
+  *max_n = b->max_event_size;
+  if (*max_n == 0 && b->n_events > 0) return max_event_size_impl(ctx, b, s, max_n);
+  return PDR_OK;
 }
 
 }  // namespace
@@ -646,10 +709,31 @@ int pdr_run(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_la
   if ((rc = check_outputs(o))) return rc;
   cudaSetDevice(ctx->device);
   std::lock_guard<std::mutex> g(ctx->mu);
-  Shape S;
   uint32_t max_n = 0;
-  if ((rc = resolve_shape(ctx, b, l, (cudaStream_t)stream, max_n, S))) return rc;
-  return run_shape(ctx, b, o, S, max_n, (cudaStream_t)stream);
+  if ((rc = batch_max_n(ctx, b, (cudaStream_t)stream, &max_n))) return rc;
+  return launch_batches(ctx, b, o, 1, plan_launch(ctx, b->card_id, max_n, l), max_n, (cudaStream_t)stream);
+}
+
+int pdr_run_multi(pdr_ctx* ctx, const pdr_batch* bs, uint32_t n, const pdr_outputs* os, const pdr_launch* l,
+                  void* stream) {
+  if (!ctx || (n > 0 && (!bs || !os))) return fail(PDR_EINVAL, "null argument");
+  for (uint32_t k = 0; k < n; ++k) {
+    int rc = check_batch(ctx, &bs[k]);
+    if (rc) return rc;
+    if ((rc = check_outputs(&os[k]))) return rc;
+  }
+  if (n == 0) return PDR_OK;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t max_n = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    uint32_t m = 0;
+    int rc = batch_max_n(ctx, &bs[k], s, &m);
+    if (rc) return rc;
+    max_n = std::max(max_n, m);
+  }
+  return launch_batches(ctx, bs, os, n, plan_launch(ctx, bs[0].card_id, max_n, l), max_n, s);
 }
 
 int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* stream) {
@@ -659,11 +743,21 @@ int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, vo
   cudaSetDevice(ctx->device);
   std::lock_guard<std::mutex> g(ctx->mu);
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t max_n = b->max_event_size;
-  if (max_n == 0 && b->n_events > 0 && (rc = max_event_size_impl(ctx, b, s, &max_n))) return rc;
+  uint32_t max_n = 0;
+  if ((rc = batch_max_n(ctx, b, s, &max_n))) return rc;
+  const CardEntry& ce = ctx->cards[b->card_id];
   Shape S;
-  if ((rc = make_shape(ctx, 256, 256, slots_for(max_n), 1, ctx->cards[b->card_id].hot_bytes, S))) return rc;
+  if ((rc = make_shape(ctx, 256, 256, slots_for(max_n), 1, ce.hot_bytes, S))) return rc;
   S.grid = 1;
+  static thread_local KParams p;
+  std::memset(&p, 0, sizeof p);
+  p.n_cards = 1;
+  p.hot[0] = ce.hot;
+  p.hot_bytes[0] = ce.hot_bytes;
+  p.hot_total = ce.hot_bytes;
+  p.n_segs = 1;
+  p.n_events = 1;
+  if ((rc = set_tables(ctx, p, S, max_n))) return rc;
   for (uint64_t e = 0; e < b->n_events; ++e) {
     pdr_batch one = *b;
     one.n_events = 1;
@@ -671,7 +765,8 @@ int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, vo
     one.event_index_base = b->event_index_base + (uint32_t)e;
     pdr_outputs oe = *o;
     oe.counts = o->counts + 4 * e;
-    if ((rc = run_shape(ctx, &one, &oe, S, max_n, s))) return rc;
+    fill_seg(p.seg[0], &one, &oe, 0, 0);
+    PDR_CUDA(launch_fused(S.team, S.block, p, S.grid, S.smem, s), "fused kernel launch");
   }
   return PDR_OK;
 }
@@ -721,9 +816,10 @@ int pdr_autotune(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* s
         if (make_shape(ctx, team, block, want, 0, ctx->cards[b->card_id].hot_bytes, S) != PDR_OK) continue;
         // a team must not walk a huge event alone in tiny chunks
         if (team == 32 && max_n > 1024) continue;
-        if (run_shape(ctx, b, o, S, max_n, s) != PDR_OK) continue;  // warm-up
+        const Plan P{team, block, want, 0};
+        if (launch_batches(ctx, b, o, 1, P, max_n, s) != PDR_OK) continue;  // warm-up
         cudaEventRecord(e0, s);
-        if (run_shape(ctx, b, o, S, max_n, s) != PDR_OK) continue;
+        if (launch_batches(ctx, b, o, 1, P, max_n, s) != PDR_OK) continue;
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0;
@@ -814,10 +910,9 @@ int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const
   db.flags &= ~PDR_BATCH_DEBUG;
   {
     std::lock_guard<std::mutex> g2(ctx->mu);
-    Shape S;
     uint32_t max_n = 0;
-    if ((rc = resolve_shape(ctx, &db, l, s, max_n, S))) return done(rc);
-    if ((rc = run_shape(ctx, &db, &so, S, max_n, s))) return done(rc);
+    if ((rc = batch_max_n(ctx, &db, s, &max_n))) return done(rc);
+    if ((rc = launch_batches(ctx, &db, &so, 1, plan_launch(ctx, db.card_id, max_n, l), max_n, s))) return done(rc);
   }
   if (ne > 0) {
     cudaError_t e = launch_dense(db.offsets, ne, so.counts, dense_off, so, dd, ctx->n_sms, s);
@@ -887,9 +982,9 @@ int pdr_submit(pdr_ctx* ctx, const pdr_batch* b, void* stream, uint64_t* ticket)
   uint64_t* offs = (uint64_t*)carve((b->n_events + 1) * 8);
   if (b->n_events > 0)
     PDR_CUDA(cudaMemcpyAsync(offs, b->offsets, (b->n_events + 1) * 8, cudaMemcpyDeviceToDevice, s), "copy offsets");
-  Shape S;
   uint32_t max_n = 0;
-  if ((rc = resolve_shape(ctx, b, nullptr, s, max_n, S)) || (rc = run_shape(ctx, b, &o, S, max_n, s))) {
+  if ((rc = batch_max_n(ctx, b, s, &max_n)) ||
+      (rc = launch_batches(ctx, b, &o, 1, plan_launch(ctx, b->card_id, max_n, nullptr), max_n, s))) {
     ctx->pool.release(t.mem);
     return rc;
   }

@@ -205,6 +205,42 @@ def test_rerun_and_per_event_form_are_bitwise_identical(ctx, cards, synth):
     _same(h1, h3, b)
 
 
+def _host(o, n_events):
+    h = {k: (v.cpu().numpy() if v is not None else None) for k, v in o.items()}
+    h["counts"] = h["counts"].view(np.uint32)[:n_events]
+    return h
+
+
+def test_multi_card_launch_matches_single_batches(B, ctx, cards, synth):
+    """Batches of different cards in one fused launch give each batch's own bits;
+    40 batches over 5 card loads exercise the split into several launches."""
+    specs = [("batched", "cms_like", 30, 1), ("ee", "ee_like", 120, 2), ("batched", "atlas_like", 25, 3),
+             ("pileup", "cms_like", 2, 4)]
+    extra = [ctx.card_load("cms_like"), ctx.card_load("ee_like")]  # same tables, distinct card ids
+    for k in range(36):
+        specs.append(("tiny", ["cms_like", "atlas_like", "ee_like"][k % 3], 3 + k % 5, 10 + k))
+    batches, singles, devs, outs = [], [], [], []
+    for k, (wl, card, nev, seed) in enumerate(specs):
+        b = synth.make(wl, n_events=nev)
+        cid = cards[card][0] if k < 38 else extra[k - 38]
+        dev = B.batch_to_device(b)
+        devs.append(dev)
+        o = B.alloc_outputs(b.n_events, b.n_particles, debug=True)
+        outs.append(o)
+        bt = B.make_batch(dev, cid, seed, event_base=100 * k, debug=True)
+        batches.append(bt)
+        singles.append(P.run_gpu(ctx, cid, b, seed, event_base=100 * k, debug=True, dev=dev))
+        singles[-1]["batch"] = b
+    ctx.run_multi(batches, [B.make_outputs(o) for o in outs])
+    torch.cuda.synchronize()
+    ctx.check()
+    for k, o in enumerate(outs):
+        b = singles[k]["batch"]
+        h = _host(o, b.n_events)
+        _same(singles[k], h, b)
+        assert np.array_equal(singles[k]["debug"].view(np.uint32), h["debug"].view(np.uint32))
+
+
 def test_results_do_not_depend_on_batching(ctx, cards, synth):
     cid, _ = cards["cms_like"]
     b = synth.make("batched", n_events=30)
