@@ -300,6 +300,43 @@ int pdr_fetch(pdr_ctx* ctx, uint64_t ticket, pdr_result* r);
 /* Return a ticket's buffers to the pool. */
 int pdr_release(pdr_ctx* ctx, uint64_t ticket);
 
+/* ---------------------------------------------------------------- serving -- */
+/* A request loop on the device's behalf: requests (HOST batches) are admitted
+ * in arrival order as soon as the context pool has room for their inputs and
+ * results (admission by free device memory), their inputs are copied on a copy
+ * stream, and admitted requests are grouped into waves - one fused launch of
+ * up to 32 requests and 4 cards, replayed from a captured CUDA graph per launch
+ * shape - while up to max_inflight_waves waves run, so requests that arrive
+ * while others are on the GPU join the next wave (continuous batching).  Card
+ * tables stay on the device; random numbers are counter-based, so a request's
+ * results are the bits it gets alone (pdr_run with the same batch).  Tickets
+ * are the same as pdr_submit's: pdr_wait / pdr_fetch (device results in the
+ * slot layout of pdr_outputs) / pdr_release (which returns the memory used by
+ * admission). */
+typedef struct pdr_serve_options {
+  uint32_t max_inflight_waves;   /* waves on the device at once (0: 2)            */
+  uint32_t max_wave_requests;    /* requests in one wave (0 or > 32: 32)          */
+  uint64_t max_wave_particles;   /* particles in one wave (0: 64M)                */
+  uint32_t use_graphs;           /* 1: replay captured graphs, 0: plain launches  */
+  uint32_t flags;                /* reserved, 0                                   */
+} pdr_serve_options;
+
+typedef struct pdr_serve_stats {
+  uint64_t requests_done, events_done, particles_done, waves, admission_waits, graph_launches;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* submit -> results complete on the device */
+  double span_s;                           /* first submit -> last completion          */
+} pdr_serve_stats;
+
+/* Start the loop (one per context).  opt may be NULL. */
+int pdr_serve_start(pdr_ctx* ctx, const pdr_serve_options* opt);
+/* Queue a request: HOST pointers (pinned memory copies fastest) that the caller
+ * keeps alive and unchanged until pdr_wait returns PDR_OK.  Returns at once. */
+int pdr_serve_submit(pdr_ctx* ctx, const pdr_batch* host_batch, uint64_t* ticket);
+/* Latency and throughput of the requests completed so far. */
+int pdr_serve_stats_get(pdr_ctx* ctx, pdr_serve_stats* out);
+/* Finish queued and running requests, then stop the loop. */
+int pdr_serve_stop(pdr_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,20 @@ class pdr_options(C.Structure):
     _fields_ = [("pool_bytes", C.c_uint64), ("max_tickets", C.c_uint32), ("flags", C.c_uint32)]
 
 
+class pdr_serve_options(C.Structure):
+    _fields_ = [("max_inflight_waves", C.c_uint32), ("max_wave_requests", C.c_uint32),
+                ("max_wave_particles", C.c_uint64), ("use_graphs", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class pdr_serve_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("requests_done", "events_done", "particles_done", "waves",
+                                          "admission_waits", "graph_launches")] + [
+        (n, C.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "span_s")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class pdr_result(C.Structure):
     _fields_ = [("n_events", C.c_uint64), ("n_particles", C.c_uint64)] + [
         (n, C.c_void_p) for n in ("offsets", "counts", "tracks", "towers", "eflow", "cands", "iso", "debug")]
@@ -123,6 +137,11 @@ def lib():
             "pdr_wait": ([P, C.c_uint64, I], I),
             "pdr_fetch": ([P, C.c_uint64, C.POINTER(pdr_result)], I),
             "pdr_release": ([P, C.c_uint64], I),
+            "pdr_serve_start": ([P, C.POINTER(pdr_serve_options)], I),
+            "pdr_serve_submit": ([P, C.POINTER(pdr_batch), C.POINTER(C.c_uint64)], I),
+            "pdr_serve_stats_get": ([P, C.POINTER(pdr_serve_stats)], I),
+            "pdr_serve_stop": ([P], I),
+            "pdr_run_noalloc": ([C.POINTER(pdr_card), C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -354,6 +373,71 @@ class Context:
 
     def release(self, ticket: int):
         self._check(self.L.pdr_release(self.h, ticket), "pdr_release")
+
+    # ---- serving
+    def serve_start(self, max_inflight_waves=0, max_wave_requests=0, max_wave_particles=0, use_graphs=1):
+        o = pdr_serve_options(max_inflight_waves, max_wave_requests, max_wave_particles, use_graphs, 0)
+        self._check(self.L.pdr_serve_start(self.h, C.byref(o)), "pdr_serve_start")
+
+    def serve_submit(self, host_batch: pdr_batch) -> int:
+        t = C.c_uint64()
+        self._check(self.L.pdr_serve_submit(self.h, C.byref(host_batch), C.byref(t)), "pdr_serve_submit")
+        return t.value
+
+    def serve_stats(self) -> dict:
+        st = pdr_serve_stats()
+        self._check(self.L.pdr_serve_stats_get(self.h, C.byref(st)), "pdr_serve_stats_get")
+        return st.as_dict()
+
+    def serve_stop(self):
+        self._check(self.L.pdr_serve_stop(self.h), "pdr_serve_stop")
+
+
+def pinned_host_batch(batch, card_id: int, seed: int, event_base: int = 0):
+    """A pdr_batch with HOST pointers into pinned copies of a synth.EventBatch.
+
+    Returns (pdr_batch, keepalive) - keep the second value alive while the
+    library may read the arrays."""
+    import torch
+    keep = {}
+    b = pdr_batch()
+    b.n_events = batch.n_events
+    for k in ("offsets", "pt", "eta", "phi", "mass", "pdg", "charge", "vz"):
+        v = getattr(batch, k)
+        if v is None:
+            setattr(b, k, None)
+            continue
+        a = np.ascontiguousarray(v)
+        if k == "offsets":
+            a = a.astype(np.int64)
+        t = torch.from_numpy(a).pin_memory()
+        keep[k] = t
+        setattr(b, k, t.data_ptr())
+    b.seed = seed & (2**64 - 1)
+    b.event_index_base = event_base & 0xFFFFFFFF
+    b.card_id = card_id
+    b.max_event_size = int(batch.multiplicities().max()) if batch.n_events else 0
+    b.flags = 0
+    return b, keep
+
+
+def result_to_host(res: pdr_result) -> dict:
+    """Copy a pdr_result (device, slot layout) into host numpy arrays."""
+    cudart = C.CDLL("libcudart.so.13")
+    cudart.cudaMemcpy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+    n, ne = int(res.n_particles), int(res.n_events)
+    cap = max(n, 1)
+    out = dict(tracks=np.zeros((cap, 4), np.float32), towers=np.zeros((cap, 3), np.float32),
+               eflow=np.zeros((cap, 3), np.float32), cands=np.zeros((cap, 4), np.float32),
+               iso=np.zeros((cap, 2), np.float32), counts=np.zeros((max(ne, 1), 4), np.uint32),
+               offsets=np.zeros(ne + 1, np.uint64))
+    for k in ("tracks", "towers", "eflow", "cands", "iso", "counts", "offsets"):
+        src = getattr(res, k)
+        if src and out[k].nbytes:
+            nb = out[k][:ne].nbytes if k == "counts" else out[k].nbytes
+            assert cudart.cudaMemcpy(out[k].ctypes.data, src, nb, 2) == 0, k
+    out["counts"] = out["counts"][:ne]
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -4,7 +4,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -143,6 +147,7 @@ struct Ticket {
   cudaEvent_t done = nullptr;
   void* mem = nullptr;
   pdr_result res{};
+  int state = 2;   // 0 queued (serving), 1 inputs on the device, 2 launched (done is recorded), -1 failed
 };
 
 }  // namespace
@@ -151,6 +156,8 @@ namespace pdr {
 // Record a failure message for pdr_last_error from other files of the library.
 int set_last_error(int code, const char* msg) { return fail(code, msg); }
 }  // namespace pdr
+
+struct Server;  // the serving loop (defined with its code below)
 
 struct pdr_ctx {
   int device = 0;
@@ -168,6 +175,7 @@ struct pdr_ctx {
   std::map<uint64_t, pdr_launch> tuned;  // (card, size class) -> shape
   unsigned char* gscratch = nullptr;      // global tower tables for large events
   uint64_t gscratch_bytes = 0;
+  Server* serve = nullptr;                // serving loop, if started
   std::mutex mu;
 };
 
@@ -513,11 +521,10 @@ int set_tables(pdr_ctx* ctx, KParams& p, const Shape& S, uint32_t max_n) {
   return PDR_OK;
 }
 
-// One fused launch over up to PDR_LAUNCH_SEGS batches using up to
-// PDR_LAUNCH_CARDS distinct cards (the caller groups them).
-int launch_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* const* os, uint32_t n,
-                 const Plan& P, uint32_t max_n, cudaStream_t s) {
-  static thread_local KParams p;  // 5 KB: keep it off the stack
+// Parameter block and shape of one fused launch over up to PDR_LAUNCH_SEGS
+// batches using up to PDR_LAUNCH_CARDS distinct cards (the caller groups them).
+int prepare_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* const* os, uint32_t n,
+                  const Plan& P, uint32_t max_n, KParams& p, Shape& S) {
   std::memset(&p, 0, sizeof p);
   uint64_t start = 0;
   for (uint32_t k = 0; k < n; ++k) {
@@ -538,11 +545,18 @@ int launch_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* co
   }
   p.n_segs = n;
   p.n_events = start;
-  if (p.n_events == 0) return PDR_OK;
-  Shape S;
   int rc = make_shape(ctx, P.team, P.block, P.want_slots, P.grid, p.hot_total, S);
   if (rc) return rc;
-  if ((rc = set_tables(ctx, p, S, max_n))) return rc;
+  return set_tables(ctx, p, S, max_n);
+}
+
+int launch_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* const* os, uint32_t n,
+                 const Plan& P, uint32_t max_n, cudaStream_t s) {
+  static thread_local KParams p;  // 5 KB: keep it off the stack
+  Shape S;
+  int rc = prepare_group(ctx, bs, os, n, P, max_n, p, S);
+  if (rc) return rc;
+  if (p.n_events == 0) return PDR_OK;
   PDR_CUDA(launch_fused(S.team, S.block, p, S.grid, S.smem, s), "fused kernel launch");
   return PDR_OK;
 }
@@ -625,6 +639,7 @@ int pdr_create(pdr_ctx** out, int cuda_device, const pdr_options* opt) {
 
 int pdr_destroy(pdr_ctx* ctx) {
   if (!ctx) return PDR_OK;
+  if (ctx->serve) pdr_serve_stop(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   for (auto& kv : ctx->tickets)
@@ -1010,19 +1025,24 @@ int pdr_submit(pdr_ctx* ctx, const pdr_batch* b, void* stream, uint64_t* ticket)
 
 int pdr_wait(pdr_ctx* ctx, uint64_t ticket, int timeout_ms) {
   if (!ctx) return fail(PDR_EINVAL, "null context");
-  cudaEvent_t ev;
-  {
-    std::lock_guard<std::mutex> g(ctx->mu);
-    auto it = ctx->tickets.find(ticket);
-    if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
-    ev = it->second.done;
-  }
   cudaSetDevice(ctx->device);
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
-    cudaError_t e = cudaEventQuery(ev);
-    if (e == cudaSuccess) break;
-    if (e != cudaErrorNotReady) return cuda_fail(e, "ticket");
+    cudaEvent_t ev = nullptr;
+    int state;
+    {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      auto it = ctx->tickets.find(ticket);
+      if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
+      state = it->second.state;
+      ev = it->second.done;
+    }
+    if (state < 0) return fail(PDR_EDEVICE, "the request failed");
+    if (state == 2) {
+      cudaError_t e = cudaEventQuery(ev);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return cuda_fail(e, "ticket");
+    }
     if (timeout_ms >= 0 &&
         std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
       return fail(PDR_ETIMEDOUT, "ticket still running");
@@ -1036,7 +1056,8 @@ int pdr_fetch(pdr_ctx* ctx, uint64_t ticket, pdr_result* r) {
   std::lock_guard<std::mutex> g(ctx->mu);
   auto it = ctx->tickets.find(ticket);
   if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
-  if (cudaEventQuery(it->second.done) != cudaSuccess) return fail(PDR_EBUSY, "ticket not finished");
+  if (it->second.state != 2 || cudaEventQuery(it->second.done) != cudaSuccess)
+    return fail(PDR_EBUSY, "ticket not finished");
   *r = it->second.res;
   return PDR_OK;
 }
@@ -1046,11 +1067,409 @@ int pdr_release(pdr_ctx* ctx, uint64_t ticket) {
   std::lock_guard<std::mutex> g(ctx->mu);
   auto it = ctx->tickets.find(ticket);
   if (it == ctx->tickets.end()) return fail(PDR_ENOTFOUND, "unknown ticket");
+  if (it->second.state == 0 || it->second.state == 1) return fail(PDR_EBUSY, "request not launched yet");
   cudaSetDevice(ctx->device);
-  cudaEventSynchronize(it->second.done);
+  if (it->second.state == 2) cudaEventSynchronize(it->second.done);
   cudaEventDestroy(it->second.done);
   ctx->pool.release(it->second.mem);
   ctx->tickets.erase(it);
+  return PDR_OK;
+}
+
+}  // extern "C"
+
+// =================================================================== serving
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct ServeReq {
+  uint64_t ticket = 0;
+  pdr_batch hb{};         // caller's host batch
+  pdr_batch db{};         // device copy of the inputs
+  pdr_outputs o{};        // device results
+  unsigned char* mem = nullptr;
+  uint64_t np = 0, bytes = 0;
+  uint32_t max_n = 0;
+  bool waited = false;
+  cudaEvent_t in_ready = nullptr;
+  Clock::time_point t_submit;
+};
+
+struct Wave {
+  cudaEvent_t done = nullptr;
+  std::vector<ServeReq*> reqs;
+};
+
+struct GraphSlot {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t node = nullptr;
+};
+
+}  // namespace
+
+struct Server {
+  pdr_serve_options opt{};
+  std::thread th;
+  std::mutex m;  // arrivals, stop, statistics
+  std::condition_variable cv;
+  std::deque<ServeReq*> arrivals;
+  std::deque<ServeReq*> admitted;
+  std::deque<Wave> inflight;
+  bool stop = false;
+  cudaStream_t s_copy = nullptr, s_comp = nullptr, s_cap = nullptr;
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t, size_t>, GraphSlot> graphs;
+  std::vector<double> lat_ms;
+  uint64_t requests_done = 0, events_done = 0, particles_done = 0, waves = 0, admission_waits = 0,
+           graph_launches = 0;
+  Clock::time_point t_first, t_last;
+  bool any = false;
+};
+
+namespace {
+
+// Carve a request's device memory and queue its input copies (ctx->mu held).
+void serve_admit(pdr_ctx* ctx, Server& sv, ServeReq* r) {
+  unsigned char* m = r->mem;
+  auto carve = [&](uint64_t bytes) {
+    unsigned char* q = m;
+    m += (bytes + 255) & ~255ull;
+    return (void*)q;
+  };
+  const uint64_t ne = r->hb.n_events, np = r->np, cap = np ? np : 1;
+  r->db = r->hb;
+  r->db.offsets = (const uint64_t*)carve((ne + 1) * 8);
+  r->db.pt = (const float*)carve(np * 4);
+  r->db.eta = (const float*)carve(np * 4);
+  r->db.phi = (const float*)carve(np * 4);
+  r->db.mass = (const float*)carve(np * 4);
+  r->db.pdg = (const int32_t*)carve(np * 4);
+  r->db.charge = (const int8_t*)carve(np);
+  r->db.vz = r->hb.vz ? (const float*)carve(np * 4) : nullptr;
+  r->db.max_event_size = r->max_n;
+  r->db.flags &= ~PDR_BATCH_DEBUG;
+  r->o.tracks = (pdr_track*)carve(cap * sizeof(pdr_track));
+  r->o.towers = (pdr_tower*)carve(cap * sizeof(pdr_tower));
+  r->o.eflow = (pdr_eflow*)carve(cap * sizeof(pdr_eflow));
+  r->o.cands = (pdr_cand*)carve(cap * sizeof(pdr_cand));
+  r->o.iso = (pdr_iso*)carve(cap * sizeof(pdr_iso));
+  r->o.counts = (uint32_t*)carve((ne + 1) * 16);
+  r->o.debug = nullptr;
+  cudaStream_t s = sv.s_copy;
+  cudaMemcpyAsync((void*)r->db.offsets, r->hb.offsets, (ne + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (np) {
+    cudaMemcpyAsync((void*)r->db.pt, r->hb.pt, np * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)r->db.eta, r->hb.eta, np * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)r->db.phi, r->hb.phi, np * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)r->db.mass, r->hb.mass, np * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)r->db.pdg, r->hb.pdg, np * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)r->db.charge, r->hb.charge, np, cudaMemcpyHostToDevice, s);
+    if (r->hb.vz) cudaMemcpyAsync((void*)r->db.vz, r->hb.vz, np * 4, cudaMemcpyHostToDevice, s);
+  }
+  cudaEventRecord(r->in_ready, s);
+  Ticket& t = ctx->tickets[r->ticket];
+  t.mem = r->mem;
+  t.state = 1;
+  t.res.n_events = ne;
+  t.res.n_particles = np;
+  t.res.offsets = r->db.offsets;
+  t.res.counts = r->o.counts;
+  t.res.tracks = r->o.tracks;
+  t.res.towers = r->o.towers;
+  t.res.eflow = r->o.eflow;
+  t.res.cands = r->o.cands;
+  t.res.iso = r->o.iso;
+  t.res.debug = nullptr;
+}
+
+// Launch a prepared parameter block through a captured graph of its shape.
+cudaError_t graph_launch(Server& sv, const KParams& p, const Shape& S) {
+  const auto key = std::make_tuple(S.team, S.block, S.grid, S.smem);
+  auto it = sv.graphs.find(key);
+  if (it == sv.graphs.end()) {
+    GraphSlot g;
+    cudaError_t e = cudaStreamBeginCapture(sv.s_cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = launch_fused(S.team, S.block, p, S.grid, S.smem, sv.s_cap);
+    e = cudaStreamEndCapture(sv.s_cap, &g.graph);
+    if (le != cudaSuccess) return le;
+    if (e != cudaSuccess) return e;
+    size_t nn = 1;
+    if ((e = cudaGraphGetNodes(g.graph, &g.node, &nn)) != cudaSuccess) return e;
+    if (nn != 1) return cudaErrorUnknown;
+    if ((e = cudaGraphInstantiate(&g.exec, g.graph, 0)) != cudaSuccess) return e;
+    it = sv.graphs.emplace(key, g).first;
+  } else {
+    cudaKernelNodeParams kp;
+    cudaError_t e = cudaGraphKernelNodeGetParams(it->second.node, &kp);
+    if (e != cudaSuccess) return e;
+    void* args[1] = {(void*)&p};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if ((e = cudaGraphExecKernelNodeSetParams(it->second.exec, it->second.node, &kp)) != cudaSuccess) return e;
+  }
+  ++sv.graph_launches;
+  return cudaGraphLaunch(it->second.exec, sv.s_comp);
+}
+
+void fail_wave(pdr_ctx* ctx, std::vector<ServeReq*>& reqs) {
+  for (ServeReq* r : reqs) {
+    auto it = ctx->tickets.find(r->ticket);
+    if (it != ctx->tickets.end()) it->second.state = -1;
+    cudaEventDestroy(r->in_ready);
+    delete r;
+  }
+  reqs.clear();
+}
+
+// One wave: the first admitted requests (up to the limits), one fused launch.
+bool serve_launch_wave(pdr_ctx* ctx, Server& sv) {
+  std::vector<ServeReq*> reqs;
+  std::vector<uint32_t> cards;
+  uint64_t particles = 0;
+  uint32_t max_n = 0;
+  const uint32_t max_req = std::min<uint32_t>(sv.opt.max_wave_requests, PDR_LAUNCH_SEGS);
+  while (!sv.admitted.empty() && reqs.size() < max_req) {
+    ServeReq* r = sv.admitted.front();
+    const bool new_card = std::find(cards.begin(), cards.end(), r->hb.card_id) == cards.end();
+    if (new_card && cards.size() == PDR_LAUNCH_CARDS) break;
+    if (!reqs.empty() && particles + r->np > sv.opt.max_wave_particles) break;
+    if (new_card) cards.push_back(r->hb.card_id);
+    sv.admitted.pop_front();
+    reqs.push_back(r);
+    particles += r->np;
+    max_n = std::max(max_n, r->max_n);
+  }
+  if (reqs.empty()) return false;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  std::vector<const pdr_batch*> bs;
+  std::vector<const pdr_outputs*> os;
+  for (ServeReq* r : reqs) {
+    cudaStreamWaitEvent(sv.s_comp, r->in_ready, 0);
+    bs.push_back(&r->db);
+    os.push_back(&r->o);
+  }
+  static thread_local KParams p;
+  Shape S;
+  const Plan P = plan_launch(ctx, reqs[0]->hb.card_id, max_n, nullptr);
+  int rc = prepare_group(ctx, bs.data(), os.data(), (uint32_t)bs.size(), P, max_n, p, S);
+  cudaError_t e = cudaSuccess;
+  if (rc == PDR_OK && p.n_events > 0)
+    e = sv.opt.use_graphs ? graph_launch(sv, p, S) : launch_fused(S.team, S.block, p, S.grid, S.smem, sv.s_comp);
+  if (rc != PDR_OK || e != cudaSuccess) {
+    fail_wave(ctx, reqs);
+    return true;
+  }
+  Wave w;
+  cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+  for (ServeReq* r : reqs) {
+    Ticket& t = ctx->tickets[r->ticket];
+    cudaEventRecord(t.done, sv.s_comp);
+    t.state = 2;
+  }
+  cudaEventRecord(w.done, sv.s_comp);
+  w.reqs = std::move(reqs);
+  sv.inflight.push_back(std::move(w));
+  return true;
+}
+
+void serve_loop(pdr_ctx* ctx) {
+  Server& sv = *ctx->serve;
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    bool progress = false;
+    // admission in arrival order, while the pool has room
+    for (;;) {
+      ServeReq* r = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(sv.m);
+        if (!sv.arrivals.empty()) r = sv.arrivals.front();
+      }
+      if (!r) break;
+      bool ok = false;
+      {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        r->mem = (unsigned char*)ctx->pool.alloc(r->bytes);
+        if (r->mem) {
+          serve_admit(ctx, sv, r);
+          ok = true;
+        }
+      }
+      std::lock_guard<std::mutex> lk(sv.m);
+      if (!ok) {
+        if (!r->waited) { r->waited = true; ++sv.admission_waits; }
+        break;
+      }
+      sv.arrivals.pop_front();
+      sv.admitted.push_back(r);
+      progress = true;
+    }
+    // waves
+    while (sv.inflight.size() < sv.opt.max_inflight_waves && !sv.admitted.empty())
+      progress |= serve_launch_wave(ctx, sv);
+    // completions (waves finish in launch order on the compute stream)
+    while (!sv.inflight.empty() && cudaEventQuery(sv.inflight.front().done) == cudaSuccess) {
+      Wave& w = sv.inflight.front();
+      const Clock::time_point now = Clock::now();
+      {
+        std::lock_guard<std::mutex> lk(sv.m);
+        for (ServeReq* r : w.reqs) {
+          sv.lat_ms.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
+          ++sv.requests_done;
+          sv.events_done += r->hb.n_events;
+          sv.particles_done += r->np;
+        }
+        ++sv.waves;
+        sv.t_last = now;
+      }
+      for (ServeReq* r : w.reqs) {
+        cudaEventDestroy(r->in_ready);
+        delete r;
+      }
+      cudaEventDestroy(w.done);
+      sv.inflight.pop_front();
+      progress = true;
+    }
+    std::unique_lock<std::mutex> lk(sv.m);
+    if (sv.stop && sv.arrivals.empty() && sv.admitted.empty() && sv.inflight.empty()) break;
+    if (!progress) sv.cv.wait_for(lk, std::chrono::microseconds(50));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdr_serve_start(pdr_ctx* ctx, const pdr_serve_options* opt) {
+  if (!ctx) return fail(PDR_EINVAL, "null context");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (ctx->serve) return fail(PDR_EBUSY, "serving loop already running");
+  cudaSetDevice(ctx->device);
+  Server* sv = new Server();
+  if (opt) sv->opt = *opt;
+  else sv->opt.use_graphs = 1;
+  if (sv->opt.max_inflight_waves == 0) sv->opt.max_inflight_waves = 2;
+  if (sv->opt.max_wave_requests == 0 || sv->opt.max_wave_requests > PDR_LAUNCH_SEGS)
+    sv->opt.max_wave_requests = PDR_LAUNCH_SEGS;
+  if (sv->opt.max_wave_particles == 0) sv->opt.max_wave_particles = 64ull << 20;
+  if (cudaStreamCreateWithFlags(&sv->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sv->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sv->s_cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete sv;
+    return fail(PDR_EDEVICE, "cannot create serving streams");
+  }
+  ctx->serve = sv;
+  sv->th = std::thread(serve_loop, ctx);
+  return PDR_OK;
+}
+
+int pdr_serve_submit(pdr_ctx* ctx, const pdr_batch* hb, uint64_t* ticket) {
+  int rc = check_batch(ctx, hb);
+  if (rc) return rc;
+  if (!ticket) return fail(PDR_EINVAL, "null ticket");
+  if (!ctx->serve) return fail(PDR_EINVAL, "serving loop not started");
+  ServeReq* r = new ServeReq();
+  r->hb = *hb;
+  const uint64_t ne = hb->n_events;
+  r->np = ne ? hb->offsets[ne] : 0;
+  uint32_t mx = 0;
+  for (uint64_t e = 0; e < ne; ++e) {
+    if (hb->offsets[e + 1] < hb->offsets[e]) {
+      delete r;
+      return fail(PDR_EINVAL, "offsets not monotone");
+    }
+    mx = std::max<uint32_t>(mx, (uint32_t)(hb->offsets[e + 1] - hb->offsets[e]));
+  }
+  r->max_n = mx;
+  const uint64_t cap = r->np ? r->np : 1;
+  r->bytes = (ne + 1) * (8 + 16) + r->np * (4 * 4 + 4 + 1) + (hb->vz ? r->np * 4 : 0) +
+             cap * (sizeof(pdr_track) + sizeof(pdr_tower) + sizeof(pdr_eflow) + sizeof(pdr_cand) +
+                    sizeof(pdr_iso)) + 16 * 256;
+  cudaSetDevice(ctx->device);
+  Ticket t;
+  t.state = 0;
+  if (cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->in_ready, cudaEventDisableTiming) != cudaSuccess) {
+    delete r;
+    return fail(PDR_EDEVICE, "cannot create events");
+  }
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (r->bytes > ctx->pool.size) {
+      cudaEventDestroy(t.done);
+      cudaEventDestroy(r->in_ready);
+      delete r;
+      return fail(PDR_ENOMEM, "request larger than the device pool");
+    }
+    r->ticket = ctx->next_ticket++;
+    ctx->tickets[r->ticket] = t;
+  }
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(ctx->serve->m);
+    if (!ctx->serve->any) {
+      ctx->serve->any = true;
+      ctx->serve->t_first = r->t_submit;
+    }
+    ctx->serve->arrivals.push_back(r);
+  }
+  ctx->serve->cv.notify_one();
+  *ticket = r->ticket;
+  return PDR_OK;
+}
+
+int pdr_serve_stats_get(pdr_ctx* ctx, pdr_serve_stats* out) {
+  if (!ctx || !out) return fail(PDR_EINVAL, "null argument");
+  if (!ctx->serve) return fail(PDR_EINVAL, "serving loop not started");
+  Server& sv = *ctx->serve;
+  std::lock_guard<std::mutex> lk(sv.m);
+  std::memset(out, 0, sizeof *out);
+  out->requests_done = sv.requests_done;
+  out->events_done = sv.events_done;
+  out->particles_done = sv.particles_done;
+  out->waves = sv.waves;
+  out->admission_waits = sv.admission_waits;
+  out->graph_launches = sv.graph_launches;
+  if (!sv.lat_ms.empty()) {
+    std::vector<double> v = sv.lat_ms;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double f) { return v[std::min<size_t>(v.size() - 1, (size_t)(f * (double)(v.size() - 1) + 0.5))]; };
+    out->p50_ms = q(0.50);
+    out->p99_ms = q(0.99);
+    out->max_ms = v.back();
+    double sum = 0;
+    for (double x : v) sum += x;
+    out->mean_ms = sum / (double)v.size();
+    out->span_s = std::chrono::duration<double>(sv.t_last - sv.t_first).count();
+  }
+  return PDR_OK;
+}
+
+int pdr_serve_stop(pdr_ctx* ctx) {
+  if (!ctx) return fail(PDR_EINVAL, "null context");
+  Server* sv = ctx->serve;
+  if (!sv) return PDR_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->m);
+    sv->stop = true;
+  }
+  sv->cv.notify_one();
+  if (sv->th.joinable()) sv->th.join();
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(sv->s_comp);
+  for (auto& kv : sv->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
+  cudaStreamDestroy(sv->s_copy);
+  cudaStreamDestroy(sv->s_comp);
+  cudaStreamDestroy(sv->s_cap);
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->serve = nullptr;
+  }
+  delete sv;
   return PDR_OK;
 }
 
