@@ -285,10 +285,105 @@ def bench_ours(args, dist, rank, ws):
         "clocks": clk,
         "gpu_launches": args.steps,
     }
+    if not args.no_serving and ws == 1:
+        line["serving"] = bench_serving(args, B, ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, card_name, args.seed, args.cpu_seconds)
     ctx.close()
     return line
+
+
+def bench_serving(args, B, ctx):
+    """Continuous-batching serving loop vs one plain launch per request, on the
+    same Poisson arrival schedules; latency = submit -> results on the device."""
+    import threading as th
+
+    import torch
+
+    from paper_2606_26089_b300 import synth
+
+    pools = synth.serving_pools(args.serving_pool)
+    cards = {n: ctx.card_load(n) for n in synth.SERVING_CARDS}
+    pinned = {}
+    for g, pb in pools.items():
+        pinned[g] = {k: (None if getattr(pb, k) is None else
+                         torch.from_numpy(np.ascontiguousarray(getattr(pb, k))).pin_memory())
+                     for k in ("pt", "eta", "phi", "mass", "pdg", "charge", "vz")}
+
+    def host_batch(r):
+        pb = pools[r.generator]
+        off = (pb.offsets[r.start:r.start + r.n_events + 1] - pb.offsets[r.start]).astype(np.int64)
+        o = torch.from_numpy(off).pin_memory()
+        a0 = int(pb.offsets[r.start])
+        hb = B.pdr_batch()
+        hb.n_events = r.n_events
+        hb.offsets = o.data_ptr()
+        for k, t in pinned[r.generator].items():
+            setattr(hb, k, None if t is None else t.data_ptr() + a0 * t.element_size())
+        hb.seed, hb.event_index_base, hb.card_id, hb.flags = r.seed, 0, cards[r.card], 0
+        hb.max_event_size = int(np.diff(off).max()) if r.n_events else 0
+        return hb, o, a0, int(off[-1])
+
+    out = {"workload": "Poisson arrivals; requests of log-uniform(1, 5000) events from the batched, "
+                       "e+e- and pile-up generators, card uniform among CMS-like, ATLAS-like, e+e-",
+           "duration_s": args.serving_seconds, "rates": {}}
+    for rate in args.serving_rates:
+        sched = synth.serving_schedule(rate, args.serving_seconds, args.serving_pool)
+        reqs = [host_batch(r) for r in sched]
+        parts = sum(x[3] for x in reqs)
+        # ---- served: submit at arrival times, a helper thread releases finished tickets
+        ctx.serve_start()
+        tickets = []
+        done = th.Event()
+
+        def releaser():
+            i = 0
+            while not (done.is_set() and i >= len(tickets)):
+                if i < len(tickets):
+                    if ctx.wait(tickets[i], 120_000) != 0:
+                        raise RuntimeError("serving request failed")
+                    ctx.release(tickets[i])
+                    i += 1
+                else:
+                    time.sleep(0.0005)
+
+        rt = th.Thread(target=releaser)
+        rt.start()
+        t0 = time.perf_counter()
+        for r, (hb, o, a0, np_) in zip(sched, reqs):
+            while time.perf_counter() - t0 < r.t_arrival:
+                time.sleep(0.0002)
+            tickets.append(ctx.serve_submit(hb))
+        done.set()
+        rt.join()
+        st = ctx.serve_stats()
+        ctx.serve_stop()
+        # ---- baseline: one request at a time, one plain launch each (H2D, run, sync)
+        lat = []
+        t0 = time.perf_counter()
+        s = torch.cuda.current_stream()
+        for r, (hb, o, a0, np_) in zip(sched, reqs):
+            while time.perf_counter() - t0 < r.t_arrival:
+                time.sleep(0.0002)
+            pb = pools[r.generator]
+            dev = {"offsets": o.to("cuda", non_blocking=True)}
+            for k, t in pinned[r.generator].items():
+                dev[k] = None if t is None else t[a0:a0 + np_].to("cuda", non_blocking=True)
+            dev["n_events"], dev["max_event_size"] = r.n_events, hb.max_event_size
+            outb = B.alloc_outputs(r.n_events, np_)
+            ctx.run(B.make_batch(dev, cards[r.card], r.seed), B.make_outputs(outb))
+            s.synchronize()
+            lat.append((time.perf_counter() - t0 - r.t_arrival) * 1e3)
+        span = time.perf_counter() - t0 - sched[0].t_arrival if sched else 1.0
+        lat = np.array(lat) if lat else np.zeros(1)
+        out["rates"][str(rate)] = {
+            "requests": len(sched), "particles": parts,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "particles_per_s": st["particles_done"] / st["span_s"] if st["span_s"] > 0 else None,
+            "waves": st["waves"], "admission_waits": st["admission_waits"],
+            "per_request_p50_ms": float(np.percentile(lat, 50)), "per_request_p99_ms": float(np.percentile(lat, 99)),
+            "per_request_particles_per_s": parts / span if span > 0 else None}
+    return out
 
 
 def cpu_baseline(batch, card_name, seed, target_s):
@@ -366,6 +461,10 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--launch", default=None, help="fixed launch shape 'team,block' (skips autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[50, 100, 200, 500])
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-pool", type=int, default=5000)
     ap.add_argument("--no-per-event", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

@@ -286,3 +286,50 @@ def from_particles(events: list) -> EventBatch:
     return EventBatch(_offsets(counts), col(0, np.float32), col(1, np.float32),
                       col(2, np.float32), col(3, np.float32), col(4, np.int32),
                       col(5, np.int8), vz, "hand")
+
+
+# ---------------------------------------------------------------------------
+# serving workload
+# ---------------------------------------------------------------------------
+SERVING_GENERATORS = ("batched", "ee", "pileup")
+SERVING_CARDS = ("cms_like", "atlas_like", "ee_like")
+
+
+@dataclasses.dataclass
+class Request:
+    t_arrival: float      # seconds after the start
+    generator: str        # which event pool the events come from
+    card: str             # detector card of the request
+    n_events: int
+    start: int            # first event of the request in its pool
+    seed: int
+
+
+def serving_schedule(rate_hz: float, duration_s: float, pool_events: int = 5000,
+                     seed: int = 4, max_events: int = 5000) -> list:
+    """Poisson arrivals at rate_hz for duration_s; each request holds
+    log-uniform(1, max_events) events from a generator drawn uniformly among the
+    batched, e+e- and pile-up workloads, with a card drawn uniformly among the
+    three; its events are a random contiguous range of that generator's pool."""
+    rng = np.random.default_rng(seed + int(rate_hz * 1000))
+    out = []
+    t = 0.0
+    k = 0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            break
+        n = int(np.floor(np.exp(rng.uniform(0.0, np.log(max_events + 1)))))
+        n = max(1, min(n, max_events, pool_events))
+        gen = SERVING_GENERATORS[int(rng.integers(3))]
+        card = SERVING_CARDS[int(rng.integers(3))]
+        start = int(rng.integers(0, pool_events - n + 1))
+        out.append(Request(t, gen, card, n, start, 1000 + k))
+        k += 1
+    return out
+
+
+def serving_pools(pool_events: int = 5000) -> dict:
+    """The event pools the serving requests slice (one per generator)."""
+    return {"batched": make_batched(pool_events, seed=11), "ee": make_ee(pool_events, seed=12),
+            "pileup": make_pileup(pool_events, seed=13)}
