@@ -58,6 +58,30 @@ def _dist():
     return None, 0, 1
 
 
+def max_over_ranks(dist, x: float) -> float:
+    """The slowest rank's value (all-reduce MAX); x itself on one process.
+    The tensor lives where the process group's backend wants it."""
+    if not dist:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_event_base(rank: int, n_events: int) -> int:
+    """First event index of a rank's replica: ranks draw disjoint event indices
+    (every random draw is keyed by the event index), so no two ranks repeat
+    the same events."""
+    return rank * n_events
+
+
+def job_rate(units_per_rank: int, ws: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: units all ranks processed / the slowest rank's time."""
+    return ws * units_per_rank * steps / (max_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -153,7 +177,7 @@ def bench_ours(args, dist, rank, ws):
     dev = B.batch_to_device(batch)
     out = B.alloc_outputs(n_ev, n_p)
     ob = B.make_outputs(out)
-    base = rank * n_ev  # replicas process different events
+    base = replica_event_base(rank, n_ev)
     bt = B.make_batch(dev, cid, args.seed, event_base=base)
     if args.launch:
         best = B.pdr_launch()
@@ -195,12 +219,9 @@ def bench_ours(args, dist, rank, ws):
     ctx.check()
     total_ms = t_all0.elapsed_time(t_all1)
     launch_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, total_ms)
     ms_per_step = total_ms / args.steps
-    value = ws * n_p * args.steps / (total_ms / 1e3)
+    value = job_rate(n_p, ws, args.steps, total_ms)
     avg_launch_s = statistics.mean(launch_ms) / 1e3
     achieved = alg_bytes / avg_launch_s / 1e9
     peaks = _peaks()
@@ -236,11 +257,7 @@ def bench_ours(args, dist, rank, ws):
             t0 = time.perf_counter()
             ctx.run_host(hb, ho, launch=best)
             times.append(time.perf_counter() - t0)
-        e2e_s = statistics.mean(times)
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(dist, statistics.mean(times))
         c2 = h_out["counts"].view(np.uint32).astype(np.int64).sum(axis=0)
         d2h = int(16 * c2[0] + 12 * c2[1] + 12 * c2[2] + (16 + 8) * c2[3] + 16 * n_ev)
         e2e = {"value": ws * n_p / e2e_s, "unit": "particles/s", "h2d_bytes_per_step": int(in_bytes),
@@ -270,7 +287,7 @@ def bench_ours(args, dist, rank, ws):
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "events_per_s": ws * n_ev * args.steps / (total_ms / 1e3),
+        "events_per_s": job_rate(n_ev, ws, args.steps, total_ms),
         "config": {"workload": WORKLOAD_DESC[args.workload], "card": card_name, "n_events": n_ev,
                    "n_particles": n_p, "seed": args.seed, "launch": best.as_dict(),
                    "l2": f"inputs {in_bytes / 1e6:.0f} MB per step > 126 MB L2; no flush",
