@@ -31,7 +31,7 @@ inline size_t build_hot_card(const DevCard& D, unsigned char* out, size_t cap) {
     hc.ring_off = (int32_t)nf;
     for (int r = 0; r < C.nring; ++r) {
       data[nf++] = C.eta_c[r];
-      data[nf++] = C.cosh_c[r];
+      data[nf++] = C.inv_cosh_c[r];
       std::memcpy(&data[nf++], &C.resbin[r], sizeof(float));
     }
     for (int s = 0; s < C.nseg; ++s) {

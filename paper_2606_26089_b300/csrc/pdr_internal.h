@@ -38,7 +38,7 @@ struct DevCalo {
   int32_t phioff[PDR_MAXRING];   // offset of the ring's phi table in DevCard::phi_pool
   float phi_scale[PDR_MAXRING];  // nphi / (2 pi), guess only
   float eta_c[PDR_MAXRING];      // ring centre (float32 of the double midpoint)
-  float cosh_c[PDR_MAXRING];     // cosh(eta_c) (float32 of the double value)
+  float inv_cosh_c[PDR_MAXRING]; // 1 / cosh(eta_c) (float32 of the double value)
   int32_t resbin[PDR_MAXRING];   // resolution row of |eta_c|
   // ring groups: runs of rings with the same phi segmentation, in ring order
   // (tower id -> ring without a search: ring = first + (id - base) / nphi)
@@ -78,7 +78,7 @@ struct DevCard {
 // The part of a card the kernel touches per particle and per tower, laid out
 // compactly so each persistent CTA copies it once into shared memory.  A fixed
 // header (below) is followed by `data_floats` floats: per calorimeter the ring
-// edges (nring + 1), per-ring data (eta_c, cosh(eta_c), resolution row as int
+// edges (nring + 1), per-ring data (eta_c, 1 / cosh(eta_c), resolution row as int
 // bits: 3 floats a ring), and per eta segment its phi table (nphi + 1 edges,
 // then nphi centres).  Tower ids are computed from per-segment bases, so no
 // per-ring table is read to place a deposit.

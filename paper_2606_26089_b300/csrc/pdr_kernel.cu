@@ -48,15 +48,43 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
                                         uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
-    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    // one 32 x 32 -> 64-bit product gives both halves
+    const unsigned long long p0 = 0xD2511F53ull * c0;
+    const unsigned long long p1 = 0xCD9E8D57ull * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
+}
+
+// Reciprocal to 1 ulp (the hardware approximation); used where the result
+// only needs a few ulp: every such quotient feeds either an output compared at
+// 2e-6 relative or a decision taken with the 1e-5 marginal band.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float fdiv(float a, float b) { return a * rcp_approx(b); }
+
+// cosh and sinh from one exponential: cosh = (e + 1/e) / 2; sinh likewise for
+// |x| >= 1/2 (no cancellation there: e - 1/e >= 1.04) and from its odd Taylor
+// series through x^9 below 1/2 (truncation < 3e-11 relative).
+__device__ __forceinline__ void cosh_sinh(float x, float& ch, float& sh) {
+  const float ax = fabsf(x);
+  const float e = expf(ax);
+  const float ie = rcp_approx(e);
+  ch = 0.5f * (e + ie);
+  const float x2 = ax * ax;
+  const float series =
+      ax * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 362880.0f, 1.0f / 5040.0f), 1.0f / 120.0f), 1.0f / 6.0f),
+                1.0f);
+  const float s = ax < 0.5f ? series : 0.5f * (e - ie);
+  sh = copysignf(s, x);
 }
 
 // (2k + 1) / 2^24 for the top 23 bits k of w: exact in float32.
@@ -78,7 +106,7 @@ __device__ __forceinline__ float lognormal(float x, float rel2, float z) {
 
 // (sigma/x)^2 = a^2/x + b^2/x^2 + c^2 + d^2 x^2.
 __device__ __forceinline__ float rel2_of(float a2, float b2, float c2, float d2, float x) {
-  const float ix = 1.0f / x;
+  const float ix = rcp_approx(x);
   return fmaf(fmaf(b2, ix, a2), ix, fmaf(d2 * x, x, c2));
 }
 
@@ -130,68 +158,65 @@ struct Prop {
 // cylinder R, +-L.  Helix radius r = pT / (0.299792458 |q| |B|); the barrel is
 // reached iff 2 pT >= c = 0.299792458 |q| |B| R, at turning angle
 // 2 asin(c / 2pT); otherwise the endcap after psi = s_z / r < 2 pi.
-__device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta, float phi,
+__device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta, float sh, float phi,
                                           int q, float vz) {
   Prop P;
   P.reach = 0; P.barrel = 0; P.eta_pos = 0.0f; P.phi_pos = 0.0f;
   if (!(fabsf(vz) <= K.L)) return P;
-  const float sh = sinhf(eta);
+  // every branch ends in eta_pos = asinh(num / den) and phi_pos = phi - turn
+  float num, den, turn = 0.0f;
   if (q == 0 || !K.has_field) {
-    P.reach = 1;
-    P.phi_pos = phi;
     if (vz == 0.0f) {  // from the axis origin a straight line keeps its direction
+      P.reach = 1;
       P.barrel = fabsf(K.R * sh) <= K.L;
       P.eta_pos = eta;
+      P.phi_pos = phi;
       return P;
     }
     const float z = fmaf(K.R, sh, vz);
     P.barrel = fabsf(z) <= K.L;
     if (P.barrel) {
-      P.eta_pos = asinhf(z / K.R);
-    } else {
+      num = z; den = K.R;
+    } else {  // z_e / rho with rho = (z_e - vz) / sinh(eta)
       const float ze = sh > 0.0f ? K.L : -K.L;
-      const float rho = (ze - vz) / sh;
-      P.eta_pos = asinhf(ze / rho);
+      num = ze * sh; den = ze - vz;
     }
-    return P;
-  }
-  const int aq = q < 0 ? -q : q;
-  const float kq = K.kB * (float)aq;
-  const float r = pt / kq;
-  const float h = ((q > 0) == (K.Bsign > 0)) ? 1.0f : -1.0f;
-  float cR, cRl;
-  if (aq <= PDR_MAXQ) { cR = K.cR_hi[aq]; cRl = K.cR_lo[aq]; }
-  else { cR = kq * K.R; cRl = 0.0f; }
-  const float twopt = 2.0f * pt;
-  float a = 0.0f, z = 0.0f;
-  if (twopt >= cR) {
-    const float x = cR / twopt;
-    if (x <= 0.5f) {
-      a = asinf(x);
-    } else {
-      // near the tangent point use asin(x) = pi/2 - 2 asin(sqrt((1 - x)/2)) with
-      // 1 - x = (2pT - c) / 2pT; 2pT - c_hi is exact (Sterbenz) for x > 1/2.
-      const float d = (twopt - cR) - cRl;
-      const float omx = fmaxf(d / twopt, 0.0f);
-      a = (PIO2_HI - 2.0f * asinf(sqrtf(0.5f * omx))) + PIO2_LO;
-    }
-    z = fmaf(2.0f * r * a, sh, vz);
-    P.barrel = fabsf(z) <= K.L;
-  }
-  float pphi;
-  if (P.barrel) {
-    P.eta_pos = asinhf(z / K.R);
-    pphi = phi - h * a;
   } else {
-    if (sh == 0.0f) return P;  // pz = 0 and the barrel out of reach
-    const float ze = sh > 0.0f ? K.L : -K.L;
-    const float sz = (ze - vz) / sh;
-    const float psi = sz / r;
-    if (!(psi < TWO_PI_F)) return P;  // looper
-    const float rho = 2.0f * r * fabsf(sinf(0.5f * psi));
-    P.eta_pos = asinhf(ze / rho);
-    pphi = phi - h * (0.5f * psi);
+    const int aq = q < 0 ? -q : q;
+    const float kq = K.kB * (float)aq;
+    const float r = fdiv(pt, kq);
+    const float h = ((q > 0) == (K.Bsign > 0)) ? 1.0f : -1.0f;
+    float cR, cRl;
+    if (aq <= PDR_MAXQ) { cR = K.cR_hi[aq]; cRl = K.cR_lo[aq]; }
+    else { cR = kq * K.R; cRl = 0.0f; }
+    const float twopt = 2.0f * pt;
+    float a = 0.0f;
+    if (twopt >= cR) {
+      // a = asin(x), x = c / 2pT; near the tangent point (x > 1/2) through
+      // pi/2 - 2 asin(sqrt((1 - x)/2)) with 1 - x = (2pT - c) / 2pT, where
+      // 2pT - c_hi is exact (Sterbenz)
+      const float x = fdiv(cR, twopt);
+      const bool near = x > 0.5f;
+      const float d = (twopt - cR) - cRl;
+      const float omx = fmaxf(fdiv(d, twopt), 0.0f);
+      const float as = asinf(near ? sqrtf(0.5f * omx) : x);
+      a = near ? (PIO2_HI - 2.0f * as) + PIO2_LO : as;
+      const float z = fmaf(2.0f * r * a, sh, vz);
+      P.barrel = fabsf(z) <= K.L;
+      num = z; den = K.R; turn = h * a;
+    }
+    if (!P.barrel) {
+      if (sh == 0.0f) return P;  // pz = 0 and the barrel out of reach
+      const float ze = sh > 0.0f ? K.L : -K.L;
+      const float sz = fdiv(ze - vz, sh);
+      const float psi = fdiv(sz, r);
+      if (!(psi < TWO_PI_F)) return P;  // looper
+      num = ze; den = 2.0f * r * fabsf(sinf(0.5f * psi));
+      turn = h * (0.5f * psi);
+    }
   }
+  P.eta_pos = asinhf(fdiv(num, den));
+  float pphi = phi - turn;
   if (pphi < -PI_F) pphi += TWO_PI_F;
   else if (pphi >= PI_F) pphi -= TWO_PI_F;
   P.phi_pos = pphi;
@@ -238,6 +263,19 @@ __device__ __forceinline__ bool tower_of(const HotCard& K, const float* KD, int 
   id = (uint32_t)(base + k);
   ring = r;
   return true;
+}
+
+// phi_c of tower id in a known ring (the segment base formula of tower_of).
+__device__ __forceinline__ float tower_phi_c(const HotCard& K, const float* KD, int calo, uint32_t id, int r) {
+  const HotCalo& C = K.calo[calo];
+  const int m = C.m;
+  const int jj = r >= m ? r - m : m - 1 - r;
+  int s = 0;
+  while (s < C.nseg - 1 && jj >= C.seg[s].first + C.seg[s].n) ++s;
+  const HotSeg& S = C.seg[s];
+  const int base = r >= m ? S.base_pos + (jj - S.first) * S.nphi
+                          : S.base_neg + (r - (m - S.first - S.n)) * S.nphi;
+  return KD[S.phioff + S.nphi + 1 + ((int)id - base)];
 }
 
 // Ring, eta_c and phi_c of a tower id.
@@ -324,12 +362,13 @@ __device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, 
   o.etrk = 0.0f; o.ptp = 0.0f; o.cpt = 0.0f; o.eta_pos = 0.0f; o.phi_pos = 0.0f;
   o.cc = -1; o.tracked = false; o.cand = false;
   const int cls = classify(PDG, Q);
-  const float ch = coshf(ETA);
+  float ch, sh;
+  cosh_sinh(ETA, ch, sh);
   const float pc = PT * ch;
   o.E = sqrtf(fmaf(pc, pc, M * M));
   if (cls == CLS_INVIS) return;
   // S1
-  const Prop P = propagate(K, PT, ETA, PHI, Q, VZ);
+  const Prop P = propagate(K, PT, ETA, sh, PHI, Q, VZ);
   if (!P.reach) return;
   o.flags = PDR_F_REACH | (P.barrel ? PDR_F_BARREL : 0u);
   o.eta_pos = P.eta_pos;
@@ -339,8 +378,9 @@ __device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, 
   uint32_t id = 0;
   const bool em = cls == CLS_E || cls == CLS_GAMMA;
   if (em || cls == CLS_CHAD || cls == CLS_NHAD) {
-    if (em && tower_of(K, KD, 0, P.eta_pos, P.phi_pos, id, ring)) calo = 0;
-    else if (tower_of(K, KD, 1, P.eta_pos, P.phi_pos, id, ring)) calo = 1;
+    const float* e0 = KD + K.calo[0].edge_off;
+    const int cal = (em && P.eta_pos >= e0[0] && P.eta_pos < e0[K.calo[0].nring]) ? 0 : 1;
+    if (tower_of(K, KD, cal, P.eta_pos, P.phi_pos, id, ring)) calo = cal;
   }
   if (calo >= 0) {
     o.key = ((uint32_t)calo << 24) | id;
@@ -354,7 +394,7 @@ __device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, 
     const int kp = small_lookup(K.trk_pt_edges, K.trk_npt, PT);
     const int ke = small_lookup(K.trk_eta_edges, K.trk_neta, aeta);
     const unsigned long long T = (kp >= 0 && ke >= 0) ? K.trk_T[tc][kp][ke] : 0ull;
-    const uint4 w = philox(i, event, 1u, 0u, S.seed_lo, S.seed_hi);
+    const uint4 w = T != 0ull ? philox(i, event, 1u, 0u, S.seed_lo, S.seed_hi) : make_uint4(0, 0, 0, 0);
     if ((unsigned long long)w.x < T) {
       o.tracked = true;
       o.flags |= PDR_F_TRACKED;
@@ -375,7 +415,7 @@ __device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, 
   if (cc >= 0 && PT > K.cand_ptmin) {
     const int ke = small_lookup(K.id_edges, K.id_n, aeta);
     const unsigned long long T = ke >= 0 ? K.id_T[cc][ke] : 0ull;
-    const uint4 w = philox(i, event, 2u, 0u, S.seed_lo, S.seed_hi);
+    const uint4 w = T != 0ull ? philox(i, event, 2u, 0u, S.seed_lo, S.seed_hi) : make_uint4(0, 0, 0, 0);
     if ((unsigned long long)w.x < T) {
       const float z = normal(w.y, w.z);
       const int comp = cc != 1 ? RES_ECAL : RES_MUON;
@@ -461,7 +501,7 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
   const int calo = (int)(key >> 24);
   const uint32_t id = key & 0xFFFFFFu;
   const float* rd = KD + K.calo[calo].ring_off + 3 * ring;
-  const float chc = rd[1];
+  const float ich = rd[1];  // 1 / cosh(eta_c)
   const int rb = __float_as_int(rd[2]);
   const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
   const float a2 = K.res_a2[comp][rb], b2 = K.res_b2[comp][rb];
@@ -471,15 +511,16 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
   const uint4 w = philox(id, event, 3u + (uint32_t)calo, 0u, s0, s1);
   const float z = normal(w.x, w.y);
   const float E1 = lognormal(Es, rel2_of(a2, b2, c2, d2, Es), z);
-  const float sig = E1 * sqrtf(rel2_of(a2, b2, c2, d2, E1));
+  // E'/sigma(E') = 1 / sqrt(rel2(E')); dE/sigma(E') = dE / E' * that
+  const float rs = rsqrtf(rel2_of(a2, b2, c2, d2, E1));
   const float emin = K.e_min[calo], smin = K.s_min[calo];
-  o.kept = (E1 > emin) & (E1 / sig > smin);
+  o.kept = (E1 > emin) & (rs > smin);
   o.e = E1;
-  o.et = E1 / chc;
+  o.et = E1 * ich;
   const float dE = E1 - Et;
-  o.ef = (dE > emin) & (dE / sig > smin);
+  o.ef = (dE > emin) & (dE * rs > smin * E1);
   o.de = dE;
-  o.det = dE / chc;
+  o.det = dE * ich;
 }
 
 // ------------------------------------------------------------- one event
@@ -538,8 +579,10 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
   }
   tc.sync();
 
-  // ---- phase 2: towers (S6, S7), each by its lowest-index depositing particle
+  // ---- phase 2: towers (S6, S7), each by its lowest-index depositing particle;
+  // an EFlow neutral adds its pT to the staged candidates' cones right away (S8)
   uint32_t n_twr = 0, n_ef = 0;
+  const uint32_t gn0 = min(n_cand, (uint32_t)PDR_CMAX);
   for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
     const uint32_t i = c0 + (uint32_t)tc.tid;
     TowerOut to;
@@ -553,6 +596,22 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
           key = T.keys[slot];
           tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, S.seed_lo, S.seed_hi, to);
           T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
+          if (to.ef && gn0 > 0 && to.det > K.iso_ptmin) {
+            const int calo = (int)(key >> 24), ring = (int)(pi >> 16);
+            const float oe = KD[K.calo[calo].ring_off + 3 * ring];
+            const float op = tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring);
+            const unsigned long long wgt = to_fp(to.det);
+            for (uint32_t c = 0; c < gn0; ++c) {
+              if (key == ckey[c]) continue;  // the candidate's own tower
+              const float4 cv = cf[c];
+              const float de = oe - cv.x;
+              float dp = op - cv.y;
+              if (dp >= PI_F) dp -= TWO_PI_F;
+              else if (dp < -PI_F) dp += TWO_PI_F;
+              const float dr2 = fmaf(de, de, dp * dp);
+              if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
+            }
+          }
         }
       }
     }
@@ -572,10 +631,11 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
   }
 
   // ---- phase 3: isolation (S8): every EFlow object above the pT floor adds
-  // its fixed-point pT to each candidate cone holding it
+  // its fixed-point pT to each candidate cone holding it (the EFlow neutrals of
+  // the first candidate group did so in phase 2)
   if (n_cand > 0) {
-    const uint32_t n_obj = n_trk + n_ef;
     for (uint32_t g0 = 0; g0 < n_cand; g0 += PDR_CMAX) {
+      const uint32_t n_obj = g0 == 0 ? n_trk : n_trk + n_ef;
       const uint32_t gn = min((uint32_t)PDR_CMAX, n_cand - g0);
       tc.sync();
       if (g0 > 0 && (uint32_t)tc.tid < gn) {  // candidates beyond the staged ones

@@ -162,7 +162,7 @@ int expand_calo_fixed(const pdr_card* c, int calo, DevCalo& D, float* pool, int&
     D.phi_scale[r] = (float)(nphi[r] / (2.0 * M_PI));
     const double ec = 0.5 * (edge[r] + edge[r + 1]);
     D.eta_c[r] = (float)ec;
-    D.cosh_c[r] = (float)std::cosh(ec);
+    D.inv_cosh_c[r] = (float)(1.0 / std::cosh(ec));
   }
   D.ntowers = base;
   // ring groups in ring order: negative-side segments outermost first, then
