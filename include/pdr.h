@@ -161,8 +161,9 @@ typedef struct pdr_outputs {
 /* Launch shape of the fused kernel: `team` threads work on one event (32 =
  * warp per event ... 1024 = block per event), `block` threads per CTA (a
  * multiple of team), `table_slots` shared-memory tower-table slots per team
- * (power of two; events with more than 3/4 x table_slots particles use a
- * global-memory table), `grid` CTAs (0 = fill the GPU, persistent). */
+ * (rounded up to a multiple of 32; events with more than 3/4 x table_slots
+ * particles use a global-memory table), `grid` CTAs (0 = fill the GPU,
+ * persistent). */
 typedef struct pdr_launch {
   uint32_t team, block, table_slots, grid;
 } pdr_launch;

@@ -147,9 +147,9 @@ struct KParams {
   uint32_t hot_bytes[PDR_LAUNCH_CARDS];         // each a multiple of 16
   uint32_t hot_off[PDR_LAUNCH_CARDS];           // offset of each image in shared memory
   uint32_t hot_total;                // shared memory of all card images
-  uint32_t table_slots, log2_slots;  // shared-memory table per team
+  uint32_t table_slots;              // shared-memory table per team (multiple of 32)
   uint32_t nmax_smem;                // largest event handled in shared memory
-  uint32_t g_slots, g_log2, g_nmax;  // global-memory table per team for larger events
+  uint32_t g_slots, g_nmax;          // global-memory table per team for larger events
   unsigned char* gscratch;           // g_team_bytes per team, or null
   uint64_t g_team_bytes;
   uint32_t* err;                     // device error word (bit flags below)
@@ -162,10 +162,11 @@ enum : uint32_t {
   ERR_TABLE = 4u,      // tower table full (cannot happen when sized as documented)
 };
 
-// Bytes of a team's tower table: keys, owner, esum, etrk per slot and one
-// info word per particle (16-byte multiple).
+// Bytes of a team's event workspace: the tower table (keys, owner, esum, etrk
+// per slot), then per particle an info word and a smearing-job entry
+// (16-byte multiple).
 PDR_HD inline uint64_t table_bytes(uint32_t slots, uint32_t nmax) {
-  const uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * 4;
+  const uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * (4 + 4);
   return (b + 15) & ~15ull;
 }
 

@@ -344,23 +344,30 @@ __device__ __forceinline__ uint32_t team_scan2(bool fa, bool fb, uint32_t* wbuf,
 }
 
 // ------------------------------------------------------- per-particle stage
-struct PartOut {
-  uint32_t key, ring, flags;
-  float E, etrk, ptp, cpt, eta_pos, phi_pos;
-  int cc;
-  bool tracked, cand;
+// Phase 1a of a particle: S0, S1 and the tower of S5, plus its smearing job,
+// if any: a tracking job (S2, S3, and S4 for a tracked e/mu) for a charged
+// particle that reached the surface inside a tracking-efficiency bin with
+// non-zero efficiency, or an identification job (S4) for a photon in ECAL
+// above the candidate pT floor.  Jobs run afterwards from a dense list in
+// particle order, so the warps that hold no job skip their arithmetic.
+struct PartA {
+  uint32_t key, ring, flags, job;  // job: entry below, or PDR_EMPTY
+  float E, eta_pos, phi_pos;
 };
 
-__device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, const float* KD,
-                                               uint64_t g, uint32_t i, uint32_t event, PartOut& o) {
+// Job entry: particle index (16 bits) | pT bin << 16 | |eta| bin << 20 |
+// tracking-efficiency table (0 hadron, 1 electron, 2 muon) << 24 | photon << 28.
+#define PDR_JOB_PHOTON (1u << 28)
+
+__device__ __forceinline__ void particle_stage_a(const KSeg& S, const HotCard& K, const float* KD,
+                                                 uint64_t g, uint32_t i, PartA& o) {
   const float PT = __ldg(S.pt + g), ETA = __ldg(S.eta + g), PHI = __ldg(S.phi + g);
   const float M = __ldg(S.mass + g);
   const int32_t PDG = __ldg(S.pdg + g);
   const int Q = (int)__ldg(S.charge + g);
   const float VZ = S.vz ? __ldg(S.vz + g) : 0.0f;
-  o.key = PDR_NO_KEY; o.ring = 0; o.flags = 0;
-  o.etrk = 0.0f; o.ptp = 0.0f; o.cpt = 0.0f; o.eta_pos = 0.0f; o.phi_pos = 0.0f;
-  o.cc = -1; o.tracked = false; o.cand = false;
+  o.key = PDR_NO_KEY; o.ring = 0; o.flags = 0; o.job = PDR_EMPTY;
+  o.eta_pos = 0.0f; o.phi_pos = 0.0f;
   const int cls = classify(PDG, Q);
   float ch, sh;
   cosh_sinh(ETA, ch, sh);
@@ -387,76 +394,108 @@ __device__ __forceinline__ void particle_stage(const KSeg& S, const HotCard& K, 
     o.ring = (uint32_t)ring;
     o.flags |= calo == 0 ? PDR_F_ECAL : PDR_F_HCAL;
   }
-  const float aeta = fabsf(ETA);
-  // S2, S3 tracking efficiency and momentum smearing
   if (Q != 0) {
     const int tc = cls == CLS_E ? 1 : (cls == CLS_MU ? 2 : 0);
     const int kp = small_lookup(K.trk_pt_edges, K.trk_npt, PT);
-    const int ke = small_lookup(K.trk_eta_edges, K.trk_neta, aeta);
-    const unsigned long long T = (kp >= 0 && ke >= 0) ? K.trk_T[tc][kp][ke] : 0ull;
-    const uint4 w = T != 0ull ? philox(i, event, 1u, 0u, S.seed_lo, S.seed_hi) : make_uint4(0, 0, 0, 0);
-    if ((unsigned long long)w.x < T) {
-      o.tracked = true;
-      o.flags |= PDR_F_TRACKED;
-      const float z = normal(w.y, w.z);
-      const int rb = max(small_lookup(K.res_edges[RES_TRACK], K.res_n[RES_TRACK], aeta), 0);
-      const float r2 = rel2_of(K.res_a2[RES_TRACK][rb], K.res_b2[RES_TRACK][rb],
-                               K.res_c2[RES_TRACK][rb], K.res_d2[RES_TRACK][rb], PT);
-      o.ptp = lognormal(PT, r2, z);
-      const float pcp = o.ptp * ch;
-      o.etrk = sqrtf(fmaf(pcp, pcp, M * M));
-    }
+    const int ke = small_lookup(K.trk_eta_edges, K.trk_neta, fabsf(ETA));
+    if (kp >= 0 && ke >= 0 && K.trk_T[tc][kp][ke] != 0ull)
+      o.job = i | ((uint32_t)kp << 16) | ((uint32_t)ke << 20) | ((uint32_t)tc << 24);
+  } else if (cls == CLS_GAMMA && calo == 0 && PT > K.cand_ptmin) {
+    o.job = i | PDR_JOB_PHOTON;
   }
-  // S4 e/mu/gamma identification and smearing
-  int cc = -1;
-  if (cls == CLS_E && o.tracked) cc = 0;
-  else if (cls == CLS_MU && o.tracked) cc = 1;
-  else if (cls == CLS_GAMMA && calo == 0) cc = 2;
-  if (cc >= 0 && PT > K.cand_ptmin) {
+}
+
+// Phase 1b: one job.  Each stage is an efficiency draw and, if accepted, a
+// log-normal smearing: S2 + S3 for a tracking job (then S4 for a tracked e/mu
+// above the candidate pT floor), S4 alone for a photon.  Returns the smeared
+// track pT and energy and the candidate pT and class through the references.
+struct JobOut {
+  bool tracked, cand;
+  float ptp, etrk, cpt;
+  int cc;
+};
+
+__device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_t a, uint32_t job,
+                                        uint32_t event, JobOut& r) {
+  const uint32_t i = job & 0xFFFFu;
+  const bool photon = (job & PDR_JOB_PHOTON) != 0u;
+  const float PT = __ldg(S.pt + a + i), ETA = __ldg(S.eta + a + i), M = __ldg(S.mass + a + i);
+  const float aeta = fabsf(ETA);
+  float ch, sh;
+  cosh_sinh(ETA, ch, sh);
+  const float pc = PT * ch;
+  const float E = sqrtf(fmaf(pc, pc, M * M));
+  r.tracked = false; r.cand = false; r.ptp = 0.0f; r.etrk = 0.0f; r.cpt = 0.0f;
+  // first stage
+  uint32_t purpose;
+  unsigned long long T;
+  int comp;
+  float x;
+  if (!photon) {
+    const int kp = (int)((job >> 16) & 15u), ke = (int)((job >> 20) & 15u), tc = (int)((job >> 24) & 3u);
+    purpose = 1u; T = K.trk_T[tc][kp][ke]; comp = RES_TRACK; x = PT;
+    r.cc = tc == 1 ? 0 : (tc == 2 ? 1 : -1);
+  } else {
     const int ke = small_lookup(K.id_edges, K.id_n, aeta);
-    const unsigned long long T = ke >= 0 ? K.id_T[cc][ke] : 0ull;
-    const uint4 w = T != 0ull ? philox(i, event, 2u, 0u, S.seed_lo, S.seed_hi) : make_uint4(0, 0, 0, 0);
-    if ((unsigned long long)w.x < T) {
-      const float z = normal(w.y, w.z);
-      const int comp = cc != 1 ? RES_ECAL : RES_MUON;
-      const float x = cc != 1 ? o.E : PT;
-      const int rb = max(small_lookup(K.res_edges[comp], K.res_n[comp], aeta), 0);
-      const float r2 = rel2_of(K.res_a2[comp][rb], K.res_b2[comp][rb], K.res_c2[comp][rb],
-                               K.res_d2[comp][rb], x);
-      const float sm = lognormal(x, r2, z);
-      o.cpt = cc != 1 ? sm / ch : sm;
-      o.cand = true;
-      o.cc = cc;
-      o.flags |= PDR_F_CAND;
-    }
+    purpose = 2u; T = ke >= 0 ? K.id_T[2][ke] : 0ull; comp = RES_ECAL; x = E;
+    r.cc = 2;
   }
-  // the track energy is subtracted from the particle's own tower (e, hadrons)
-  if (o.key == PDR_NO_KEY) o.etrk = 0.0f;
+  for (;;) {
+    bool ok = false;
+    float sm = 0.0f;
+    if (T != 0ull) {
+      const uint4 w = philox(i, event, purpose, 0u, S.seed_lo, S.seed_hi);
+      if ((unsigned long long)w.x < T) {
+        ok = true;
+        const float z = normal(w.y, w.z);
+        const int rb = max(small_lookup(K.res_edges[comp], K.res_n[comp], aeta), 0);
+        const float r2 = rel2_of(K.res_a2[comp][rb], K.res_b2[comp][rb], K.res_c2[comp][rb],
+                                 K.res_d2[comp][rb], x);
+        sm = lognormal(x, r2, z);
+      }
+    }
+    if (purpose == 2u) {  // identification stage: done
+      r.cand = ok;
+      if (ok) r.cpt = r.cc != 1 ? sm / ch : sm;
+      return;
+    }
+    r.tracked = ok;
+    if (!ok) return;
+    r.ptp = sm;
+    const float pcp = sm * ch;
+    r.etrk = sqrtf(fmaf(pcp, pcp, M * M));
+    if (r.cc < 0 || !(PT > K.cand_ptmin)) return;
+    // a tracked e/mu goes on to identification
+    const int ke = small_lookup(K.id_edges, K.id_n, aeta);
+    purpose = 2u; T = ke >= 0 ? K.id_T[r.cc][ke] : 0ull;
+    comp = r.cc == 0 ? RES_ECAL : RES_MUON; x = r.cc == 0 ? E : PT;
+  }
 }
 
 // ------------------------------------------------------------ tower table
 // Per-team open-addressing table (linear probing, multiplicative hash) keyed
-// by tower key, plus one info word per particle (slot | ring << 16, or empty).
-// Between events every key is empty; the other slot fields are initialised by
-// the thread that claims the slot.
+// by tower key; per particle an info word (slot | ring << 16, or empty); the
+// event's job list.  Between events every key is empty; the
+// other slot fields are initialised by the thread that claims the slot.
 struct Tbl {
   uint32_t* keys;
   uint32_t* owner;
   unsigned long long* esum;
   unsigned long long* etrk;
   uint32_t* pinfo;
-  uint32_t mask, shift;
+  uint32_t* jobs;   // smearing jobs of the event, in particle order
+  uint32_t nslots;  // any multiple of 32 (the hash is scaled, not masked)
 };
 
-__device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t log2) {
+__device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t nmax) {
   Tbl t;
   t.keys = (uint32_t*)base;
   t.owner = t.keys + slots;
   t.esum = (unsigned long long*)(t.owner + slots);
   t.etrk = t.esum + slots;
   t.pinfo = (uint32_t*)(t.etrk + slots);
-  t.mask = slots - 1;
-  t.shift = 32 - log2;
+  t.jobs = t.pinfo + nmax;
+  t.nslots = slots;
   return t;
 }
 
@@ -467,9 +506,10 @@ __device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32
 __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uint32_t i,
                                                  unsigned long long e_fp, unsigned long long t_fp,
                                                  bool* claimed, uint32_t* err) {
-  uint32_t h = (key * 0x9E3779B1u) >> T.shift;
+  // multiplicative hash scaled to [0, nslots): the high word of h * nslots
+  uint32_t h = __umulhi(key * 0x9E3779B1u, T.nslots);
   *claimed = false;
-  for (uint32_t probe = 0; probe <= T.mask; ++probe) {
+  for (uint32_t probe = 0; probe < T.nslots; ++probe) {
     const uint32_t cur = T.keys[h];
     if (cur == key) return h;
     if (cur == PDR_EMPTY) {
@@ -483,7 +523,7 @@ __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uin
       }
       if (prev == key) return h;
     }
-    h = (h + 1) & T.mask;
+    h = h + 1 == T.nslots ? 0u : h + 1;
   }
   atomicOr(err, ERR_TABLE);
   return PDR_EMPTY;
@@ -524,6 +564,16 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
 }
 
 // ------------------------------------------------------------- one event
+// A team of TEAM threads walks the event in chunks of TEAM particles:
+//   1a  particles: S0, S1, S5 placement and deposit; the smearing jobs, in
+//       particle order (one team scan per chunk)
+//   1b  smearing jobs (S2, S3, S4), team-strided over the job list; tracks
+//       and candidates in particle order; candidates staged for the isolation
+//   2   towers (S6, S7) by their lowest-index depositor, records in that
+//       order; EFlow neutrals and tracks add their pT to the staged
+//       candidates' cones (S8)
+//   3   isolation results; candidates beyond the staged ones loop over all
+//       EFlow objects
 template <int TEAM>
 __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
                                               const Tbl& T, uint32_t* wbuf, float4* cf, uint32_t* ckey,
@@ -533,54 +583,82 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
   const bool dbg = S.debug != nullptr;
   uint32_t n_trk = 0, n_cand = 0, flip = 0;
 
-  // ---- phase 1: particles (S0-S5); tracks and candidates in particle order
+  // ---- 1a: particles (S0, S1, S5 placement and deposit); job list
+  uint32_t n_job = 0;
   for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
     const uint32_t i = c0 + (uint32_t)tc.tid;
     const bool valid = i < n;
-    PartOut o;
-    o.tracked = false; o.cand = false; o.key = PDR_NO_KEY; o.E = 0.0f; o.etrk = 0.0f;
-    if (valid) particle_stage(S, K, KD, a + i, i, event, o);
+    PartA o;
+    o.key = PDR_NO_KEY; o.E = 0.0f; o.job = PDR_EMPTY;
+    if (valid) particle_stage_a(S, K, KD, a + i, i, o);
     uint32_t slot = PDR_EMPTY;
     bool claimed = false;
     const unsigned long long e_fp = to_fp(o.E);
-    const unsigned long long t_fp = o.etrk > 0.0f ? to_fp(o.etrk) : 0ull;
-    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, t_fp, &claimed, err);
+    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, 0ull, &claimed, err);
     if (valid) T.pinfo[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
+    const bool has_job = o.job != PDR_EMPTY;
     uint32_t tot;
-    const uint32_t pre = team_scan2<TEAM>(o.tracked, o.cand, wbuf + 32 * flip, tot, tc);
+    const uint32_t pre = team_scan2<TEAM>(has_job, false, wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
-    if (slot != PDR_EMPTY && !claimed) {
+    if (slot != PDR_EMPTY && !claimed) {  // after the barrier that orders the claimers' stores
       atomicAdd(&T.esum[slot], e_fp);
-      if (t_fp) atomicAdd(&T.etrk[slot], t_fp);
       atomicMin(&T.owner[slot], i);
     }
-    if (o.tracked || o.cand) {
-      const float eta = __ldg(S.eta + a + i), phi = __ldg(S.phi + a + i);
-      if (o.tracked)
-        reinterpret_cast<float4*>(S.tracks)[a + n_trk + (pre & 0xFFFFu)] =
-            make_float4(o.ptp, eta, phi, __uint_as_float(i));
-      if (o.cand) {
-        const uint32_t j = n_cand + (pre >> 16);
-        reinterpret_cast<float4*>(S.cands)[a + j] =
-            make_float4(o.cpt, eta, phi, __uint_as_float(i | ((uint32_t)o.cc << 28)));
-        // own tower key, read back by the isolation of candidates beyond the staged ones
-        reinterpret_cast<float2*>(S.iso)[a + j] = make_float2(__uint_as_float(o.key), 0.0f);
-        if (j < PDR_CMAX) {  // staged for the isolation phase
-          cf[j] = make_float4(eta, phi, o.cpt, __uint_as_float(i));
-          ckey[j] = o.key;
-        }
-      }
-    }
+    if (has_job) T.jobs[n_job + (pre & 0xFFFFu)] = o.job;
     if (dbg && valid)
       reinterpret_cast<float4*>(S.debug)[a + i] =
           make_float4(__uint_as_float(o.key), o.eta_pos, o.phi_pos, __uint_as_float(o.flags));
+    n_job += tot & 0xFFFFu;
+  }
+  tc.sync();
+
+  // ---- 1b: smearing jobs (S2, S3, S4) in particle order
+  for (uint32_t j0 = 0; j0 < n_job; j0 += TEAM) {
+    const uint32_t j = j0 + (uint32_t)tc.tid;
+    JobOut r;
+    r.tracked = false; r.cand = false;
+    uint32_t i = 0;
+    if (j < n_job) {
+      const uint32_t job = T.jobs[j];
+      i = job & 0xFFFFu;
+      run_job(S, K, a, job, event, r);
+      if (r.tracked) {
+        const uint32_t pi = T.pinfo[i];
+        if (pi != PDR_EMPTY) atomicAdd(&T.etrk[pi & 0xFFFFu], to_fp(r.etrk));
+      }
+      if (dbg && (r.tracked || r.cand))
+        reinterpret_cast<uint32_t*>(S.debug + a + i)[3] |=
+            (r.tracked ? PDR_F_TRACKED : 0u) | (r.cand ? PDR_F_CAND : 0u);
+    }
+    uint32_t tot;
+    const uint32_t pre = team_scan2<TEAM>(r.tracked, r.cand, wbuf + 32 * flip, tot, tc);
+    flip ^= 1u;
+    if (r.tracked || r.cand) {
+      const float eta = __ldg(S.eta + a + i), phi = __ldg(S.phi + a + i);
+      if (r.tracked)
+        reinterpret_cast<float4*>(S.tracks)[a + n_trk + (pre & 0xFFFFu)] =
+            make_float4(r.ptp, eta, phi, __uint_as_float(i));
+      if (r.cand) {
+        const uint32_t jc = n_cand + (pre >> 16);
+        const uint32_t pi = T.pinfo[i];
+        const uint32_t key = pi == PDR_EMPTY ? PDR_NO_KEY : T.keys[pi & 0xFFFFu];
+        reinterpret_cast<float4*>(S.cands)[a + jc] =
+            make_float4(r.cpt, eta, phi, __uint_as_float(i | ((uint32_t)r.cc << 28)));
+        // own tower key, read back by the isolation of candidates beyond the staged ones
+        reinterpret_cast<float2*>(S.iso)[a + jc] = make_float2(__uint_as_float(key), 0.0f);
+        if (jc < PDR_CMAX) {  // staged for the isolation
+          cf[jc] = make_float4(eta, phi, r.cpt, __uint_as_float(i));
+          ckey[jc] = key;
+        }
+      }
+    }
     n_trk += tot & 0xFFFFu;
     n_cand += tot >> 16;
   }
   tc.sync();
 
-  // ---- phase 2: towers (S6, S7), each by its lowest-index depositing particle;
-  // an EFlow neutral adds its pT to the staged candidates' cones right away (S8)
+  // ---- 2: towers (S6, S7), each by its lowest-index depositing particle;
+  // EFlow neutrals and tracks add their pT to the staged candidates' cones (S8)
   uint32_t n_twr = 0, n_ef = 0;
   const uint32_t gn0 = min(n_cand, (uint32_t)PDR_CMAX);
   for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
@@ -615,6 +693,23 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
         }
       }
     }
+    if (gn0 > 0 && i < n_trk) {
+      const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + i];
+      if (t.x > K.iso_ptmin) {
+        const unsigned long long wgt = to_fp(t.x);
+        const uint32_t oid = __float_as_uint(t.w);
+        for (uint32_t c = 0; c < gn0; ++c) {
+          const float4 cv = cf[c];
+          if (oid == __float_as_uint(cv.w)) continue;  // the candidate's own track
+          const float de = t.y - cv.x;
+          float dp = t.z - cv.y;
+          if (dp >= PI_F) dp -= TWO_PI_F;
+          else if (dp < -PI_F) dp += TWO_PI_F;
+          const float dr2 = fmaf(de, de, dp * dp);
+          if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
+        }
+      }
+    }
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
@@ -630,59 +725,64 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     n_ef += tot >> 16;
   }
 
-  // ---- phase 3: isolation (S8): every EFlow object above the pT floor adds
-  // its fixed-point pT to each candidate cone holding it (the EFlow neutrals of
-  // the first candidate group did so in phase 2)
-  if (n_cand > 0) {
-    for (uint32_t g0 = 0; g0 < n_cand; g0 += PDR_CMAX) {
-      const uint32_t n_obj = g0 == 0 ? n_trk : n_trk + n_ef;
-      const uint32_t gn = min((uint32_t)PDR_CMAX, n_cand - g0);
-      tc.sync();
-      if (g0 > 0 && (uint32_t)tc.tid < gn) {  // candidates beyond the staged ones
-        const uint64_t j = a + g0 + tc.tid;
-        const float4 c = reinterpret_cast<const float4*>(S.cands)[j];
-        cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
-        ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(S.iso)[j].x);
+  // ---- 3: isolation results (S8).  The staged candidates received every
+  // object's pT during 2 (its last team scan orders those sums before this
+  // read); further groups of PDR_CMAX candidates loop over all EFlow objects.
+  if ((uint32_t)tc.tid < gn0) {
+    const float s = from_fp(csum[tc.tid]);
+    csum[tc.tid] = 0ull;  // clean for the next group / event
+    const float rel = s / cf[tc.tid].z;
+    reinterpret_cast<float2*>(S.iso)[a + tc.tid] = make_float2(s, rel);
+    if (rel < K.imax) reinterpret_cast<uint32_t*>(S.cands + a + tc.tid)[3] |= 0x80000000u;
+  }
+  for (uint32_t g0 = PDR_CMAX; g0 < n_cand; g0 += PDR_CMAX) {
+    const uint32_t gn = min((uint32_t)PDR_CMAX, n_cand - g0);
+    const uint32_t n_obj = n_trk + n_ef;
+    tc.sync();
+    if ((uint32_t)tc.tid < gn) {  // candidates beyond the staged ones
+      const uint64_t j = a + g0 + tc.tid;
+      const float4 c = reinterpret_cast<const float4*>(S.cands)[j];
+      cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
+      ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(S.iso)[j].x);
+    }
+    tc.sync();
+    for (uint32_t j = tc.tid; j < n_obj; j += TEAM) {
+      float oe, op, opt;
+      uint32_t oid;
+      bool is_trk;
+      if (j < n_trk) {
+        const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + j];
+        opt = t.x; oe = t.y; op = t.z; oid = __float_as_uint(t.w); is_trk = true;
+      } else {
+        const pdr_eflow f = S.eflow[a + (j - n_trk)];
+        int r;
+        tower_decode(K, KD, (int)(f.key >> 24), f.key & 0xFFFFFFu, r, oe, op);
+        opt = f.et; oid = f.key; is_trk = false;
       }
-      if (g0 > 0) tc.sync();
-      for (uint32_t j = tc.tid; j < n_obj; j += TEAM) {
-        float oe, op, opt;
-        uint32_t oid;
-        bool is_trk;
-        if (j < n_trk) {
-          const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + j];
-          opt = t.x; oe = t.y; op = t.z; oid = __float_as_uint(t.w); is_trk = true;
-        } else {
-          const pdr_eflow f = S.eflow[a + (j - n_trk)];
-          int r;
-          tower_decode(K, KD, (int)(f.key >> 24), f.key & 0xFFFFFFu, r, oe, op);
-          opt = f.et; oid = f.key; is_trk = false;
-        }
-        if (!(opt > K.iso_ptmin)) continue;
-        const unsigned long long wgt = to_fp(opt);
-        for (uint32_t c = 0; c < gn; ++c) {
-          const float4 cv = cf[c];
-          if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == ckey[c])) continue;
-          const float de = oe - cv.x;
-          float dp = op - cv.y;
-          if (dp >= PI_F) dp -= TWO_PI_F;
-          else if (dp < -PI_F) dp += TWO_PI_F;
-          const float dr2 = fmaf(de, de, dp * dp);
-          if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
-        }
-      }
-      tc.sync();
-      if ((uint32_t)tc.tid < gn) {
-        const uint64_t j = a + g0 + tc.tid;
-        const float s = from_fp(csum[tc.tid]);
-        csum[tc.tid] = 0ull;  // clean for the next group / event
-        const float rel = s / cf[tc.tid].z;
-        reinterpret_cast<float2*>(S.iso)[j] = make_float2(s, rel);
-        if (rel < K.imax) reinterpret_cast<uint32_t*>(S.cands + j)[3] |= 0x80000000u;
+      if (!(opt > K.iso_ptmin)) continue;
+      const unsigned long long wgt = to_fp(opt);
+      for (uint32_t c = 0; c < gn; ++c) {
+        const float4 cv = cf[c];
+        if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == ckey[c])) continue;
+        const float de = oe - cv.x;
+        float dp = op - cv.y;
+        if (dp >= PI_F) dp -= TWO_PI_F;
+        else if (dp < -PI_F) dp += TWO_PI_F;
+        const float dr2 = fmaf(de, de, dp * dp);
+        if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
       }
     }
+    tc.sync();
+    if ((uint32_t)tc.tid < gn) {
+      const uint64_t j = a + g0 + tc.tid;
+      const float s = from_fp(csum[tc.tid]);
+      csum[tc.tid] = 0ull;
+      const float rel = s / cf[tc.tid].z;
+      reinterpret_cast<float2*>(S.iso)[j] = make_float2(s, rel);
+      if (rel < K.imax) reinterpret_cast<uint32_t*>(S.cands + j)[3] |= 0x80000000u;
+    }
   }
-  // the next event reuses the table, the staged candidates and the scan buffers
+  // the next event reuses the table, the staged candidates and the buffers
   tc.sync();
   if (tc.tid == 0)
     reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
@@ -707,7 +807,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
   tc.tid = (int)threadIdx.x % TEAM;
   const uint64_t tbytes = team_smem_bytes(TEAM, p.table_slots, p.nmax_smem);
   unsigned char* mine = smem + p.hot_total + (uint64_t)tc.tix * tbytes;
-  const Tbl st = carve(mine, p.table_slots, p.log2_slots);
+  const Tbl st = carve(mine, p.table_slots, p.nmax_smem);
   unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
   uint32_t* wbuf = (uint32_t*)tail;
   float4* cf = (float4*)(tail + 2 * 32 * 4);
@@ -741,7 +841,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
     if (n <= p.nmax_smem) {
       process_event<TEAM>(S, p.err, K, KD, st, wbuf, cf, ckey, csum, tc, e, a, n);
     } else if (p.gscratch != nullptr && n <= p.g_nmax) {
-      const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_log2);
+      const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_nmax);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys[s] = PDR_EMPTY;
       tc.sync();
       process_event<TEAM>(S, p.err, K, KD, gt, wbuf, cf, ckey, csum, tc, e, a, n);

@@ -272,16 +272,10 @@ int expand_card_fixed(const pdr_card* c, DevCard& D) {
   return PDR_OK;
 }
 
-uint32_t pow2_at_least(uint64_t v) {
-  uint32_t p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
-
-uint32_t log2_of(uint32_t v) {
-  uint32_t l = 0;
-  while ((1u << l) < v) ++l;
-  return l;
+// Tower-table slots for events up to max_n particles: at least 4/3 max_n,
+// a multiple of 32 (at most 3/4 of the slots are ever in use).
+uint32_t slots_at_least(uint32_t max_n) {
+  return std::max<uint32_t>(64, (uint32_t)((((uint64_t)max_n * 4 + 2) / 3 + 31) & ~31ull));
 }
 
 }  // namespace
@@ -327,9 +321,9 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   else if (max_n <= 3000) { team = 512; block = 512; }
   else { team = 1024; block = 1024; }
   const uint32_t nt = block / team;
-  uint32_t slots = std::max<uint32_t>(64, pow2_at_least((uint64_t)max_n * 4 / 3 + 1));
+  uint32_t slots = slots_at_least(max_n);
   while (slots > 64 && hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4) > (uint64_t)slot->smem_optin)
-    slots >>= 1;
+    slots = std::max<uint32_t>(64, (slots / 2) & ~31u);
   const size_t smem = (size_t)(hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4));
   int per_sm = 0;
   if (occupancy_fused(team, block, smem, &per_sm) != cudaSuccess || per_sm < 1)
@@ -358,14 +352,12 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   sg.iso = o->iso; sg.counts = o->counts;
   sg.debug = (b->flags & PDR_BATCH_DEBUG) ? o->debug : nullptr;
   p.table_slots = slots;
-  p.log2_slots = log2_of(slots);
   p.nmax_smem = slots * 3 / 4;
   p.err = d_err;
   if (max_n > p.nmax_smem) {
     // global tower tables in the static array; fewer teams if they do not fit
-    const uint32_t gs = std::max<uint32_t>(64, pow2_at_least((uint64_t)max_n * 4 / 3 + 1));
+    const uint32_t gs = slots_at_least(max_n);
     p.g_slots = gs;
-    p.g_log2 = log2_of(gs);
     p.g_nmax = gs * 3 / 4;
     p.g_team_bytes = global_team_bytes(gs, p.g_nmax);
     const uint64_t room = PDR_NOALLOC_SCRATCH_BYTES - kTableOffset;

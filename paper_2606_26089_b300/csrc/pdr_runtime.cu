@@ -61,12 +61,6 @@ uint32_t next_pow2(uint64_t v) {
   return p;
 }
 
-uint32_t ilog2(uint32_t v) {
-  uint32_t l = 0;
-  while ((1u << l) < v) ++l;
-  return l;
-}
-
 // ---------------------------------------------------------------- pool
 // First-fit allocator over one device region (results of submit(), staging
 // of the host-buffer path, scratch).  256-byte granularity.
@@ -385,7 +379,8 @@ const uint32_t kTeams[] = {32, 64, 128, 256, 512, 1024};
 uint32_t slots_for(uint32_t max_n) {
   // at most 3/4 of the slots can be in use (an event never has more distinct
   // towers than particles); probing stays short at that load
-  return std::max<uint32_t>(64, next_pow2((uint64_t)max_n * 4 / 3 + 1));
+  // (a multiple of 32 slots: the kernel scales its hash to any table size)
+  return std::max<uint32_t>(64, (uint32_t)((((uint64_t)max_n * 4 + 2) / 3 + 31) & ~31ull));
 }
 
 // Build a concrete shape for (team, block) handling events up to max_n in shared
@@ -394,9 +389,10 @@ int make_shape(pdr_ctx* ctx, uint32_t team, uint32_t block, uint32_t want_slots,
                uint32_t hot_bytes, Shape& S) {
   if (!shape_supported(team, block)) return fail(PDR_EINVAL, "unsupported launch shape (team, block)");
   const uint32_t nt = block / team;
-  uint32_t slots = std::max<uint32_t>(64, next_pow2(want_slots));
+  uint32_t slots = std::max<uint32_t>(64, (want_slots + 31u) & ~31u);
   // shrink until the CTA fits in shared memory
-  while (slots > 64 && hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4) > ctx->smem_optin) slots >>= 1;
+  while (slots > 64 && hot_bytes + nt * team_smem_bytes(team, slots, slots * 3 / 4) > ctx->smem_optin)
+    slots = std::max<uint32_t>(64, (slots / 2) & ~31u);
   S.team = team;
   S.block = block;
   S.slots = slots;
@@ -503,14 +499,12 @@ void fill_seg(KSeg& g, const pdr_batch* b, const pdr_outputs* o, uint64_t start,
 // Table and scratch parameters of a launch for events up to max_n.
 int set_tables(pdr_ctx* ctx, KParams& p, const Shape& S, uint32_t max_n) {
   p.table_slots = S.slots;
-  p.log2_slots = ilog2(S.slots);
   p.nmax_smem = S.nmax;
   p.err = ctx->d_err;
   if (max_n > S.nmax) {
     const uint32_t gs = slots_for(max_n);
     if (gs > 65536) return fail(PDR_EOVERFLOW, "event larger than 49152 particles");
     p.g_slots = gs;
-    p.g_log2 = ilog2(gs);
     p.g_nmax = gs * 3 / 4;
     p.g_team_bytes = global_team_bytes(gs, p.g_nmax);
     const uint64_t need = p.g_team_bytes * (uint64_t)S.grid * (S.block / S.team);
