@@ -224,10 +224,18 @@ int pdr_run_multi(pdr_ctx* ctx, const pdr_batch* batches, uint32_t n, const pdr_
 int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,
                       void* stream);
 
-/* End-to-end call with HOST buffers: copies the batch (HOST pointers, ideally
- * pinned) to device memory from the context pool, runs it, and copies every
- * output back into HOST buffers laid out as pdr_outputs (HOST pointers, same
- * sizes), then synchronises `stream`.  Blocking. */
+/* End-to-end call with HOST buffers (pinned memory gives overlapped copies):
+ * the batch (HOST pointers) goes to device memory from the context pool in
+ * chunks of whole events (about 2 M particles each), each chunk runs as soon
+ * as its inputs have arrived, and its records come back while later chunks
+ * are copied in and computed.  Outputs are HOST buffers with the pdr_outputs
+ * record types, DENSE: all tracks of event 0, then of event 1, ... without
+ * gaps, likewise towers, eflow, cands and iso (one iso record per candidate);
+ * counts[4e .. 4e + 3] gives each event's share.  Each record buffer needs
+ * room for n_particles records, counts for n_events; debug is ignored.  The
+ * results are those of pdr_run on the same batch (same bits).  Blocking; the
+ * kernels run on `stream`, the copies on two streams of the context; calls
+ * on one context are serialised. */
 int pdr_run_host(pdr_ctx* ctx, const pdr_batch* host_batch, const pdr_outputs* host_out,
                  const pdr_launch* launch, void* stream);
 

@@ -868,14 +868,18 @@ __global__ void max_event_kernel(const uint64_t* __restrict__ offsets, uint64_t 
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// Dense compaction for host delivery: exclusive scan of per-event counts per
-// collection (single block per collection, chunked), then a gather.
+// Dense compaction for host delivery, one chunk of events at a time: an
+// exclusive scan of the chunk's per-event counts per collection, continuing
+// from the running totals in carry[4] (single block per collection, chunked),
+// then a gather into the dense arrays.  dense_off holds the four collections'
+// offsets with a stride of `stride` entries.
 __global__ void scan_counts_kernel(const uint32_t* __restrict__ counts, uint64_t n_events,
-                                   uint64_t* __restrict__ dense_off /* [4][n_events + 1] */) {
+                                   uint64_t* __restrict__ dense_off, uint64_t stride,
+                                   unsigned long long* __restrict__ carry) {
   const int c = blockIdx.x;  // collection
   __shared__ unsigned long long part[1024];
-  uint64_t* out = dense_off + (uint64_t)c * (n_events + 1);
-  unsigned long long carry = 0;
+  uint64_t* out = dense_off + (uint64_t)c * stride;
+  unsigned long long run = carry[c];
   for (uint64_t base = 0; base < n_events; base += blockDim.x) {
     const uint64_t e = base + threadIdx.x;
     const unsigned long long v = e < n_events ? counts[4 * e + c] : 0ull;
@@ -887,17 +891,20 @@ __global__ void scan_counts_kernel(const uint32_t* __restrict__ counts, uint64_t
       part[threadIdx.x] += u;
       __syncthreads();
     }
-    if (e < n_events) out[e] = carry + part[threadIdx.x] - v;
+    if (e < n_events) out[e] = run + part[threadIdx.x] - v;
     const unsigned long long blk = part[blockDim.x - 1];
     __syncthreads();
-    carry += blk;
+    run += blk;
   }
-  if (threadIdx.x == 0) out[n_events] = carry;
+  if (threadIdx.x == 0) {
+    out[n_events] = run;
+    carry[c] = run;
+  }
 }
 
 __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64_t n_events,
                                     const uint32_t* __restrict__ counts,
-                                    const uint64_t* __restrict__ dense_off, pdr_outputs src,
+                                    const uint64_t* __restrict__ dense_off, uint64_t stride, pdr_outputs src,
                                     pdr_outputs dst) {
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -905,8 +912,8 @@ __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64
   for (uint64_t e = warp; e < n_events; e += nwarps) {
     const uint64_t a = offsets[e];
     const uint32_t nt = counts[4 * e], nw = counts[4 * e + 1], nf = counts[4 * e + 2], nc = counts[4 * e + 3];
-    const uint64_t dt = dense_off[e], dw = dense_off[(n_events + 1) + e];
-    const uint64_t df = dense_off[2 * (n_events + 1) + e], dc = dense_off[3 * (n_events + 1) + e];
+    const uint64_t dt = dense_off[e], dw = dense_off[stride + e];
+    const uint64_t df = dense_off[2 * stride + e], dc = dense_off[3 * stride + e];
     for (uint32_t k = lane; k < nt; k += 32) dst.tracks[dt + k] = src.tracks[a + k];
     for (uint32_t k = lane; k < nw; k += 32) dst.towers[dw + k] = src.towers[a + k];
     for (uint32_t k = lane; k < nf; k += 32) dst.eflow[df + k] = src.eflow[a + k];
@@ -967,12 +974,12 @@ cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_
 }
 
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
-                         uint64_t* dense_off, const pdr_outputs& src, const pdr_outputs& dst,
-                         int n_sms, cudaStream_t s) {
-  scan_counts_kernel<<<4, 1024, 0, s>>>(counts, n_events, dense_off);
+                         uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
+                         const pdr_outputs& src, const pdr_outputs& dst, int n_sms, cudaStream_t s) {
+  scan_counts_kernel<<<4, 1024, 0, s>>>(counts, n_events, dense_off, stride, carry);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gather_dense_kernel<<<n_sms * 8, 256, 0, s>>>(offsets, n_events, counts, dense_off, src, dst);
+  gather_dense_kernel<<<n_sms * 8, 256, 0, s>>>(offsets, n_events, counts, dense_off, stride, src, dst);
   return cudaGetLastError();
 }
 

@@ -30,8 +30,8 @@ cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blo
 cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
                              cudaStream_t s);
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
-                         uint64_t* dense_off, const pdr_outputs& src, const pdr_outputs& dst, int n_sms,
-                         cudaStream_t s);
+                         uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
+                         const pdr_outputs& src, const pdr_outputs& dst, int n_sms, cudaStream_t s);
 }  // namespace pdr
 
 using namespace pdr;
@@ -153,6 +153,8 @@ int set_last_error(int code, const char* msg) { return fail(code, msg); }
 
 struct Server;  // the serving loop (defined with its code below)
 
+#define PDR_HOST_CHUNKS 16  // pipeline depth of the end-to-end host path
+
 struct pdr_ctx {
   int device = 0;
   int n_sms = 0;
@@ -171,6 +173,12 @@ struct pdr_ctx {
   uint64_t gscratch_bytes = 0;
   Server* serve = nullptr;                // serving loop, if started
   std::mutex mu;
+  // end-to-end host path: its copy streams, per-chunk events and a pinned
+  // block for the chunks' record totals (created on first use)
+  std::mutex host_mu;                     // one pdr_run_host at a time per context
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_aux = nullptr;
+  cudaEvent_t ev_in[PDR_HOST_CHUNKS] = {}, ev_comp[PDR_HOST_CHUNKS] = {}, ev_tot[PDR_HOST_CHUNKS] = {};
+  unsigned long long* h_tot = nullptr;    // [PDR_HOST_CHUNKS][4]
 };
 
 namespace {
@@ -641,6 +649,15 @@ int pdr_destroy(pdr_ctx* ctx) {
   for (auto& kv : ctx->cards) cudaFree(kv.second.dev);
   ctx->pool.destroy();
   if (ctx->gscratch) cudaFree(ctx->gscratch);
+  if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
+  if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
+  if (ctx->s_aux) cudaStreamDestroy(ctx->s_aux);
+  for (int k = 0; k < PDR_HOST_CHUNKS; ++k) {
+    if (ctx->ev_in[k]) cudaEventDestroy(ctx->ev_in[k]);
+    if (ctx->ev_comp[k]) cudaEventDestroy(ctx->ev_comp[k]);
+    if (ctx->ev_tot[k]) cudaEventDestroy(ctx->ev_tot[k]);
+  }
+  if (ctx->h_tot) cudaFreeHost(ctx->h_tot);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_word);
   delete ctx;
@@ -857,15 +874,33 @@ int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const
   if (!ho || !ho->tracks || !ho->towers || !ho->eflow || !ho->cands || !ho->iso || !ho->counts)
     return fail(PDR_EINVAL, "null host output buffer");
   cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> hg(ctx->host_mu);
   cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->s_h2d) {
+    if (cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s_aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaHostAlloc((void**)&ctx->h_tot, sizeof(unsigned long long) * 4 * PDR_HOST_CHUNKS, 0) != cudaSuccess)
+      return fail(PDR_EDEVICE, "cannot create the host-path streams");
+    for (int k = 0; k < PDR_HOST_CHUNKS; ++k)
+      if (cudaEventCreateWithFlags(&ctx->ev_in[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_comp[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_tot[k], cudaEventDisableTiming) != cudaSuccess)
+        return fail(PDR_EDEVICE, "cannot create the host-path events");
+  }
   const uint64_t ne = hb->n_events;
   const uint64_t np = ne ? hb->offsets[ne] : 0;
   const uint64_t cap = np ? np : 1;
+  for (uint64_t e = 0; e < ne; ++e)
+    if (hb->offsets[e + 1] < hb->offsets[e]) return fail(PDR_EINVAL, "offsets not monotone");
+  uint32_t max_n = hb->max_event_size;
+  if (max_n == 0)
+    for (uint64_t e = 0; e < ne; ++e) max_n = std::max<uint32_t>(max_n, (uint32_t)(hb->offsets[e + 1] - hb->offsets[e]));
   // device staging from the pool: inputs, slot-layout outputs, dense outputs
   const uint64_t in_bytes = (ne + 1) * 8 + np * (4 * 4 + 4 + 1) + (hb->vz ? np * 4 : 0) + 8 * 256;
   const uint64_t out_bytes = cap * (sizeof(pdr_track) + sizeof(pdr_tower) + sizeof(pdr_eflow) +
                                     sizeof(pdr_cand) + sizeof(pdr_iso)) + (ne + 1) * 16 + 8 * 256;
-  const uint64_t dense_bytes = out_bytes + 4 * (ne + 1) * 8 + 256;
+  const uint64_t dense_bytes = out_bytes + 4 * (ne + 1) * 8 + 4 * 8 + 2 * 256;
   std::unique_lock<std::mutex> g(ctx->mu);
   unsigned char* m = (unsigned char*)ctx->pool.alloc(in_bytes + out_bytes + dense_bytes);
   g.unlock();
@@ -885,6 +920,8 @@ int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const
   db.pdg = (const int32_t*)carve(np * 4);
   db.charge = (const int8_t*)carve(np);
   db.vz = hb->vz ? (const float*)carve(np * 4) : nullptr;
+  db.max_event_size = max_n;
+  db.flags &= ~PDR_BATCH_DEBUG;
   pdr_outputs so{};
   so.tracks = (pdr_track*)carve(cap * sizeof(pdr_track));
   so.towers = (pdr_tower*)carve(cap * sizeof(pdr_tower));
@@ -899,55 +936,87 @@ int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const
   dd.cands = (pdr_cand*)carve(cap * sizeof(pdr_cand));
   dd.iso = (pdr_iso*)carve(cap * sizeof(pdr_iso));
   uint64_t* dense_off = (uint64_t*)carve(4 * (ne + 1) * 8);
+  unsigned long long* carry = (unsigned long long*)carve(4 * 8);
+  cudaStream_t s_in = ctx->s_h2d, s_out = ctx->s_d2h, s_aux = ctx->s_aux;
   auto done = [&](int code) {
+    cudaStreamSynchronize(s_in);
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(s_aux);
+    cudaStreamSynchronize(s_out);
     std::lock_guard<std::mutex> g2(ctx->mu);
     ctx->pool.release(mem0);
     return code;
   };
-#define PDR_H2D(dst, src, bytes)                                                              \
-  if ((bytes) && cudaMemcpyAsync((void*)(dst), (src), (bytes), cudaMemcpyHostToDevice, s) != cudaSuccess) \
-    return done(fail(PDR_EDEVICE, "host-to-device copy"));
-  PDR_H2D(db.offsets, hb->offsets, (ne + 1) * 8);
-  PDR_H2D(db.pt, hb->pt, np * 4);
-  PDR_H2D(db.eta, hb->eta, np * 4);
-  PDR_H2D(db.phi, hb->phi, np * 4);
-  PDR_H2D(db.mass, hb->mass, np * 4);
-  PDR_H2D(db.pdg, hb->pdg, np * 4);
-  PDR_H2D(db.charge, hb->charge, np);
-  if (hb->vz) PDR_H2D(db.vz, hb->vz, np * 4);
-#undef PDR_H2D
-  db.flags &= ~PDR_BATCH_DEBUG;
-  {
-    std::lock_guard<std::mutex> g2(ctx->mu);
-    uint32_t max_n = 0;
-    if ((rc = batch_max_n(ctx, &db, s, &max_n))) return done(rc);
-    if ((rc = launch_batches(ctx, &db, &so, 1, plan_launch(ctx, db.card_id, max_n, l), max_n, s))) return done(rc);
+  // Chunks of whole events, about 2 M particles each (at most PDR_HOST_CHUNKS):
+  // all input copies are queued at once (copy stream), each chunk's kernels
+  // wait for its inputs (the caller's stream), a third stream brings back each
+  // chunk's record totals and counts, and each chunk's records follow on the
+  // second copy stream as soon as its totals are known on the host.
+  const uint32_t K = ne == 0 ? 0 : (uint32_t)std::min<uint64_t>(
+      std::min<uint64_t>(PDR_HOST_CHUNKS, ne), std::max<uint64_t>(1, np >> 21));
+  std::vector<uint64_t> eb(K + 1, ne);
+  for (uint32_t k = 0; k < K; ++k)  // first event of each chunk, by particle count
+    eb[k] = (uint64_t)(std::lower_bound(hb->offsets, hb->offsets + ne, np * k / K) - hb->offsets);
+  eb[0] = 0;
+  for (uint32_t k = 1; k < K; ++k) eb[k] = std::max(eb[k], eb[k - 1]);
+  const Plan P = plan_launch(ctx, db.card_id, max_n, l);
+  if (K > 0 && cudaMemsetAsync(carry, 0, 4 * 8, s) != cudaSuccess) return done(fail(PDR_EDEVICE, "memset"));
+#define PDR_CP(dst, src, bytes, kind, st)                                                      \
+  if ((bytes) && cudaMemcpyAsync((void*)(dst), (const void*)(src), (bytes), kind, st) != cudaSuccess) \
+    return done(fail(PDR_EDEVICE, "host-device copy"));
+  for (uint32_t k = 0; k < K; ++k) {
+    const uint64_t e0 = eb[k], e1 = eb[k + 1], nk = e1 - e0;
+    const uint64_t a0 = hb->offsets[e0], a1 = hb->offsets[e1], pk = a1 - a0;
+    PDR_CP(db.offsets + e0, hb->offsets + e0, (nk + 1) * 8, cudaMemcpyHostToDevice, s_in);
+    PDR_CP(db.pt + a0, hb->pt + a0, pk * 4, cudaMemcpyHostToDevice, s_in);
+    PDR_CP(db.eta + a0, hb->eta + a0, pk * 4, cudaMemcpyHostToDevice, s_in);
+    PDR_CP(db.phi + a0, hb->phi + a0, pk * 4, cudaMemcpyHostToDevice, s_in);
+    PDR_CP(db.mass + a0, hb->mass + a0, pk * 4, cudaMemcpyHostToDevice, s_in);
+    PDR_CP(db.pdg + a0, hb->pdg + a0, pk * 4, cudaMemcpyHostToDevice, s_in);
+    PDR_CP(db.charge + a0, hb->charge + a0, pk, cudaMemcpyHostToDevice, s_in);
+    if (hb->vz) PDR_CP(db.vz + a0, hb->vz + a0, pk * 4, cudaMemcpyHostToDevice, s_in);
+    cudaEventRecord(ctx->ev_in[k], s_in);
+    cudaStreamWaitEvent(s, ctx->ev_in[k], 0);
+    if (nk > 0) {
+      // the chunk as a batch of its own: same arrays (absolute offsets), its
+      // events' indices, its counts
+      pdr_batch bk = db;
+      bk.n_events = nk;
+      bk.offsets = db.offsets + e0;
+      bk.event_index_base = hb->event_index_base + (uint32_t)e0;
+      pdr_outputs ok = so;
+      ok.counts = so.counts + 4 * e0;
+      {
+        std::lock_guard<std::mutex> g2(ctx->mu);
+        if ((rc = launch_batches(ctx, &bk, &ok, 1, P, max_n, s))) return done(rc);
+      }
+      cudaError_t e = launch_dense(bk.offsets, nk, ok.counts, dense_off + e0, ne + 1, carry, so, dd, ctx->n_sms, s);
+      if (e != cudaSuccess) return done(cuda_fail(e, "dense compaction"));
+    }
+    cudaEventRecord(ctx->ev_comp[k], s);
+    // the chunk's record totals (running, after the chunk) and its counts
+    cudaStreamWaitEvent(s_aux, ctx->ev_comp[k], 0);
+    PDR_CP(ctx->h_tot + 4 * k, carry, 4 * 8, cudaMemcpyDeviceToHost, s_aux);
+    cudaEventRecord(ctx->ev_tot[k], s_aux);
+    PDR_CP(ho->counts + 4 * e0, so.counts + 4 * e0, nk * 16, cudaMemcpyDeviceToHost, s_aux);
   }
-  if (ne > 0) {
-    cudaError_t e = launch_dense(db.offsets, ne, so.counts, dense_off, so, dd, ctx->n_sms, s);
-    if (e != cudaSuccess) return done(cuda_fail(e, "dense compaction"));
+  // dense records of each chunk, as soon as its totals are known on the host
+  // (their kernels are then complete: the totals' copy waited for them)
+  uint64_t prev[4] = {0, 0, 0, 0};
+  for (uint32_t k = 0; k < K; ++k) {
+    if (cudaEventSynchronize(ctx->ev_tot[k]) != cudaSuccess) return done(fail(PDR_EDEVICE, "event synchronise"));
+    const unsigned long long* t = ctx->h_tot + 4 * k;
+    PDR_CP(ho->tracks + prev[0], dd.tracks + prev[0], (t[0] - prev[0]) * sizeof(pdr_track), cudaMemcpyDeviceToHost, s_out);
+    PDR_CP(ho->towers + prev[1], dd.towers + prev[1], (t[1] - prev[1]) * sizeof(pdr_tower), cudaMemcpyDeviceToHost, s_out);
+    PDR_CP(ho->eflow + prev[2], dd.eflow + prev[2], (t[2] - prev[2]) * sizeof(pdr_eflow), cudaMemcpyDeviceToHost, s_out);
+    PDR_CP(ho->cands + prev[3], dd.cands + prev[3], (t[3] - prev[3]) * sizeof(pdr_cand), cudaMemcpyDeviceToHost, s_out);
+    PDR_CP(ho->iso + prev[3], dd.iso + prev[3], (t[3] - prev[3]) * sizeof(pdr_iso), cudaMemcpyDeviceToHost, s_out);
+    for (int c = 0; c < 4; ++c) prev[c] = t[c];
   }
-  // totals per collection, then copy back exactly the records produced
-  uint64_t totals[4] = {0, 0, 0, 0};
-  if (ne > 0) {
-    for (int c = 0; c < 4; ++c)
-      if (cudaMemcpyAsync(&totals[c], dense_off + (uint64_t)c * (ne + 1) + ne, 8, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess)
-        return done(fail(PDR_EDEVICE, "device-to-host copy"));
-  }
-  if (cudaMemcpyAsync(ho->counts, so.counts, ne * 16, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return done(fail(PDR_EDEVICE, "device-to-host copy"));
-  if (cudaStreamSynchronize(s) != cudaSuccess) return done(fail(PDR_EDEVICE, "stream synchronise"));
-#define PDR_D2H(dst, src, bytes)                                                               \
-  if ((bytes) && cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyDeviceToHost, s) != cudaSuccess) \
-    return done(fail(PDR_EDEVICE, "device-to-host copy"));
-  PDR_D2H(ho->tracks, dd.tracks, totals[0] * sizeof(pdr_track));
-  PDR_D2H(ho->towers, dd.towers, totals[1] * sizeof(pdr_tower));
-  PDR_D2H(ho->eflow, dd.eflow, totals[2] * sizeof(pdr_eflow));
-  PDR_D2H(ho->cands, dd.cands, totals[3] * sizeof(pdr_cand));
-  PDR_D2H(ho->iso, dd.iso, totals[3] * sizeof(pdr_iso));
-#undef PDR_D2H
-  if (cudaStreamSynchronize(s) != cudaSuccess) return done(fail(PDR_EDEVICE, "stream synchronise"));
+#undef PDR_CP
+  if (cudaStreamSynchronize(s_out) != cudaSuccess || cudaStreamSynchronize(s_aux) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return done(fail(PDR_EDEVICE, "stream synchronise"));
   return done(PDR_OK);
 }
 

@@ -286,6 +286,38 @@ def test_host_buffer_path_returns_dense_records(B, ctx, cards, synth):
             cum[c] += m
 
 
+def _dense_index(offsets, counts):
+    """Slot-layout positions of the dense records of one collection."""
+    starts = np.repeat(offsets[:-1].astype(np.int64), counts)
+    within = np.arange(int(counts.sum()), dtype=np.int64) - np.repeat(np.cumsum(counts) - counts, counts)
+    return starts + within
+
+
+def test_host_buffer_path_pipelined_chunks_bitwise(B, ctx, cards, synth):
+    """A batch large enough for several pipeline chunks (about 2 M particles
+    each): the dense host records equal pdr_run's slot-layout records."""
+    cid, _ = cards["cms_like"]
+    b = synth.make("batched", n_events=16000)
+    assert b.n_particles > 3 * (1 << 21)
+    ref = P.run_gpu(ctx, cid, b, seed=12, debug=False)
+    n = b.n_particles
+    hb, keep = B.pinned_host_batch(b, cid, 12)
+    out = dict(tracks=np.zeros((n, 4), np.float32), towers=np.zeros((n, 3), np.float32),
+               eflow=np.zeros((n, 3), np.float32), cands=np.zeros((n, 4), np.float32),
+               iso=np.zeros((n, 2), np.float32), counts=np.zeros((b.n_events, 4), np.uint32))
+    ho = B.pdr_outputs()
+    for k, v in out.items():
+        setattr(ho, k, v.ctypes.data)
+    ctx.run_host(hb, ho)
+    assert np.array_equal(out["counts"], ref["counts"])
+    for c, k in enumerate(("tracks", "towers", "eflow", "cands")):
+        idx = _dense_index(b.offsets, ref["counts"][:, c].astype(np.int64))
+        m = idx.shape[0]
+        assert np.array_equal(out[k][:m].view(np.uint32), ref[k][idx].view(np.uint32)), k
+        if k == "cands":
+            assert np.array_equal(out["iso"][:m].view(np.uint32), ref["iso"][idx].view(np.uint32))
+
+
 def test_tickets_submit_wait_fetch_release(B, ctx, cards, synth):
     cid, _ = cards["cms_like"]
     b = synth.make("batched", n_events=20)
