@@ -3,6 +3,7 @@
 // library only.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "pdr.h"
@@ -170,13 +171,21 @@ PDR_HD inline uint64_t table_bytes(uint32_t slots, uint32_t nmax) {
   return (b + 15) & ~15ull;
 }
 
+// A team's shared scratch after its table: scan buffers (double-buffered),
+// the staged isolation candidates (eta, phi, pT', particle index; own tower
+// key; record info word; fixed-point cone sums).
+struct TeamTail {
+  uint32_t wbuf[2 * 32];
+  float4 cf[PDR_CMAX];
+  uint32_t ckey[PDR_CMAX];
+  uint32_t cinfo[PDR_CMAX];
+  unsigned long long csum[PDR_CMAX];
+};
+
 // Shared-memory bytes needed by one team of a launch shape (the card cache is
 // counted separately, once per CTA).
 PDR_HD inline uint64_t team_smem_bytes(uint32_t team, uint32_t slots, uint32_t nmax) {
-  uint64_t b = table_bytes(slots, nmax);
-  b += 2 * 32 * 4;                                  // scan buffers (double-buffered)
-  b += PDR_CMAX * (16 + 4 + 4 + 8);                 // isolation candidates (eta, phi, pt, idx; key; pad) and sums
-  return (b + 15) & ~15ull;
+  return table_bytes(slots, nmax) + sizeof(TeamTail);
 }
 
 PDR_HD inline uint64_t global_team_bytes(uint32_t slots, uint32_t nmax) {

@@ -87,6 +87,14 @@ __device__ __forceinline__ void cosh_sinh(float x, float& ch, float& sh) {
   sh = copysignf(s, x);
 }
 
+// asinh(u) = sign(u) log(|u| + sqrt(u^2 + 1)) with the hardware log2 (absolute
+// error about 1e-7; the argument is >= 1, so no cancellation): used for the
+// surface pseudorapidity, whose tolerance is 2e-6 max(|eta|, 1).
+__device__ __forceinline__ float asinh_fast(float u) {
+  const float au = fabsf(u);
+  return copysignf(__logf(au + sqrtf(fmaf(au, au, 1.0f))), u);
+}
+
 // (2k + 1) / 2^24 for the top 23 bits k of w: exact in float32.
 __device__ __forceinline__ float u01(uint32_t w) {
   return (__uint2float_rn(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
@@ -215,7 +223,7 @@ __device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta,
       turn = h * (0.5f * psi);
     }
   }
-  P.eta_pos = asinhf(fdiv(num, den));
+  P.eta_pos = asinh_fast(fdiv(num, den));
   float pphi = phi - turn;
   if (pphi < -PI_F) pphi += TWO_PI_F;
   else if (pphi >= PI_F) pphi -= TWO_PI_F;
@@ -563,6 +571,28 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
   o.det = dE * ich;
 }
 
+// ------------------------------------------------------------ isolation
+#define PDR_ISO_TRACK 0x80000000u    // object tag: a track (particle index), else a tower key
+
+// Adds an object's fixed-point pT to every staged candidate whose cone holds it.
+__device__ __forceinline__ void iso_object(const HotCard& K, float4 obj, uint32_t gn, TeamTail& tt) {
+  const uint32_t tag = __float_as_uint(obj.w);
+  const bool is_trk = (tag & PDR_ISO_TRACK) != 0u;
+  const uint32_t oid = tag & ~PDR_ISO_TRACK;
+  const unsigned long long wgt = to_fp(obj.z);
+  for (uint32_t c = 0; c < gn; ++c) {
+    const float4 cv = tt.cf[c];
+    // the candidate's own track / own tower
+    if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == tt.ckey[c])) continue;
+    const float de = obj.x - cv.x;
+    float dp = obj.y - cv.y;
+    if (dp >= PI_F) dp -= TWO_PI_F;
+    else if (dp < -PI_F) dp += TWO_PI_F;
+    const float dr2 = fmaf(de, de, dp * dp);
+    if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&tt.csum[c], wgt);
+  }
+}
+
 // ------------------------------------------------------------- one event
 // A team of TEAM threads walks the event in chunks of TEAM particles:
 //   1a  particles: S0, S1, S5 placement and deposit; the smearing jobs, in
@@ -576,8 +606,7 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
 //       EFlow objects
 template <int TEAM>
 __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
-                                              const Tbl& T, uint32_t* wbuf, float4* cf, uint32_t* ckey,
-                                              unsigned long long* csum, const TeamCtx<TEAM>& tc,
+                                              const Tbl& T, TeamTail& tt, const TeamCtx<TEAM>& tc,
                                               uint64_t e, uint64_t a, uint32_t n) {
   const uint32_t event = S.event_base + (uint32_t)e;
   const bool dbg = S.debug != nullptr;
@@ -598,7 +627,7 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     if (valid) T.pinfo[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
     const bool has_job = o.job != PDR_EMPTY;
     uint32_t tot;
-    const uint32_t pre = team_scan2<TEAM>(has_job, false, wbuf + 32 * flip, tot, tc);
+    const uint32_t pre = team_scan2<TEAM>(has_job, false, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (slot != PDR_EMPTY && !claimed) {  // after the barrier that orders the claimers' stores
       atomicAdd(&T.esum[slot], e_fp);
@@ -631,7 +660,7 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
             (r.tracked ? PDR_F_TRACKED : 0u) | (r.cand ? PDR_F_CAND : 0u);
     }
     uint32_t tot;
-    const uint32_t pre = team_scan2<TEAM>(r.tracked, r.cand, wbuf + 32 * flip, tot, tc);
+    const uint32_t pre = team_scan2<TEAM>(r.tracked, r.cand, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (r.tracked || r.cand) {
       const float eta = __ldg(S.eta + a + i), phi = __ldg(S.phi + a + i);
@@ -647,8 +676,9 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
         // own tower key, read back by the isolation of candidates beyond the staged ones
         reinterpret_cast<float2*>(S.iso)[a + jc] = make_float2(__uint_as_float(key), 0.0f);
         if (jc < PDR_CMAX) {  // staged for the isolation
-          cf[jc] = make_float4(eta, phi, r.cpt, __uint_as_float(i));
-          ckey[jc] = key;
+          tt.cf[jc] = make_float4(eta, phi, r.cpt, __uint_as_float(i));
+          tt.ckey[jc] = key;
+          tt.cinfo[jc] = i | ((uint32_t)r.cc << 28);
         }
       }
     }
@@ -656,7 +686,6 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     n_cand += tot >> 16;
   }
   tc.sync();
-
   // ---- 2: towers (S6, S7), each by its lowest-index depositing particle;
   // EFlow neutrals and tracks add their pT to the staged candidates' cones (S8)
   uint32_t n_twr = 0, n_ef = 0;
@@ -677,41 +706,19 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
           if (to.ef && gn0 > 0 && to.det > K.iso_ptmin) {
             const int calo = (int)(key >> 24), ring = (int)(pi >> 16);
             const float oe = KD[K.calo[calo].ring_off + 3 * ring];
-            const float op = tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring);
-            const unsigned long long wgt = to_fp(to.det);
-            for (uint32_t c = 0; c < gn0; ++c) {
-              if (key == ckey[c]) continue;  // the candidate's own tower
-              const float4 cv = cf[c];
-              const float de = oe - cv.x;
-              float dp = op - cv.y;
-              if (dp >= PI_F) dp -= TWO_PI_F;
-              else if (dp < -PI_F) dp += TWO_PI_F;
-              const float dr2 = fmaf(de, de, dp * dp);
-              if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
-            }
+            iso_object(K, make_float4(oe, tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring), to.det,
+                                      __uint_as_float(key)), gn0, tt);
           }
         }
       }
     }
     if (gn0 > 0 && i < n_trk) {
       const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + i];
-      if (t.x > K.iso_ptmin) {
-        const unsigned long long wgt = to_fp(t.x);
-        const uint32_t oid = __float_as_uint(t.w);
-        for (uint32_t c = 0; c < gn0; ++c) {
-          const float4 cv = cf[c];
-          if (oid == __float_as_uint(cv.w)) continue;  // the candidate's own track
-          const float de = t.y - cv.x;
-          float dp = t.z - cv.y;
-          if (dp >= PI_F) dp -= TWO_PI_F;
-          else if (dp < -PI_F) dp += TWO_PI_F;
-          const float dr2 = fmaf(de, de, dp * dp);
-          if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
-        }
-      }
+      if (t.x > K.iso_ptmin)
+        iso_object(K, make_float4(t.y, t.z, t.x, __uint_as_float(__float_as_uint(t.w) | PDR_ISO_TRACK)), gn0, tt);
     }
     uint32_t tot;
-    const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, wbuf + 32 * flip, tot, tc);
+    const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (to.kept) {
       pdr_tower* r = S.towers + a + n_twr + (pre & 0xFFFFu);
@@ -728,12 +735,15 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
   // ---- 3: isolation results (S8).  The staged candidates received every
   // object's pT during 2 (its last team scan orders those sums before this
   // read); further groups of PDR_CMAX candidates loop over all EFlow objects.
-  if ((uint32_t)tc.tid < gn0) {
-    const float s = from_fp(csum[tc.tid]);
-    csum[tc.tid] = 0ull;  // clean for the next group / event
-    const float rel = s / cf[tc.tid].z;
-    reinterpret_cast<float2*>(S.iso)[a + tc.tid] = make_float2(s, rel);
-    if (rel < K.imax) reinterpret_cast<uint32_t*>(S.cands + a + tc.tid)[3] |= 0x80000000u;
+  if (gn0 > 0) {
+    if ((uint32_t)tc.tid < gn0) {
+      const uint32_t c = tc.tid;
+      const float s = from_fp(tt.csum[c]);
+      tt.csum[c] = 0ull;  // clean for the next group / event
+      const float rel = s / tt.cf[c].z;
+      reinterpret_cast<float2*>(S.iso)[a + c] = make_float2(s, rel);
+      reinterpret_cast<uint32_t*>(S.cands + a + c)[3] = tt.cinfo[c] | (rel < K.imax ? 0x80000000u : 0u);
+    }
   }
   for (uint32_t g0 = PDR_CMAX; g0 < n_cand; g0 += PDR_CMAX) {
     const uint32_t gn = min((uint32_t)PDR_CMAX, n_cand - g0);
@@ -742,8 +752,9 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     if ((uint32_t)tc.tid < gn) {  // candidates beyond the staged ones
       const uint64_t j = a + g0 + tc.tid;
       const float4 c = reinterpret_cast<const float4*>(S.cands)[j];
-      cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
-      ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(S.iso)[j].x);
+      tt.cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
+      tt.ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(S.iso)[j].x);
+      tt.cinfo[tc.tid] = __float_as_uint(c.w);
     }
     tc.sync();
     for (uint32_t j = tc.tid; j < n_obj; j += TEAM) {
@@ -762,24 +773,24 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
       if (!(opt > K.iso_ptmin)) continue;
       const unsigned long long wgt = to_fp(opt);
       for (uint32_t c = 0; c < gn; ++c) {
-        const float4 cv = cf[c];
-        if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == ckey[c])) continue;
+        const float4 cv = tt.cf[c];
+        if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == tt.ckey[c])) continue;
         const float de = oe - cv.x;
         float dp = op - cv.y;
         if (dp >= PI_F) dp -= TWO_PI_F;
         else if (dp < -PI_F) dp += TWO_PI_F;
         const float dr2 = fmaf(de, de, dp * dp);
-        if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&csum[c], wgt);
+        if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&tt.csum[c], wgt);
       }
     }
     tc.sync();
     if ((uint32_t)tc.tid < gn) {
       const uint64_t j = a + g0 + tc.tid;
-      const float s = from_fp(csum[tc.tid]);
-      csum[tc.tid] = 0ull;
-      const float rel = s / cf[tc.tid].z;
+      const float s = from_fp(tt.csum[tc.tid]);
+      tt.csum[tc.tid] = 0ull;
+      const float rel = s / tt.cf[tc.tid].z;
       reinterpret_cast<float2*>(S.iso)[j] = make_float2(s, rel);
-      if (rel < K.imax) reinterpret_cast<uint32_t*>(S.cands + j)[3] |= 0x80000000u;
+      reinterpret_cast<uint32_t*>(S.cands + j)[3] = tt.cinfo[tc.tid] | (rel < K.imax ? 0x80000000u : 0u);
     }
   }
   // the next event reuses the table, the staged candidates and the buffers
@@ -809,12 +820,9 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
   unsigned char* mine = smem + p.hot_total + (uint64_t)tc.tix * tbytes;
   const Tbl st = carve(mine, p.table_slots, p.nmax_smem);
   unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
-  uint32_t* wbuf = (uint32_t*)tail;
-  float4* cf = (float4*)(tail + 2 * 32 * 4);
-  uint32_t* ckey = (uint32_t*)(cf + PDR_CMAX);
-  unsigned long long* csum = (unsigned long long*)(ckey + 2 * PDR_CMAX);
+  TeamTail& tt = *reinterpret_cast<TeamTail*>(tail);
   for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys[s] = PDR_EMPTY;
-  if ((uint32_t)tc.tid < PDR_CMAX) csum[tc.tid] = 0ull;
+  if ((uint32_t)tc.tid < PDR_CMAX) tt.csum[tc.tid] = 0ull;
   __syncthreads();
   const uint64_t gteam = (uint64_t)blockIdx.x * NT + tc.tix;
   const uint64_t nteams = (uint64_t)gridDim.x * NT;
@@ -839,12 +847,12 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
       continue;
     }
     if (n <= p.nmax_smem) {
-      process_event<TEAM>(S, p.err, K, KD, st, wbuf, cf, ckey, csum, tc, e, a, n);
+      process_event<TEAM>(S, p.err, K, KD, st, tt, tc, e, a, n);
     } else if (p.gscratch != nullptr && n <= p.g_nmax) {
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_nmax);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys[s] = PDR_EMPTY;
       tc.sync();
-      process_event<TEAM>(S, p.err, K, KD, gt, wbuf, cf, ckey, csum, tc, e, a, n);
+      process_event<TEAM>(S, p.err, K, KD, gt, tt, tc, e, a, n);
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);
