@@ -799,37 +799,20 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
 }
 
-// ------------------------------------------------------------------ kernel
-// Shared memory: the card images of the launch (hot_total), then per team its
-// tower table, particle info, scan buffers and isolation candidates.
-// Register cap: at most 64 registers a thread (1024 / BLOCK resident CTAs).
-// The launch covers up to PDR_LAUNCH_SEGS batches (each with its own card,
-// inputs, outputs and seed) as one launch-wide sequence of events.
-template <int TEAM, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1)
-    fused_kernel(const __grid_constant__ KParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// The persistent event loop of one team.  ONE: the launch holds a single
+// batch, whose fields the compiler then reads straight from the parameter
+// block (no per-event segment lookup).
+template <int TEAM, int BLOCK, bool ONE>
+__device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem, const TeamCtx<TEAM>& tc,
+                                           const Tbl& st, TeamTail& tt) {
   constexpr int NT = BLOCK / TEAM;
-  for (uint32_t c = 0; c < p.n_cards; ++c)
-    for (uint32_t k = threadIdx.x; k < p.hot_bytes[c] / 16; k += BLOCK)
-      reinterpret_cast<uint4*>(smem + p.hot_off[c])[k] = __ldg(reinterpret_cast<const uint4*>(p.hot[c]) + k);
-  TeamCtx<TEAM> tc;
-  tc.tix = (int)threadIdx.x / TEAM;
-  tc.tid = (int)threadIdx.x % TEAM;
-  const uint64_t tbytes = team_smem_bytes(TEAM, p.table_slots, p.nmax_smem);
-  unsigned char* mine = smem + p.hot_total + (uint64_t)tc.tix * tbytes;
-  const Tbl st = carve(mine, p.table_slots, p.nmax_smem);
-  unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
-  TeamTail& tt = *reinterpret_cast<TeamTail*>(tail);
-  for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys[s] = PDR_EMPTY;
-  if ((uint32_t)tc.tid < PDR_CMAX) tt.csum[tc.tid] = 0ull;
-  __syncthreads();
   const uint64_t gteam = (uint64_t)blockIdx.x * NT + tc.tix;
   const uint64_t nteams = (uint64_t)gridDim.x * NT;
   uint32_t sg = 0;  // segment cursor: a team's events only move forward
   for (uint64_t ge = gteam; ge < p.n_events; ge += nteams) {
-    while (sg + 1 < p.n_segs && ge >= p.seg[sg + 1].event_start) ++sg;
-    const KSeg& S = p.seg[sg];
+    if (!ONE)
+      while (sg + 1 < p.n_segs && ge >= p.seg[sg + 1].event_start) ++sg;
+    const KSeg& S = p.seg[ONE ? 0 : sg];
     const uint64_t e = ge - S.event_start;
     const HotCard& K = *reinterpret_cast<const HotCard*>(smem + p.hot_off[S.card]);
     const float* KD = reinterpret_cast<const float*>(smem + p.hot_off[S.card] + sizeof(HotCard));
@@ -860,6 +843,34 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
       }
     }
   }
+}
+
+// ------------------------------------------------------------------ kernel
+// Shared memory: the card images of the launch (hot_total), then per team its
+// tower table, particle info, scan buffers and isolation candidates.
+// Register cap: at most 64 registers a thread (1024 / BLOCK resident CTAs).
+// The launch covers up to PDR_LAUNCH_SEGS batches (each with its own card,
+// inputs, outputs and seed) as one launch-wide sequence of events.
+template <int TEAM, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1)
+    fused_kernel(const __grid_constant__ KParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (uint32_t c = 0; c < p.n_cards; ++c)
+    for (uint32_t k = threadIdx.x; k < p.hot_bytes[c] / 16; k += BLOCK)
+      reinterpret_cast<uint4*>(smem + p.hot_off[c])[k] = __ldg(reinterpret_cast<const uint4*>(p.hot[c]) + k);
+  TeamCtx<TEAM> tc;
+  tc.tix = (int)threadIdx.x / TEAM;
+  tc.tid = (int)threadIdx.x % TEAM;
+  const uint64_t tbytes = team_smem_bytes(TEAM, p.table_slots, p.nmax_smem);
+  unsigned char* mine = smem + p.hot_total + (uint64_t)tc.tix * tbytes;
+  const Tbl st = carve(mine, p.table_slots, p.nmax_smem);
+  unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
+  TeamTail& tt = *reinterpret_cast<TeamTail*>(tail);
+  for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys[s] = PDR_EMPTY;
+  if ((uint32_t)tc.tid < PDR_CMAX) tt.csum[tc.tid] = 0ull;
+  __syncthreads();
+  if (p.n_segs == 1) event_loop<TEAM, BLOCK, true>(p, smem, tc, st, tt);
+  else event_loop<TEAM, BLOCK, false>(p, smem, tc, st, tt);
 }
 
 // ------------------------------------------------------- auxiliary kernels
