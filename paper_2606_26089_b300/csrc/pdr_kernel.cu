@@ -71,6 +71,67 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 __device__ __forceinline__ float fdiv(float a, float b) { return a * rcp_approx(b); }
 
+// Square root to 1 ulp (the hardware approximation; measured over a spread of
+// magnitudes: relative error below 1e-7): energies, smearing widths and the
+// Box-Muller radius need only a few ulp.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Polynomial approximations, coefficients from a least-squares fit on
+// Chebyshev nodes in double precision (truncation error far below float
+// rounding on the stated ranges):
+//   asin(x) = x + x^3 P(x^2) on [0, 1/2]             (fit error ~1e-9)
+//   sin(x)  = x + x^3 Q(x^2) on [0, pi/2]            (fit error ~2e-10)
+//   ln(1 - v) = -v L(v)      on [0, 1/4]             (fit error ~3e-9)
+__device__ __forceinline__ float asin_half(float x) {
+  const float t = x * x;
+  float p = fmaf(t, 0.033805817f, 0.017077811f);
+  p = fmaf(t, p, 0.031116169f);
+  p = fmaf(t, p, 0.04459803f);
+  p = fmaf(t, p, 0.07500099f);
+  p = fmaf(t, p, 0.16666666f);
+  return fmaf(x * t, p, x);
+}
+
+__device__ __forceinline__ float sin_quarter(float x) {
+  const float t = x * x;
+  float q = fmaf(t, -2.4080528e-08f, 2.753648e-06f);
+  q = fmaf(t, q, -0.00019841087f);
+  q = fmaf(t, q, 0.008333333f);
+  q = fmaf(t, q, -0.16666667f);
+  return fmaf(x * t, q, x);
+}
+
+// sin on [0, pi]: reflected to [0, pi/2] with pi split in two floats.
+__device__ __forceinline__ float sin_half_turn(float y) {
+  return sin_quarter(y > PIO2_HI ? (3.14159274101257324f - y) + -8.74227766e-8f : y);
+}
+
+// ln u for u in (0, 1): hardware log2 below 3/4 (relative error < 5e-7
+// there, |ln u| > 0.28), -v L(v) with v = 1 - u (exact) above.
+__device__ __forceinline__ float ln_unit(float u) {
+  const float v = 1.0f - u;
+  float p = fmaf(v, 0.33390906f, 0.08952039f);
+  p = fmaf(v, p, 0.21425246f);
+  p = fmaf(v, p, 0.24869019f);
+  p = fmaf(v, p, 0.33338976f);
+  p = fmaf(v, p, 0.4999991f);
+  p = fmaf(v, p, 1.0f);
+  return u > 0.75f ? -v * p : __logf(u);
+}
+
+// cos(2 pi u) for u in (0, 1): folded exactly in turns to sin of at most a
+// quarter turn (cos(2 pi u) = -cos(pi t), t = |2u - 1|).
+__device__ __forceinline__ float cos_two_pi(float u) {
+  const float t = fabsf(2.0f * u - 1.0f);
+  const float r = t > 0.5f ? t - 0.5f : 0.5f - t;
+  const float s = sin_quarter(PI_F * r);
+  return t > 0.5f ? s : -s;
+}
+
 // cosh and sinh from one exponential: cosh = (e + 1/e) / 2; sinh likewise for
 // |x| >= 1/2 (no cancellation there: e - 1/e >= 1.04) and from its odd Taylor
 // series through x^9 below 1/2 (truncation < 3e-11 relative).
@@ -92,7 +153,7 @@ __device__ __forceinline__ void cosh_sinh(float x, float& ch, float& sh) {
 // surface pseudorapidity, whose tolerance is 2e-6 max(|eta|, 1).
 __device__ __forceinline__ float asinh_fast(float u) {
   const float au = fabsf(u);
-  return copysignf(__logf(au + sqrtf(fmaf(au, au, 1.0f))), u);
+  return copysignf(__logf(au + sqrt_approx(fmaf(au, au, 1.0f))), u);
 }
 
 // (2k + 1) / 2^24 for the top 23 bits k of w: exact in float32.
@@ -100,15 +161,16 @@ __device__ __forceinline__ float u01(uint32_t w) {
   return (__uint2float_rn(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
 }
 
-// Box-Muller, cosine branch.
+// Box-Muller, cosine branch (over all 2^23 inputs of each word the deviate
+// is within 1e-6 absolute of its FP64 value).
 __device__ __forceinline__ float normal(uint32_t wa, uint32_t wb) {
-  return sqrtf(-2.0f * logf(u01(wa))) * cospif(2.0f * u01(wb));
+  return sqrt_approx(-2.0f * ln_unit(u01(wa))) * cos_two_pi(u01(wb));
 }
 
 // Log-normal with mean x and relative variance rel2 = (sigma/x)^2.
 __device__ __forceinline__ float lognormal(float x, float rel2, float z) {
   const float s2 = log1pf(rel2);
-  const float s = sqrtf(s2);
+  const float s = sqrt_approx(s2);
   return x * expf(fmaf(s, z, -0.5f * s2));
 }
 
@@ -165,70 +227,48 @@ struct Prop {
 // S1: straight line (neutral, or B = 0) or helix from (0, 0, vz) to the
 // cylinder R, +-L.  Helix radius r = pT / (0.299792458 |q| |B|); the barrel is
 // reached iff 2 pT >= c = 0.299792458 |q| |B| R, at turning angle
-// 2 asin(c / 2pT); otherwise the endcap after psi = s_z / r < 2 pi.
+// 2 asin(c / 2pT); otherwise the endcap after psi = s_z / r < 2 pi.  Both
+// crossings are computed for every particle and the valid one is selected
+// (one path for the warp instead of four).
 __device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta, float sh, float phi,
                                           int q, float vz) {
+  const bool charged = q != 0 && K.has_field;
+  const int aq = q < 0 ? -q : q;
+  const float kq = K.kB * (float)aq;
+  const float r = fdiv(pt, kq);
+  const float h = ((q > 0) == (K.Bsign > 0)) ? 1.0f : -1.0f;
+  const int qi = min(aq, PDR_MAXQ);
+  const float cR = aq <= PDR_MAXQ ? K.cR_hi[qi] : kq * K.R;
+  const float cRl = aq <= PDR_MAXQ ? K.cR_lo[qi] : 0.0f;
+  const float twopt = 2.0f * pt;
+  // barrel: half turning angle a = asin(x), x = c / 2pT; near the tangent
+  // point (x > 1/2) through pi/2 - 2 asin(sqrt((1 - x)/2)) with
+  // 1 - x = (2pT - c) / 2pT, where 2pT - c_hi is exact (Sterbenz)
+  const float x = fdiv(cR, twopt);
+  const bool near = x > 0.5f;
+  const float omx = fmaxf(fdiv((twopt - cR) - cRl, twopt), 0.0f);
+  const float as = asin_half(near ? sqrt_approx(0.5f * omx) : fminf(x, 0.5f));
+  const float a = near ? (PIO2_HI - 2.0f * as) + PIO2_LO : as;
+  // crossing z: helix 2 r a sinh(eta), straight line R sinh(eta)
+  const float zb = fmaf(charged ? 2.0f * r * a : K.R, sh, vz);
+  const bool barrel = (!charged || twopt >= cR) && fabsf(zb) <= K.L;
+  // endcap: the transverse distance rho at z = +-L is s_z = (z_e - vz) / sinh(eta)
+  // for a straight line, 2 r sin(psi / 2) for the helix (psi = s_z / r)
+  const float ze = sh > 0.0f ? K.L : -K.L;
+  const float sz = fdiv(ze - vz, sh);
+  const float psi = fdiv(sz, r);
+  const float rho = charged ? 2.0f * r * sin_half_turn(fminf(0.5f * psi, PI_F)) : sz;
+  const bool endcap = sh != 0.0f && (!charged || psi < TWO_PI_F);  // else pz = 0, or a looper
   Prop P;
-  P.reach = 0; P.barrel = 0; P.eta_pos = 0.0f; P.phi_pos = 0.0f;
-  if (!(fabsf(vz) <= K.L)) return P;
-  // every branch ends in eta_pos = asinh(num / den) and phi_pos = phi - turn
-  float num, den, turn = 0.0f;
-  if (q == 0 || !K.has_field) {
-    if (vz == 0.0f) {  // from the axis origin a straight line keeps its direction
-      P.reach = 1;
-      P.barrel = fabsf(K.R * sh) <= K.L;
-      P.eta_pos = eta;
-      P.phi_pos = phi;
-      return P;
-    }
-    const float z = fmaf(K.R, sh, vz);
-    P.barrel = fabsf(z) <= K.L;
-    if (P.barrel) {
-      num = z; den = K.R;
-    } else {  // z_e / rho with rho = (z_e - vz) / sinh(eta)
-      const float ze = sh > 0.0f ? K.L : -K.L;
-      num = ze * sh; den = ze - vz;
-    }
-  } else {
-    const int aq = q < 0 ? -q : q;
-    const float kq = K.kB * (float)aq;
-    const float r = fdiv(pt, kq);
-    const float h = ((q > 0) == (K.Bsign > 0)) ? 1.0f : -1.0f;
-    float cR, cRl;
-    if (aq <= PDR_MAXQ) { cR = K.cR_hi[aq]; cRl = K.cR_lo[aq]; }
-    else { cR = kq * K.R; cRl = 0.0f; }
-    const float twopt = 2.0f * pt;
-    float a = 0.0f;
-    if (twopt >= cR) {
-      // a = asin(x), x = c / 2pT; near the tangent point (x > 1/2) through
-      // pi/2 - 2 asin(sqrt((1 - x)/2)) with 1 - x = (2pT - c) / 2pT, where
-      // 2pT - c_hi is exact (Sterbenz)
-      const float x = fdiv(cR, twopt);
-      const bool near = x > 0.5f;
-      const float d = (twopt - cR) - cRl;
-      const float omx = fmaxf(fdiv(d, twopt), 0.0f);
-      const float as = asinf(near ? sqrtf(0.5f * omx) : x);
-      a = near ? (PIO2_HI - 2.0f * as) + PIO2_LO : as;
-      const float z = fmaf(2.0f * r * a, sh, vz);
-      P.barrel = fabsf(z) <= K.L;
-      num = z; den = K.R; turn = h * a;
-    }
-    if (!P.barrel) {
-      if (sh == 0.0f) return P;  // pz = 0 and the barrel out of reach
-      const float ze = sh > 0.0f ? K.L : -K.L;
-      const float sz = fdiv(ze - vz, sh);
-      const float psi = fdiv(sz, r);
-      if (!(psi < TWO_PI_F)) return P;  // looper
-      num = ze; den = 2.0f * r * fabsf(sinf(0.5f * psi));
-      turn = h * (0.5f * psi);
-    }
-  }
-  P.eta_pos = asinh_fast(fdiv(num, den));
+  P.reach = (fabsf(vz) <= K.L) && (barrel || endcap);
+  // a straight line from the axis origin keeps its direction
+  const bool origin = !charged && vz == 0.0f;
+  P.barrel = P.reach && (origin ? fabsf(K.R * sh) <= K.L : barrel);
+  P.eta_pos = P.reach ? (origin ? eta : asinh_fast(barrel ? fdiv(zb, K.R) : fdiv(ze, rho))) : 0.0f;
+  const float turn = charged ? h * (barrel ? a : 0.5f * psi) : 0.0f;
   float pphi = phi - turn;
-  if (pphi < -PI_F) pphi += TWO_PI_F;
-  else if (pphi >= PI_F) pphi -= TWO_PI_F;
-  P.phi_pos = pphi;
-  P.reach = 1;
+  pphi = pphi < -PI_F ? pphi + TWO_PI_F : (pphi >= PI_F ? pphi - TWO_PI_F : pphi);
+  P.phi_pos = P.reach ? pphi : 0.0f;
   return P;
 }
 
@@ -380,7 +420,7 @@ __device__ __forceinline__ void particle_stage_a(const KSeg& S, const HotCard& K
   float ch, sh;
   cosh_sinh(ETA, ch, sh);
   const float pc = PT * ch;
-  o.E = sqrtf(fmaf(pc, pc, M * M));
+  o.E = sqrt_approx(fmaf(pc, pc, M * M));
   if (cls == CLS_INVIS) return;
   // S1
   const Prop P = propagate(K, PT, ETA, sh, PHI, Q, VZ);
@@ -432,7 +472,7 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
   float ch, sh;
   cosh_sinh(ETA, ch, sh);
   const float pc = PT * ch;
-  const float E = sqrtf(fmaf(pc, pc, M * M));
+  const float E = sqrt_approx(fmaf(pc, pc, M * M));
   r.tracked = false; r.cand = false; r.ptp = 0.0f; r.etrk = 0.0f; r.cpt = 0.0f;
   // first stage
   uint32_t purpose;
@@ -471,7 +511,7 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
     if (!ok) return;
     r.ptp = sm;
     const float pcp = sm * ch;
-    r.etrk = sqrtf(fmaf(pcp, pcp, M * M));
+    r.etrk = sqrt_approx(fmaf(pcp, pcp, M * M));
     if (r.cc < 0 || !(PT > K.cand_ptmin)) return;
     // a tracked e/mu goes on to identification
     const int ke = small_lookup(K.id_edges, K.id_n, aeta);
