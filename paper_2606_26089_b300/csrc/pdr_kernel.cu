@@ -86,6 +86,7 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 //   asin(x) = x + x^3 P(x^2) on [0, 1/2]             (fit error ~1e-9)
 //   sin(x)  = x + x^3 Q(x^2) on [0, pi/2]            (fit error ~2e-10)
 //   ln(1 - v) = -v L(v)      on [0, 1/4]             (fit error ~3e-9)
+//   ln(1 + x) = x M(x)       on [0, 1/4]             (fit error ~4e-10)
 __device__ __forceinline__ float asin_half(float x) {
   const float t = x * x;
   float p = fmaf(t, 0.033805817f, 0.017077811f);
@@ -121,6 +122,18 @@ __device__ __forceinline__ float ln_unit(float u) {
   p = fmaf(v, p, 0.4999991f);
   p = fmaf(v, p, 1.0f);
   return u > 0.75f ? -v * p : __logf(u);
+}
+
+// ln(1 + x) for x >= 0: x M(x) up to 1/4, hardware log2 of 1 + x above
+// (relative error < 6e-7 there, ln(1 + x) > 0.22).
+__device__ __forceinline__ float log1p_pos(float x) {
+  float m = fmaf(x, 0.070751615f, -0.14544724f);
+  m = fmaf(x, m, 0.19665538f);
+  m = fmaf(x, m, -0.24972063f);
+  m = fmaf(x, m, 0.33332205f);
+  m = fmaf(x, m, -0.49999982f);
+  m = fmaf(x, m, 1.0f);
+  return x > 0.25f ? __logf(1.0f + x) : x * m;
 }
 
 // cos(2 pi u) for u in (0, 1): folded exactly in turns to sin of at most a
@@ -169,7 +182,7 @@ __device__ __forceinline__ float normal(uint32_t wa, uint32_t wb) {
 
 // Log-normal with mean x and relative variance rel2 = (sigma/x)^2.
 __device__ __forceinline__ float lognormal(float x, float rel2, float z) {
-  const float s2 = log1pf(rel2);
+  const float s2 = log1p_pos(rel2);
   const float s = sqrt_approx(s2);
   return x * expf(fmaf(s, z, -0.5f * s2));
 }
@@ -547,7 +560,8 @@ __device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32
   return t;
 }
 
-// Find or claim the slot of key.  The thread that claims an empty slot writes
+// Find or claim the slot of key (each probe is one compare-and-swap, which also
+// reads the slot).  The thread that claims an empty slot writes
 // its own deposit, track energy and index with plain stores (before the team
 // barrier that precedes any accumulation); every other depositor adds with
 // atomics after that barrier.  Returns the slot; *claimed tells which case.
@@ -558,19 +572,15 @@ __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uin
   uint32_t h = __umulhi(key * 0x9E3779B1u, T.nslots);
   *claimed = false;
   for (uint32_t probe = 0; probe < T.nslots; ++probe) {
-    const uint32_t cur = T.keys[h];
-    if (cur == key) return h;
-    if (cur == PDR_EMPTY) {
-      const uint32_t prev = atomicCAS(&T.keys[h], PDR_EMPTY, key);
-      if (prev == PDR_EMPTY) {
-        T.owner[h] = i;
-        T.esum[h] = e_fp;
-        T.etrk[h] = t_fp;
-        *claimed = true;
-        return h;
-      }
-      if (prev == key) return h;
+    const uint32_t prev = atomicCAS(&T.keys[h], PDR_EMPTY, key);
+    if (prev == PDR_EMPTY) {
+      T.owner[h] = i;
+      T.esum[h] = e_fp;
+      T.etrk[h] = t_fp;
+      *claimed = true;
+      return h;
     }
+    if (prev == key) return h;
     h = h + 1 == T.nslots ? 0u : h + 1;
   }
   atomicOr(err, ERR_TABLE);
