@@ -25,15 +25,9 @@ inline size_t build_hot_card(const DevCard& D, unsigned char* out, size_t cap) {
     hc.nring = C.nring;
     hc.m = C.nring / 2;
     hc.nseg = C.nseg;
-    if (!need((size_t)C.nring + 1 + 3 * (size_t)C.nring)) return 0;
+    if (!need((size_t)C.nring + 1)) return 0;
     hc.edge_off = (int32_t)nf;
     for (int j = 0; j <= C.nring; ++j) data[nf++] = C.edge[j];
-    hc.ring_off = (int32_t)nf;
-    for (int r = 0; r < C.nring; ++r) {
-      data[nf++] = C.eta_c[r];
-      data[nf++] = C.inv_cosh_c[r];
-      std::memcpy(&data[nf++], &C.resbin[r], sizeof(float));
-    }
     for (int s = 0; s < C.nseg; ++s) {
       HotSeg& hs = hc.seg[s];
       hs.lo = C.seg_lo[s];
@@ -51,6 +45,27 @@ inline size_t build_hot_card(const DevCard& D, unsigned char* out, size_t cap) {
       hs.phioff = (int32_t)nf;
       const float* src = D.phi_pool + C.phioff[r_pos];
       for (int k = 0; k < 2 * hs.nphi + 1; ++k) data[nf++] = src[k];
+    }
+    // per ring, 16-byte aligned: eta_c, 1 / cosh(eta_c), first tower id, and
+    // phi-table offset | nphi << 16 | resolution row << 27
+    while (nf & 3) {
+      if (!need(1)) return 0;
+      data[nf++] = 0.0f;
+    }
+    if (!need(4 * (size_t)C.nring)) return 0;
+    hc.ring_off = (int32_t)nf;
+    for (int r = 0; r < C.nring; ++r) {
+      const int jj = r >= hc.m ? r - hc.m : hc.m - 1 - r;
+      int s = 0;
+      while (s < C.nseg - 1 && jj >= hc.seg[s].first + hc.seg[s].n) ++s;
+      const uint32_t phioff = (uint32_t)hc.seg[s].phioff, nphi = (uint32_t)C.nphi[r], rb = (uint32_t)C.resbin[r];
+      if (phioff >= (1u << 16) || nphi >= (1u << 11) || rb >= (1u << 5)) return 0;
+      const uint32_t packed = phioff | (nphi << 16) | (rb << 27);
+      const int32_t base = C.base[r];
+      data[nf++] = C.eta_c[r];
+      data[nf++] = C.inv_cosh_c[r];
+      std::memcpy(&data[nf++], &base, sizeof(float));
+      std::memcpy(&data[nf++], &packed, sizeof(float));
     }
   }
   H.R = D.R; H.L = D.L; H.kB = D.kB;

@@ -79,10 +79,10 @@ struct DevCard {
 // The part of a card the kernel touches per particle and per tower, laid out
 // compactly so each persistent CTA copies it once into shared memory.  A fixed
 // header (below) is followed by `data_floats` floats: per calorimeter the ring
-// edges (nring + 1), per-ring data (eta_c, 1 / cosh(eta_c), resolution row as int
-// bits: 3 floats a ring), and per eta segment its phi table (nphi + 1 edges,
-// then nphi centres).  Tower ids are computed from per-segment bases, so no
-// per-ring table is read to place a deposit.
+// edges (nring + 1), per eta segment its phi table (nphi + 1 edges, then nphi
+// centres), and a 16-byte record per ring (eta_c, 1 / cosh(eta_c), first tower
+// id, phi-table offset | nphi << 16 | resolution row << 27), so one vector
+// load gives a ring's tower numbering, phi binning and smearing row.
 struct HotSeg {
   float lo, hi, scale;      // |eta| range of the segment, n / (hi - lo) (guess only)
   int32_t n, first;         // rings in the segment; first ring counting from eta = 0
@@ -95,7 +95,7 @@ struct HotSeg {
 
 struct HotCalo {
   int32_t nring, m, nseg, edge_off;  // m = nring / 2; edge_off: offset of the ring edges
-  int32_t ring_off, pad[3];          // offset of the per-ring data (3 floats a ring)
+  int32_t ring_off, pad[3];          // offset of the per-ring records (4 words a ring, 16-byte aligned)
   HotSeg seg[PDR_MAXSEG];
 };
 

@@ -285,19 +285,17 @@ __device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta,
   return P;
 }
 
-// Phi bin of v: largest k with edge[k] <= v, clamped to [0, nphi - 1].
-__device__ __forceinline__ int phi_bin(const float* pe, int nphi, float scale, float v) {
-  int k = (int)((v + PI_F) * scale);
-  k = min(max(k, 0), nphi - 1);
-  while (k > 0 && v < pe[k]) --k;
-  while (k < nphi - 1 && v >= pe[k + 1]) ++k;
-  return k;
+// Ring record of the shared-memory card: x = eta_c, y = 1 / cosh(eta_c),
+// z = first tower id (int bits), w = phi-table offset | nphi << 16 | row << 27.
+__device__ __forceinline__ float4 ring_rec(const HotCard& K, const float* KD, int calo, int r) {
+  return reinterpret_cast<const float4*>(KD + K.calo[calo].ring_off)[r];
 }
 
 // S5 tower of a surface position in one calorimeter, from the shared-memory
 // card: ring = largest r with edge[r] <= eta (guessed from the segment's
-// uniform binning, then checked against the float32 edges), phi bin likewise,
-// tower id from the segment's base.  Returns false outside coverage.
+// uniform binning, then checked against the float32 edges), phi bin likewise
+// from the ring's record, tower id = the ring's first id + phi bin.  Returns
+// false outside coverage.
 __device__ __forceinline__ bool tower_of(const HotCard& K, const float* KD, int calo, float v, float phi,
                                          uint32_t& id, int& ring) {
   const HotCalo& C = K.calo[calo];
@@ -314,29 +312,25 @@ __device__ __forceinline__ bool tower_of(const HotCard& K, const float* KD, int 
   r = min(max(r, 0), nr - 1);
   while (r > 0 && v < edge[r]) --r;
   while (r < nr - 1 && v >= edge[r + 1]) ++r;
-  const int jj = r >= m ? r - m : m - 1 - r;
-  s = 0;
-  while (s < C.nseg - 1 && jj >= C.seg[s].first + C.seg[s].n) ++s;
-  const HotSeg& S = C.seg[s];
-  const int k = phi_bin(KD + S.phioff, S.nphi, S.phi_scale, phi);
-  const int base = r >= m ? S.base_pos + (jj - S.first) * S.nphi
-                          : S.base_neg + (r - (m - S.first - S.n)) * S.nphi;
-  id = (uint32_t)(base + k);
+  const float4 rec = ring_rec(K, KD, calo, r);
+  const uint32_t w = __float_as_uint(rec.w);
+  const int nphi = (int)((w >> 16) & 0x7FFu);
+  const float* pe = KD + (w & 0xFFFFu);
+  // phi bin: largest k with edge[k] <= phi, clamped to [0, nphi - 1]
+  int k = (int)((phi + PI_F) * ((float)nphi * (1.0f / TWO_PI_F)));
+  k = min(max(k, 0), nphi - 1);
+  while (k > 0 && phi < pe[k]) --k;
+  while (k < nphi - 1 && phi >= pe[k + 1]) ++k;
+  id = (uint32_t)(__float_as_int(rec.z) + k);
   ring = r;
   return true;
 }
 
-// phi_c of tower id in a known ring (the segment base formula of tower_of).
+// phi_c of tower id in a known ring.
 __device__ __forceinline__ float tower_phi_c(const HotCard& K, const float* KD, int calo, uint32_t id, int r) {
-  const HotCalo& C = K.calo[calo];
-  const int m = C.m;
-  const int jj = r >= m ? r - m : m - 1 - r;
-  int s = 0;
-  while (s < C.nseg - 1 && jj >= C.seg[s].first + C.seg[s].n) ++s;
-  const HotSeg& S = C.seg[s];
-  const int base = r >= m ? S.base_pos + (jj - S.first) * S.nphi
-                          : S.base_neg + (r - (m - S.first - S.n)) * S.nphi;
-  return KD[S.phioff + S.nphi + 1 + ((int)id - base)];
+  const float4 rec = ring_rec(K, KD, calo, r);
+  const uint32_t w = __float_as_uint(rec.w);
+  return KD[(w & 0xFFFFu) + ((w >> 16) & 0x7FFu) + 1 + ((int)id - __float_as_int(rec.z))];
 }
 
 // Ring, eta_c and phi_c of a tower id.
@@ -344,24 +338,16 @@ __device__ __forceinline__ void tower_decode(const HotCard& K, const float* KD, 
                                              int& ring, float& eta_c, float& phi_c) {
   const HotCalo& C = K.calo[calo];
   const int m = C.m;
-  int r = 0, k = 0;
+  int r = 0;
   for (int s = 0; s < C.nseg; ++s) {
     const HotSeg& S = C.seg[s];
     const uint32_t span = (uint32_t)(S.n * S.nphi);
-    if (id - (uint32_t)S.base_neg < span) {
-      const uint32_t rel = id - (uint32_t)S.base_neg;
-      r = (m - S.first - S.n) + (int)(rel / (uint32_t)S.nphi);
-      k = (int)(rel % (uint32_t)S.nphi);
-      phi_c = KD[S.phioff + S.nphi + 1 + k];
-    } else if (id - (uint32_t)S.base_pos < span) {
-      const uint32_t rel = id - (uint32_t)S.base_pos;
-      r = m + S.first + (int)(rel / (uint32_t)S.nphi);
-      k = (int)(rel % (uint32_t)S.nphi);
-      phi_c = KD[S.phioff + S.nphi + 1 + k];
-    }
+    if (id - (uint32_t)S.base_neg < span) r = (m - S.first - S.n) + (int)((id - (uint32_t)S.base_neg) / (uint32_t)S.nphi);
+    else if (id - (uint32_t)S.base_pos < span) r = m + S.first + (int)((id - (uint32_t)S.base_pos) / (uint32_t)S.nphi);
   }
   ring = r;
-  eta_c = KD[C.ring_off + 3 * r];
+  eta_c = ring_rec(K, KD, calo, r).x;
+  phi_c = tower_phi_c(K, KD, calo, id, r);
 }
 
 // ------------------------------------------------------------------ teams
@@ -598,9 +584,9 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
                                             uint32_t event, uint32_t s0, uint32_t s1, TowerOut& o) {
   const int calo = (int)(key >> 24);
   const uint32_t id = key & 0xFFFFFFu;
-  const float* rd = KD + K.calo[calo].ring_off + 3 * ring;
-  const float ich = rd[1];  // 1 / cosh(eta_c)
-  const int rb = __float_as_int(rd[2]);
+  const float4 rec = ring_rec(K, KD, calo, (int)ring);
+  const float ich = rec.y;  // 1 / cosh(eta_c)
+  const int rb = (int)(__float_as_uint(rec.w) >> 27);
   const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
   const float a2 = K.res_a2[comp][rb], b2 = K.res_b2[comp][rb];
   const float c2 = K.res_c2[comp][rb], d2 = K.res_d2[comp][rb];
@@ -755,7 +741,7 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
           T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
           if (to.ef && gn0 > 0 && to.det > K.iso_ptmin) {
             const int calo = (int)(key >> 24), ring = (int)(pi >> 16);
-            const float oe = KD[K.calo[calo].ring_off + 3 * ring];
+            const float oe = ring_rec(K, KD, calo, ring).x;
             iso_object(K, make_float4(oe, tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring), to.det,
                                       __uint_as_float(key)), gn0, tt);
           }
