@@ -131,6 +131,7 @@ struct KSeg {
   const int32_t* pdg;
   const int8_t* charge;
   uint32_t seed_lo, seed_hi, event_base, card;  // card: slot of KParams::hot
+  uint32_t rk[20];                   // Philox round keys of the seed: (k0, k1) of rounds 0..9
   pdr_track* tracks;
   pdr_tower* towers;
   pdr_eflow* eflow;
@@ -139,6 +140,20 @@ struct KSeg {
   uint32_t* counts;
   pdr_debug* debug;                  // null: no debug records
 };
+
+// Philox4x32-10 round keys of a 64-bit seed: round r uses key (lo + r W0,
+// hi + r W1) with the Weyl constants W0 = 0x9E3779B9, W1 = 0xBB67AE85.
+PDR_HD inline void set_round_keys(KSeg& g, uint64_t seed) {
+  g.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
+  g.seed_hi = (uint32_t)(seed >> 32);
+  uint32_t k0 = g.seed_lo, k1 = g.seed_hi;
+  for (int r = 0; r < 10; ++r) {
+    g.rk[2 * r] = k0;
+    g.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
 
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {

@@ -43,19 +43,17 @@ static constexpr float PIO2_LO = -4.37113900018624283e-8f;     // pi/2 - PIO2_HI
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten multiply/xor rounds on a 128-bit
-// counter under a 64-bit key bumped by the Weyl constants.
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        uint32_t k0, uint32_t k1) {
+// counter under a 64-bit key bumped by the Weyl constants each round.  The
+// round keys of the batch's seed are precomputed (KSeg::rk), so a round is two
+// 32 x 32 -> 64-bit products and two three-way xors.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    // one 32 x 32 -> 64-bit product gives both halves
     const unsigned long long p0 = 0xD2511F53ull * c0;
     const unsigned long long p1 = 0xCD9E8D57ull * c2;
-    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk[2 * r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
     c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
 }
@@ -491,7 +489,7 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
     bool ok = false;
     float sm = 0.0f;
     if (T != 0ull) {
-      const uint4 w = philox(i, event, purpose, 0u, S.seed_lo, S.seed_hi);
+      const uint4 w = philox(i, event, purpose, 0u, S.rk);
       if ((unsigned long long)w.x < T) {
         ok = true;
         const float z = normal(w.y, w.z);
@@ -581,7 +579,7 @@ struct TowerOut {
 
 __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, uint32_t key,
                                             uint32_t ring, unsigned long long es, unsigned long long et,
-                                            uint32_t event, uint32_t s0, uint32_t s1, TowerOut& o) {
+                                            uint32_t event, const uint32_t* rk, TowerOut& o) {
   const int calo = (int)(key >> 24);
   const uint32_t id = key & 0xFFFFFFu;
   const float4 rec = ring_rec(K, KD, calo, (int)ring);
@@ -592,7 +590,7 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
   const float c2 = K.res_c2[comp][rb], d2 = K.res_d2[comp][rb];
   const float Es = from_fp(es);
   const float Et = from_fp(et);
-  const uint4 w = philox(id, event, 3u + (uint32_t)calo, 0u, s0, s1);
+  const uint4 w = philox(id, event, 3u + (uint32_t)calo, 0u, rk);
   const float z = normal(w.x, w.y);
   const float E1 = lognormal(Es, rel2_of(a2, b2, c2, d2, Es), z);
   // E'/sigma(E') = 1 / sqrt(rel2(E')); dE/sigma(E') = dE / E' * that
@@ -737,7 +735,7 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
         const uint32_t slot = pi & 0xFFFFu;
         if (T.owner[slot] == i) {
           key = T.keys[slot];
-          tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, S.seed_lo, S.seed_hi, to);
+          tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, S.rk, to);
           T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
           if (to.ef && gn0 > 0 && to.det > K.iso_ptmin) {
             const int calo = (int)(key >> 24), ring = (int)(pi >> 16);

@@ -344,8 +344,7 @@ extern "C" int pdr_run_noalloc(const pdr_card* card, const pdr_batch* b, const p
   sg.offsets = b->offsets;
   sg.pt = b->pt; sg.eta = b->eta; sg.phi = b->phi; sg.mass = b->mass; sg.vz = b->vz;
   sg.pdg = b->pdg; sg.charge = b->charge;
-  sg.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
-  sg.seed_hi = (uint32_t)(b->seed >> 32);
+  set_round_keys(sg, b->seed);
   sg.event_base = b->event_index_base;
   sg.card = 0;
   sg.tracks = o->tracks; sg.towers = o->towers; sg.eflow = o->eflow; sg.cands = o->cands;

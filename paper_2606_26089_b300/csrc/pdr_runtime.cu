@@ -495,8 +495,7 @@ void fill_seg(KSeg& g, const pdr_batch* b, const pdr_outputs* o, uint64_t start,
   g.offsets = b->offsets;
   g.pt = b->pt; g.eta = b->eta; g.phi = b->phi; g.mass = b->mass; g.vz = b->vz;
   g.pdg = b->pdg; g.charge = b->charge;
-  g.seed_lo = (uint32_t)(b->seed & 0xFFFFFFFFu);
-  g.seed_hi = (uint32_t)(b->seed >> 32);
+  set_round_keys(g, b->seed);
   g.event_base = b->event_index_base;
   g.card = card;
   g.tracks = o->tracks; g.towers = o->towers; g.eflow = o->eflow; g.cands = o->cands;
