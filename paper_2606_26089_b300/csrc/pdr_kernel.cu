@@ -523,24 +523,28 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
 // event's job list.  Between events every key is empty; the
 // other slot fields are initialised by the thread that claims the slot.
 struct Tbl {
-  uint32_t* keys;
-  uint32_t* owner;
-  unsigned long long* esum;
-  unsigned long long* etrk;
-  uint32_t* pinfo;
-  uint32_t* jobs;   // smearing jobs of the event, in particle order
+  unsigned char* base;
   uint32_t nslots;  // any multiple of 32 (the hash is scaled, not masked)
+  uint32_t nmax;    // particles per event
+  // field addresses are recomputed from the base (fewer live registers)
+  __device__ __forceinline__ uint32_t* keys() const { return reinterpret_cast<uint32_t*>(base); }
+  __device__ __forceinline__ uint32_t* owner() const { return reinterpret_cast<uint32_t*>(base) + nslots; }
+  __device__ __forceinline__ unsigned long long* esum() const {
+    return reinterpret_cast<unsigned long long*>(base + 8ull * nslots);
+  }
+  __device__ __forceinline__ unsigned long long* etrk() const {
+    return reinterpret_cast<unsigned long long*>(base + 16ull * nslots);
+  }
+  __device__ __forceinline__ uint32_t* pinfo() const { return reinterpret_cast<uint32_t*>(base + 24ull * nslots); }
+  // smearing jobs of the event, in particle order
+  __device__ __forceinline__ uint32_t* jobs() const { return pinfo() + nmax; }
 };
 
 __device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t nmax) {
   Tbl t;
-  t.keys = (uint32_t*)base;
-  t.owner = t.keys + slots;
-  t.esum = (unsigned long long*)(t.owner + slots);
-  t.etrk = t.esum + slots;
-  t.pinfo = (uint32_t*)(t.etrk + slots);
-  t.jobs = t.pinfo + nmax;
+  t.base = base;
   t.nslots = slots;
+  t.nmax = nmax;
   return t;
 }
 
@@ -556,11 +560,11 @@ __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uin
   uint32_t h = __umulhi(key * 0x9E3779B1u, T.nslots);
   *claimed = false;
   for (uint32_t probe = 0; probe < T.nslots; ++probe) {
-    const uint32_t prev = atomicCAS(&T.keys[h], PDR_EMPTY, key);
+    const uint32_t prev = atomicCAS(&T.keys()[h], PDR_EMPTY, key);
     if (prev == PDR_EMPTY) {
-      T.owner[h] = i;
-      T.esum[h] = e_fp;
-      T.etrk[h] = t_fp;
+      T.owner()[h] = i;
+      T.esum()[h] = e_fp;
+      T.etrk()[h] = t_fp;
       *claimed = true;
       return h;
     }
@@ -658,16 +662,16 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     bool claimed = false;
     const unsigned long long e_fp = to_fp(o.E);
     if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, 0ull, &claimed, err);
-    if (valid) T.pinfo[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
+    if (valid) T.pinfo()[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
     const bool has_job = o.job != PDR_EMPTY;
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(has_job, false, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (slot != PDR_EMPTY && !claimed) {  // after the barrier that orders the claimers' stores
-      atomicAdd(&T.esum[slot], e_fp);
-      atomicMin(&T.owner[slot], i);
+      atomicAdd(&T.esum()[slot], e_fp);
+      atomicMin(&T.owner()[slot], i);
     }
-    if (has_job) T.jobs[n_job + (pre & 0xFFFFu)] = o.job;
+    if (has_job) T.jobs()[n_job + (pre & 0xFFFFu)] = o.job;
     if (dbg && valid)
       reinterpret_cast<float4*>(S.debug)[a + i] =
           make_float4(__uint_as_float(o.key), o.eta_pos, o.phi_pos, __uint_as_float(o.flags));
@@ -682,12 +686,12 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     r.tracked = false; r.cand = false;
     uint32_t i = 0;
     if (j < n_job) {
-      const uint32_t job = T.jobs[j];
+      const uint32_t job = T.jobs()[j];
       i = job & 0xFFFFu;
       run_job(S, K, a, job, event, r);
       if (r.tracked) {
-        const uint32_t pi = T.pinfo[i];
-        if (pi != PDR_EMPTY) atomicAdd(&T.etrk[pi & 0xFFFFu], to_fp(r.etrk));
+        const uint32_t pi = T.pinfo()[i];
+        if (pi != PDR_EMPTY) atomicAdd(&T.etrk()[pi & 0xFFFFu], to_fp(r.etrk));
       }
       if (dbg && (r.tracked || r.cand))
         reinterpret_cast<uint32_t*>(S.debug + a + i)[3] |=
@@ -703,8 +707,8 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
             make_float4(r.ptp, eta, phi, __uint_as_float(i));
       if (r.cand) {
         const uint32_t jc = n_cand + (pre >> 16);
-        const uint32_t pi = T.pinfo[i];
-        const uint32_t key = pi == PDR_EMPTY ? PDR_NO_KEY : T.keys[pi & 0xFFFFu];
+        const uint32_t pi = T.pinfo()[i];
+        const uint32_t key = pi == PDR_EMPTY ? PDR_NO_KEY : T.keys()[pi & 0xFFFFu];
         reinterpret_cast<float4*>(S.cands)[a + jc] =
             make_float4(r.cpt, eta, phi, __uint_as_float(i | ((uint32_t)r.cc << 28)));
         // own tower key, read back by the isolation of candidates beyond the staged ones
@@ -730,13 +734,13 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     to.kept = false; to.ef = false;
     uint32_t key = PDR_NO_KEY;
     if (i < n) {
-      const uint32_t pi = T.pinfo[i];
+      const uint32_t pi = T.pinfo()[i];
       if (pi != PDR_EMPTY) {
         const uint32_t slot = pi & 0xFFFFu;
-        if (T.owner[slot] == i) {
-          key = T.keys[slot];
-          tower_stage(K, KD, key, pi >> 16, T.esum[slot], T.etrk[slot], event, S.rk, to);
-          T.keys[slot] = PDR_EMPTY;  // leave the table empty for the next event
+        if (T.owner()[slot] == i) {
+          key = T.keys()[slot];
+          tower_stage(K, KD, key, pi >> 16, T.esum()[slot], T.etrk()[slot], event, S.rk, to);
+          T.keys()[slot] = PDR_EMPTY;  // leave the table empty for the next event
           if (to.ef && gn0 > 0 && to.det > K.iso_ptmin) {
             const int calo = (int)(key >> 24), ring = (int)(pi >> 16);
             const float oe = ring_rec(K, KD, calo, ring).x;
@@ -867,7 +871,7 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
       process_event<TEAM>(S, p.err, K, KD, st, tt, tc, e, a, n);
     } else if (p.gscratch != nullptr && n <= p.g_nmax) {
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_nmax);
-      for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys[s] = PDR_EMPTY;
+      for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys()[s] = PDR_EMPTY;
       tc.sync();
       process_event<TEAM>(S, p.err, K, KD, gt, tt, tc, e, a, n);
     } else {
@@ -900,7 +904,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
   const Tbl st = carve(mine, p.table_slots, p.nmax_smem);
   unsigned char* tail = mine + table_bytes(p.table_slots, p.nmax_smem);
   TeamTail& tt = *reinterpret_cast<TeamTail*>(tail);
-  for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys[s] = PDR_EMPTY;
+  for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys()[s] = PDR_EMPTY;
   if ((uint32_t)tc.tid < PDR_CMAX) tt.csum[tc.tid] = 0ull;
   __syncthreads();
   if (p.n_segs == 1) event_loop<TEAM, BLOCK, true>(p, smem, tc, st, tt);
