@@ -76,10 +76,9 @@ inline size_t build_hot_card(const DevCard& D, unsigned char* out, size_t cap) {
   std::memcpy(H.trk_eta_edges, D.trk_eta_edges, sizeof H.trk_eta_edges);
   std::memcpy(H.id_edges, D.id_edges, sizeof H.id_edges);
   std::memcpy(H.res_edges, D.res_edges, sizeof H.res_edges);
-  std::memcpy(H.res_a2, D.res_a2, sizeof H.res_a2);
-  std::memcpy(H.res_b2, D.res_b2, sizeof H.res_b2);
-  std::memcpy(H.res_c2, D.res_c2, sizeof H.res_c2);
-  std::memcpy(H.res_d2, D.res_d2, sizeof H.res_d2);
+  for (int c = 0; c < 4; ++c)
+    for (int k = 0; k < PDR_MAXEDGE; ++k)
+      H.res[c][k] = make_float4(D.res_a2[c][k], D.res_b2[c][k], D.res_c2[c][k], D.res_d2[c][k]);
   std::memcpy(H.cR_hi, D.cR_hi, sizeof H.cR_hi);
   std::memcpy(H.cR_lo, D.cR_lo, sizeof H.cR_lo);
   std::memcpy(H.trk_T, D.trk_T, sizeof H.trk_T);

@@ -108,7 +108,7 @@ struct alignas(16) HotCard {
   alignas(16) float trk_eta_edges[PDR_MAXEDGE];
   alignas(16) float id_edges[PDR_MAXEDGE];
   alignas(16) float res_edges[4][PDR_MAXEDGE];
-  float res_a2[4][PDR_MAXEDGE], res_b2[4][PDR_MAXEDGE], res_c2[4][PDR_MAXEDGE], res_d2[4][PDR_MAXEDGE];
+  float4 res[4][PDR_MAXEDGE];       // (a^2, b^2, c^2, d^2) per resolution component and |eta| row
   float cR_hi[PDR_MAXQ + 1], cR_lo[PDR_MAXQ + 1];
   unsigned long long trk_T[3][PDR_MAXEDGE][PDR_MAXEDGE];
   unsigned long long id_T[3][PDR_MAXEDGE];

@@ -185,10 +185,10 @@ __device__ __forceinline__ float lognormal(float x, float rel2, float z) {
   return x * expf(fmaf(s, z, -0.5f * s2));
 }
 
-// (sigma/x)^2 = a^2/x + b^2/x^2 + c^2 + d^2 x^2.
-__device__ __forceinline__ float rel2_of(float a2, float b2, float c2, float d2, float x) {
+// (sigma/x)^2 = a^2/x + b^2/x^2 + c^2 + d^2 x^2, coefficients r = (a^2, b^2, c^2, d^2).
+__device__ __forceinline__ float rel2_of(float4 r, float x) {
   const float ix = rcp_approx(x);
-  return fmaf(fmaf(b2, ix, a2), ix, fmaf(d2 * x, x, c2));
+  return fmaf(fmaf(r.y, ix, r.x), ix, fmaf(r.w * x, x, r.z));
 }
 
 // Largest k < n with edges[k] <= x (-1 if none): piecewise-constant tables.
@@ -494,8 +494,7 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
         ok = true;
         const float z = normal(w.y, w.z);
         const int rb = max(small_lookup(K.res_edges[comp], K.res_n[comp], aeta), 0);
-        const float r2 = rel2_of(K.res_a2[comp][rb], K.res_b2[comp][rb], K.res_c2[comp][rb],
-                                 K.res_d2[comp][rb], x);
+        const float r2 = rel2_of(K.res[comp][rb], x);
         sm = lognormal(x, r2, z);
       }
     }
@@ -590,15 +589,14 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
   const float ich = rec.y;  // 1 / cosh(eta_c)
   const int rb = (int)(__float_as_uint(rec.w) >> 27);
   const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
-  const float a2 = K.res_a2[comp][rb], b2 = K.res_b2[comp][rb];
-  const float c2 = K.res_c2[comp][rb], d2 = K.res_d2[comp][rb];
+  const float4 rc = K.res[comp][rb];
   const float Es = from_fp(es);
   const float Et = from_fp(et);
   const uint4 w = philox(id, event, 3u + (uint32_t)calo, 0u, rk);
   const float z = normal(w.x, w.y);
-  const float E1 = lognormal(Es, rel2_of(a2, b2, c2, d2, Es), z);
+  const float E1 = lognormal(Es, rel2_of(rc, Es), z);
   // E'/sigma(E') = 1 / sqrt(rel2(E')); dE/sigma(E') = dE / E' * that
-  const float rs = rsqrtf(rel2_of(a2, b2, c2, d2, E1));
+  const float rs = rsqrtf(rel2_of(rc, E1));
   const float emin = K.e_min[calo], smin = K.s_min[calo];
   o.kept = (E1 > emin) & (rs > smin);
   o.e = E1;
