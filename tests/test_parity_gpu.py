@@ -153,6 +153,32 @@ def test_empty_and_degenerate_events(B, ctx, cards, synth):
     assert h["counts"].shape[0] == 0
 
 
+def test_charges_and_field_directions(B, ctx, synth):
+    """Multiply charged particles (|q| = 2, and |q| = 10 beyond the table of
+    precomputed reach constants), vertices off the origin, and the CMS-like
+    card with its field reversed and switched off: every propagation branch
+    (helix either way round, straight line, endcap, looper) against the oracle."""
+    import json
+    rng = np.random.default_rng(31)
+    events = []
+    for e in range(24):
+        ev = []
+        for k in range(60):
+            q = int(rng.choice([1, -1, 2, -2, 10, -10, 0]))
+            pdg = {1: 211, -1: -211, 2: 1000020040, -2: -1000020040, 10: 1000200400, -10: -1000200400, 0: 22}[q]
+            mass = {211: 0.13957039, 22: 0.0}.get(abs(pdg), 3.727 if abs(q) == 2 else 37.2)
+            pt = float(0.3 * np.exp(rng.uniform(0.0, 5.0)))
+            vz = float(rng.uniform(-0.3, 0.3)) if e % 2 else 0.0
+            ev.append((pt, float(rng.uniform(-4.8, 4.8)), float(rng.uniform(-np.pi, np.pi)), mass, pdg, q, vz))
+        events.append(ev)
+    b = synth.from_particles(events)
+    base = json.load(open(B.card_path("cms_like")))
+    for field in (3.8, -3.8, 0.0):
+        d = dict(base, B=field, name=f"cms_like_B{field}")
+        ctx_card = {f"B{field}": (ctx.card_load(d), oracle.load_card(d))}
+        _check_all(ctx, ctx_card, f"B{field}", b, seed=17)
+
+
 def test_event_larger_than_shared_table(B, ctx, cards, synth):
     # one 12k-particle event (beyond the 8192-slot shared-memory table) next to normal ones
     big = synth.make("pileup", n_events=3)
