@@ -93,6 +93,11 @@ class Counts(C.Structure):
                 ("n_trk", "n_twr", "n_twr_kept", "n_eflow", "n_cand", "n_marg", "err", "pad")]
 
 
+class PileUp(C.Structure):
+    _fields_ = [("mean", C.c_double), ("sigma_z", C.c_double), ("max_z", C.c_double),
+                ("smear_hs", C.c_int32), ("pad", C.c_int32)]
+
+
 _lib = None
 
 
@@ -127,6 +132,11 @@ def lib():
                                           P, P, P, P, P, C.c_int32, C.POINTER(Counts)]
         _lib.oracle_run_batch.argtypes = [C.POINTER(Card), C.c_int64, P, P, P, P, P, P, P, P,
                                           C.c_uint64, C.c_uint32, C.c_int32, P]
+        _lib.oracle_poisson_thresholds.argtypes = [C.c_double, P, C.c_int32]
+        _lib.oracle_poisson_thresholds.restype = C.c_int32
+        _lib.oracle_pileup_draws.argtypes = [C.POINTER(PileUp), P, C.c_int32, C.c_uint64, C.c_uint64,
+                                             C.c_uint32, C.c_double, P, P, P, C.c_int32, P]
+        _lib.oracle_pileup_draws.restype = C.c_int32
     return _lib
 
 
@@ -347,3 +357,80 @@ def run_batch(card: Card, batch, seed: int, event_base: int = 0, nthreads: Optio
     if rc:
         raise RuntimeError(f"oracle_run_batch failed: {rc}")
     return counts[:ne]
+
+
+# ----------------------------------------------------------------------------
+# pile-up merging (Sec. 2.2; readings in oracle.h)
+# ----------------------------------------------------------------------------
+def poisson_thresholds(mean: float, kmax: int = 8192) -> np.ndarray:
+    """Integer thresholds T[k] = floor(P(N <= k) 2^32) of the Poisson(mean) CDF (last entry 2^32)."""
+    T = np.zeros(kmax, np.uint64)
+    K = lib().oracle_poisson_thresholds(float(mean), _ptr(T), int(kmax))
+    if K < 0:
+        raise ValueError("Poisson table does not end within kmax entries")
+    return T[:K]
+
+
+def pileup_draws(pu: PileUp, T: np.ndarray, n_pool: int, seed: int, event: int, g: float = DEFAULT_G,
+                 cap: int = 65536):
+    """(n, pool indices, vertex z [m], hard vertex shift z_hs, marginal count) of one hard event."""
+    n = C.c_int32()
+    zhs = C.c_double()
+    idx = np.zeros(cap, np.uint32)
+    z = np.zeros(cap, np.float64)
+    T = np.ascontiguousarray(T, np.uint64)
+    m = lib().oracle_pileup_draws(C.byref(pu), _ptr(T), int(T.shape[0]), int(n_pool), int(seed) & (2**64 - 1),
+                                  int(event) & 0xFFFFFFFF, float(g), C.byref(n), _ptr(idx), _ptr(z), int(cap),
+                                  C.byref(zhs))
+    if m < 0:
+        raise ValueError("more interactions than cap")
+    k = n.value
+    return k, idx[:k].copy(), z[:k].copy(), zhs.value, m
+
+
+def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs: bool, seed: int,
+                 event_base: int = 0, g: float = DEFAULT_G) -> dict:
+    """The merged batch: per hard event its own particles (vertex z plus the hard
+    shift), then the pool events of its interactions in draw order, each at its
+    interaction's vertex z.  Returns the merged CSR arrays (vz in float64) and the
+    draws."""
+    pu = PileUp(float(mean), float(sigma_z), float(max_z), int(bool(smear_hs)), 0)
+    T = poisson_thresholds(mean)
+    po = np.asarray(pool.offsets, np.int64)
+    psz = np.diff(po)
+    ho = np.asarray(hard.offsets, np.int64)
+    starts, lens, zs, srcs = [], [], [], []
+    draws = []
+    n_marg = 0
+    for e in range(hard.n_events):
+        k, idx, z, zhs, m = pileup_draws(pu, T, pool.n_events, seed, event_base + e, g)
+        n_marg += m
+        draws.append((k, idx, z, zhs))
+        starts.append(ho[e]); lens.append(ho[e + 1] - ho[e]); zs.append(zhs); srcs.append(0)
+        for j in range(k):
+            starts.append(po[idx[j]]); lens.append(psz[idx[j]]); zs.append(z[j]); srcs.append(1)
+    starts = np.asarray(starts, np.int64); lens = np.asarray(lens, np.int64)
+    zs = np.asarray(zs, np.float64); srcs = np.asarray(srcs, np.int8)
+    seg = np.repeat(np.arange(lens.shape[0]), lens)
+    pos = np.arange(int(lens.sum()), dtype=np.int64) - np.repeat(np.cumsum(lens) - lens, lens)
+    src_index = starts[seg] + pos
+    from_pool = srcs[seg] == 1
+    out = {}
+    for key in ("pt", "eta", "phi", "mass", "pdg", "charge"):
+        h, pl = np.asarray(getattr(hard, key)), np.asarray(getattr(pool, key))
+        v = np.empty(src_index.shape[0], h.dtype)
+        v[~from_pool] = h[src_index[~from_pool]]
+        v[from_pool] = pl[src_index[from_pool]]
+        out[key] = v
+    hvz = np.zeros(ho[-1] if ho.shape[0] else 0, np.float64) if hard.vz is None else np.asarray(hard.vz, np.float64)
+    vz = zs[seg].copy()
+    vz[~from_pool] += hvz[src_index[~from_pool]]
+    out["vz"] = vz
+    per_event = np.asarray([ho[e + 1] - ho[e] + sum(int(psz[i]) for i in d[1]) for e, d in enumerate(draws)],
+                           np.int64)
+    off = np.zeros(hard.n_events + 1, np.uint64)
+    np.cumsum(per_event, out=off[1:])
+    out["offsets"] = off
+    out["draws"] = draws
+    out["marginal"] = n_marg
+    return out

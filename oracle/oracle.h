@@ -186,6 +186,42 @@ int oracle_run_batch(const oracle_card* c, int64_t n_events, const uint64_t* off
                      uint64_t seed, uint32_t event_base, int32_t nthreads,
                      uint32_t* counts_out);
 
+/* ---- pile-up merging (Sec. 2.2: with a pile-up block, the parametric path
+ * first merges minimum-bias interactions with the hard-scatter event; the
+ * block's parameters are listed with the generator configuration: mean
+ * pile-up, vertex-z width sigma_z and truncation max_z_spread, and whether the
+ * hard-scatter vertex is smeared).  Readings of what the paper leaves open:
+ *   - N ~ Poisson(mean) interactions per hard event, drawn by inversion: N is
+ *     the smallest k with w0 < T[k] (thresholds below), w0 from Philox counter
+ *     (0, event, 5, 0);
+ *   - interaction k (0 <= k < N) takes minimum-bias event floor(w0 * n_pool / 2^32)
+ *     of the pool, w0 from counter (k, event, 6, 0), at vertex z = sigma_z * z
+ *     with z the Box-Muller normal of (w1, w2) of counter (k, event, 6, a), a the
+ *     first attempt with |z sigma_z| <= max_z (a truncated Gaussian);
+ *   - the hard-scatter vertex, if smeared, is z_hs from counter (0, event, 5, a)
+ *     likewise; its particles keep their own z plus z_hs;
+ *   - the pool event's particles are used as stored (no rotation).
+ * The truncation is a decision on a float32 value; a draw whose |z| lies
+ * within g max(|z|, max_z) of max_z is counted as marginal. */
+typedef struct oracle_pileup {
+  double mean, sigma_z, max_z;
+  int32_t smear_hs, pad;
+} oracle_pileup;
+
+/* Thresholds T[0..K-1] of the Poisson(mean) CDF: T[k] = floor(P(N <= k) 2^32),
+ * the CDF summed in double from P(N = 0) = exp(-mean) by P(N = k) = P(N = k-1)
+ * mean / k; the first entry at or above 2^32 - 1 is the last and becomes 2^32.
+ * Returns K, or -1 if kmax entries do not reach it. */
+int32_t oracle_poisson_thresholds(double mean, uint64_t* T, int32_t kmax);
+
+/* The draws of one hard event: *n interactions (at most cap are written) with
+ * pool indices idx[] and vertices z[] (metres), and the hard vertex shift
+ * *z_hs (0 unless smeared).  Returns the number of marginal truncation
+ * decisions, or -1 if n exceeds cap. */
+int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K, uint64_t n_pool,
+                            uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
+                            double* z, int32_t cap, double* z_hs);
+
 #ifdef __cplusplus
 }
 #endif

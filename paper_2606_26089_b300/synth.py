@@ -24,6 +24,10 @@ Workloads (sizes as the benchmark configurations name them):
 * ``ee``       1M events, Poisson(35), isotropic, sum E = 91.2 GeV       seed 2
 * ``pileup``   10k events, Poisson(400) + 170 vertices x Poisson(30)     seed 3
 
+For pile-up merging on the device: a minimum-bias pool (``make_minbias_pool``,
+Poisson(30) particles an interaction, seed 5) and hard-scatter events
+(``make_hard``, Poisson(400), seed 6).
+
 All use numpy's PCG64 ``default_rng(seed)``, so a workload is a pure function of
 (seed, n_events).
 """
@@ -252,6 +256,30 @@ def make_pileup(n_events: int = 10_000, seed: int = 3, n_vertices: int = 170,
     eta = rng.uniform(-ETA_MAX, ETA_MAX, n).astype(np.float32)
     phi = _phi32(rng, n)
     return EventBatch(off, pt, eta, phi, _MASS[sp].astype(np.float32), pdg, q, vz, "pileup")
+
+
+def make_minbias_pool(n_events: int = 10_000, seed: int = 5, mu: float = 30.0) -> EventBatch:
+    """Minimum-bias interactions for pile-up merging: Poisson(mu) particles of
+    the soft species mix, pT = 0.3 (1-u)^(-1/3) capped at 500 GeV, flat
+    |eta| < 4.9; no vertex (the merger assigns one per interaction)."""
+    rng = np.random.default_rng(seed)
+    counts = rng.poisson(mu, n_events)
+    n = int(counts.sum())
+    sp, pdg, q = _species(rng, n)
+    u = rng.random(n)
+    pt = np.minimum(0.3 * (1.0 - u) ** (-1.0 / 3.0), PT_CAP).astype(np.float32)
+    eta = rng.uniform(-ETA_MAX, ETA_MAX, n).astype(np.float32)
+    phi = _phi32(rng, n)
+    return EventBatch(_offsets(counts), pt, eta, phi, _MASS[sp].astype(np.float32), pdg, q, None, "minbias")
+
+
+def make_hard(n_events: int = 10_000, seed: int = 6) -> EventBatch:
+    """Hard-scatter events for pile-up merging: Poisson(400) soft particles at
+    the origin (the pile-up workload's hard event)."""
+    rng = np.random.default_rng(seed)
+    counts = rng.poisson(400.0, n_events)
+    pt, eta, phi, mass, pdg, q = _soft(rng, int(counts.sum()), 0.5, 2.5)
+    return EventBatch(_offsets(counts), pt, eta, phi, mass, pdg, q, None, "hard")
 
 
 WORKLOADS = {
