@@ -304,6 +304,8 @@ def bench_ours(args, dist, rank, ws):
     }
     if not args.no_serving and ws == 1:
         line["serving"] = bench_serving(args, B, ctx)
+    if not args.no_pileup_merge and ws == 1:
+        line["pileup_merge"] = bench_pileup_merge(args, B, ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, card_name, args.seed, args.cpu_seconds)
     ctx.close()
@@ -403,6 +405,89 @@ def bench_serving(args, B, ctx):
     return out
 
 
+def bench_pileup_merge(args, B, ctx):
+    """Pile-up merging on the device (Sec. 2.2) at the pile-up workload's scale:
+    10k hard events of Poisson(400) particles, Poisson(170) interactions each
+    from a 10k-event minimum-bias pool, vertex z ~ N(0, 50 mm) truncated at
+    250 mm; then the detector response of the merged batch."""
+    import torch
+
+    from paper_2606_26089_b300 import synth
+
+    hard = synth.make_hard(args.pileup_events)
+    pool = synth.make_minbias_pool(10_000)
+    hd, pd = B.batch_to_device(hard), B.batch_to_device(pool)
+    mean, sz, mz, seed = 170.0, 0.05, 0.25, 3
+    hb = B.make_batch(hd, 0, seed)
+    pu = B.make_pileup(pd, mean, sz, mz, True)
+    n = hard.n_events
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    total = ctx.pileup_offsets(hb, pu, off)
+    f = dict(dtype=torch.float32, device="cuda")
+    m = {k: torch.empty(total, **f) for k in ("pt", "eta", "phi", "mass", "vz")}
+    m["pdg"] = torch.empty(total, dtype=torch.int32, device="cuda")
+    m["charge"] = torch.empty(total, dtype=torch.int8, device="cuda")
+    stream = torch.cuda.current_stream()
+    reps = max(3, args.steps // 3)
+    for _ in range(3):
+        ctx.pileup_merge(hb, pu, off, m)
+    torch.cuda.synchronize()
+    ctx.check()
+    t_off = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ctx.pileup_offsets(hb, pu, off)
+        t_off.append(time.perf_counter() - t0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    for k in range(reps):
+        ev[2 * k].record(stream)
+        ctx.pileup_merge(hb, pu, off, m)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    fill_s = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / 1e3
+    # algorithmic bytes: every merged particle written once (4 floats, vz, pdg,
+    # charge = 25 B), the hard particles and the pool read once, the offsets
+    n_int = int(total - hard.n_particles)
+    alg = 25 * total + hard.nbytes_input() + pool.nbytes_input() + 8 * (n + 1)
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+
+    # detector response of the merged batch
+    mdev = dict(m, offsets=off, n_events=n, n_particles=total, max_event_size=0)
+    cid = ctx.card_load("cms_like")
+    out = B.alloc_outputs(n, total)
+    bt = B.make_batch(mdev, cid, seed)
+    sizes = torch.diff(off)
+    bt.max_event_size = int(sizes.max().item())
+    launch = B.pdr_launch()
+    launch.team, launch.block, launch.table_slots, launch.grid = 1024, 1024, 0, 0
+    ob = B.make_outputs(out)
+    for _ in range(2):
+        ctx.run(bt, ob, launch=launch)
+    torch.cuda.synchronize()
+    ctx.check()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(reps):
+        ctx.run(bt, ob, launch=launch)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    resp_s = r0.elapsed_time(r1) / 1e3 / reps
+    achieved = alg / fill_s / 1e9
+    return {"hard_events": n, "pool_events": pool.n_events, "mean_interactions": mean,
+            "sigma_z_m": sz, "max_z_m": mz, "merged_particles": int(total), "pool_particles_copied": n_int,
+            "fill_ms": fill_s * 1e3, "offsets_ms_incl_sync": statistics.mean(t_off) * 1e3,
+            "fill_particles_per_s": total / fill_s,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes_per_launch": int(alg),
+                         "kernel": "pdr::pu_fill_kernel"},
+            "response_ms": resp_s * 1e3, "response_launch": launch.as_dict(),
+            "merge_and_response_particles_per_s": total / (fill_s + resp_s),
+            "reps": reps}
+
+
 def cpu_baseline(batch, card_name, seed, target_s):
     """The oracle as it stands, on the host cores, on a bounded prefix of the workload."""
     import oracle
@@ -483,6 +568,8 @@ def main(argv=None):
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-pool", type=int, default=5000)
     ap.add_argument("--no-per-event", action="store_true")
+    ap.add_argument("--no-pileup-merge", action="store_true")
+    ap.add_argument("--pileup-events", type=int, default=10_000, help="hard events of the pile-up merge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.seed is None:

@@ -254,6 +254,66 @@ int pdr_max_event_size(pdr_ctx* ctx, const pdr_batch* batch, void* stream, uint3
  * PDR_OK, or PDR_EDEVICE with the reason in pdr_last_error. */
 int pdr_check(pdr_ctx* ctx, void* stream);
 
+/* ------------------------------------------------------------ pile-up merging -- */
+/* Sec. 2.2: with a pile-up block, the parametric path first merges
+ * minimum-bias interactions with each hard-scatter event, then applies the
+ * detector card; the block gives the mean number of interactions, the Gaussian
+ * vertex-z width and its truncation, and whether the hard-scatter vertex is
+ * smeared too.  Per hard event e (event index event_index_base + e, the hard
+ * batch's seed; Philox purposes 5 and 6, disjoint from the response's 1-4):
+ *   - N ~ Poisson(mean) by inversion: the smallest k with w0 < T[k], where
+ *     T[k] = floor(P(N <= k) 2^32) from the CDF summed in double from
+ *     P(N = 0) = exp(-mean) by P(N = k) = P(N = k-1) mean / k, the first entry
+ *     at or above 2^32 - 1 becoming 2^32 (w0: counter (0, event, 5, 0));
+ *   - interaction k < N takes pool event floor(w0 n_pool / 2^32) (w0: counter
+ *     (k, event, 6, 0)) at vertex z = sigma_z x (Box-Muller normal of words 1
+ *     and 2 of counter (k, event, 6, a)), a the first attempt with
+ *     |z| <= max_z in float32 (a truncated Gaussian);
+ *   - the hard vertex shift z_hs is drawn likewise from counter (0, event, 5, a)
+ *     if smear_hs, else 0;
+ *   - the merged event holds the hard particles (vertex z = own vz, or 0, plus
+ *     z_hs) followed by the pool events of interactions 0..N-1 in that order,
+ *     each particle at its interaction's z; pool particles are copied as stored.
+ * The pool is a CSR batch in DEVICE memory and stays owned by the caller. */
+typedef struct pdr_pileup {
+  uint64_t n_pool;                /* minimum-bias events in the pool (>= 1)        */
+  const uint64_t* offsets;        /* [n_pool + 1]                                  */
+  const float *pt, *eta, *phi, *mass;
+  const int32_t* pdg;
+  const int8_t* charge;
+  double mean;                    /* mean interactions per hard event (>= 0)       */
+  double sigma_z;                 /* vertex-z width (m)                            */
+  double max_z;                   /* vertex-z truncation |z| <= max_z (m, > 0)     */
+  uint32_t smear_hs;              /* 1: shift the hard-scatter vertex as well      */
+  uint32_t pad;
+} pdr_pileup;
+
+/* DEVICE arrays of a merged batch, each with room for the merged particle
+ * count that pdr_pileup_offsets returns. */
+typedef struct pdr_particles {
+  float *pt, *eta, *phi, *mass, *vz;
+  int32_t* pdg;
+  int8_t* charge;
+} pdr_particles;
+
+/* First pass: the merged CSR offsets [n_events + 1] (DEVICE, caller-owned)
+ * and their total *total (HOST); synchronises `stream`.  The hard batch's
+ * card_id and flags are ignored.  PDR_EINVAL for bad arguments, PDR_EOVERFLOW
+ * if mean is too large for the Poisson table (mean > 4000), PDR_ENOMEM if the
+ * context pool has no room for the per-event counts (8 B an event). */
+int pdr_pileup_offsets(pdr_ctx* ctx, const pdr_batch* hard, const pdr_pileup* pu, uint64_t* merged_offsets,
+                       uint64_t* total, void* stream);
+
+/* Second pass: fill `out` from the same hard batch and pool.  Every event
+ * recomputes its merged size and, if it differs from merged_offsets (a call
+ * with other arguments than the first pass), writes nothing and sets the
+ * device error word (pdr_check reports it).  Asynchronous on `stream`; the
+ * result is a batch for pdr_run with merged_offsets and these arrays.
+ * Events whose hard or drawn pool offsets decrease are skipped in both
+ * passes and reported as malformed offsets by pdr_check. */
+int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* hard, const pdr_pileup* pu, const uint64_t* merged_offsets,
+                     const pdr_particles* out, void* stream);
+
 /* ------------------------------------------------------- allocation-free run -- */
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that may not allocate device memory when they run the response:

@@ -392,8 +392,9 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
                  event_base: int = 0, g: float = DEFAULT_G) -> dict:
     """The merged batch: per hard event its own particles (vertex z plus the hard
     shift), then the pool events of its interactions in draw order, each at its
-    interaction's vertex z.  Returns the merged CSR arrays (vz in float64) and the
-    draws."""
+    interaction's vertex z.  Returns the merged CSR arrays (vz in float64), the
+    draws, the number of marginal truncation decisions and the events holding
+    them."""
     pu = PileUp(float(mean), float(sigma_z), float(max_z), int(bool(smear_hs)), 0)
     T = poisson_thresholds(mean)
     po = np.asarray(pool.offsets, np.int64)
@@ -402,9 +403,12 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
     starts, lens, zs, srcs = [], [], [], []
     draws = []
     n_marg = 0
+    marg_events = []
     for e in range(hard.n_events):
         k, idx, z, zhs, m = pileup_draws(pu, T, pool.n_events, seed, event_base + e, g)
         n_marg += m
+        if m:
+            marg_events.append(e)
         draws.append((k, idx, z, zhs))
         starts.append(ho[e]); lens.append(ho[e + 1] - ho[e]); zs.append(zhs); srcs.append(0)
         for j in range(k):
@@ -433,4 +437,5 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
     out["offsets"] = off
     out["draws"] = draws
     out["marginal"] = n_marg
+    out["marginal_events"] = marg_events
     return out

@@ -100,6 +100,17 @@ class pdr_serve_stats(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class pdr_pileup(C.Structure):
+    _fields_ = [("n_pool", C.c_uint64)] + [(n, C.c_void_p) for n in (
+        "offsets", "pt", "eta", "phi", "mass", "pdg", "charge")] + [
+        ("mean", C.c_double), ("sigma_z", C.c_double), ("max_z", C.c_double),
+        ("smear_hs", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class pdr_particles(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge")]
+
+
 class pdr_result(C.Structure):
     _fields_ = [("n_events", C.c_uint64), ("n_particles", C.c_uint64)] + [
         (n, C.c_void_p) for n in ("offsets", "counts", "tracks", "towers", "eflow", "cands", "iso", "debug")]
@@ -142,6 +153,8 @@ def lib():
             "pdr_serve_stats_get": ([P, C.POINTER(pdr_serve_stats)], I),
             "pdr_serve_stop": ([P], I),
             "pdr_run_noalloc": ([C.POINTER(pdr_card), C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P], I),
+            "pdr_pileup_offsets": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(C.c_uint64), P], I),
+            "pdr_pileup_merge": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(pdr_particles), P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -374,6 +387,20 @@ class Context:
     def release(self, ticket: int):
         self._check(self.L.pdr_release(self.h, ticket), "pdr_release")
 
+    # ---- pile-up merging
+    def pileup_offsets(self, hard: pdr_batch, pu: pdr_pileup, merged_offsets, stream=None) -> int:
+        """First pass: merged CSR offsets into a device tensor [n_events + 1]; returns the total."""
+        tot = C.c_uint64()
+        self._check(self.L.pdr_pileup_offsets(self.h, C.byref(hard), C.byref(pu), _ptr(merged_offsets),
+                                              C.byref(tot), self._stream(stream)), "pdr_pileup_offsets")
+        return tot.value
+
+    def pileup_merge(self, hard: pdr_batch, pu: pdr_pileup, merged_offsets, out: dict, stream=None):
+        """Second pass: fill the merged particle arrays (device tensors)."""
+        o = pdr_particles(*[_ptr(out[k]) for k in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge")])
+        self._check(self.L.pdr_pileup_merge(self.h, C.byref(hard), C.byref(pu), _ptr(merged_offsets), C.byref(o),
+                                            self._stream(stream)), "pdr_pileup_merge")
+
     # ---- serving
     def serve_start(self, max_inflight_waves=0, max_wave_requests=0, max_wave_particles=0, use_graphs=1):
         o = pdr_serve_options(max_inflight_waves, max_wave_requests, max_wave_particles, use_graphs, 0)
@@ -464,3 +491,38 @@ def event_records(out_host: dict, counts: np.ndarray, offsets: np.ndarray, e: in
         r["debug"] = dict(key=d[:, 0].view(np.uint32), eta_pos=d[:, 1], phi_pos=d[:, 2],
                           flags=d[:, 3].view(np.uint32))
     return r
+
+
+# ---------------------------------------------------------------------------
+# pile-up merging helpers
+# ---------------------------------------------------------------------------
+def make_pileup(pool_dev: dict, mean: float, sigma_z: float, max_z: float, smear_hs: bool) -> pdr_pileup:
+    """pdr_pileup over a device pool (batch_to_device of the minimum-bias batch)."""
+    p = pdr_pileup()
+    p.n_pool = pool_dev["n_events"]
+    for k in ("offsets", "pt", "eta", "phi", "mass", "pdg", "charge"):
+        setattr(p, k, _ptr(pool_dev[k]))
+    p.mean, p.sigma_z, p.max_z, p.smear_hs = float(mean), float(sigma_z), float(max_z), int(bool(smear_hs))
+    return p
+
+
+def merge_pileup(ctx: "Context", hard_dev: dict, pool_dev: dict, mean: float, sigma_z: float, max_z: float,
+                 smear_hs: bool, seed: int, event_base: int = 0, stream=None) -> dict:
+    """Both passes; returns the merged batch as device tensors (batch_to_device layout)."""
+    torch = _torch()
+    hb = make_batch(hard_dev, 0, seed, event_base=event_base)
+    pu = make_pileup(pool_dev, mean, sigma_z, max_z, smear_hs)
+    n = hard_dev["n_events"]
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    total = ctx.pileup_offsets(hb, pu, off, stream)
+    cap = max(total, 1)
+    f = dict(dtype=torch.float32, device="cuda")
+    out = dict(pt=torch.empty(cap, **f), eta=torch.empty(cap, **f), phi=torch.empty(cap, **f),
+               mass=torch.empty(cap, **f), vz=torch.empty(cap, **f),
+               pdg=torch.empty(cap, dtype=torch.int32, device="cuda"),
+               charge=torch.empty(cap, dtype=torch.int8, device="cuda"))
+    ctx.pileup_merge(hb, pu, off, out, stream)
+    out["offsets"] = off
+    out["n_events"] = n
+    out["n_particles"] = total
+    return out

@@ -143,17 +143,45 @@ struct KSeg {
 
 // Philox4x32-10 round keys of a 64-bit seed: round r uses key (lo + r W0,
 // hi + r W1) with the Weyl constants W0 = 0x9E3779B9, W1 = 0xBB67AE85.
-PDR_HD inline void set_round_keys(KSeg& g, uint64_t seed) {
-  g.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
-  g.seed_hi = (uint32_t)(seed >> 32);
-  uint32_t k0 = g.seed_lo, k1 = g.seed_hi;
+PDR_HD inline void fill_round_keys(uint32_t* rk, uint64_t seed) {
+  uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
   for (int r = 0; r < 10; ++r) {
-    g.rk[2 * r] = k0;
-    g.rk[2 * r + 1] = k1;
+    rk[2 * r] = k0;
+    rk[2 * r + 1] = k1;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
 }
+
+PDR_HD inline void set_round_keys(KSeg& g, uint64_t seed) {
+  g.seed_lo = (uint32_t)(seed & 0xFFFFFFFFu);
+  g.seed_hi = (uint32_t)(seed >> 32);
+  fill_round_keys(g.rk, seed);
+}
+
+// Pile-up merging: the hard batch, the minimum-bias pool, the Poisson
+// thresholds, the vertex parameters and the outputs of both passes.
+struct PuParams {
+  uint64_t n_events, n_pool;
+  const uint64_t* hoff;
+  const float *hpt, *heta, *hphi, *hmass, *hvz;
+  const int32_t* hpdg;
+  const int8_t* hcharge;
+  const uint64_t* poff;
+  const float *ppt, *peta, *pphi, *pmass;
+  const int32_t* ppdg;
+  const int8_t* pcharge;
+  const unsigned long long* T;       // Poisson CDF thresholds, K entries, T[K-1] = 2^32
+  uint32_t K, event_base, smear_hs, pad;
+  float sigma_z, max_z;
+  uint32_t rk[20];
+  uint64_t* counts;                  // first pass: merged size of each event
+  const uint64_t* moff;              // second pass: merged offsets
+  float *opt, *oeta, *ophi, *omass, *ovz;
+  int32_t* opdg;
+  int8_t* ocharge;
+  uint32_t* err;
+};
 
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {
@@ -176,6 +204,8 @@ enum : uint32_t {
   ERR_CSR = 1u,        // offsets not monotone
   ERR_OVERSIZE = 2u,   // event larger than any table available to the launch
   ERR_TABLE = 4u,      // tower table full (cannot happen when sized as documented)
+  ERR_PILEUP = 8u,     // pile-up merge: an event's size differs from the offsets given
+  ERR_VERTEX = 16u,    // pile-up merge: no vertex inside the truncation in 1024 draws
 };
 
 // Bytes of a team's event workspace: the tower table (keys, owner, esum, etrk

@@ -979,6 +979,156 @@ __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64
   }
 }
 
+// ------------------------------------------------------- pile-up merging
+// (Sec. 2.2; the draws are documented with pdr_pileup in the C header.)
+// Interactions of a hard event: the smallest k with w0 < T[k].
+__device__ __forceinline__ uint32_t pu_interactions(const PuParams& p, uint32_t event) {
+  const uint4 w = philox(0u, event, 5u, 0u, p.rk);
+  uint32_t lo = 0, hi = p.K - 1;  // T[K - 1] = 2^32 > w0
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((unsigned long long)w.x < __ldg(p.T + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Pool event of interaction k.
+__device__ __forceinline__ uint64_t pu_pool_event(const PuParams& p, uint32_t k, uint32_t event) {
+  const uint4 w = philox(k, event, 6u, 0u, p.rk);
+  return ((uint64_t)w.x * p.n_pool) >> 32;
+}
+
+// Vertex z: sigma_z times a normal, redrawn (attempt a in counter word 3)
+// until |z| <= max_z; at most 1024 attempts, then ERR_VERTEX.
+__device__ __forceinline__ float pu_vertex_z(const PuParams& p, uint32_t slot, uint32_t event, uint32_t purpose) {
+  for (uint32_t a = 0; a < 1024u; ++a) {
+    const uint4 w = philox(slot, event, purpose, a, p.rk);
+    const float z = p.sigma_z * normal(w.y, w.z);
+    if (fabsf(z) <= p.max_z) return z;
+  }
+  atomicOr(p.err, ERR_VERTEX);
+  return 0.0f;
+}
+
+// Merged size of hard event e, summed by the warp (every lane gets it).  ok
+// is false when the hard event's or a drawn pool event's offsets decrease.
+__device__ __forceinline__ uint64_t pu_event_size(const PuParams& p, uint64_t e, uint32_t event, uint32_t lane,
+                                                  uint32_t n_int, bool& ok) {
+  const uint64_t a = p.hoff[e], b = p.hoff[e + 1];
+  uint64_t sum = 0;
+  bool bad = false;
+  for (uint32_t k = lane; k < n_int; k += 32u) {
+    const uint64_t q = pu_pool_event(p, k, event);
+    const uint64_t q0 = __ldg(p.poff + q), q1 = __ldg(p.poff + q + 1);
+    bad |= q1 < q0;
+    sum += q1 - q0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(PDR_FULL, sum, o);
+  ok = b >= a && !__any_sync(PDR_FULL, bad);
+  return (b >= a ? b - a : 0) + sum;
+}
+
+// First pass: one warp per hard event writes the event's merged size.
+__global__ void pu_count_kernel(const __grid_constant__ PuParams p) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t e = w0; e < p.n_events; e += nw) {
+    const uint32_t event = p.event_base + (uint32_t)e;
+    bool ok;
+    const uint64_t size = pu_event_size(p, e, event, lane, pu_interactions(p, event), ok);
+    if (lane == 0) {
+      p.counts[e] = size;
+      if (!ok) atomicOr(p.err, ERR_CSR);
+    }
+  }
+}
+
+// Exclusive scan of the merged sizes into offsets [n_events + 1] (one block, chunked).
+__global__ void pu_scan_kernel(const uint64_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ off) {
+  __shared__ unsigned long long part[1024];
+  unsigned long long run = 0;
+  for (uint64_t base = 0; base < n; base += blockDim.x) {
+    const uint64_t e = base + threadIdx.x;
+    const unsigned long long v = e < n ? counts[e] : 0ull;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (unsigned o = 1; o < blockDim.x; o <<= 1) {
+      const unsigned long long u = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      part[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (e < n) off[e] = run + part[threadIdx.x] - v;
+    const unsigned long long blk = part[blockDim.x - 1];
+    __syncthreads();
+    run += blk;
+  }
+  if (threadIdx.x == 0) off[n] = run;
+}
+
+// Second pass: one warp per hard event copies its particles, then the pool
+// events of its interactions, each at its vertex z.
+__global__ void pu_fill_kernel(const __grid_constant__ PuParams p) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t e = w0; e < p.n_events; e += nw) {
+    const uint32_t event = p.event_base + (uint32_t)e;
+    const uint32_t n_int = pu_interactions(p, event);
+    bool ok;
+    const uint64_t size = pu_event_size(p, e, event, lane, n_int, ok);
+    const uint64_t m0 = p.moff[e];
+    if (!ok || p.moff[e + 1] < m0 || p.moff[e + 1] - m0 != size) {  // other arguments than the first pass
+      if (lane == 0) atomicOr(p.err, ok ? ERR_PILEUP : ERR_CSR);
+      continue;
+    }
+    const uint64_t a = p.hoff[e], nh = p.hoff[e + 1] - a;
+    const float zhs = p.smear_hs ? pu_vertex_z(p, 0u, event, 5u) : 0.0f;
+    for (uint64_t t = lane; t < nh; t += 32u) {
+      const uint64_t s = a + t, d = m0 + t;
+      p.opt[d] = __ldg(p.hpt + s); p.oeta[d] = __ldg(p.heta + s); p.ophi[d] = __ldg(p.hphi + s);
+      p.omass[d] = __ldg(p.hmass + s); p.opdg[d] = __ldg(p.hpdg + s); p.ocharge[d] = __ldg(p.hcharge + s);
+      p.ovz[d] = (p.hvz ? __ldg(p.hvz + s) : 0.0f) + zhs;
+    }
+    uint64_t pos = m0 + nh;
+    for (uint32_t k0 = 0; k0 < n_int; k0 += 32u) {
+      const uint32_t k = k0 + lane;
+      uint64_t src = 0, sz = 0;
+      float z = 0.0f;
+      if (k < n_int) {
+        const uint64_t q = pu_pool_event(p, k, event);
+        src = __ldg(p.poff + q);
+        sz = __ldg(p.poff + q + 1) - src;
+        z = pu_vertex_z(p, k, event, 6u);
+      }
+      uint64_t excl = sz;  // inclusive, then exclusive, warp scan of the sizes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(PDR_FULL, excl, o);
+        if (lane >= (uint32_t)o) excl += u;
+      }
+      const uint64_t tot = __shfl_sync(PDR_FULL, excl, 31);
+      excl -= sz;
+      const uint32_t nk = min(32u, n_int - k0);
+      for (uint32_t j = 0; j < nk; ++j) {
+        const uint64_t js = __shfl_sync(PDR_FULL, src, j), jn = __shfl_sync(PDR_FULL, sz, j);
+        const uint64_t jd = pos + __shfl_sync(PDR_FULL, excl, j);
+        const float jz = __shfl_sync(PDR_FULL, z, j);
+        for (uint64_t t = lane; t < jn; t += 32u) {
+          const uint64_t s = js + t, d = jd + t;
+          p.opt[d] = __ldg(p.ppt + s); p.oeta[d] = __ldg(p.peta + s); p.ophi[d] = __ldg(p.pphi + s);
+          p.omass[d] = __ldg(p.pmass + s); p.opdg[d] = __ldg(p.ppdg + s); p.ocharge[d] = __ldg(p.pcharge + s);
+          p.ovz[d] = jz;
+        }
+      }
+      pos += tot;
+    }
+  }
+}
+
 // ------------------------------------------------------- launch helpers
 template <int TEAM, int BLOCK>
 static cudaError_t launch_t(const KParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
@@ -1035,6 +1185,19 @@ cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint3
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gather_dense_kernel<<<n_sms * 8, 256, 0, s>>>(offsets, n_events, counts, dense_off, stride, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s) {
+  pu_count_kernel<<<n_sms * 8, 256, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  pu_scan_kernel<<<1, 1024, 0, s>>>(p.counts, p.n_events, const_cast<uint64_t*>(p.moff));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s) {
+  pu_fill_kernel<<<n_sms * 8, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@ cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32
 cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks);
 cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
                              cudaStream_t s);
+cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s);
+cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
                          uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
                          const pdr_outputs& src, const pdr_outputs& dst, int n_sms, cudaStream_t s);
@@ -123,11 +125,6 @@ struct Pool {
     }
     free_[o] = len;
   }
-  uint64_t free_bytes() const {
-    uint64_t s = 0;
-    for (auto& kv : free_) s += kv.second;
-    return s;
-  }
 };
 
 struct CardEntry {
@@ -179,6 +176,11 @@ struct pdr_ctx {
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_aux = nullptr;
   cudaEvent_t ev_in[PDR_HOST_CHUNKS] = {}, ev_comp[PDR_HOST_CHUNKS] = {}, ev_tot[PDR_HOST_CHUNKS] = {};
   unsigned long long* h_tot = nullptr;    // [PDR_HOST_CHUNKS][4]
+  // pile-up merging: the Poisson thresholds of the last mean on the device
+  unsigned long long* pu_T = nullptr;
+  uint32_t pu_K = 0, pu_cap = 0;
+  double pu_mean = -1.0;
+  uint64_t* pu_hoff_total = nullptr;      // pinned: the merged total of a first pass
 };
 
 namespace {
@@ -657,6 +659,8 @@ int pdr_destroy(pdr_ctx* ctx) {
     if (ctx->ev_tot[k]) cudaEventDestroy(ctx->ev_tot[k]);
   }
   if (ctx->h_tot) cudaFreeHost(ctx->h_tot);
+  if (ctx->pu_T) cudaFree(ctx->pu_T);
+  if (ctx->pu_hoff_total) cudaFreeHost(ctx->pu_hoff_total);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_word);
   delete ctx;
@@ -810,6 +814,8 @@ int pdr_check(pdr_ctx* ctx, void* stream) {
     if (w & ERR_CSR) m += " malformed CSR offsets;";
     if (w & ERR_OVERSIZE) m += " event larger than the launch allows;";
     if (w & ERR_TABLE) m += " tower table full;";
+    if (w & ERR_PILEUP) m += " pile-up merge arguments differ from the first pass;";
+    if (w & ERR_VERTEX) m += " no pile-up vertex inside the truncation in 1024 draws;";
     return fail(PDR_EDEVICE, m);
   }
   return PDR_OK;
@@ -1532,6 +1538,131 @@ int pdr_serve_stop(pdr_ctx* ctx) {
     ctx->serve = nullptr;
   }
   delete sv;
+  return PDR_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ pile-up merging
+namespace {
+
+// Poisson(mean) CDF thresholds (the definition in the C header): the CDF
+// summed in double from exp(-mean), T[k] = floor(cdf 2^32), the first entry
+// at or above 2^32 - 1 becoming 2^32.
+int poisson_table(double mean, std::vector<unsigned long long>& T) {
+  T.clear();
+  double p = std::exp(-mean), cdf = p;
+  for (int k = 0; k < 16384; ++k) {
+    if (k > 0) {
+      p = p * mean / (double)k;
+      cdf = cdf + p;
+    }
+    const double t = std::floor(cdf * 4294967296.0);
+    if (t >= 4294967295.0) {
+      T.push_back(4294967296ull);
+      return PDR_OK;
+    }
+    T.push_back((unsigned long long)t);
+  }
+  return fail(PDR_EOVERFLOW, "Poisson table does not end (mean too large)");
+}
+
+int pileup_args(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu) {
+  if (!ctx || !h || !pu) return fail(PDR_EINVAL, "null argument");
+  if (h->n_events >= (1ull << 31)) return fail(PDR_EINVAL, "n_events must be < 2^31");
+  if (h->n_events > 0 && (!h->offsets || !h->pt || !h->eta || !h->phi || !h->mass || !h->pdg || !h->charge))
+    return fail(PDR_EINVAL, "null hard-scatter array");
+  if (pu->n_pool < 1 || pu->n_pool >= (1ull << 32) || !pu->offsets || !pu->pt || !pu->eta || !pu->phi ||
+      !pu->mass || !pu->pdg || !pu->charge)
+    return fail(PDR_EINVAL, "empty pool or null pool array");
+  if (!(pu->mean >= 0.0) || !(pu->mean <= 4000.0)) return fail(PDR_EOVERFLOW, "mean pile-up outside [0, 4000]");
+  if (!(pu->sigma_z >= 0.0) || !std::isfinite(pu->sigma_z) || !(pu->max_z > 0.0) || !std::isfinite(pu->max_z))
+    return fail(PDR_EINVAL, "vertex width must be >= 0 and the truncation > 0");
+  if (pu->max_z < 0.05 * pu->sigma_z) return fail(PDR_EINVAL, "vertex truncation below 0.05 sigma_z");
+  return PDR_OK;
+}
+
+// Parameter block of a merge; uploads the thresholds when the mean changed.
+int pileup_params(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, cudaStream_t s, PuParams& p) {
+  if (pu->mean != ctx->pu_mean) {
+    std::vector<unsigned long long> T;
+    int rc = poisson_table(pu->mean, T);
+    if (rc) return rc;
+    if (T.size() > ctx->pu_cap) {
+      if (ctx->pu_T) cudaFree(ctx->pu_T);
+      ctx->pu_T = nullptr;
+      ctx->pu_cap = 0;
+      PDR_CUDA(cudaMalloc(&ctx->pu_T, T.size() * sizeof(unsigned long long)), "pile-up table");
+      ctx->pu_cap = (uint32_t)T.size();
+    }
+    PDR_CUDA(cudaMemcpyAsync(ctx->pu_T, T.data(), T.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice, s),
+             "pile-up table copy");
+    PDR_CUDA(cudaStreamSynchronize(s), "sync");  // T is a host temporary
+    ctx->pu_K = (uint32_t)T.size();
+    ctx->pu_mean = pu->mean;
+  }
+  std::memset(&p, 0, sizeof p);
+  p.n_events = h->n_events;
+  p.n_pool = pu->n_pool;
+  p.hoff = h->offsets; p.hpt = h->pt; p.heta = h->eta; p.hphi = h->phi; p.hmass = h->mass; p.hvz = h->vz;
+  p.hpdg = h->pdg; p.hcharge = h->charge;
+  p.poff = pu->offsets; p.ppt = pu->pt; p.peta = pu->eta; p.pphi = pu->phi; p.pmass = pu->mass;
+  p.ppdg = pu->pdg; p.pcharge = pu->charge;
+  p.T = ctx->pu_T;
+  p.K = ctx->pu_K;
+  p.event_base = h->event_index_base;
+  p.smear_hs = pu->smear_hs ? 1u : 0u;
+  p.sigma_z = (float)pu->sigma_z;
+  p.max_z = (float)pu->max_z;
+  fill_round_keys(p.rk, h->seed);
+  p.err = ctx->d_err;
+  return PDR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdr_pileup_offsets(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, uint64_t* merged_offsets,
+                       uint64_t* total, void* stream) {
+  int rc = pileup_args(ctx, h, pu);
+  if (rc) return rc;
+  if (!merged_offsets || !total) return fail(PDR_EINVAL, "null offsets or total");
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->pu_hoff_total) PDR_CUDA(cudaHostAlloc((void**)&ctx->pu_hoff_total, 8, 0), "pinned word");
+  PuParams p;
+  if ((rc = pileup_params(ctx, h, pu, s, p))) return rc;
+  uint64_t* counts = (uint64_t*)ctx->pool.alloc(std::max<uint64_t>(h->n_events, 1) * 8);
+  if (!counts) return fail(PDR_ENOMEM, "device pool too small for the pile-up counts");
+  p.counts = counts;
+  p.moff = merged_offsets;
+  cudaError_t e = launch_pileup_count(p, ctx->n_sms, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->pu_hoff_total, merged_offsets + h->n_events, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  ctx->pool.release(counts);
+  if (e != cudaSuccess) return cuda_fail(e, "pile-up counting");
+  *total = *ctx->pu_hoff_total;
+  return PDR_OK;
+}
+
+int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, const uint64_t* merged_offsets,
+                     const pdr_particles* out, void* stream) {
+  int rc = pileup_args(ctx, h, pu);
+  if (rc) return rc;
+  if (!merged_offsets || !out || !out->pt || !out->eta || !out->phi || !out->mass || !out->vz || !out->pdg ||
+      !out->charge)
+    return fail(PDR_EINVAL, "null offsets or output array");
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  PuParams p;
+  if ((rc = pileup_params(ctx, h, pu, s, p))) return rc;
+  p.moff = merged_offsets;
+  p.opt = out->pt; p.oeta = out->eta; p.ophi = out->phi; p.omass = out->mass; p.ovz = out->vz;
+  p.opdg = out->pdg; p.ocharge = out->charge;
+  PDR_CUDA(launch_pileup_fill(p, ctx->n_sms, s), "pile-up fill");
   return PDR_OK;
 }
 

@@ -40,7 +40,8 @@ def test_abi_version(libpdr):
     assert libpdr.pdr_abi_version() == 1
 
 
-STRUCTS = ("pdr_card", "pdr_batch", "pdr_outputs", "pdr_launch", "pdr_options", "pdr_result")
+STRUCTS = ("pdr_card", "pdr_batch", "pdr_outputs", "pdr_launch", "pdr_options", "pdr_result",
+           "pdr_serve_options", "pdr_serve_stats", "pdr_pileup", "pdr_particles")
 
 
 def test_binding_structs_match_header_layout(tmp_path):

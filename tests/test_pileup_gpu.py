@@ -1,0 +1,159 @@
+"""Pile-up merging on the GPU (pdr_pileup_offsets / pdr_pileup_merge) against
+the oracle's merge (Sec. 2.2: minimum-bias interactions merged with each
+hard-scatter event before the detector response).
+
+Offsets, pool indices and every copied particle field are compared bit for
+bit; the vertex z of a particle (float32 on the GPU, float64 in the oracle)
+within 2e-6 relative to max(|z|, sigma_z).  The merged batch then goes
+through the detector response and is compared with the oracle as usual.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SEED = 23
+SIGMA, ZMAX = 0.053, 0.25
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_26089_b300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0, pool_bytes=2 << 30)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def synth():
+    from paper_2606_26089_b300 import synth as s
+    return s
+
+
+def _gpu_merge(B, ctx, hard, pool, mean, sigma=SIGMA, zmax=ZMAX, smear=True, event_base=0):
+    hd, pd = B.batch_to_device(hard), B.batch_to_device(pool)
+    m = B.merge_pileup(ctx, hd, pd, mean, sigma, zmax, smear, SEED, event_base)
+    torch.cuda.synchronize()
+    ctx.check()
+    h = {k: (m[k].cpu().numpy() if k not in ("n_events", "n_particles") else m[k]) for k in m}
+    n = h["n_particles"]
+    for k in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge"):
+        h[k] = h[k][:n]
+    h["offsets"] = h["offsets"].astype(np.uint64)
+    return h
+
+
+def _compare(g, o, sigma=SIGMA):
+    """Offsets and copied fields bit for bit; vz within tolerance except in
+    events holding a truncation decision within rounding of the bound (there
+    the two sides may keep different attempts: counts and copies still agree)."""
+    assert np.array_equal(g["offsets"], o["offsets"])
+    for k in ("pt", "eta", "phi", "mass"):
+        assert np.array_equal(g[k].view(np.uint32), o[k].astype(np.float32).view(np.uint32)), k
+    for k in ("pdg", "charge"):
+        assert np.array_equal(g[k], o[k]), k
+    keep = np.ones(g["vz"].shape[0], bool)
+    off = o["offsets"].astype(np.int64)
+    for e in o["marginal_events"]:
+        keep[off[e]:off[e + 1]] = False
+    assert keep.mean() > 0.9
+    tol = 2e-6 * np.maximum(np.abs(o["vz"]), sigma)
+    assert np.all((np.abs(g["vz"].astype(np.float64) - o["vz"]) <= tol)[keep])
+
+
+def test_merge_matches_the_oracle(B, ctx, synth):
+    pool = synth.make_minbias_pool(400)
+    hard = synth.make_hard(48)
+    g = _gpu_merge(B, ctx, hard, pool, 20.0)
+    o = oracle.pileup_merge(hard, pool, 20.0, SIGMA, ZMAX, True, SEED)
+    _compare(g, o)
+
+
+def test_tight_truncation_own_hard_vertices_and_no_hard_smearing(B, ctx, synth):
+    pool = synth.make_minbias_pool(200)
+    hard = synth.make_hard(30)
+    hard.vz = np.random.default_rng(3).uniform(-0.1, 0.1, hard.n_particles).astype(np.float32)
+    g = _gpu_merge(B, ctx, hard, pool, 15.0, zmax=0.03, smear=False, event_base=1000)
+    o = oracle.pileup_merge(hard, pool, 15.0, SIGMA, 0.03, False, SEED, event_base=1000)
+    _compare(g, o)
+    assert np.max(np.abs(g["vz"][g["vz"] != 0.0])) <= 0.1  # truncated interactions and the hard vz
+
+
+def test_no_pileup_returns_the_hard_events(B, ctx, synth):
+    pool = synth.make_minbias_pool(20)
+    hard = synth.make_hard(10)
+    g = _gpu_merge(B, ctx, hard, pool, 0.0, smear=False)
+    assert np.array_equal(g["offsets"], hard.offsets)
+    assert np.array_equal(g["pt"], hard.pt) and np.all(g["vz"] == 0.0)
+
+
+def test_second_pass_with_other_arguments_writes_nothing(B, ctx, synth):
+    pool = synth.make_minbias_pool(100)
+    hard = synth.make_hard(16)
+    hd, pd = B.batch_to_device(hard), B.batch_to_device(pool)
+    hb = B.make_batch(hd, 0, SEED)
+    off = torch.empty(hard.n_events + 1, dtype=torch.int64, device="cuda")
+    total = ctx.pileup_offsets(hb, B.make_pileup(pd, 10.0, SIGMA, ZMAX, True), off)
+    out = {k: torch.full((total,), -7.0, device="cuda") for k in ("pt", "eta", "phi", "mass", "vz")}
+    out["pdg"] = torch.zeros(total, dtype=torch.int32, device="cuda")
+    out["charge"] = torch.zeros(total, dtype=torch.int8, device="cuda")
+    ctx.pileup_merge(hb, B.make_pileup(pd, 30.0, SIGMA, ZMAX, True), off, out)  # another mean
+    torch.cuda.synchronize()
+    with pytest.raises(B.PdrError, match="pile-up"):
+        ctx.check()
+    # events whose size happens to agree may be filled; the others are untouched
+    assert (out["pt"] == -7.0).any()
+
+
+def test_full_size_pileup_configuration(B, ctx, synth):
+    """10k hard events x Poisson(170) interactions of a 10k-event pool (the
+    pile-up workload's scale): all offsets against the oracle's draws, every
+    field of a sample of events."""
+    mean = 170.0
+    pool = synth.make_minbias_pool(10_000)
+    hard = synth.make_hard(10_000)
+    g = _gpu_merge(B, ctx, hard, pool, mean)
+    T = oracle.poisson_thresholds(mean)
+    pu = oracle.PileUp(mean, SIGMA, ZMAX, 1, 0)
+    psz = np.diff(np.asarray(pool.offsets, np.int64))
+    hsz = np.diff(np.asarray(hard.offsets, np.int64))
+    sizes = np.empty(hard.n_events, np.int64)
+    for e in range(hard.n_events):
+        n, idx, z, zhs, m = oracle.pileup_draws(pu, T, pool.n_events, SEED, e)
+        sizes[e] = hsz[e] + psz[idx].sum()
+    assert np.array_equal(np.diff(g["offsets"].astype(np.int64)), sizes)
+    assert g["n_particles"] > 50_000_000
+    for e0 in (0, 4321, 9990):
+        sub = hard.slice_events(e0, e0 + 10)
+        o = oracle.pileup_merge(sub, pool, mean, SIGMA, ZMAX, True, SEED, event_base=e0)
+        a, b = int(g["offsets"][e0]), int(g["offsets"][e0 + 10])
+        part = {k: g[k][a:b] for k in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge")}
+        part["offsets"] = (g["offsets"][e0:e0 + 11] - g["offsets"][e0]).astype(np.uint64)
+        _compare(part, o)
+
+
+def test_response_of_a_merged_batch(B, ctx, synth):
+    pool = synth.make_minbias_pool(300)
+    hard = synth.make_hard(6)
+    g = _gpu_merge(B, ctx, hard, pool, 25.0)
+    merged = synth.EventBatch(g["offsets"], g["pt"], g["eta"], g["phi"], g["mass"], g["pdg"], g["charge"],
+                              g["vz"], "merged")
+    cid = ctx.card_load("cms_like")
+    ocard = oracle.load_card("cms_like")
+    host = P.run_gpu(ctx, cid, merged, 31, debug=True)
+    P.check_counts_sane(host, merged)
+    stats = P.Stats()
+    for e in range(merged.n_events):
+        P.compare_event(ocard, merged.event(e), P.gpu_event(host, merged, e), 31, e, stats)
