@@ -135,23 +135,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_fingerprint() -> str:
-    """sha1 of the kernel source without comments and whitespace (comment edits keep it)."""
-    src = open(os.path.join(ROOT, "paper_2606_26089_b300", "csrc", "pdr_kernel.cu")).read()
+KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh"),
+                  "pu_fill_kernel": ("pdr_pileup.cu", "pdr_math.cuh")}
+
+
+def kernel_fingerprint(kernel: str = "fused_kernel") -> str:
+    """sha1 of a kernel's source files without comments and whitespace (comment edits keep it)."""
+    src = "".join(open(os.path.join(ROOT, "paper_2606_26089_b300", "csrc", f)).read()
+                  for f in KERNEL_SOURCES[kernel])
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
     src = re.sub(r"\s+", "", src)
     return hashlib.sha1(src.encode()).hexdigest()[:12]
 
 
-def _traffic_from_profile(workload: str):
+def _traffic_from_profile(workload: str, kernel: str = "fused_kernel"):
     """Per-launch DRAM bytes from the committed ncu summary, if it matches the kernel source."""
-    path = os.path.join(ROOT, "profiles", f"fused_kernel_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
-    sha = kernel_fingerprint()
+    sha = kernel_fingerprint(kernel)
     m_sha = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
     m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_t or m_sha.group(1) != sha:
@@ -481,11 +486,27 @@ def bench_pileup_merge(args, B, ctx):
             "fill_ms": fill_s * 1e3, "offsets_ms_incl_sync": statistics.mean(t_off) * 1e3,
             "fill_particles_per_s": total / fill_s,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "algorithmic_bytes_per_launch": int(alg),
-                         "kernel": "pdr::pu_fill_kernel"},
+                         "frac": achieved / peak, "traffic": _traffic_from_profile("pileup", "pu_fill_kernel"),
+                         "algorithmic_bytes_per_launch": int(alg), "kernel": "pdr::pu_fill_kernel"},
             "response_ms": resp_s * 1e3, "response_launch": launch.as_dict(),
             "merge_and_response_particles_per_s": total / (fill_s + resp_s),
             "reps": reps}
+
+
+def merge_only(args):
+    """The pile-up merge object alone on one GPU (for profiling the merge)."""
+    import torch
+
+    from paper_2606_26089_b300 import binding as B
+    from paper_2606_26089_b300 import build as pdr_build
+
+    pdr_build.build()
+    torch.cuda.set_device(0)
+    ctx = B.Context(0, pool_bytes=int(args.pool_gb * (1 << 30)))
+    try:
+        return {"pileup_merge": bench_pileup_merge(args, B, ctx)}
+    finally:
+        ctx.close()
 
 
 def cpu_baseline(batch, card_name, seed, target_s):
@@ -569,6 +590,8 @@ def main(argv=None):
     ap.add_argument("--serving-pool", type=int, default=5000)
     ap.add_argument("--no-per-event", action="store_true")
     ap.add_argument("--no-pileup-merge", action="store_true")
+    ap.add_argument("--merge-only", action="store_true",
+                    help="time only the pile-up merge (and the merged batch's response); prints that object")
     ap.add_argument("--pileup-events", type=int, default=10_000, help="hard events of the pile-up merge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
@@ -581,6 +604,9 @@ def main(argv=None):
         line = bench_reference(args, rank)
         if rank == 0 and line is not None:
             print(json.dumps(line), flush=True)
+        return
+    if args.merge_only:
+        print(json.dumps(merge_only(args)), flush=True)
         return
     dist, rank, ws = _dist()
     line = bench_ours(args, dist, rank, ws)

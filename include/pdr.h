@@ -309,8 +309,9 @@ int pdr_pileup_offsets(pdr_ctx* ctx, const pdr_batch* hard, const pdr_pileup* pu
  * with other arguments than the first pass), writes nothing and sets the
  * device error word (pdr_check reports it).  Asynchronous on `stream`; the
  * result is a batch for pdr_run with merged_offsets and these arrays.
- * Events whose hard or drawn pool offsets decrease are skipped in both
- * passes and reported as malformed offsets by pdr_check. */
+ * Events whose hard or drawn pool offsets decrease, or that draw a pool
+ * event of 2^32 particles or more, are skipped in both passes and reported
+ * as malformed offsets by pdr_check. */
 int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* hard, const pdr_pileup* pu, const uint64_t* merged_offsets,
                      const pdr_particles* out, void* stream);
 

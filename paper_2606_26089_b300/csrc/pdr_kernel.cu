@@ -31,152 +31,9 @@
 #include <stdint.h>
 
 #include "pdr_internal.h"
+#include "pdr_math.cuh"
 
 namespace pdr {
-
-#define PDR_FULL 0xFFFFFFFFu
-
-static constexpr float PI_F = 3.14159265358979323846f;
-static constexpr float TWO_PI_F = 6.28318530717958647692f;
-static constexpr float PIO2_HI = 1.57079637050628662109375f;  // float32(pi/2)
-static constexpr float PIO2_LO = -4.37113900018624283e-8f;     // pi/2 - PIO2_HI
-
-// ------------------------------------------------------------------ Philox
-// Philox4x32-10 (Salmon et al., SC'11): ten multiply/xor rounds on a 128-bit
-// counter under a 64-bit key bumped by the Weyl constants each round.  The
-// round keys of the batch's seed are precomputed (KSeg::rk), so a round is two
-// 32 x 32 -> 64-bit products and two three-way xors.
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* rk) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long p0 = 0xD2511F53ull * c0;
-    const unsigned long long p1 = 0xCD9E8D57ull * c2;
-    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk[2 * r];
-    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk[2 * r + 1];
-    c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
-  }
-  return make_uint4(c0, c1, c2, c3);
-}
-
-// Reciprocal to 1 ulp (the hardware approximation); used where the result
-// only needs a few ulp: every such quotient feeds either an output compared at
-// 2e-6 relative or a decision taken with the 1e-5 marginal band.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ float fdiv(float a, float b) { return a * rcp_approx(b); }
-
-// Square root to 1 ulp (the hardware approximation; measured over a spread of
-// magnitudes: relative error below 1e-7): energies, smearing widths and the
-// Box-Muller radius need only a few ulp.
-__device__ __forceinline__ float sqrt_approx(float x) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-// Polynomial approximations, coefficients from a least-squares fit on
-// Chebyshev nodes in double precision (truncation error far below float
-// rounding on the stated ranges):
-//   asin(x) = x + x^3 P(x^2) on [0, 1/2]             (fit error ~1e-9)
-//   sin(x)  = x + x^3 Q(x^2) on [0, pi/2]            (fit error ~2e-10)
-//   ln(1 - v) = -v L(v)      on [0, 1/4]             (fit error ~3e-9)
-//   ln(1 + x) = x M(x)       on [0, 1/4]             (fit error ~4e-10)
-__device__ __forceinline__ float asin_half(float x) {
-  const float t = x * x;
-  float p = fmaf(t, 0.033805817f, 0.017077811f);
-  p = fmaf(t, p, 0.031116169f);
-  p = fmaf(t, p, 0.04459803f);
-  p = fmaf(t, p, 0.07500099f);
-  p = fmaf(t, p, 0.16666666f);
-  return fmaf(x * t, p, x);
-}
-
-__device__ __forceinline__ float sin_quarter(float x) {
-  const float t = x * x;
-  float q = fmaf(t, -2.4080528e-08f, 2.753648e-06f);
-  q = fmaf(t, q, -0.00019841087f);
-  q = fmaf(t, q, 0.008333333f);
-  q = fmaf(t, q, -0.16666667f);
-  return fmaf(x * t, q, x);
-}
-
-// sin on [0, pi]: reflected to [0, pi/2] with pi split in two floats.
-__device__ __forceinline__ float sin_half_turn(float y) {
-  return sin_quarter(y > PIO2_HI ? (3.14159274101257324f - y) + -8.74227766e-8f : y);
-}
-
-// ln u for u in (0, 1): hardware log2 below 3/4 (relative error < 5e-7
-// there, |ln u| > 0.28), -v L(v) with v = 1 - u (exact) above.
-__device__ __forceinline__ float ln_unit(float u) {
-  const float v = 1.0f - u;
-  float p = fmaf(v, 0.33390906f, 0.08952039f);
-  p = fmaf(v, p, 0.21425246f);
-  p = fmaf(v, p, 0.24869019f);
-  p = fmaf(v, p, 0.33338976f);
-  p = fmaf(v, p, 0.4999991f);
-  p = fmaf(v, p, 1.0f);
-  return u > 0.75f ? -v * p : __logf(u);
-}
-
-// ln(1 + x) for x >= 0: x M(x) up to 1/4, hardware log2 of 1 + x above
-// (relative error < 6e-7 there, ln(1 + x) > 0.22).
-__device__ __forceinline__ float log1p_pos(float x) {
-  float m = fmaf(x, 0.070751615f, -0.14544724f);
-  m = fmaf(x, m, 0.19665538f);
-  m = fmaf(x, m, -0.24972063f);
-  m = fmaf(x, m, 0.33332205f);
-  m = fmaf(x, m, -0.49999982f);
-  m = fmaf(x, m, 1.0f);
-  return x > 0.25f ? __logf(1.0f + x) : x * m;
-}
-
-// cos(2 pi u) for u in (0, 1): folded exactly in turns to sin of at most a
-// quarter turn (cos(2 pi u) = -cos(pi t), t = |2u - 1|).
-__device__ __forceinline__ float cos_two_pi(float u) {
-  const float t = fabsf(2.0f * u - 1.0f);
-  const float r = t > 0.5f ? t - 0.5f : 0.5f - t;
-  const float s = sin_quarter(PI_F * r);
-  return t > 0.5f ? s : -s;
-}
-
-// cosh and sinh from one exponential: cosh = (e + 1/e) / 2; sinh likewise for
-// |x| >= 1/2 (no cancellation there: e - 1/e >= 1.04) and from its odd Taylor
-// series through x^9 below 1/2 (truncation < 3e-11 relative).
-__device__ __forceinline__ void cosh_sinh(float x, float& ch, float& sh) {
-  const float ax = fabsf(x);
-  const float e = expf(ax);
-  const float ie = rcp_approx(e);
-  ch = 0.5f * (e + ie);
-  const float x2 = ax * ax;
-  const float series =
-      ax * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 362880.0f, 1.0f / 5040.0f), 1.0f / 120.0f), 1.0f / 6.0f),
-                1.0f);
-  const float s = ax < 0.5f ? series : 0.5f * (e - ie);
-  sh = copysignf(s, x);
-}
-
-// asinh(u) = sign(u) log(|u| + sqrt(u^2 + 1)) with the hardware log2 (absolute
-// error about 1e-7; the argument is >= 1, so no cancellation): used for the
-// surface pseudorapidity, whose tolerance is 2e-6 max(|eta|, 1).
-__device__ __forceinline__ float asinh_fast(float u) {
-  const float au = fabsf(u);
-  return copysignf(__logf(au + sqrt_approx(fmaf(au, au, 1.0f))), u);
-}
-
-// (2k + 1) / 2^24 for the top 23 bits k of w: exact in float32.
-__device__ __forceinline__ float u01(uint32_t w) {
-  return (__uint2float_rn(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
-}
-
-// Box-Muller, cosine branch (over all 2^23 inputs of each word the deviate
-// is within 1e-6 absolute of its FP64 value).
-__device__ __forceinline__ float normal(uint32_t wa, uint32_t wb) {
-  return sqrt_approx(-2.0f * ln_unit(u01(wa))) * cos_two_pi(u01(wb));
-}
 
 // Log-normal with mean x and relative variance rel2 = (sigma/x)^2.
 __device__ __forceinline__ float lognormal(float x, float rel2, float z) {
@@ -979,156 +836,6 @@ __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64
   }
 }
 
-// ------------------------------------------------------- pile-up merging
-// (Sec. 2.2; the draws are documented with pdr_pileup in the C header.)
-// Interactions of a hard event: the smallest k with w0 < T[k].
-__device__ __forceinline__ uint32_t pu_interactions(const PuParams& p, uint32_t event) {
-  const uint4 w = philox(0u, event, 5u, 0u, p.rk);
-  uint32_t lo = 0, hi = p.K - 1;  // T[K - 1] = 2^32 > w0
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if ((unsigned long long)w.x < __ldg(p.T + mid)) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
-
-// Pool event of interaction k.
-__device__ __forceinline__ uint64_t pu_pool_event(const PuParams& p, uint32_t k, uint32_t event) {
-  const uint4 w = philox(k, event, 6u, 0u, p.rk);
-  return ((uint64_t)w.x * p.n_pool) >> 32;
-}
-
-// Vertex z: sigma_z times a normal, redrawn (attempt a in counter word 3)
-// until |z| <= max_z; at most 1024 attempts, then ERR_VERTEX.
-__device__ __forceinline__ float pu_vertex_z(const PuParams& p, uint32_t slot, uint32_t event, uint32_t purpose) {
-  for (uint32_t a = 0; a < 1024u; ++a) {
-    const uint4 w = philox(slot, event, purpose, a, p.rk);
-    const float z = p.sigma_z * normal(w.y, w.z);
-    if (fabsf(z) <= p.max_z) return z;
-  }
-  atomicOr(p.err, ERR_VERTEX);
-  return 0.0f;
-}
-
-// Merged size of hard event e, summed by the warp (every lane gets it).  ok
-// is false when the hard event's or a drawn pool event's offsets decrease.
-__device__ __forceinline__ uint64_t pu_event_size(const PuParams& p, uint64_t e, uint32_t event, uint32_t lane,
-                                                  uint32_t n_int, bool& ok) {
-  const uint64_t a = p.hoff[e], b = p.hoff[e + 1];
-  uint64_t sum = 0;
-  bool bad = false;
-  for (uint32_t k = lane; k < n_int; k += 32u) {
-    const uint64_t q = pu_pool_event(p, k, event);
-    const uint64_t q0 = __ldg(p.poff + q), q1 = __ldg(p.poff + q + 1);
-    bad |= q1 < q0;
-    sum += q1 - q0;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(PDR_FULL, sum, o);
-  ok = b >= a && !__any_sync(PDR_FULL, bad);
-  return (b >= a ? b - a : 0) + sum;
-}
-
-// First pass: one warp per hard event writes the event's merged size.
-__global__ void pu_count_kernel(const __grid_constant__ PuParams p) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t e = w0; e < p.n_events; e += nw) {
-    const uint32_t event = p.event_base + (uint32_t)e;
-    bool ok;
-    const uint64_t size = pu_event_size(p, e, event, lane, pu_interactions(p, event), ok);
-    if (lane == 0) {
-      p.counts[e] = size;
-      if (!ok) atomicOr(p.err, ERR_CSR);
-    }
-  }
-}
-
-// Exclusive scan of the merged sizes into offsets [n_events + 1] (one block, chunked).
-__global__ void pu_scan_kernel(const uint64_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ off) {
-  __shared__ unsigned long long part[1024];
-  unsigned long long run = 0;
-  for (uint64_t base = 0; base < n; base += blockDim.x) {
-    const uint64_t e = base + threadIdx.x;
-    const unsigned long long v = e < n ? counts[e] : 0ull;
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (unsigned o = 1; o < blockDim.x; o <<= 1) {
-      const unsigned long long u = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
-      __syncthreads();
-      part[threadIdx.x] += u;
-      __syncthreads();
-    }
-    if (e < n) off[e] = run + part[threadIdx.x] - v;
-    const unsigned long long blk = part[blockDim.x - 1];
-    __syncthreads();
-    run += blk;
-  }
-  if (threadIdx.x == 0) off[n] = run;
-}
-
-// Second pass: one warp per hard event copies its particles, then the pool
-// events of its interactions, each at its vertex z.
-__global__ void pu_fill_kernel(const __grid_constant__ PuParams p) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t e = w0; e < p.n_events; e += nw) {
-    const uint32_t event = p.event_base + (uint32_t)e;
-    const uint32_t n_int = pu_interactions(p, event);
-    bool ok;
-    const uint64_t size = pu_event_size(p, e, event, lane, n_int, ok);
-    const uint64_t m0 = p.moff[e];
-    if (!ok || p.moff[e + 1] < m0 || p.moff[e + 1] - m0 != size) {  // other arguments than the first pass
-      if (lane == 0) atomicOr(p.err, ok ? ERR_PILEUP : ERR_CSR);
-      continue;
-    }
-    const uint64_t a = p.hoff[e], nh = p.hoff[e + 1] - a;
-    const float zhs = p.smear_hs ? pu_vertex_z(p, 0u, event, 5u) : 0.0f;
-    for (uint64_t t = lane; t < nh; t += 32u) {
-      const uint64_t s = a + t, d = m0 + t;
-      p.opt[d] = __ldg(p.hpt + s); p.oeta[d] = __ldg(p.heta + s); p.ophi[d] = __ldg(p.hphi + s);
-      p.omass[d] = __ldg(p.hmass + s); p.opdg[d] = __ldg(p.hpdg + s); p.ocharge[d] = __ldg(p.hcharge + s);
-      p.ovz[d] = (p.hvz ? __ldg(p.hvz + s) : 0.0f) + zhs;
-    }
-    uint64_t pos = m0 + nh;
-    for (uint32_t k0 = 0; k0 < n_int; k0 += 32u) {
-      const uint32_t k = k0 + lane;
-      uint64_t src = 0, sz = 0;
-      float z = 0.0f;
-      if (k < n_int) {
-        const uint64_t q = pu_pool_event(p, k, event);
-        src = __ldg(p.poff + q);
-        sz = __ldg(p.poff + q + 1) - src;
-        z = pu_vertex_z(p, k, event, 6u);
-      }
-      uint64_t excl = sz;  // inclusive, then exclusive, warp scan of the sizes
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(PDR_FULL, excl, o);
-        if (lane >= (uint32_t)o) excl += u;
-      }
-      const uint64_t tot = __shfl_sync(PDR_FULL, excl, 31);
-      excl -= sz;
-      const uint32_t nk = min(32u, n_int - k0);
-      for (uint32_t j = 0; j < nk; ++j) {
-        const uint64_t js = __shfl_sync(PDR_FULL, src, j), jn = __shfl_sync(PDR_FULL, sz, j);
-        const uint64_t jd = pos + __shfl_sync(PDR_FULL, excl, j);
-        const float jz = __shfl_sync(PDR_FULL, z, j);
-        for (uint64_t t = lane; t < jn; t += 32u) {
-          const uint64_t s = js + t, d = jd + t;
-          p.opt[d] = __ldg(p.ppt + s); p.oeta[d] = __ldg(p.peta + s); p.ophi[d] = __ldg(p.pphi + s);
-          p.omass[d] = __ldg(p.pmass + s); p.opdg[d] = __ldg(p.ppdg + s); p.ocharge[d] = __ldg(p.pcharge + s);
-          p.ovz[d] = jz;
-        }
-      }
-      pos += tot;
-    }
-  }
-}
-
 // ------------------------------------------------------- launch helpers
 template <int TEAM, int BLOCK>
 static cudaError_t launch_t(const KParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
@@ -1185,19 +892,6 @@ cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint3
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gather_dense_kernel<<<n_sms * 8, 256, 0, s>>>(offsets, n_events, counts, dense_off, stride, src, dst);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s) {
-  pu_count_kernel<<<n_sms * 8, 256, 0, s>>>(p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  pu_scan_kernel<<<1, 1024, 0, s>>>(p.counts, p.n_events, const_cast<uint64_t*>(p.moff));
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s) {
-  pu_fill_kernel<<<n_sms * 8, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

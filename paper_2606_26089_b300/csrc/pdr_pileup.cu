@@ -1,0 +1,289 @@
+// Pile-up merging on the device (sm_103a; Sec. 2.2): for every hard-scatter
+// event of a CSR batch, a Poisson number of minimum-bias interactions is
+// drawn, each takes a pool event and a vertex z, and the merged event (hard
+// particles, then the interactions in draw order) is written as a new CSR
+// batch in two passes: merged sizes and offsets, then the particles.  Every
+// draw comes from Philox counters keyed by the event index (the contract is
+// documented with pdr_pileup in the C header), so the result does not depend
+// on the launch shape or on how events are batched.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdr_internal.h"
+#include "pdr_math.cuh"
+
+namespace pdr {
+
+// Interactions of a hard event: the smallest k with w0 < T[k].
+__device__ __forceinline__ uint32_t pu_interactions(const PuParams& p, uint32_t event) {
+  const uint4 w = philox(0u, event, 5u, 0u, p.rk);
+  uint32_t lo = 0, hi = p.K - 1;  // T[K - 1] = 2^32 > w0
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if ((unsigned long long)w.x < __ldg(p.T + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Pool event of interaction k.
+__device__ __forceinline__ uint64_t pu_pool_event(const PuParams& p, uint32_t k, uint32_t event) {
+  const uint4 w = philox(k, event, 6u, 0u, p.rk);
+  return ((uint64_t)w.x * p.n_pool) >> 32;
+}
+
+// Vertex z: sigma_z times a normal, redrawn (attempt a in counter word 3)
+// until |z| <= max_z; at most 1024 attempts, then ERR_VERTEX.
+__device__ __forceinline__ float pu_vertex_z(const PuParams& p, uint32_t slot, uint32_t event, uint32_t purpose) {
+  for (uint32_t a = 0; a < 1024u; ++a) {
+    const uint4 w = philox(slot, event, purpose, a, p.rk);
+    const float z = p.sigma_z * normal(w.y, w.z);
+    if (fabsf(z) <= p.max_z) return z;
+  }
+  atomicOr(p.err, ERR_VERTEX);
+  return 0.0f;
+}
+
+// Merged size of hard event e, summed by the warp (every lane gets it).  ok
+// is false when the hard event's or a drawn pool event's offsets decrease
+// (or a pool event has 2^32 particles or more).
+__device__ __forceinline__ uint64_t pu_event_size(const PuParams& p, uint64_t e, uint32_t event, uint32_t lane,
+                                                  uint32_t n_int, bool& ok) {
+  const uint64_t a = p.hoff[e], b = p.hoff[e + 1];
+  uint64_t sum = 0;
+  bool bad = false;
+  for (uint32_t k = lane; k < n_int; k += 32u) {
+    const uint64_t q = pu_pool_event(p, k, event);
+    const uint64_t q0 = __ldg(p.poff + q), q1 = __ldg(p.poff + q + 1);
+    bad |= q1 < q0 || q1 - q0 >= (1ull << 32);
+    sum += q1 - q0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(PDR_FULL, sum, o);
+  ok = b >= a && !__any_sync(PDR_FULL, bad);
+  return (b >= a ? b - a : 0) + sum;
+}
+
+// First pass: one warp per hard event writes the event's merged size.
+__global__ void pu_count_kernel(const __grid_constant__ PuParams p) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t e = w0; e < p.n_events; e += nw) {
+    const uint32_t event = p.event_base + (uint32_t)e;
+    bool ok;
+    const uint64_t size = pu_event_size(p, e, event, lane, pu_interactions(p, event), ok);
+    if (lane == 0) {
+      p.counts[e] = size;
+      if (!ok) atomicOr(p.err, ERR_CSR);
+    }
+  }
+}
+
+// Exclusive scan of the merged sizes into offsets [n_events + 1] (one block, chunked).
+__global__ void pu_scan_kernel(const uint64_t* __restrict__ counts, uint64_t n, uint64_t* __restrict__ off) {
+  __shared__ unsigned long long part[1024];
+  unsigned long long run = 0;
+  for (uint64_t base = 0; base < n; base += blockDim.x) {
+    const uint64_t e = base + threadIdx.x;
+    const unsigned long long v = e < n ? counts[e] : 0ull;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (unsigned o = 1; o < blockDim.x; o <<= 1) {
+      const unsigned long long u = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
+      __syncthreads();
+      part[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (e < n) off[e] = run + part[threadIdx.x] - v;
+    const unsigned long long blk = part[blockDim.x - 1];
+    __syncthreads();
+    run += blk;
+  }
+  if (threadIdx.x == 0) off[n] = run;
+}
+
+// Second pass: one block per hard event.  The block first re-sums the
+// event's merged size (and writes nothing if it differs from the offsets
+// given), then copies the hard particles and, 256 interactions at a time,
+// the pool events: each chunk's interactions are drawn by one thread each,
+// their sizes scanned, and the chunk's particles copied element-parallel
+// (each thread finds its particle's interaction by a binary search over the
+// scanned starts), so that every output store is a contiguous, coalesced run.
+// (Measured on the 10k-event pile-up merge: one warp per event 0.57 ms, one
+// warp per interaction 0.47 ms, this 0.43 ms.)
+constexpr int PU_BLOCK = 256;
+constexpr int PU_UNROLL = 2;
+
+// Block-wide exclusive scan of one 64-bit value per thread; returns the
+// exclusive prefix and writes the block total to *total (all threads).
+__device__ __forceinline__ uint64_t pu_block_scan(uint64_t v, uint64_t* warp_sums, uint64_t* total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_up_sync(PDR_FULL, inc, o);
+    if (lane >= (uint32_t)o) inc += u;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  uint64_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < PU_BLOCK / 32; ++w) {
+    const uint64_t x = warp_sums[w];
+    before += (w < (int)warp) ? x : 0ull;
+    all += x;
+  }
+  __syncthreads();
+  *total = all;
+  return before + inc - v;
+}
+
+// Copies the n hard particles from src0 to out[dst0, dst0 + n), each at its
+// own vertex z plus the hard shift zhs (element-parallel, PU_UNROLL
+// particles in flight per thread).
+__device__ __forceinline__ void pu_copy_hard(const PuParams& p, uint64_t src0, uint64_t dst0, uint64_t n,
+                                             float zhs) {
+  for (uint64_t i0 = 0; i0 < n; i0 += (uint64_t)PU_UNROLL * PU_BLOCK) {
+    float pt[PU_UNROLL], eta[PU_UNROLL], phi[PU_UNROLL], m[PU_UNROLL], vz[PU_UNROLL];
+    int32_t pdg[PU_UNROLL];
+    int8_t q[PU_UNROLL];
+#pragma unroll
+    for (int u = 0; u < PU_UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * PU_BLOCK + threadIdx.x;
+      if (i < n) {
+        const uint64_t s = src0 + i;
+        pt[u] = __ldg(p.hpt + s); eta[u] = __ldg(p.heta + s); phi[u] = __ldg(p.hphi + s);
+        m[u] = __ldg(p.hmass + s); pdg[u] = __ldg(p.hpdg + s); q[u] = __ldg(p.hcharge + s);
+        vz[u] = (p.hvz ? __ldg(p.hvz + s) : 0.0f) + zhs;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PU_UNROLL; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * PU_BLOCK + threadIdx.x;
+      if (i < n) {
+        const uint64_t d = dst0 + i;
+        p.opt[d] = pt[u]; p.oeta[d] = eta[u]; p.ophi[d] = phi[u]; p.omass[d] = m[u];
+        p.opdg[d] = pdg[u]; p.ocharge[d] = q[u]; p.ovz[d] = vz[u];
+      }
+    }
+  }
+}
+
+// Interactions of a hard event, counted by the whole block: the number of
+// thresholds T[j] <= w0 (T is nondecreasing and T[K - 1] = 2^32 > w0), so
+// every load is independent instead of a chain of binary-search steps.
+__device__ __forceinline__ uint32_t pu_interactions_block(const PuParams& p, uint32_t event) {
+  const uint4 w = philox(0u, event, 5u, 0u, p.rk);
+  uint32_t n = 0;
+  for (uint32_t j0 = 0; j0 < p.K - 1; j0 += PU_BLOCK) {
+    const uint32_t j = j0 + threadIdx.x;
+    n += (uint32_t)__syncthreads_count(j < p.K - 1 && __ldg(p.T + j) <= (unsigned long long)w.x);
+  }
+  return n;
+}
+
+__global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_constant__ PuParams p) {
+  __shared__ uint64_t s_src[PU_BLOCK], s_off[PU_BLOCK];
+  __shared__ float s_z[PU_BLOCK];
+  __shared__ uint64_t s_wsum[PU_BLOCK / 32];
+  const uint32_t tid = threadIdx.x;
+  for (uint64_t e = blockIdx.x; e < p.n_events; e += gridDim.x) {
+    const uint32_t event = p.event_base + (uint32_t)e;
+    const uint32_t n_int = pu_interactions_block(p, event);
+    const uint64_t a = p.hoff[e], b = p.hoff[e + 1];
+    // the merged size, recomputed
+    uint64_t part = 0;
+    bool bad = false;
+    for (uint32_t k = tid; k < n_int; k += PU_BLOCK) {
+      const uint64_t q = pu_pool_event(p, k, event);
+      const uint64_t q0 = __ldg(p.poff + q), q1 = __ldg(p.poff + q + 1);
+      bad |= q1 < q0 || q1 - q0 >= (1ull << 32);
+      part += q1 - q0;
+    }
+    const int any_bad = __syncthreads_or(bad);
+    uint64_t pool_size;
+    (void)pu_block_scan(part, s_wsum, &pool_size);
+    const uint64_t m0 = p.moff[e], m1 = p.moff[e + 1];
+    if (any_bad || b < a) {
+      if (tid == 0) atomicOr(p.err, ERR_CSR);
+      continue;
+    }
+    if (m1 < m0 || m1 - m0 != (b - a) + pool_size) {  // other arguments than the first pass
+      if (tid == 0) atomicOr(p.err, ERR_PILEUP);
+      continue;
+    }
+    const float zhs = p.smear_hs ? pu_vertex_z(p, 0u, event, 5u) : 0.0f;
+    pu_copy_hard(p, a, m0, b - a, zhs);
+    uint64_t pos = m0 + (b - a);
+    for (uint32_t k0 = 0; k0 < n_int; k0 += PU_BLOCK) {
+      const uint32_t k = k0 + tid;
+      uint64_t src = 0, len = 0;
+      float z = 0.0f;
+      if (k < n_int) {
+        const uint64_t q = pu_pool_event(p, k, event);
+        src = __ldg(p.poff + q);
+        len = __ldg(p.poff + q + 1) - src;
+        z = pu_vertex_z(p, k, event, 6u);
+      }
+      uint64_t chunk;
+      const uint64_t off = pu_block_scan(len, s_wsum, &chunk);
+      s_src[tid] = src;
+      s_off[tid] = off;
+      s_z[tid] = z;
+      __syncthreads();
+      const uint32_t nk = min((uint32_t)PU_BLOCK, n_int - k0);
+      for (uint64_t i0 = 0; i0 < chunk; i0 += (uint64_t)PU_UNROLL * PU_BLOCK) {
+        float pt[PU_UNROLL], eta[PU_UNROLL], phi[PU_UNROLL], m[PU_UNROLL], vz[PU_UNROLL];
+        int32_t pdg[PU_UNROLL];
+        int8_t q[PU_UNROLL];
+#pragma unroll
+        for (int u = 0; u < PU_UNROLL; ++u) {
+          const uint64_t i = i0 + (uint64_t)u * PU_BLOCK + tid;
+          if (i < chunk) {
+            // the last interaction whose range starts at or before i
+            uint32_t lo = 0, hi = nk - 1;
+            while (lo < hi) {
+              const uint32_t mid = (lo + hi + 1) >> 1;
+              if (s_off[mid] <= i) lo = mid;
+              else hi = mid - 1;
+            }
+            const uint64_t x = s_src[lo] + (i - s_off[lo]);
+            pt[u] = __ldg(p.ppt + x); eta[u] = __ldg(p.peta + x); phi[u] = __ldg(p.pphi + x);
+            m[u] = __ldg(p.pmass + x); pdg[u] = __ldg(p.ppdg + x); q[u] = __ldg(p.pcharge + x);
+            vz[u] = s_z[lo];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < PU_UNROLL; ++u) {
+          const uint64_t i = i0 + (uint64_t)u * PU_BLOCK + tid;
+          if (i < chunk) {
+            const uint64_t d = pos + i;
+            p.opt[d] = pt[u]; p.oeta[d] = eta[u]; p.ophi[d] = phi[u]; p.omass[d] = m[u];
+            p.opdg[d] = pdg[u]; p.ocharge[d] = q[u]; p.ovz[d] = vz[u];
+          }
+        }
+      }
+      pos += chunk;
+      __syncthreads();  // s_src / s_off / s_z are rewritten by the next chunk
+    }
+  }
+}
+
+// ------------------------------------------------------- launch helpers
+cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s) {
+  pu_count_kernel<<<n_sms * 8, 256, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  pu_scan_kernel<<<1, 1024, 0, s>>>(p.counts, p.n_events, const_cast<uint64_t*>(p.moff));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s) {
+  const uint64_t cap = (uint64_t)n_sms * 1024;
+  const uint64_t grid = p.n_events < cap ? (p.n_events > 0 ? p.n_events : 1) : cap;
+  pu_fill_kernel<<<(unsigned)grid, PU_BLOCK, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pdr
