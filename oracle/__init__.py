@@ -95,7 +95,14 @@ class Counts(C.Structure):
 
 class PileUp(C.Structure):
     _fields_ = [("mean", C.c_double), ("sigma_z", C.c_double), ("max_z", C.c_double),
+                ("sigma_t", C.c_double), ("max_t", C.c_double),
                 ("smear_hs", C.c_int32), ("pad", C.c_int32)]
+
+
+# vertex-time width and truncation of the pile-up block's defaults (Sec. 2.2,
+# parametric pile-up fields): 160 ps and 800 ps
+SIGMA_T = 160e-12
+MAX_T = 800e-12
 
 
 _lib = None
@@ -135,7 +142,7 @@ def lib():
         _lib.oracle_poisson_thresholds.argtypes = [C.c_double, P, C.c_int32]
         _lib.oracle_poisson_thresholds.restype = C.c_int32
         _lib.oracle_pileup_draws.argtypes = [C.POINTER(PileUp), P, C.c_int32, C.c_uint64, C.c_uint64,
-                                             C.c_uint32, C.c_double, P, P, P, C.c_int32, P]
+                                             C.c_uint32, C.c_double, P, P, P, P, C.c_int32, P, P]
         _lib.oracle_pileup_draws.restype = C.c_int32
     return _lib
 
@@ -373,48 +380,51 @@ def poisson_thresholds(mean: float, kmax: int = 8192) -> np.ndarray:
 
 def pileup_draws(pu: PileUp, T: np.ndarray, n_pool: int, seed: int, event: int, g: float = DEFAULT_G,
                  cap: int = 65536):
-    """(n, pool indices, vertex z [m], hard vertex shift z_hs, marginal count) of one hard event."""
+    """(n, pool indices, vertex z [m], vertex t [s], hard vertex shift z_hs [m],
+    hard vertex time t_hs [s], marginal count) of one hard event."""
     n = C.c_int32()
-    zhs = C.c_double()
+    zhs, ths = C.c_double(), C.c_double()
     idx = np.zeros(cap, np.uint32)
     z = np.zeros(cap, np.float64)
+    t = np.zeros(cap, np.float64)
     T = np.ascontiguousarray(T, np.uint64)
     m = lib().oracle_pileup_draws(C.byref(pu), _ptr(T), int(T.shape[0]), int(n_pool), int(seed) & (2**64 - 1),
-                                  int(event) & 0xFFFFFFFF, float(g), C.byref(n), _ptr(idx), _ptr(z), int(cap),
-                                  C.byref(zhs))
+                                  int(event) & 0xFFFFFFFF, float(g), C.byref(n), _ptr(idx), _ptr(z), _ptr(t),
+                                  int(cap), C.byref(zhs), C.byref(ths))
     if m < 0:
         raise ValueError("more interactions than cap")
     k = n.value
-    return k, idx[:k].copy(), z[:k].copy(), zhs.value, m
+    return k, idx[:k].copy(), z[:k].copy(), t[:k].copy(), zhs.value, ths.value, m
 
 
 def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs: bool, seed: int,
-                 event_base: int = 0, g: float = DEFAULT_G) -> dict:
+                 event_base: int = 0, g: float = DEFAULT_G, sigma_t: float = SIGMA_T, max_t: float = MAX_T) -> dict:
     """The merged batch: per hard event its own particles (vertex z plus the hard
     shift), then the pool events of its interactions in draw order, each at its
-    interaction's vertex z.  Returns the merged CSR arrays (vz in float64), the
+    interaction's vertex z and time (the hard particles at time t_hs).  Returns
+    the merged CSR arrays (vz and vt in float64), the
     draws, the number of marginal truncation decisions and the events holding
     them."""
-    pu = PileUp(float(mean), float(sigma_z), float(max_z), int(bool(smear_hs)), 0)
+    pu = PileUp(float(mean), float(sigma_z), float(max_z), float(sigma_t), float(max_t), int(bool(smear_hs)), 0)
     T = poisson_thresholds(mean)
     po = np.asarray(pool.offsets, np.int64)
     psz = np.diff(po)
     ho = np.asarray(hard.offsets, np.int64)
-    starts, lens, zs, srcs = [], [], [], []
+    starts, lens, zs, ts, srcs = [], [], [], [], []
     draws = []
     n_marg = 0
     marg_events = []
     for e in range(hard.n_events):
-        k, idx, z, zhs, m = pileup_draws(pu, T, pool.n_events, seed, event_base + e, g)
+        k, idx, z, t, zhs, ths, m = pileup_draws(pu, T, pool.n_events, seed, event_base + e, g)
         n_marg += m
         if m:
             marg_events.append(e)
-        draws.append((k, idx, z, zhs))
-        starts.append(ho[e]); lens.append(ho[e + 1] - ho[e]); zs.append(zhs); srcs.append(0)
+        draws.append((k, idx, z, t, zhs, ths))
+        starts.append(ho[e]); lens.append(ho[e + 1] - ho[e]); zs.append(zhs); ts.append(ths); srcs.append(0)
         for j in range(k):
-            starts.append(po[idx[j]]); lens.append(psz[idx[j]]); zs.append(z[j]); srcs.append(1)
+            starts.append(po[idx[j]]); lens.append(psz[idx[j]]); zs.append(z[j]); ts.append(t[j]); srcs.append(1)
     starts = np.asarray(starts, np.int64); lens = np.asarray(lens, np.int64)
-    zs = np.asarray(zs, np.float64); srcs = np.asarray(srcs, np.int8)
+    zs = np.asarray(zs, np.float64); ts = np.asarray(ts, np.float64); srcs = np.asarray(srcs, np.int8)
     seg = np.repeat(np.arange(lens.shape[0]), lens)
     pos = np.arange(int(lens.sum()), dtype=np.int64) - np.repeat(np.cumsum(lens) - lens, lens)
     src_index = starts[seg] + pos
@@ -430,6 +440,7 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
     vz = zs[seg].copy()
     vz[~from_pool] += hvz[src_index[~from_pool]]
     out["vz"] = vz
+    out["vt"] = ts[seg].copy()
     per_event = np.asarray([ho[e + 1] - ho[e] + sum(int(psz[i]) for i in d[1]) for e, d in enumerate(draws)],
                            np.int64)
     off = np.zeros(hard.n_events + 1, np.uint64)

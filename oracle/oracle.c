@@ -794,7 +794,7 @@ int oracle_run_batch(const oracle_card* c, int64_t n_events, const uint64_t* off
 /* ------------------------------------------------------------------------ */
 /* Pile-up merging (Sec. 2.2; parameters of the pile-up block).  See oracle.h */
 /* for the readings: Poisson(mean) interactions by inversion of the CDF on    */
-/* integer thresholds, uniform pool events, truncated-Gaussian vertex z.      */
+/* integer thresholds, uniform pool events, truncated-Gaussian vertex z and t.*/
 /* ------------------------------------------------------------------------ */
 int32_t oracle_poisson_thresholds(double mean, uint64_t* T, int32_t kmax) {
   double p = exp(-mean), cdf = p;  /* P(N = 0), P(N <= 0) */
@@ -815,36 +815,39 @@ int32_t oracle_poisson_thresholds(double mean, uint64_t* T, int32_t kmax) {
   return -1;
 }
 
-/* sigma_z times a standard normal, redrawn until |z| <= max_z (decided on the
- * float32 value); *marg counts decisions within the band g of max_z. */
-static double vertex_z(const oracle_pileup* p, uint64_t seed, uint32_t slot, uint32_t event,
-                       uint32_t purpose, double g, int32_t* marg) {
+/* sigma times a standard normal, redrawn until |v| <= bound (decided on the
+ * float32 value): a Gaussian truncated at +-bound.  *marg counts decisions
+ * within the band g of the bound. */
+static double truncated_normal(double sigma, double bound, uint64_t seed, uint32_t slot, uint32_t event,
+                               uint32_t purpose, double g, int32_t* marg) {
   for (uint32_t a = 0;; ++a) {
     uint32_t w[4];
     uint32_t ctr[4] = {slot, event, purpose, a};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     oracle_philox4x32_10(ctr, key, w);
-    double z = p->sigma_z * oracle_normal(w[1], w[2]);
-    if (fabs(fabs(z) - p->max_z) <= g * fmax(fabs(z), p->max_z)) ++*marg;
-    if (fabsf((float)z) <= (float)p->max_z) return z;
+    double v = sigma * oracle_normal(w[1], w[2]);
+    if (fabs(fabs(v) - bound) <= g * fmax(fabs(v), bound)) ++*marg;
+    if (fabsf((float)v) <= (float)bound) return v;
   }
 }
 
 int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K, uint64_t n_pool,
                             uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
-                            double* z, int32_t cap, double* z_hs) {
+                            double* z, double* t, int32_t cap, double* z_hs, double* t_hs) {
   int32_t marg = 0;
   uint32_t w[4];
   draw(seed, 0u, event, 5u, w);
   int32_t N = 0;
   while (N < K - 1 && (uint64_t)w[0] >= T[N]) ++N;  /* smallest N with w0 < T[N] */
   *n = N;
-  *z_hs = p->smear_hs ? vertex_z(p, seed, 0u, event, 5u, g, &marg) : 0.0;
+  *z_hs = p->smear_hs ? truncated_normal(p->sigma_z, p->max_z, seed, 0u, event, 5u, g, &marg) : 0.0;
+  *t_hs = p->smear_hs ? truncated_normal(p->sigma_t, p->max_t, seed, 0u, event, 8u, g, &marg) : 0.0;
   if (N > cap) return -1;
   for (int32_t k = 0; k < N; ++k) {
     draw(seed, (uint32_t)k, event, 6u, w);
     idx[k] = (uint32_t)(((uint64_t)w[0] * n_pool) >> 32);
-    z[k] = vertex_z(p, seed, (uint32_t)k, event, 6u, g, &marg);
+    z[k] = truncated_normal(p->sigma_z, p->max_z, seed, (uint32_t)k, event, 6u, g, &marg);
+    t[k] = truncated_normal(p->sigma_t, p->max_t, seed, (uint32_t)k, event, 7u, g, &marg);
   }
   return marg;
 }

@@ -198,13 +198,17 @@ int oracle_run_batch(const oracle_card* c, int64_t n_events, const uint64_t* off
  *     of the pool, w0 from counter (k, event, 6, 0), at vertex z = sigma_z * z
  *     with z the Box-Muller normal of (w1, w2) of counter (k, event, 6, a), a the
  *     first attempt with |z sigma_z| <= max_z (a truncated Gaussian);
+ *   - its vertex time is t = sigma_t * (the normal of (w1, w2) of counter
+ *     (k, event, 7, a)), a the first attempt with |t| <= max_t;
  *   - the hard-scatter vertex, if smeared, is z_hs from counter (0, event, 5, a)
- *     likewise; its particles keep their own z plus z_hs;
- *   - the pool event's particles are used as stored (no rotation).
- * The truncation is a decision on a float32 value; a draw whose |z| lies
- * within g max(|z|, max_z) of max_z is counted as marginal. */
+ *     and t_hs from counter (0, event, 8, a) likewise; its particles keep
+ *     their own z plus z_hs and have time t_hs;
+ *   - the pool event's particles are used as stored (no rotation, no
+ *     transverse vertex offset: the pile-up block has no x/y spread).
+ * Each truncation is a decision on a float32 value; a draw whose |v| lies
+ * within g max(|v|, bound) of its bound is counted as marginal. */
 typedef struct oracle_pileup {
-  double mean, sigma_z, max_z;
+  double mean, sigma_z, max_z, sigma_t, max_t;
   int32_t smear_hs, pad;
 } oracle_pileup;
 
@@ -215,12 +219,12 @@ typedef struct oracle_pileup {
 int32_t oracle_poisson_thresholds(double mean, uint64_t* T, int32_t kmax);
 
 /* The draws of one hard event: *n interactions (at most cap are written) with
- * pool indices idx[] and vertices z[] (metres), and the hard vertex shift
- * *z_hs (0 unless smeared).  Returns the number of marginal truncation
- * decisions, or -1 if n exceeds cap. */
+ * pool indices idx[], vertex z[] (metres) and vertex times t[] (seconds), and
+ * the hard vertex shift *z_hs and time *t_hs (0 unless smeared).  Returns the
+ * number of marginal truncation decisions, or -1 if n exceeds cap. */
 int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K, uint64_t n_pool,
                             uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
-                            double* z, int32_t cap, double* z_hs);
+                            double* z, double* t, int32_t cap, double* z_hs, double* t_hs);
 
 #ifdef __cplusplus
 }

@@ -1,7 +1,7 @@
 """Pins of the oracle's pile-up merging (Sec. 2.2: with a pile-up block the
 parametric path merges minimum-bias interactions with the hard-scatter event
 before the detector response; the block's parameters are mean pile-up,
-vertex-z width and truncation, and hard-vertex smearing).
+vertex-z and vertex-time widths and truncations, and hard-vertex smearing).
 
 Each pin checks the oracle against something independent of its arithmetic:
 scipy's Poisson CDF and truncated normal, the Philox words recomputed from the
@@ -17,8 +17,8 @@ from paper_2606_26089_b300 import synth
 SEED = 7
 
 
-def _pu(mean, smear=True, sigma_z=0.053, max_z=0.25):
-    return oracle.PileUp(float(mean), sigma_z, max_z, int(smear), 0)
+def _pu(mean, smear=True, sigma_z=0.053, max_z=0.25, sigma_t=160e-12, max_t=800e-12):
+    return oracle.PileUp(float(mean), sigma_z, max_z, sigma_t, max_t, int(smear), 0)
 
 
 def _words(slot, event, purpose, attempt=0, seed=SEED):
@@ -54,7 +54,7 @@ def test_pool_indices_follow_the_counter_contract_and_are_uniform():
     T = oracle.poisson_thresholds(mean)
     idx_all = []
     for ev in range(200):
-        n, idx, z, zhs, m = oracle.pileup_draws(_pu(mean), T, n_pool, SEED, ev)
+        n, idx, z, t, zhs, ths, m = oracle.pileup_draws(_pu(mean), T, n_pool, SEED, ev)
         for k in range(0, n, 7):
             assert idx[k] == (int(_words(k, ev, 6)[0]) * n_pool) >> 32
         idx_all.append(idx)
@@ -80,17 +80,42 @@ def test_vertex_z_is_a_truncated_gaussian():
     ref = stats.truncnorm(-zmax / sigma, zmax / sigma, loc=0.0, scale=sigma)
     assert stats.kstest(z, ref.cdf).pvalue > 1e-4
     # first attempt: sigma times the Box-Muller normal of words 1, 2 of counter (k, event, 6, 0)
-    n, idx, zz, zhs, m = oracle.pileup_draws(_pu(30.0, sigma_z=sigma, max_z=1.0), T, 10, SEED, 3)
+    n, idx, zz, tt, zhs, ths, m = oracle.pileup_draws(_pu(30.0, sigma_z=sigma, max_z=1.0), T, 10, SEED, 3)
     w = _words(0, 3, 6)
     assert zz[0] == pytest.approx(sigma * oracle.normal(int(w[1]), int(w[2])), rel=1e-15)
 
 
+def test_vertex_time_is_a_truncated_gaussian_of_its_own_counters():
+    """t = sigma_t x the normal of words 1, 2 of counter (k, event, 7, a),
+    redrawn until |t| <= max_t: independent of z (its own counters), and a
+    truncated normal by a KS test against scipy's."""
+    st, mt = 160e-12, 200e-12  # a tight truncation so that redraws happen
+    T = oracle.poisson_thresholds(30.0)
+    z_all, t_all = [], []
+    for ev in range(600):
+        n, idx, z, t, zhs, ths, m = oracle.pileup_draws(_pu(30.0, sigma_t=st, max_t=mt), T, 10, SEED, ev)
+        z_all.append(z)
+        t_all.append(t)
+    z, t = np.concatenate(z_all), np.concatenate(t_all)
+    assert np.all(np.abs(t) <= mt * (1 + 1e-7))
+    ref = stats.truncnorm(-mt / st, mt / st, loc=0.0, scale=st)
+    assert stats.kstest(t, ref.cdf).pvalue > 1e-4
+    assert abs(stats.pearsonr(z, t)[0]) < 5 / np.sqrt(z.shape[0])
+    n, idx, z, t, zhs, ths, m = oracle.pileup_draws(_pu(30.0, max_t=1.0), T, 10, SEED, 5)
+    w = _words(2, 5, 7)
+    assert t[2] == pytest.approx(160e-12 * oracle.normal(int(w[1]), int(w[2])), rel=1e-15)
+    # the hard-scatter time comes from counter (0, event, 8, 0) when accepted at once
+    w = _words(0, 5, 8)
+    assert ths == pytest.approx(160e-12 * oracle.normal(int(w[1]), int(w[2])), rel=1e-15)
+
+
 def test_hard_vertex_smearing_switch():
     T = oracle.poisson_thresholds(5.0)
-    zs_on = [oracle.pileup_draws(_pu(5.0, smear=True), T, 10, SEED, ev)[3] for ev in range(400)]
-    zs_off = [oracle.pileup_draws(_pu(5.0, smear=False), T, 10, SEED, ev)[3] for ev in range(400)]
-    assert all(z == 0.0 for z in zs_off)
-    assert np.std(zs_on) == pytest.approx(0.053, rel=0.15)
+    on = [oracle.pileup_draws(_pu(5.0, smear=True), T, 10, SEED, ev) for ev in range(400)]
+    off = [oracle.pileup_draws(_pu(5.0, smear=False), T, 10, SEED, ev) for ev in range(400)]
+    assert all(d[4] == 0.0 and d[5] == 0.0 for d in off)
+    assert np.std([d[4] for d in on]) == pytest.approx(0.053, rel=0.15)
+    assert np.std([d[5] for d in on]) == pytest.approx(160e-12, rel=0.15)
 
 
 def test_merged_events_are_hard_then_interactions_in_order():
@@ -98,19 +123,19 @@ def test_merged_events_are_hard_then_interactions_in_order():
     hard = synth.make_hard(12)
     m = oracle.pileup_merge(hard, pool, 20.0, 0.053, 0.25, True, SEED)
     for e in range(hard.n_events):
-        n, idx, z, zhs = m["draws"][e]
+        n, idx, z, t, zhs, ths = m["draws"][e]
         a, b = int(m["offsets"][e]), int(m["offsets"][e + 1])
         ev = hard.event(e)
         nh = len(ev["pt"])
         assert np.array_equal(m["pt"][a:a + nh], ev["pt"]) and np.array_equal(m["pdg"][a:a + nh], ev["pdg"])
-        assert np.all(m["vz"][a:a + nh] == zhs)
+        assert np.all(m["vz"][a:a + nh] == zhs) and np.all(m["vt"][a:a + nh] == ths)
         pos = a + nh
         for k in range(n):
             pe = pool.event(int(idx[k]))
             np_ = len(pe["pt"])
             for key in ("pt", "eta", "phi", "mass", "pdg", "charge"):
                 assert np.array_equal(m[key][pos:pos + np_], pe[key])
-            assert np.all(m["vz"][pos:pos + np_] == z[k])
+            assert np.all(m["vz"][pos:pos + np_] == z[k]) and np.all(m["vt"][pos:pos + np_] == t[k])
             pos += np_
         assert pos == b
 
@@ -120,7 +145,7 @@ def test_no_pileup_leaves_the_hard_events():
     hard = synth.make_hard(8)
     m = oracle.pileup_merge(hard, pool, 0.0, 0.053, 0.25, False, SEED)
     assert np.array_equal(m["offsets"], hard.offsets)
-    assert np.array_equal(m["pt"], hard.pt) and np.all(m["vz"] == 0.0)
+    assert np.array_equal(m["pt"], hard.pt) and np.all(m["vz"] == 0.0) and np.all(m["vt"] == 0.0)
 
 
 def test_merging_does_not_depend_on_batching():
@@ -129,5 +154,5 @@ def test_merging_does_not_depend_on_batching():
     whole = oracle.pileup_merge(hard, pool, 15.0, 0.053, 0.25, True, SEED)
     part = oracle.pileup_merge(hard.slice_events(3, 8), pool, 15.0, 0.053, 0.25, True, SEED, event_base=3)
     a, b = int(whole["offsets"][3]), int(whole["offsets"][8])
-    for key in ("pt", "eta", "pdg", "vz"):
+    for key in ("pt", "eta", "pdg", "vz", "vt"):
         assert np.array_equal(part[key], whole[key][a:b])

@@ -126,12 +126,12 @@ def test_full_size_pileup_configuration(B, ctx, synth):
     hard = synth.make_hard(10_000)
     g = _gpu_merge(B, ctx, hard, pool, mean)
     T = oracle.poisson_thresholds(mean)
-    pu = oracle.PileUp(mean, SIGMA, ZMAX, 1, 0)
+    pu = oracle.PileUp(mean, SIGMA, ZMAX, oracle.SIGMA_T, oracle.MAX_T, 1, 0)
     psz = np.diff(np.asarray(pool.offsets, np.int64))
     hsz = np.diff(np.asarray(hard.offsets, np.int64))
     sizes = np.empty(hard.n_events, np.int64)
     for e in range(hard.n_events):
-        n, idx, z, zhs, m = oracle.pileup_draws(pu, T, pool.n_events, SEED, e)
+        n, idx = oracle.pileup_draws(pu, T, pool.n_events, SEED, e)[:2]
         sizes[e] = hsz[e] + psz[idx].sum()
     assert np.array_equal(np.diff(g["offsets"].astype(np.int64)), sizes)
     assert g["n_particles"] > 50_000_000
