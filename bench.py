@@ -414,7 +414,8 @@ def bench_pileup_merge(args, B, ctx):
     """Pile-up merging on the device (Sec. 2.2) at the pile-up workload's scale:
     10k hard events of Poisson(400) particles, Poisson(170) interactions each
     from a 10k-event minimum-bias pool, vertex z ~ N(0, 50 mm) truncated at
-    250 mm; then the detector response of the merged batch."""
+    250 mm and t ~ N(0, 160 ps) truncated at 800 ps; then the detector response
+    of the merged batch."""
     import torch
 
     from paper_2606_26089_b300 import synth
@@ -429,7 +430,7 @@ def bench_pileup_merge(args, B, ctx):
     off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
     total = ctx.pileup_offsets(hb, pu, off)
     f = dict(dtype=torch.float32, device="cuda")
-    m = {k: torch.empty(total, **f) for k in ("pt", "eta", "phi", "mass", "vz")}
+    m = {k: torch.empty(total, **f) for k in ("pt", "eta", "phi", "mass", "vz", "vt")}
     m["pdg"] = torch.empty(total, dtype=torch.int32, device="cuda")
     m["charge"] = torch.empty(total, dtype=torch.int8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -451,15 +452,16 @@ def bench_pileup_merge(args, B, ctx):
     torch.cuda.synchronize()
     ctx.check()
     fill_s = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) / 1e3
-    # algorithmic bytes: every merged particle written once (4 floats, vz, pdg,
-    # charge = 25 B), the hard particles and the pool read once, the offsets
+    # algorithmic bytes: every merged particle written once (4 floats, vz, vt,
+    # pdg, charge = 29 B), the hard particles and the pool read once, the offsets
     n_int = int(total - hard.n_particles)
-    alg = 25 * total + hard.nbytes_input() + pool.nbytes_input() + 8 * (n + 1)
+    alg = 29 * total + hard.nbytes_input() + pool.nbytes_input() + 8 * (n + 1)
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6400.0
 
     # detector response of the merged batch
     mdev = dict(m, offsets=off, n_events=n, n_particles=total, max_event_size=0)
+    del mdev["vt"]
     cid = ctx.card_load("cms_like")
     out = B.alloc_outputs(n, total)
     bt = B.make_batch(mdev, cid, seed)

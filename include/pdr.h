@@ -260,7 +260,7 @@ int pdr_check(pdr_ctx* ctx, void* stream);
  * detector card; the block gives the mean number of interactions, the Gaussian
  * vertex-z width and its truncation, and whether the hard-scatter vertex is
  * smeared too.  Per hard event e (event index event_index_base + e, the hard
- * batch's seed; Philox purposes 5 and 6, disjoint from the response's 1-4):
+ * batch's seed; Philox purposes 5 to 8, disjoint from the response's 1-4):
  *   - N ~ Poisson(mean) by inversion: the smallest k with w0 < T[k], where
  *     T[k] = floor(P(N <= k) 2^32) from the CDF summed in double from
  *     P(N = 0) = exp(-mean) by P(N = k) = P(N = k-1) mean / k, the first entry
@@ -269,11 +269,14 @@ int pdr_check(pdr_ctx* ctx, void* stream);
  *     (k, event, 6, 0)) at vertex z = sigma_z x (Box-Muller normal of words 1
  *     and 2 of counter (k, event, 6, a)), a the first attempt with
  *     |z| <= max_z in float32 (a truncated Gaussian);
- *   - the hard vertex shift z_hs is drawn likewise from counter (0, event, 5, a)
- *     if smear_hs, else 0;
+ *   - its vertex time is t = sigma_t x (the normal of words 1 and 2 of
+ *     counter (k, event, 7, a)), a the first attempt with |t| <= max_t;
+ *   - the hard vertex shift z_hs and time t_hs are drawn likewise from
+ *     counters (0, event, 5, a) and (0, event, 8, a) if smear_hs, else 0;
  *   - the merged event holds the hard particles (vertex z = own vz, or 0, plus
- *     z_hs) followed by the pool events of interactions 0..N-1 in that order,
- *     each particle at its interaction's z; pool particles are copied as stored.
+ *     z_hs; time t_hs) followed by the pool events of interactions 0..N-1 in
+ *     that order, each particle at its interaction's z and t; pool particles
+ *     are copied as stored (no rotation, no transverse vertex offset).
  * The pool is a CSR batch in DEVICE memory and stays owned by the caller. */
 typedef struct pdr_pileup {
   uint64_t n_pool;                /* minimum-bias events in the pool (>= 1)        */
@@ -284,14 +287,17 @@ typedef struct pdr_pileup {
   double mean;                    /* mean interactions per hard event (>= 0)       */
   double sigma_z;                 /* vertex-z width (m)                            */
   double max_z;                   /* vertex-z truncation |z| <= max_z (m, > 0)     */
+  double sigma_t;                 /* vertex-time width (s; the paper's default 160e-12) */
+  double max_t;                   /* vertex-time truncation (s, > 0; default 800e-12)   */
   uint32_t smear_hs;              /* 1: shift the hard-scatter vertex as well      */
   uint32_t pad;
 } pdr_pileup;
 
 /* DEVICE arrays of a merged batch, each with room for the merged particle
- * count that pdr_pileup_offsets returns. */
+ * count that pdr_pileup_offsets returns.  vt (vertex time, seconds) may be
+ * NULL: the times are then not written. */
 typedef struct pdr_particles {
-  float *pt, *eta, *phi, *mass, *vz;
+  float *pt, *eta, *phi, *mass, *vz, *vt;
   int32_t* pdg;
   int8_t* charge;
 } pdr_particles;

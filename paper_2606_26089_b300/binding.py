@@ -104,11 +104,12 @@ class pdr_pileup(C.Structure):
     _fields_ = [("n_pool", C.c_uint64)] + [(n, C.c_void_p) for n in (
         "offsets", "pt", "eta", "phi", "mass", "pdg", "charge")] + [
         ("mean", C.c_double), ("sigma_z", C.c_double), ("max_z", C.c_double),
+        ("sigma_t", C.c_double), ("max_t", C.c_double),
         ("smear_hs", C.c_uint32), ("pad", C.c_uint32)]
 
 
 class pdr_particles(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge")]
+    _fields_ = [(n, C.c_void_p) for n in ("pt", "eta", "phi", "mass", "vz", "vt", "pdg", "charge")]
 
 
 class pdr_result(C.Structure):
@@ -397,7 +398,7 @@ class Context:
 
     def pileup_merge(self, hard: pdr_batch, pu: pdr_pileup, merged_offsets, out: dict, stream=None):
         """Second pass: fill the merged particle arrays (device tensors)."""
-        o = pdr_particles(*[_ptr(out[k]) for k in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge")])
+        o = pdr_particles(*[_ptr(out.get(k)) for k in ("pt", "eta", "phi", "mass", "vz", "vt", "pdg", "charge")])
         self._check(self.L.pdr_pileup_merge(self.h, C.byref(hard), C.byref(pu), _ptr(merged_offsets), C.byref(o),
                                             self._stream(stream)), "pdr_pileup_merge")
 
@@ -496,22 +497,31 @@ def event_records(out_host: dict, counts: np.ndarray, offsets: np.ndarray, e: in
 # ---------------------------------------------------------------------------
 # pile-up merging helpers
 # ---------------------------------------------------------------------------
-def make_pileup(pool_dev: dict, mean: float, sigma_z: float, max_z: float, smear_hs: bool) -> pdr_pileup:
+# vertex-time width and truncation defaults of the pile-up block (Sec. 2.2)
+SIGMA_T = 160e-12
+MAX_T = 800e-12
+
+
+def make_pileup(pool_dev: dict, mean: float, sigma_z: float, max_z: float, smear_hs: bool,
+                sigma_t: float = SIGMA_T, max_t: float = MAX_T) -> pdr_pileup:
     """pdr_pileup over a device pool (batch_to_device of the minimum-bias batch)."""
     p = pdr_pileup()
     p.n_pool = pool_dev["n_events"]
     for k in ("offsets", "pt", "eta", "phi", "mass", "pdg", "charge"):
         setattr(p, k, _ptr(pool_dev[k]))
     p.mean, p.sigma_z, p.max_z, p.smear_hs = float(mean), float(sigma_z), float(max_z), int(bool(smear_hs))
+    p.sigma_t, p.max_t = float(sigma_t), float(max_t)
     return p
 
 
 def merge_pileup(ctx: "Context", hard_dev: dict, pool_dev: dict, mean: float, sigma_z: float, max_z: float,
-                 smear_hs: bool, seed: int, event_base: int = 0, stream=None) -> dict:
-    """Both passes; returns the merged batch as device tensors (batch_to_device layout)."""
+                 smear_hs: bool, seed: int, event_base: int = 0, stream=None, sigma_t: float = SIGMA_T,
+                 max_t: float = MAX_T, with_time: bool = True) -> dict:
+    """Both passes; returns the merged batch as device tensors (batch_to_device
+    layout, plus the vertex times "vt" unless with_time is false)."""
     torch = _torch()
     hb = make_batch(hard_dev, 0, seed, event_base=event_base)
-    pu = make_pileup(pool_dev, mean, sigma_z, max_z, smear_hs)
+    pu = make_pileup(pool_dev, mean, sigma_z, max_z, smear_hs, sigma_t, max_t)
     n = hard_dev["n_events"]
     off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
     total = ctx.pileup_offsets(hb, pu, off, stream)
@@ -519,6 +529,7 @@ def merge_pileup(ctx: "Context", hard_dev: dict, pool_dev: dict, mean: float, si
     f = dict(dtype=torch.float32, device="cuda")
     out = dict(pt=torch.empty(cap, **f), eta=torch.empty(cap, **f), phi=torch.empty(cap, **f),
                mass=torch.empty(cap, **f), vz=torch.empty(cap, **f),
+               vt=torch.empty(cap, **f) if with_time else None,
                pdg=torch.empty(cap, dtype=torch.int32, device="cuda"),
                charge=torch.empty(cap, dtype=torch.int8, device="cuda"))
     ctx.pileup_merge(hb, pu, off, out, stream)

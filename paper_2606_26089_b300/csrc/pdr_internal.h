@@ -173,11 +173,11 @@ struct PuParams {
   const int8_t* pcharge;
   const unsigned long long* T;       // Poisson CDF thresholds, K entries, T[K-1] = 2^32
   uint32_t K, event_base, smear_hs, pad;
-  float sigma_z, max_z;
+  float sigma_z, max_z, sigma_t, max_t;
   uint32_t rk[20];
   uint64_t* counts;                  // first pass: merged size of each event
   const uint64_t* moff;              // second pass: merged offsets
-  float *opt, *oeta, *ophi, *omass, *ovz;
+  float *opt, *oeta, *ophi, *omass, *ovz, *ovt;  // ovt may be null
   int32_t* opdg;
   int8_t* ocharge;
   uint32_t* err;

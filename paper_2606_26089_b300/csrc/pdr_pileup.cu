@@ -32,13 +32,14 @@ __device__ __forceinline__ uint64_t pu_pool_event(const PuParams& p, uint32_t k,
   return ((uint64_t)w.x * p.n_pool) >> 32;
 }
 
-// Vertex z: sigma_z times a normal, redrawn (attempt a in counter word 3)
-// until |z| <= max_z; at most 1024 attempts, then ERR_VERTEX.
-__device__ __forceinline__ float pu_vertex_z(const PuParams& p, uint32_t slot, uint32_t event, uint32_t purpose) {
+// A vertex coordinate: sigma times a normal, redrawn (attempt a in counter
+// word 3) until |v| <= bound; at most 1024 attempts, then ERR_VERTEX.
+__device__ __forceinline__ float pu_truncated_normal(const PuParams& p, float sigma, float bound, uint32_t slot,
+                                                     uint32_t event, uint32_t purpose) {
   for (uint32_t a = 0; a < 1024u; ++a) {
     const uint4 w = philox(slot, event, purpose, a, p.rk);
-    const float z = p.sigma_z * normal(w.y, w.z);
-    if (fabsf(z) <= p.max_z) return z;
+    const float v = sigma * normal(w.y, w.z);
+    if (fabsf(v) <= bound) return v;
   }
   atomicOr(p.err, ERR_VERTEX);
   return 0.0f;
@@ -140,10 +141,10 @@ __device__ __forceinline__ uint64_t pu_block_scan(uint64_t v, uint64_t* warp_sum
 }
 
 // Copies the n hard particles from src0 to out[dst0, dst0 + n), each at its
-// own vertex z plus the hard shift zhs (element-parallel, PU_UNROLL
+// own vertex z plus the hard shift zhs and at time ths (element-parallel, PU_UNROLL
 // particles in flight per thread).
 __device__ __forceinline__ void pu_copy_hard(const PuParams& p, uint64_t src0, uint64_t dst0, uint64_t n,
-                                             float zhs) {
+                                             float zhs, float ths) {
   for (uint64_t i0 = 0; i0 < n; i0 += (uint64_t)PU_UNROLL * PU_BLOCK) {
     float pt[PU_UNROLL], eta[PU_UNROLL], phi[PU_UNROLL], m[PU_UNROLL], vz[PU_UNROLL];
     int32_t pdg[PU_UNROLL];
@@ -165,6 +166,7 @@ __device__ __forceinline__ void pu_copy_hard(const PuParams& p, uint64_t src0, u
         const uint64_t d = dst0 + i;
         p.opt[d] = pt[u]; p.oeta[d] = eta[u]; p.ophi[d] = phi[u]; p.omass[d] = m[u];
         p.opdg[d] = pdg[u]; p.ocharge[d] = q[u]; p.ovz[d] = vz[u];
+        if (p.ovt) p.ovt[d] = ths;
       }
     }
   }
@@ -185,7 +187,7 @@ __device__ __forceinline__ uint32_t pu_interactions_block(const PuParams& p, uin
 
 __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_constant__ PuParams p) {
   __shared__ uint64_t s_src[PU_BLOCK], s_off[PU_BLOCK];
-  __shared__ float s_z[PU_BLOCK];
+  __shared__ float s_z[PU_BLOCK], s_t[PU_BLOCK];
   __shared__ uint64_t s_wsum[PU_BLOCK / 32];
   const uint32_t tid = threadIdx.x;
   for (uint64_t e = blockIdx.x; e < p.n_events; e += gridDim.x) {
@@ -213,28 +215,31 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
       if (tid == 0) atomicOr(p.err, ERR_PILEUP);
       continue;
     }
-    const float zhs = p.smear_hs ? pu_vertex_z(p, 0u, event, 5u) : 0.0f;
-    pu_copy_hard(p, a, m0, b - a, zhs);
+    const float zhs = p.smear_hs ? pu_truncated_normal(p, p.sigma_z, p.max_z, 0u, event, 5u) : 0.0f;
+    const float ths = p.smear_hs && p.ovt ? pu_truncated_normal(p, p.sigma_t, p.max_t, 0u, event, 8u) : 0.0f;
+    pu_copy_hard(p, a, m0, b - a, zhs, ths);
     uint64_t pos = m0 + (b - a);
     for (uint32_t k0 = 0; k0 < n_int; k0 += PU_BLOCK) {
       const uint32_t k = k0 + tid;
       uint64_t src = 0, len = 0;
-      float z = 0.0f;
+      float z = 0.0f, t = 0.0f;
       if (k < n_int) {
         const uint64_t q = pu_pool_event(p, k, event);
         src = __ldg(p.poff + q);
         len = __ldg(p.poff + q + 1) - src;
-        z = pu_vertex_z(p, k, event, 6u);
+        z = pu_truncated_normal(p, p.sigma_z, p.max_z, k, event, 6u);
+        if (p.ovt) t = pu_truncated_normal(p, p.sigma_t, p.max_t, k, event, 7u);
       }
       uint64_t chunk;
       const uint64_t off = pu_block_scan(len, s_wsum, &chunk);
       s_src[tid] = src;
       s_off[tid] = off;
       s_z[tid] = z;
+      s_t[tid] = t;
       __syncthreads();
       const uint32_t nk = min((uint32_t)PU_BLOCK, n_int - k0);
       for (uint64_t i0 = 0; i0 < chunk; i0 += (uint64_t)PU_UNROLL * PU_BLOCK) {
-        float pt[PU_UNROLL], eta[PU_UNROLL], phi[PU_UNROLL], m[PU_UNROLL], vz[PU_UNROLL];
+        float pt[PU_UNROLL], eta[PU_UNROLL], phi[PU_UNROLL], m[PU_UNROLL], vz[PU_UNROLL], vt[PU_UNROLL];
         int32_t pdg[PU_UNROLL];
         int8_t q[PU_UNROLL];
 #pragma unroll
@@ -252,6 +257,7 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
             pt[u] = __ldg(p.ppt + x); eta[u] = __ldg(p.peta + x); phi[u] = __ldg(p.pphi + x);
             m[u] = __ldg(p.pmass + x); pdg[u] = __ldg(p.ppdg + x); q[u] = __ldg(p.pcharge + x);
             vz[u] = s_z[lo];
+            vt[u] = s_t[lo];
           }
         }
 #pragma unroll
@@ -261,11 +267,12 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
             const uint64_t d = pos + i;
             p.opt[d] = pt[u]; p.oeta[d] = eta[u]; p.ophi[d] = phi[u]; p.omass[d] = m[u];
             p.opdg[d] = pdg[u]; p.ocharge[d] = q[u]; p.ovz[d] = vz[u];
+            if (p.ovt) p.ovt[d] = vt[u];
           }
         }
       }
       pos += chunk;
-      __syncthreads();  // s_src / s_off / s_z are rewritten by the next chunk
+      __syncthreads();  // the shared chunk arrays are rewritten by the next chunk
     }
   }
 }

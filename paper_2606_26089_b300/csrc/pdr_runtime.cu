@@ -1579,6 +1579,9 @@ int pileup_args(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu) {
   if (!(pu->sigma_z >= 0.0) || !std::isfinite(pu->sigma_z) || !(pu->max_z > 0.0) || !std::isfinite(pu->max_z))
     return fail(PDR_EINVAL, "vertex width must be >= 0 and the truncation > 0");
   if (pu->max_z < 0.05 * pu->sigma_z) return fail(PDR_EINVAL, "vertex truncation below 0.05 sigma_z");
+  if (!(pu->sigma_t >= 0.0) || !std::isfinite(pu->sigma_t) || !(pu->max_t > 0.0) || !std::isfinite(pu->max_t))
+    return fail(PDR_EINVAL, "vertex-time width must be >= 0 and the truncation > 0");
+  if (pu->max_t < 0.05 * pu->sigma_t) return fail(PDR_EINVAL, "vertex-time truncation below 0.05 sigma_t");
   return PDR_OK;
 }
 
@@ -1614,6 +1617,8 @@ int pileup_params(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, cudaSt
   p.smear_hs = pu->smear_hs ? 1u : 0u;
   p.sigma_z = (float)pu->sigma_z;
   p.max_z = (float)pu->max_z;
+  p.sigma_t = (float)pu->sigma_t;
+  p.max_t = (float)pu->max_t;
   fill_round_keys(p.rk, h->seed);
   p.err = ctx->d_err;
   return PDR_OK;
@@ -1660,7 +1665,7 @@ int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, con
   PuParams p;
   if ((rc = pileup_params(ctx, h, pu, s, p))) return rc;
   p.moff = merged_offsets;
-  p.opt = out->pt; p.oeta = out->eta; p.ophi = out->phi; p.omass = out->mass; p.ovz = out->vz;
+  p.opt = out->pt; p.oeta = out->eta; p.ophi = out->phi; p.omass = out->mass; p.ovz = out->vz; p.ovt = out->vt;
   p.opdg = out->pdg; p.ocharge = out->charge;
   PDR_CUDA(launch_pileup_fill(p, ctx->n_sms, s), "pile-up fill");
   return PDR_OK;

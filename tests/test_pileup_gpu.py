@@ -3,8 +3,8 @@ the oracle's merge (Sec. 2.2: minimum-bias interactions merged with each
 hard-scatter event before the detector response).
 
 Offsets, pool indices and every copied particle field are compared bit for
-bit; the vertex z of a particle (float32 on the GPU, float64 in the oracle)
-within 2e-6 relative to max(|z|, sigma_z).  The merged batch then goes
+bit; the vertex z and time of a particle (float32 on the GPU, float64 in the
+oracle) within 2e-6 relative to max(|z|, sigma_z) and max(|t|, sigma_t).  The merged batch then goes
 through the detector response and is compared with the oracle as usual.
 """
 import numpy as np
@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 
 SEED = 23
 SIGMA, ZMAX = 0.053, 0.25
+SIGMA_T, TMAX = 160e-12, 800e-12
 
 
 @pytest.fixture(scope="module")
@@ -42,15 +43,19 @@ def synth():
     return s
 
 
-def _gpu_merge(B, ctx, hard, pool, mean, sigma=SIGMA, zmax=ZMAX, smear=True, event_base=0):
+def _gpu_merge(B, ctx, hard, pool, mean, sigma=SIGMA, zmax=ZMAX, smear=True, event_base=0, tmax=TMAX,
+               with_time=True):
     hd, pd = B.batch_to_device(hard), B.batch_to_device(pool)
-    m = B.merge_pileup(ctx, hd, pd, mean, sigma, zmax, smear, SEED, event_base)
+    m = B.merge_pileup(ctx, hd, pd, mean, sigma, zmax, smear, SEED, event_base, sigma_t=SIGMA_T, max_t=tmax,
+                       with_time=with_time)
     torch.cuda.synchronize()
     ctx.check()
-    h = {k: (m[k].cpu().numpy() if k not in ("n_events", "n_particles") else m[k]) for k in m}
+    h = {k: (m[k].cpu().numpy() if k not in ("n_events", "n_particles") and m[k] is not None else m[k])
+         for k in m}
     n = h["n_particles"]
-    for k in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge"):
-        h[k] = h[k][:n]
+    for k in ("pt", "eta", "phi", "mass", "vz", "vt", "pdg", "charge"):
+        if h[k] is not None:
+            h[k] = h[k][:n]
     h["offsets"] = h["offsets"].astype(np.uint64)
     return h
 
@@ -71,6 +76,9 @@ def _compare(g, o, sigma=SIGMA):
     assert keep.mean() > 0.9
     tol = 2e-6 * np.maximum(np.abs(o["vz"]), sigma)
     assert np.all((np.abs(g["vz"].astype(np.float64) - o["vz"]) <= tol)[keep])
+    if g.get("vt") is not None:
+        tol = 2e-6 * np.maximum(np.abs(o["vt"]), SIGMA_T)
+        assert np.all((np.abs(g["vt"].astype(np.float64) - o["vt"]) <= tol)[keep])
 
 
 def test_merge_matches_the_oracle(B, ctx, synth):
@@ -85,10 +93,20 @@ def test_tight_truncation_own_hard_vertices_and_no_hard_smearing(B, ctx, synth):
     pool = synth.make_minbias_pool(200)
     hard = synth.make_hard(30)
     hard.vz = np.random.default_rng(3).uniform(-0.1, 0.1, hard.n_particles).astype(np.float32)
-    g = _gpu_merge(B, ctx, hard, pool, 15.0, zmax=0.03, smear=False, event_base=1000)
-    o = oracle.pileup_merge(hard, pool, 15.0, SIGMA, 0.03, False, SEED, event_base=1000)
+    g = _gpu_merge(B, ctx, hard, pool, 15.0, zmax=0.03, smear=False, event_base=1000, tmax=100e-12)
+    o = oracle.pileup_merge(hard, pool, 15.0, SIGMA, 0.03, False, SEED, event_base=1000, max_t=100e-12)
     _compare(g, o)
     assert np.max(np.abs(g["vz"][g["vz"] != 0.0])) <= 0.1  # truncated interactions and the hard vz
+    assert np.max(np.abs(g["vt"])) <= 100e-12 and np.all(g["vt"][:int(hard.offsets[1])] == 0.0)
+
+
+def test_vertex_times_are_optional(B, ctx, synth):
+    pool = synth.make_minbias_pool(100)
+    hard = synth.make_hard(12)
+    g = _gpu_merge(B, ctx, hard, pool, 10.0, with_time=False)
+    o = oracle.pileup_merge(hard, pool, 10.0, SIGMA, ZMAX, True, SEED)
+    assert g["vt"] is None
+    _compare(g, o)
 
 
 def test_no_pileup_returns_the_hard_events(B, ctx, synth):
@@ -126,7 +144,7 @@ def test_full_size_pileup_configuration(B, ctx, synth):
     hard = synth.make_hard(10_000)
     g = _gpu_merge(B, ctx, hard, pool, mean)
     T = oracle.poisson_thresholds(mean)
-    pu = oracle.PileUp(mean, SIGMA, ZMAX, oracle.SIGMA_T, oracle.MAX_T, 1, 0)
+    pu = oracle.PileUp(mean, SIGMA, ZMAX, SIGMA_T, TMAX, 1, 0)
     psz = np.diff(np.asarray(pool.offsets, np.int64))
     hsz = np.diff(np.asarray(hard.offsets, np.int64))
     sizes = np.empty(hard.n_events, np.int64)
@@ -139,7 +157,7 @@ def test_full_size_pileup_configuration(B, ctx, synth):
         sub = hard.slice_events(e0, e0 + 10)
         o = oracle.pileup_merge(sub, pool, mean, SIGMA, ZMAX, True, SEED, event_base=e0)
         a, b = int(g["offsets"][e0]), int(g["offsets"][e0 + 10])
-        part = {k: g[k][a:b] for k in ("pt", "eta", "phi", "mass", "vz", "pdg", "charge")}
+        part = {k: g[k][a:b] for k in ("pt", "eta", "phi", "mass", "vz", "vt", "pdg", "charge")}
         part["offsets"] = (g["offsets"][e0:e0 + 11] - g["offsets"][e0]).astype(np.uint64)
         _compare(part, o)
 
