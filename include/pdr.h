@@ -7,7 +7,7 @@
  * the solenoid field, tracking / lepton / photon efficiencies, momentum and
  * energy smearing, ECAL/HCAL eta-phi towers with smearing and thresholds,
  * energy-flow track subtraction (Towers and EFlowObjects), and the cone
- * isolation of electrons, muons and photons (Sec. 2.3, Eq. 1).
+ * isolation of electrons, muons and photons (Sec. 2.4, Eq. 1).
  *
  * Everything on the data path runs in the library's CUDA kernels.  All entry
  * points are plain C: pointers, sizes and status codes; no C++ types and no

@@ -7,7 +7,7 @@ parses the detector card JSON itself and has its own C implementation of every
 step of the method.
 
 The C oracle follows the paper's TorchDelphes module chain (Sec. 2.2, App. C)
-and the isolation definition of Sec. 2.3 (Eq. 1); see ``oracle.h``.
+and the isolation definition of Sec. 2.4 (Eq. 1); see ``oracle.h``.
 """
 
 from __future__ import annotations

@@ -9,7 +9,7 @@
  *                        efficiency, momentum smearing, calorimeter response,
  *                        energy-flow merging (Towers, EFlowObjects).
  *   App. C.2             PropagatedParticle (deterministic intermediate).
- *   Sec. 2.3, Eq. 1      lepton isolation: cone sum of charged, neutral and
+ *   Sec. 2.4, Eq. 1      lepton isolation: cone sum of charged, neutral and
  *                        photon pT, excluding the lepton itself, over pT.
  *
  * The paper gives the module list but no module formulas; the readings coded
@@ -626,7 +626,7 @@ static int run_event_impl(const oracle_card* c, const or_grid grid[2], int64_t n
     n_eflow += (int)T->eflow_kept;
   }
 
-  /* S8: isolation (Sec. 2.3, Eq. 1).  Objects are the energy-flow tracks and
+  /* S8: isolation (Sec. 2.4, Eq. 1).  Objects are the energy-flow tracks and
    * neutrals above the pT floor; the candidate's own track and the neutral of
    * the tower it deposited into are the lepton itself and are excluded, as are
    * objects closer than dR_min. */

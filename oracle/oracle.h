@@ -11,7 +11,7 @@
  * The method is the paper's parametric backend (TorchDelphes, Sec. 2.2 and
  * App. C.1): particle propagation in the solenoid field, tracking efficiency,
  * momentum smearing, calorimeter response (towers), energy-flow merging, and
- * the lepton isolation of Sec. 2.3 (Eq. 1).  The paper prints no formulas for
+ * the lepton isolation of Sec. 2.4 (Eq. 1).  The paper prints no formulas for
  * the TorchDelphes modules; the readings used here (helix geometry, log-normal
  * smearing, tower centres, thresholds, counter-based random numbers) are the
  * project's and are listed in the design notes.

@@ -1,5 +1,5 @@
 """Pins for the oracle's per-event stages: towers (S5, S6), energy flow (S7),
-efficiencies (S2, S4) and isolation (S8, Sec. 2.3 Eq. 1).
+efficiencies (S2, S4) and isolation (S8, Sec. 2.4 Eq. 1).
 
 Hand-built events with a known answer, counting identities that hold for any
 event, and binomial tests of the acceptance against the card's efficiencies.
