@@ -136,7 +136,8 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh"),
-                  "pu_fill_kernel": ("pdr_pileup.cu", "pdr_math.cuh")}
+                  "pu_fill_kernel": ("pdr_pileup.cu", "pdr_math.cuh"),
+                  "postprocess_kernel": ("pdr_postprocess.cu", "pdr_math.cuh")}
 
 
 def kernel_fingerprint(kernel: str = "fused_kernel") -> str:
@@ -307,6 +308,8 @@ def bench_ours(args, dist, rank, ws):
         "clocks": clk,
         "gpu_launches": args.steps,
     }
+    if not args.no_postprocess:
+        line["postprocess"] = bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts)
     if not args.no_serving and ws == 1:
         line["serving"] = bench_serving(args, B, ctx)
     if not args.no_pileup_merge and ws == 1:
@@ -408,6 +411,56 @@ def bench_serving(args, B, ctx):
             "per_request_p50_ms": float(np.percentile(lat, 50)), "per_request_p99_ms": float(np.percentile(lat, 99)),
             "per_request_particles_per_s": parts / span if span > 0 else None}
     return out
+
+
+def bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts):
+    """Filter pipeline + event features (Sec. 2.4) on the response's outputs:
+    PFlow objects with pT > 1 GeV and |eta| < 2.5, H_T and missing E_T of the
+    survivors; timed without compaction (the outputs stay as they are), then
+    once with the survivors moved down in place."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    feats = torch.empty((n_ev, 4), dtype=torch.float32, device="cuda")
+    spec = {"collection": "pflow", "combine": "all", "conditions": [
+        {"field": "pt", "op": ">", "value": 1.0}, {"field": "eta", "op": "<", "value": 2.5, "abs": True}]}
+    f_view = B.make_filter(spec, compact=False)
+    reps = max(3, args.steps)
+    for _ in range(3):
+        ctx.postprocess(bt, ob, f_view, feats)
+    torch.cuda.synchronize()
+    ctx.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.postprocess(bt, ob, f_view, feats)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    s_view = e0.elapsed_time(e1) / 1e3 / reps
+    # algorithmic bytes: offsets and counts (24 B an event), every track
+    # (16 B) and EFlow neutral (12 B) read once, the features (16 B) written
+    tot = counts.sum(axis=0)
+    alg = 24 * n_ev + 16 * int(tot[0]) + 12 * int(tot[2]) + 16 * n_ev
+    f_cmp = B.make_filter(spec, compact=True)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    ctx.postprocess(bt, ob, f_cmp, feats)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    kept = out["counts"].cpu().numpy().view(np.uint32)[:n_ev].astype(np.int64).sum(axis=0)
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    achieved = alg / s_view / 1e9
+    return {"filter": "pflow: pt > 1 GeV and |eta| < 2.5", "events": n_ev,
+            "objects": int(tot[0] + tot[2]), "kept_objects": int(kept[0] + kept[2]),
+            "ms": s_view * 1e3, "events_per_s": n_ev / s_view,
+            "compacting_ms": c0.elapsed_time(c1),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": _traffic_from_profile("batched", "postprocess_kernel"),
+                         "algorithmic_bytes_per_launch": int(alg), "kernel": "pdr::postprocess_kernel"},
+            "reps": reps}
 
 
 def bench_pileup_merge(args, B, ctx):
@@ -592,6 +645,7 @@ def main(argv=None):
     ap.add_argument("--serving-pool", type=int, default=5000)
     ap.add_argument("--no-per-event", action="store_true")
     ap.add_argument("--no-pileup-merge", action="store_true")
+    ap.add_argument("--no-postprocess", action="store_true")
     ap.add_argument("--merge-only", action="store_true",
                     help="time only the pile-up merge (and the merged batch's response); prints that object")
     ap.add_argument("--pileup-events", type=int, default=10_000, help="hard events of the pile-up merge")

@@ -321,6 +321,90 @@ int pdr_pileup_offsets(pdr_ctx* ctx, const pdr_batch* hard, const pdr_pileup* pu
 int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* hard, const pdr_pileup* pu, const uint64_t* merged_offsets,
                      const pdr_particles* out, void* stream);
 
+/* ------------------------------------------- filter and event features -- */
+/* Sec. 2.4: a filter drops entries of a collection in place by per-field
+ * conditions combined with "all" (AND) or "any" (OR); the event features H_T
+ * and missing E_T are recomputed from the survivors.  The paper defines
+ * neither feature; here the PFlow collection is the energy-flow tracks plus
+ * the energy-flow neutrals, H_T = sum of their pT and missing E_T = minus the
+ * vector sum of their transverse momenta.  Object fields per collection:
+ *   tracks    pt = smeared pT, eta/phi = momentum direction,
+ *             e = sqrt(pT^2 cosh^2(eta) + m^2), et = pt, pdg/charge of the
+ *             generated particle;
+ *   neutrals  (EFlow) pt = et = dE / cosh(eta_c), e = dE, eta/phi = tower
+ *             centre, pdg 22 (ECAL) or 130 (HCAL), charge 0;
+ *   towers    pt = et = E' / cosh(eta_c), e = E', tower centre, pdg 0, charge 0;
+ *   cands     pt, eta, phi as reconstructed, e = pt cosh(eta), et = pt,
+ *             pdg/charge of the generated particle.
+ * A float field is compared in float32 (the threshold rounded to float32), an
+ * integer field (pdg, charge) as an integer; abs compares the magnitude;
+ * PDR_OP_IN / PDR_OP_NOT_IN test membership in values[0..n_values).  No
+ * conditions keep everything.  PFLOW filters tracks and neutrals alike. */
+#define PDR_COLL_PFLOW 0
+#define PDR_COLL_TRACK 1
+#define PDR_COLL_NEUTRAL 2
+#define PDR_COLL_TOWER 3
+#define PDR_COLL_CAND 4
+
+#define PDR_FIELD_PT 0
+#define PDR_FIELD_ETA 1
+#define PDR_FIELD_PHI 2
+#define PDR_FIELD_E 3
+#define PDR_FIELD_ET 4
+#define PDR_FIELD_PDG 5
+#define PDR_FIELD_CHARGE 6
+
+#define PDR_OP_GT 0
+#define PDR_OP_GE 1
+#define PDR_OP_LT 2
+#define PDR_OP_LE 3
+#define PDR_OP_EQ 4
+#define PDR_OP_NE 5
+#define PDR_OP_IN 6
+#define PDR_OP_NOT_IN 7
+
+#define PDR_COMBINE_ALL 0
+#define PDR_COMBINE_ANY 1
+
+#define PDR_MAX_CONDITIONS 8
+#define PDR_MAX_VALUES 8
+
+typedef struct pdr_condition {
+  uint32_t field, op;
+  uint32_t abs;                   /* 1: compare |field|                              */
+  uint32_t n_values;              /* 1 for comparisons; 1..PDR_MAX_VALUES for in/not in */
+  double values[PDR_MAX_VALUES];  /* integral for pdg and charge                     */
+} pdr_condition;
+
+typedef struct pdr_filter {
+  uint32_t collection;            /* PDR_COLL_*                                      */
+  uint32_t combine;               /* PDR_COMBINE_*                                   */
+  uint32_t n_conditions;          /* 0..PDR_MAX_CONDITIONS                           */
+  uint32_t compact;               /* 1: drop the failing records in place            */
+  uint32_t update_features;       /* 1: features from the survivors, 0: from all     */
+  uint32_t pad;
+  pdr_condition cond[PDR_MAX_CONDITIONS];
+} pdr_filter;
+
+typedef struct pdr_features {
+  float ht;                       /* GeV */
+  float met_x, met_y, met;        /* missing E_T vector and magnitude (GeV) */
+} pdr_features;
+
+/* Post-processing of pdr_run's outputs (all DEVICE, slot layout): `batch` is
+ * the batch that produced `out` (its offsets, pdg, charge, mass and card are
+ * read).  With a filter and compact = 1 the target collection's surviving
+ * records are moved down in order (candidates together with their isolation
+ * records) and counts are updated; with compact = 0 nothing in `out` changes.
+ * filter may be NULL (no filter).  features [n_events] (DEVICE) may be NULL.
+ * Sums are exact 64-bit fixed-point (quantum 2^-24 GeV) over float32 terms,
+ * so results do not depend on the launch.  Asynchronous on `stream`; events
+ * whose counts exceed their multiplicity are skipped and reported as
+ * malformed by pdr_check.  PDR_EINVAL for a bad filter or track records that
+ * are not 16-byte aligned, PDR_ENOTFOUND for an unknown card. */
+int pdr_postprocess(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_filter* filter,
+                    pdr_features* features, void* stream);
+
 /* ------------------------------------------------------- allocation-free run -- */
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that may not allocate device memory when they run the response:

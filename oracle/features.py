@@ -28,8 +28,11 @@ defines neither feature; the readings coded here (and in the CUDA path) are:
   or neutral collection changes H_T and E_T^miss; a filter on towers or
   candidates does not (they are not PFlow objects).
 
-A float decision whose value lies within g max(|v|, |t|, 1) of its threshold
-is counted as marginal: the CUDA path may take it the other way.
+A float decision whose value lies within g max(|v|, |t|, 1, scale) of its
+threshold is counted as marginal: the CUDA path may take it the other way.
+The scale is that of the value's own rounding: for an EFlow neutral's energy
+dE = E' - E_trk (a cancellation) it is max(E', E_trk), over cosh(eta_c) for
+its pt and et; else 0.
 """
 from typing import Optional, Sequence
 
@@ -58,9 +61,10 @@ def _sorted_towers(ref, flag: str):
 def _objects_neutrals(ref) -> dict:
     n = _sorted_towers(ref, "eflow_kept")
     calo = (n["key"] >> 24).astype(np.int64)
+    scale = np.maximum(n["e"], n["etrk"])
     return {"pt": n["eflow_et"], "eta": n["eta_c"], "phi": n["phi_c"], "e": n["eflow_e"], "et": n["eflow_et"],
             "pdg": np.where(calo == ECAL, 22, 130).astype(np.int64), "charge": np.zeros(len(n), np.int64),
-            "key": n["key"]}
+            "key": n["key"], "scale_e": scale, "scale_pt": scale / np.cosh(n["eta_c"])}
 
 
 def _objects_towers(ref) -> dict:
@@ -100,8 +104,10 @@ def condition(obj: dict, cond: dict, g: float):
         v64 = np.abs(v.astype(np.float64)) if use_abs else v.astype(np.float64)
         cmp_v = v64.astype(np.float32)
         ts = [np.float32(x) for x in values]
+        scale = obj.get("scale_e" if field == "e" else "scale_pt" if field in ("pt", "et") else "", None)
+        floor = np.maximum(1.0, scale) if scale is not None else 1.0
         for t in ts:
-            marg |= np.abs(v64 - float(t)) <= g * np.maximum(np.maximum(np.abs(v64), abs(float(t))), 1.0)
+            marg |= np.abs(v64 - float(t)) <= g * np.maximum(np.maximum(np.abs(v64), abs(float(t))), floor)
     if op == ">":
         m = cmp_v > ts[0]
     elif op == ">=":
@@ -160,6 +166,8 @@ def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5) -> dic
             n_marg += m
     from_survivors = filt is None or bool(filt.get("update_event_features", True))
     ht = mx = my = 0.0
+    scale = 0.0  # sum of the terms' rounding scales (the pT, or a neutral's scale_pt if larger)
+    n_terms = 0
     for k in ("track", "neutral"):
         sel = keep[k] if from_survivors else np.ones(len(obj[k]["pt"]), bool)
         pt = np.asarray(obj[k]["pt"], np.float64)[sel]
@@ -167,5 +175,8 @@ def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5) -> dic
         ht += float(pt.sum())
         mx -= float((pt * np.cos(phi)).sum())
         my -= float((pt * np.sin(phi)).sum())
+        sc = obj[k].get("scale_pt")
+        scale += float(np.maximum(np.abs(pt), sc[sel]).sum() if sc is not None else np.abs(pt).sum())
+        n_terms += int(sel.sum())
     return {"keep": keep, "objects": obj, "ht": ht, "met_x": mx, "met_y": my, "met": float(np.hypot(mx, my)),
-            "marginal": n_marg}
+            "marginal": n_marg, "scale": scale, "n_terms": n_terms}

@@ -112,6 +112,52 @@ class pdr_particles(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("pt", "eta", "phi", "mass", "vz", "vt", "pdg", "charge")]
 
 
+MAX_CONDITIONS = 8
+MAX_VALUES = 8
+COLLECTIONS = {"pflow": 0, "track": 1, "neutral": 2, "tower": 3, "cand": 4}
+FIELDS = {"pt": 0, "eta": 1, "phi": 2, "e": 3, "et": 4, "pdg": 5, "charge": 6}
+OPS = {">": 0, ">=": 1, "<": 2, "<=": 3, "==": 4, "!=": 5, "in": 6, "not in": 7}
+
+
+class pdr_condition(C.Structure):
+    _fields_ = [("field", C.c_uint32), ("op", C.c_uint32), ("abs", C.c_uint32), ("n_values", C.c_uint32),
+                ("values", C.c_double * MAX_VALUES)]
+
+
+class pdr_filter(C.Structure):
+    _fields_ = [("collection", C.c_uint32), ("combine", C.c_uint32), ("n_conditions", C.c_uint32),
+                ("compact", C.c_uint32), ("update_features", C.c_uint32), ("pad", C.c_uint32),
+                ("cond", pdr_condition * MAX_CONDITIONS)]
+
+
+class pdr_features(C.Structure):
+    _fields_ = [("ht", C.c_float), ("met_x", C.c_float), ("met_y", C.c_float), ("met", C.c_float)]
+
+
+def make_filter(spec: dict, compact: bool = True) -> pdr_filter:
+    """pdr_filter from {"collection", "combine", "conditions": [{"field", "op",
+    "value", "abs"}], "update_event_features"} (the filter pipeline's fields)."""
+    f = pdr_filter()
+    f.collection = COLLECTIONS[spec.get("collection", "pflow")]
+    f.combine = {"all": 0, "any": 1}[spec.get("combine", "all")]
+    conds = spec.get("conditions", [])
+    if len(conds) > MAX_CONDITIONS:
+        raise ValueError("at most 8 conditions")
+    f.n_conditions = len(conds)
+    f.compact = int(bool(compact))
+    f.update_features = int(bool(spec.get("update_event_features", True)))
+    for k, c in enumerate(conds):
+        d = f.cond[k]
+        d.field, d.op, d.abs = FIELDS[c["field"]], OPS[c["op"]], int(bool(c.get("abs", False)))
+        vals = list(c["value"]) if c["op"] in ("in", "not in") else [c["value"]]
+        if len(vals) > MAX_VALUES:
+            raise ValueError("at most 8 values")
+        d.n_values = len(vals)
+        for j, v in enumerate(vals):
+            d.values[j] = float(v)
+    return f
+
+
 class pdr_result(C.Structure):
     _fields_ = [("n_events", C.c_uint64), ("n_particles", C.c_uint64)] + [
         (n, C.c_void_p) for n in ("offsets", "counts", "tracks", "towers", "eflow", "cands", "iso", "debug")]
@@ -156,6 +202,7 @@ def lib():
             "pdr_run_noalloc": ([C.POINTER(pdr_card), C.POINTER(pdr_batch), C.POINTER(pdr_outputs), P], I),
             "pdr_pileup_offsets": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(C.c_uint64), P], I),
             "pdr_pileup_merge": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(pdr_particles), P], I),
+            "pdr_postprocess": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_filter), P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -401,6 +448,15 @@ class Context:
         o = pdr_particles(*[_ptr(out.get(k)) for k in ("pt", "eta", "phi", "mass", "vz", "vt", "pdg", "charge")])
         self._check(self.L.pdr_pileup_merge(self.h, C.byref(hard), C.byref(pu), _ptr(merged_offsets), C.byref(o),
                                             self._stream(stream)), "pdr_pileup_merge")
+
+    # ---- filter and event features
+    def postprocess(self, batch: pdr_batch, out: pdr_outputs, filt: Optional[pdr_filter] = None, features=None,
+                    stream=None):
+        """Filter (in place if filt.compact) and H_T / missing E_T into `features`
+        (a device float32 tensor [n_events, 4]: ht, met_x, met_y, met) or None."""
+        self._check(self.L.pdr_postprocess(self.h, C.byref(batch), C.byref(out),
+                                           C.byref(filt) if filt is not None else None, _ptr(features),
+                                           self._stream(stream)), "pdr_postprocess")
 
     # ---- serving
     def serve_start(self, max_inflight_waves=0, max_wave_requests=0, max_wave_particles=0, use_graphs=1):

@@ -183,6 +183,36 @@ struct PuParams {
   uint32_t* err;
 };
 
+// Post-processing (filter + event features): one condition, thresholds in
+// the type the field is compared in.
+struct PostCond {
+  uint32_t field, op, abs, n;
+  float fv[PDR_MAX_VALUES];
+  int32_t iv[PDR_MAX_VALUES];
+};
+
+struct PostParams {
+  uint64_t n_events;
+  const uint64_t* offsets;
+  const int32_t* pdg;
+  const int8_t* charge;
+  const float* mass;
+  const float2* centres;             // (eta_c, phi_c) of ECAL tower ids, then HCAL ones
+  uint32_t ntowers[2];
+  pdr_track* tracks;
+  pdr_tower* towers;
+  pdr_eflow* eflow;
+  pdr_cand* cands;
+  pdr_iso* iso;
+  uint32_t* counts;
+  pdr_features* features;            // may be null
+  uint32_t* err;
+  uint32_t filtered, collection, combine, n_cond, compact, update_features;
+  uint32_t need_gen;                 // a condition reads pdg or charge
+  uint32_t need_mass;                // a track condition reads e
+  PostCond cond[PDR_MAX_CONDITIONS];
+};
+
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {
   uint64_t n_events;                 // all segments

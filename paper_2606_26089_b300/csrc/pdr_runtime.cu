@@ -30,6 +30,7 @@ cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blo
 cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
                              cudaStream_t s);
 cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s);
+cudaError_t launch_postprocess(const PostParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
                          uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
@@ -132,6 +133,7 @@ struct CardEntry {
   unsigned char* hot = nullptr;   // shared-memory card cache image (device)
   uint32_t hot_bytes = 0;
   uint32_t ntowers[2] = {0, 0};
+  float2* centres = nullptr;      // (eta_c, phi_c) of every ECAL then HCAL tower id (device)
 };
 
 struct Ticket {
@@ -685,16 +687,29 @@ int pdr_card_load(pdr_ctx* ctx, const pdr_card* card, uint32_t* card_id) {
     delete host;
     return fail(PDR_ECARD, "card tables exceed the 40 KiB shared-memory card cache");
   }
+  // tower centres by id, for the post-processing (float32 of the double centres)
+  std::vector<float2> centres;
+  centres.reserve((size_t)ce.ntowers[0] + ce.ntowers[1]);
+  for (int calo = 0; calo < 2; ++calo) {
+    const DevCalo& D = host->calo[calo];
+    for (int r = 0; r < D.nring; ++r)
+      for (int k = 0; k < D.nphi[r]; ++k)
+        centres.push_back(make_float2(D.eta_c[r], host->phi_pool[D.phioff[r] + D.nphi[r] + 1 + k]));
+  }
   cudaSetDevice(ctx->device);
   const size_t hot_off = (sizeof(DevCard) + 255) & ~(size_t)255;
-  if (cudaMalloc((void**)&ce.dev, hot_off + hot_bytes) != cudaSuccess) {
+  const size_t ctr_off = (hot_off + hot_bytes + 255) & ~(size_t)255;
+  if (cudaMalloc((void**)&ce.dev, ctr_off + centres.size() * sizeof(float2)) != cudaSuccess) {
     delete host;
     return fail(PDR_ENOMEM, "cannot allocate card tables");
   }
   ce.hot = (unsigned char*)ce.dev + hot_off;
   ce.hot_bytes = (uint32_t)hot_bytes;
+  ce.centres = (float2*)((unsigned char*)ce.dev + ctr_off);
   cudaError_t e = cudaMemcpy(ce.dev, host, sizeof(DevCard), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ce.hot, hot.data(), hot_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ce.centres, centres.data(), centres.size() * sizeof(float2), cudaMemcpyHostToDevice);
   delete host;
   if (e != cudaSuccess) {
     cudaFree(ce.dev);
@@ -1672,3 +1687,83 @@ int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, con
 }
 
 }  // extern "C"
+
+// ============================================================ post-processing
+namespace {
+
+// Filter spec -> kernel conditions (thresholds in the type they are compared in).
+int post_conditions(const pdr_filter* f, PostParams& p) {
+  if (f->collection > PDR_COLL_CAND) return fail(PDR_EINVAL, "unknown filter collection");
+  if (f->combine > PDR_COMBINE_ANY) return fail(PDR_EINVAL, "combine must be all or any");
+  if (f->n_conditions > PDR_MAX_CONDITIONS) return fail(PDR_EINVAL, "more than 8 filter conditions");
+  p.filtered = 1;
+  p.collection = f->collection;
+  p.combine = f->combine;
+  p.n_cond = f->n_conditions;
+  p.compact = f->compact ? 1u : 0u;
+  p.update_features = f->update_features ? 1u : 0u;
+  for (uint32_t k = 0; k < f->n_conditions; ++k) {
+    const pdr_condition& c = f->cond[k];
+    PostCond& d = p.cond[k];
+    if (c.field > PDR_FIELD_CHARGE) return fail(PDR_EINVAL, "unknown filter field");
+    if (c.op > PDR_OP_NOT_IN) return fail(PDR_EINVAL, "unknown filter operator");
+    const bool set = c.op == PDR_OP_IN || c.op == PDR_OP_NOT_IN;
+    if (c.n_values < 1 || c.n_values > PDR_MAX_VALUES || (!set && c.n_values != 1))
+      return fail(PDR_EINVAL, "a comparison takes one value, in / not in 1 to 8");
+    d.field = c.field;
+    d.op = c.op;
+    d.abs = c.abs ? 1u : 0u;
+    d.n = c.n_values;
+    const bool integer = c.field == PDR_FIELD_PDG || c.field == PDR_FIELD_CHARGE;
+    for (uint32_t j = 0; j < c.n_values; ++j) {
+      const double v = c.values[j];
+      if (integer) {
+        if (!(v == std::floor(v)) || v < -2147483648.0 || v > 2147483647.0)
+          return fail(PDR_EINVAL, "pdg and charge thresholds must be 32-bit integers");
+        d.iv[j] = (int32_t)v;
+      } else {
+        if (std::isnan(v)) return fail(PDR_EINVAL, "NaN filter threshold");
+        d.fv[j] = (float)v;
+      }
+    }
+    if (integer) p.need_gen = 1;
+    if (c.field == PDR_FIELD_E) p.need_mass = 1;
+  }
+  return PDR_OK;
+}
+
+}  // namespace
+
+extern "C" int pdr_postprocess(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_filter* f,
+                               pdr_features* features, void* stream) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if ((rc = check_outputs(o))) return rc;
+  if (((uintptr_t)o->tracks & 15u) != 0) return fail(PDR_EINVAL, "track records must be 16-byte aligned");
+  PostParams p;
+  std::memset(&p, 0, sizeof p);
+  p.update_features = 1;
+  if (f && (rc = post_conditions(f, p))) return rc;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (b->n_events == 0) return PDR_OK;
+  p.n_events = b->n_events;
+  p.offsets = b->offsets;
+  p.pdg = b->pdg;
+  p.charge = b->charge;
+  p.mass = b->mass;
+  const CardEntry& ce = ctx->cards[b->card_id];
+  p.centres = ce.centres;
+  p.ntowers[0] = ce.ntowers[0];
+  p.ntowers[1] = ce.ntowers[1];
+  p.tracks = o->tracks;
+  p.towers = o->towers;
+  p.eflow = o->eflow;
+  p.cands = o->cands;
+  p.iso = o->iso;
+  p.counts = o->counts;
+  p.features = features;
+  p.err = ctx->d_err;
+  PDR_CUDA(launch_postprocess(p, ctx->n_sms, (cudaStream_t)stream), "post-processing launch");
+  return PDR_OK;
+}

@@ -41,7 +41,8 @@ def test_abi_version(libpdr):
 
 
 STRUCTS = ("pdr_card", "pdr_batch", "pdr_outputs", "pdr_launch", "pdr_options", "pdr_result",
-           "pdr_serve_options", "pdr_serve_stats", "pdr_pileup", "pdr_particles")
+           "pdr_serve_options", "pdr_serve_stats", "pdr_pileup", "pdr_particles", "pdr_condition",
+           "pdr_filter", "pdr_features")
 
 
 def test_binding_structs_match_header_layout(tmp_path):
