@@ -99,6 +99,11 @@ class PileUp(C.Structure):
                 ("smear_hs", C.c_int32), ("pad", C.c_int32)]
 
 
+class IPParams(C.Structure):
+    """Impact-parameter resolutions: sigma = sqrt(a^2 + (b / pT)^2) (m, m GeV)."""
+    _fields_ = [("a_d0", C.c_double), ("b_d0", C.c_double), ("a_z0", C.c_double), ("b_z0", C.c_double)]
+
+
 # vertex-time width and truncation of the pile-up block's defaults (Sec. 2.2,
 # parametric pile-up fields): 160 ps and 800 ps
 SIGMA_T = 160e-12
@@ -144,6 +149,12 @@ def lib():
         _lib.oracle_pileup_draws.argtypes = [C.POINTER(PileUp), P, C.c_int32, C.c_uint64, C.c_uint64,
                                              C.c_uint32, C.c_double, P, P, P, P, C.c_int32, P, P]
         _lib.oracle_pileup_draws.restype = C.c_int32
+        D = C.c_double
+        _lib.oracle_track_ip.argtypes = [C.POINTER(Card), D, D, D, C.c_int32, D, D, D, P, P, P]
+        _lib.oracle_track_ip.restype = None
+        _lib.oracle_track_ip_smeared.argtypes = [C.POINTER(Card), C.POINTER(IPParams), D, D, D, C.c_int32, D, D, D,
+                                                 C.c_uint64, C.c_uint32, C.c_uint32, P]
+        _lib.oracle_track_ip_smeared.restype = None
     return _lib
 
 
@@ -449,4 +460,38 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
     out["draws"] = draws
     out["marginal"] = n_marg
     out["marginal_events"] = marg_events
+    return out
+
+
+# ----------------------------------------------------------------------------
+# track impact parameters
+# ----------------------------------------------------------------------------
+def track_ip(card: Card, pt: float, eta: float, phi: float, q: int, x0: float, y0: float, z0: float):
+    """(d0, z0, s) of one particle's helix (see oracle.h)."""
+    d0, zz, s = C.c_double(), C.c_double(), C.c_double()
+    lib().oracle_track_ip(C.byref(card), float(pt), float(eta), float(phi), int(q), float(x0), float(y0),
+                          float(z0), C.byref(d0), C.byref(zz), C.byref(s))
+    return d0.value, zz.value, s.value
+
+
+def track_ip_smeared(card: Card, ip: IPParams, pt, eta, phi, q, x0, y0, z0, seed: int, event: int, idx: int):
+    """(d0', z0', sigma_d0, sigma_z0) of one particle."""
+    out = np.zeros(4, np.float64)
+    lib().oracle_track_ip_smeared(C.byref(card), C.byref(ip), float(pt), float(eta), float(phi), int(q),
+                                  float(x0), float(y0), float(z0), int(seed) & (2**64 - 1),
+                                  int(event) & 0xFFFFFFFF, int(idx) & 0xFFFFFFFF, _ptr(out))
+    return tuple(out)
+
+
+def event_track_ip(card: Card, ip: IPParams, ev: dict, ref: "EventResult", seed: int, event: int) -> np.ndarray:
+    """[n_tracks, 4] (d0', z0', sigma_d0, sigma_z0) of an event's tracks, in the
+    order of ref.tracks; ev may hold vx, vy, vz (absent: 0)."""
+    n = len(ev["pt"])
+    vx = np.zeros(n) if ev.get("vx") is None else np.asarray(ev["vx"], np.float64)
+    vy = np.zeros(n) if ev.get("vy") is None else np.asarray(ev["vy"], np.float64)
+    vz = np.zeros(n) if ev.get("vz") is None else np.asarray(ev["vz"], np.float64)
+    out = np.zeros((len(ref.tracks), 4), np.float64)
+    for k, i in enumerate(ref.tracks["idx"].astype(np.int64)):
+        out[k] = track_ip_smeared(card, ip, ev["pt"][i], ev["eta"][i], ev["phi"][i], ev["charge"][i], vx[i], vy[i],
+                                  vz[i], seed, event, int(i))
     return out

@@ -851,3 +851,60 @@ int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K
   }
   return marg;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Track impact parameters (see oracle.h for the readings).                  */
+/* ------------------------------------------------------------------------ */
+void oracle_track_ip(const oracle_card* c, double pt, double eta, double phi, int32_t q, double x0, double y0,
+                     double z0, double* d0, double* zz0, double* s_out) {
+  const double cp = cos(phi), sp = sin(phi);
+  double s;
+  if (c->B == 0.0 || q == 0) {
+    /* straight line x = v0 + s p_hat: nearest to the axis at s = -(v0 . p_hat) */
+    s = -(x0 * cp + y0 * sp);
+    const double px = x0 + s * cp, py = y0 + s * sp;
+    *d0 = py * cp - px * sp;
+  } else {
+    const double h = (q > 0) == (c->B > 0) ? 1.0 : -1.0;
+    const double r = pt / (0.299792458 * fabs((double)q * c->B));
+    /* centre: to the right of the momentum when the track turns clockwise */
+    const double cx = x0 + h * r * sp, cy = y0 - h * r * cp;
+    const double dc = hypot(cx, cy);
+    /* position angles on the circle (measured at the centre) */
+    const double a0 = atan2(y0 - cy, x0 - cx);
+    double px, py, ap;
+    if (dc == 0.0) {
+      px = x0; py = y0; ap = a0;
+    } else {
+      px = cx - r * cx / dc;
+      py = cy - r * cy / dc;
+      ap = atan2(py - cy, px - cx);
+    }
+    /* turning angle from the vertex to the pca, the shorter way */
+    double da = ap - a0;
+    while (da > M_PI) da -= 2.0 * M_PI;
+    while (da <= -M_PI) da += 2.0 * M_PI;
+    /* the position angle decreases by h s / r along the motion */
+    s = -h * r * da;
+    /* momentum direction at the pca: tangent, in the direction of motion */
+    const double phip = ap - h * 0.5 * M_PI;
+    *d0 = py * cos(phip) - px * sin(phip);
+  }
+  *zz0 = z0 + s * sinh(eta);
+  if (s_out) *s_out = s;
+}
+
+void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, double pt, double eta, double phi,
+                             int32_t q, double x0, double y0, double z0, uint64_t seed, uint32_t event,
+                             uint32_t idx, double out[4]) {
+  double d0, zz0;
+  oracle_track_ip(c, pt, eta, phi, q, x0, y0, z0, &d0, &zz0, NULL);
+  const double sd = sqrt(ip->a_d0 * ip->a_d0 + (ip->b_d0 / pt) * (ip->b_d0 / pt));
+  const double sz = sqrt(ip->a_z0 * ip->a_z0 + (ip->b_z0 / pt) * (ip->b_z0 / pt));
+  uint32_t w[4];
+  draw(seed, idx, event, 9u, w);
+  out[0] = d0 + sd * oracle_normal(w[0], w[1]);
+  out[1] = zz0 + sz * oracle_normal(w[2], w[3]);
+  out[2] = sd;
+  out[3] = sz;
+}

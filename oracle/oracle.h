@@ -226,6 +226,37 @@ int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K
                             uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
                             double* z, double* t, int32_t cap, double* z_hs, double* t_hs);
 
+/* ---- track impact parameters (the paper's output table: d0, z0 and their
+ * errors for charged particles; Sec. 2.5) ----
+ * Readings (the paper gives no formula):
+ *   - the track is the helix of the generated particle (pT, eta, phi at its
+ *     production vertex (x0, y0, z0), charge q) in the card's field B along z:
+ *     radius r = pT / (0.299792458 |q B|), its momentum azimuth turning by
+ *     -h s / r with h = sign(q B), s the transverse path; a straight line if
+ *     B = 0;
+ *   - the point of closest approach (pca) is the point of that circle (line)
+ *     in the transverse plane nearest to the beam axis (x = y = 0), reached
+ *     by the shorter way along the helix (forward or backward, |turn| <= pi);
+ *     if the axis is the circle's centre the pca is the vertex;
+ *   - d0 = (p_hat x pca)_z = pca_y cos(phi_pca) - pca_x sin(phi_pca), with
+ *     phi_pca the momentum azimuth at the pca; z0 = z0_vertex + s sinh(eta),
+ *     s the signed transverse path from the vertex to the pca;
+ *   - errors sigma = sqrt(a^2 + (b / pT)^2) with (a, b) per parameter, and the
+ *     reconstructed values d0 + sigma_d0 n1, z0 + sigma_z0 n2 with n1 the
+ *     Box-Muller normal of words 0, 1 and n2 of words 2, 3 of Philox counter
+ *     (particle index, event, 9, 0). */
+typedef struct oracle_ip_params {
+  double a_d0, b_d0, a_z0, b_z0;   /* metres, metres x GeV */
+} oracle_ip_params;
+
+/* True d0 and z0 of one particle; *s_out (may be NULL) the signed path. */
+void oracle_track_ip(const oracle_card* c, double pt, double eta, double phi, int32_t q, double x0, double y0,
+                     double z0, double* d0, double* zz0, double* s_out);
+/* The smeared pair and the errors: out[4] = d0', z0', sigma_d0, sigma_z0. */
+void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, double pt, double eta, double phi,
+                             int32_t q, double x0, double y0, double z0, uint64_t seed, uint32_t event,
+                             uint32_t idx, double out[4]);
+
 #ifdef __cplusplus
 }
 #endif
