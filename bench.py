@@ -137,7 +137,8 @@ class ClockSampler:
 
 KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh"),
                   "pu_fill_kernel": ("pdr_pileup.cu", "pdr_math.cuh"),
-                  "postprocess_kernel": ("pdr_postprocess.cu", "pdr_math.cuh")}
+                  "postprocess_kernel": ("pdr_postprocess.cu", "pdr_math.cuh"),
+                  "track_ip_kernel": ("pdr_ip.cu", "pdr_math.cuh")}
 
 
 def kernel_fingerprint(kernel: str = "fused_kernel") -> str:
@@ -308,6 +309,8 @@ def bench_ours(args, dist, rank, ws):
         "clocks": clk,
         "gpu_launches": args.steps,
     }
+    if not args.no_track_ip:
+        line["track_ip"] = bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts)
     if not args.no_postprocess:
         line["postprocess"] = bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts)
     if not args.no_serving and ws == 1:
@@ -411,6 +414,42 @@ def bench_serving(args, B, ctx):
             "per_request_p50_ms": float(np.percentile(lat, 50)), "per_request_p99_ms": float(np.percentile(lat, 99)),
             "per_request_particles_per_s": parts / span if span > 0 else None}
     return out
+
+
+def bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts):
+    """Track impact parameters (d0, z0 and their errors) of every track of the
+    response's outputs, vertices on the axis (the workload has none off it)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    ip = torch.empty((n_p, 4), dtype=torch.float32, device="cuda")
+    prm = B.make_ip_params()
+    reps = max(3, args.steps)
+    for _ in range(3):
+        ctx.track_ip(bt, ob, prm, ip)
+    torch.cuda.synchronize()
+    ctx.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.track_ip(bt, ob, prm, ip)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    sec = e0.elapsed_time(e1) / 1e3 / reps
+    nt = int(counts[:, 0].sum())
+    # algorithmic bytes: offsets and track count (12 B an event); per track its
+    # particle index (4 B), the particle's pT, eta, phi and charge (13 B) and
+    # the record written (16 B)
+    alg = 12 * n_ev + 33 * nt
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    achieved = alg / sec / 1e9
+    return {"tracks": nt, "ms": sec * 1e3, "tracks_per_s": nt / sec,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": _traffic_from_profile("batched", "track_ip_kernel"),
+                         "algorithmic_bytes_per_launch": int(alg), "kernel": "pdr::track_ip_kernel"},
+            "reps": reps}
 
 
 def bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts):
@@ -646,6 +685,7 @@ def main(argv=None):
     ap.add_argument("--no-per-event", action="store_true")
     ap.add_argument("--no-pileup-merge", action="store_true")
     ap.add_argument("--no-postprocess", action="store_true")
+    ap.add_argument("--no-track-ip", action="store_true")
     ap.add_argument("--merge-only", action="store_true",
                     help="time only the pile-up merge (and the merged batch's response); prints that object")
     ap.add_argument("--pileup-events", type=int, default=10_000, help="hard events of the pile-up merge")

@@ -405,6 +405,40 @@ typedef struct pdr_features {
 int pdr_postprocess(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_filter* filter,
                     pdr_features* features, void* stream);
 
+/* ------------------------------------------------ track impact parameters -- */
+/* The paper's output table (Sec. 2.5) lists d0, z0 and their errors for
+ * charged particles.  For every track record of pdr_run's outputs, from the
+ * generated particle it came from (pT, eta, phi, charge at its vertex
+ * (vx, vy, vz)) and the card's field:
+ *   - the point of closest approach (pca) to the beam axis of the particle's
+ *     helix (straight line if B = 0), reached the shorter way along the helix;
+ *   - d0 = (p_hat x pca)_z (signed transverse distance, p_hat the momentum
+ *     direction at the pca), z0 = vz + s sinh(eta), s the signed transverse
+ *     path from the vertex to the pca;
+ *   - errors sigma = sqrt(a^2 + (b / pT)^2) per parameter; the record holds
+ *     d0 + sigma_d0 n1 and z0 + sigma_z0 n2, n1 / n2 the Box-Muller normals of
+ *     words (0, 1) / (2, 3) of Philox counter (particle index, event, 9, 0)
+ *     under the batch's seed.
+ * Transverse vertex offsets (vx, vy) enter only here: the detector response
+ * propagates every particle from (0, 0, vz). */
+typedef struct pdr_ip_params {
+  double a_d0, b_d0;              /* m, m GeV */
+  double a_z0, b_z0;              /* m, m GeV */
+  const float* vx;                /* [n_particles] DEVICE, m, or NULL (0) */
+  const float* vy;                /* [n_particles] DEVICE, m, or NULL (0) */
+} pdr_ip_params;
+
+typedef struct { float d0, z0, sigma_d0, sigma_z0; } pdr_ip;   /* m */
+
+/* ip (DEVICE, slot layout parallel to out->tracks: event e's k-th track's
+ * record at [offsets[e] + k]) for the tracks that pdr_run wrote into `out`
+ * from `batch` (same seed and event_index_base).  Asynchronous on `stream`;
+ * PDR_EINVAL for negative resolutions or null arrays, PDR_ENOTFOUND for an
+ * unknown card; events whose track count exceeds their multiplicity are
+ * skipped and reported by pdr_check. */
+int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_ip_params* params,
+                 pdr_ip* ip, void* stream);
+
 /* ------------------------------------------------------- allocation-free run -- */
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that may not allocate device memory when they run the response:

@@ -130,6 +130,20 @@ class pdr_filter(C.Structure):
                 ("cond", pdr_condition * MAX_CONDITIONS)]
 
 
+class pdr_ip_params(C.Structure):
+    _fields_ = [("a_d0", C.c_double), ("b_d0", C.c_double), ("a_z0", C.c_double), ("b_z0", C.c_double),
+                ("vx", C.c_void_p), ("vy", C.c_void_p)]
+
+
+# impact-parameter resolutions sigma = sqrt(a^2 + (b / pT)^2), project-chosen
+# tracker-like values (m, m GeV): d0 10 um (+) 50 um GeV / pT, z0 30 um (+) 80 um GeV / pT
+IP_RESOLUTION = (10e-6, 50e-6, 30e-6, 80e-6)
+
+
+def make_ip_params(resolution=IP_RESOLUTION, vx=None, vy=None) -> pdr_ip_params:
+    return pdr_ip_params(*[float(x) for x in resolution], _ptr(vx), _ptr(vy))
+
+
 class pdr_features(C.Structure):
     _fields_ = [("ht", C.c_float), ("met_x", C.c_float), ("met_y", C.c_float), ("met", C.c_float)]
 
@@ -203,6 +217,7 @@ def lib():
             "pdr_pileup_offsets": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(C.c_uint64), P], I),
             "pdr_pileup_merge": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(pdr_particles), P], I),
             "pdr_postprocess": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_filter), P, P], I),
+            "pdr_track_ip": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_ip_params), P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -457,6 +472,13 @@ class Context:
         self._check(self.L.pdr_postprocess(self.h, C.byref(batch), C.byref(out),
                                            C.byref(filt) if filt is not None else None, _ptr(features),
                                            self._stream(stream)), "pdr_postprocess")
+
+    # ---- track impact parameters
+    def track_ip(self, batch: pdr_batch, out: pdr_outputs, params: pdr_ip_params, ip, stream=None):
+        """d0', z0', sigma_d0, sigma_z0 of every track record into `ip` (a device
+        float32 tensor [n_particles, 4], slot layout parallel to the tracks)."""
+        self._check(self.L.pdr_track_ip(self.h, C.byref(batch), C.byref(out), C.byref(params), _ptr(ip),
+                                        self._stream(stream)), "pdr_track_ip")
 
     # ---- serving
     def serve_start(self, max_inflight_waves=0, max_wave_requests=0, max_wave_particles=0, use_graphs=1):

@@ -213,6 +213,23 @@ struct PostParams {
   PostCond cond[PDR_MAX_CONDITIONS];
 };
 
+// Track impact parameters.
+struct IPParams {
+  uint64_t n_events;
+  const uint64_t* offsets;
+  const float *pt, *eta, *phi, *vx, *vy, *vz;
+  const int8_t* charge;
+  const pdr_track* tracks;
+  const uint32_t* counts;
+  pdr_ip* ip;
+  uint32_t* err;
+  float kB;                          // 0.299792458 |B|
+  int32_t bsign, has_field;
+  uint32_t event_base;
+  float a_d0, b_d0, a_z0, b_z0;
+  uint32_t rk[20];                   // Philox round keys of the batch's seed
+};
+
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {
   uint64_t n_events;                 // all segments

@@ -31,6 +31,7 @@ cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_
                              cudaStream_t s);
 cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_postprocess(const PostParams& p, int n_sms, cudaStream_t s);
+cudaError_t launch_track_ip(const IPParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
                          uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
@@ -134,6 +135,8 @@ struct CardEntry {
   uint32_t hot_bytes = 0;
   uint32_t ntowers[2] = {0, 0};
   float2* centres = nullptr;      // (eta_c, phi_c) of every ECAL then HCAL tower id (device)
+  float kB = 0.0f;                // field terms of the device card, kept on the host
+  int32_t bsign = 1, has_field = 0;
 };
 
 struct Ticket {
@@ -680,6 +683,9 @@ int pdr_card_load(pdr_ctx* ctx, const pdr_card* card, uint32_t* card_id) {
   }
   CardEntry ce;
   ce.ntowers[0] = (uint32_t)host->calo[0].ntowers;
+  ce.kB = host->kB;
+  ce.bsign = host->Bsign;
+  ce.has_field = host->has_field;
   ce.ntowers[1] = (uint32_t)host->calo[1].ntowers;
   std::vector<unsigned char> hot(PDR_HOT_MAX_BYTES);
   const size_t hot_bytes = build_hot_card(*host, hot.data(), hot.size());
@@ -1765,5 +1771,40 @@ extern "C" int pdr_postprocess(pdr_ctx* ctx, const pdr_batch* b, const pdr_outpu
   p.features = features;
   p.err = ctx->d_err;
   PDR_CUDA(launch_postprocess(p, ctx->n_sms, (cudaStream_t)stream), "post-processing launch");
+  return PDR_OK;
+}
+
+// ============================================================ impact parameters
+extern "C" int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_ip_params* ipp,
+                            pdr_ip* ip, void* stream) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if (!o || !o->tracks || !o->counts || !ipp || !ip) return fail(PDR_EINVAL, "null track, count or ip array");
+  const double r[4] = {ipp->a_d0, ipp->b_d0, ipp->a_z0, ipp->b_z0};
+  for (double v : r)
+    if (!(v >= 0.0) || !std::isfinite(v)) return fail(PDR_EINVAL, "impact-parameter resolutions must be >= 0");
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (b->n_events == 0) return PDR_OK;
+  const CardEntry& ce = ctx->cards[b->card_id];
+  IPParams p;
+  std::memset(&p, 0, sizeof p);
+  p.n_events = b->n_events;
+  p.offsets = b->offsets;
+  p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.vz = b->vz;
+  p.vx = ipp->vx; p.vy = ipp->vy;
+  p.charge = b->charge;
+  p.tracks = o->tracks;
+  p.counts = o->counts;
+  p.ip = ip;
+  p.err = ctx->d_err;
+  p.kB = ce.kB;
+  p.bsign = ce.bsign;
+  p.has_field = ce.has_field;
+  p.event_base = b->event_index_base;
+  p.a_d0 = (float)ipp->a_d0; p.b_d0 = (float)ipp->b_d0;
+  p.a_z0 = (float)ipp->a_z0; p.b_z0 = (float)ipp->b_z0;
+  fill_round_keys(p.rk, b->seed);
+  PDR_CUDA(launch_track_ip(p, ctx->n_sms, (cudaStream_t)stream), "impact-parameter launch");
   return PDR_OK;
 }
