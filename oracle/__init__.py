@@ -155,6 +155,8 @@ def lib():
         _lib.oracle_track_ip_smeared.argtypes = [C.POINTER(Card), C.POINTER(IPParams), D, D, D, C.c_int32, D, D, D,
                                                  C.c_uint64, C.c_uint32, C.c_uint32, P]
         _lib.oracle_track_ip_smeared.restype = None
+        _lib.oracle_cluster.argtypes = [C.c_int64, P, P, P, P, D, D, D, C.c_int32, P, P]
+        _lib.oracle_cluster.restype = C.c_int32
     return _lib
 
 
@@ -495,3 +497,30 @@ def event_track_ip(card: Card, ip: IPParams, ev: dict, ref: "EventResult", seed:
         out[k] = track_ip_smeared(card, ip, ev["pt"][i], ev["eta"][i], ev["phi"][i], ev["charge"][i], vx[i], vy[i],
                                   vz[i], seed, event, int(i))
     return out
+
+
+# ----------------------------------------------------------------------------
+# jet clustering
+# ----------------------------------------------------------------------------
+JET = np.dtype([("px", "f8"), ("py", "f8"), ("pz", "f8"), ("e", "f8"), ("pt", "f8"), ("eta", "f8"),
+                ("phi", "f8"), ("mass", "f8"), ("nconst", "i4"), ("pad", "i4")])
+ALGORITHM_P = {"antikt": -1.0, "cambridge": 0.0, "kt": 1.0}
+
+
+def cluster(px, py, pz, e, p: float = -1.0, R: float = 0.5, pt_min: float = 0.0, nconst_min: int = 1):
+    """(jets structured array, marginal steps) of one event's objects (see oracle.h)."""
+    arr = [np.ascontiguousarray(x, np.float64) for x in (px, py, pz, e)]
+    n = arr[0].shape[0]
+    jets = np.zeros(max(n, 1), JET)
+    m = C.c_int32()
+    k = lib().oracle_cluster(n, *[_ptr(a) for a in arr], float(p), float(R), float(pt_min), int(nconst_min),
+                             _ptr(jets), C.byref(m))
+    if k < 0:
+        raise ValueError("bad clustering arguments")
+    return jets[:k].copy(), m.value
+
+
+def four_momenta(pt, eta, phi, e):
+    """(px, py, pz, E) of objects given pT, eta, phi and energy."""
+    pt, eta, phi, e = (np.asarray(x, np.float64) for x in (pt, eta, phi, e))
+    return pt * np.cos(phi), pt * np.sin(phi), pt * np.sinh(eta), e

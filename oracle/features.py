@@ -180,3 +180,30 @@ def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5) -> dic
         n_terms += int(sel.sum())
     return {"keep": keep, "objects": obj, "ht": ht, "met_x": mx, "met_y": my, "met": float(np.hypot(mx, my)),
             "marginal": n_marg, "scale": scale, "n_terms": n_terms}
+
+
+def pflow_four_momenta(ref, ev):
+    """(px, py, pz, E) of the PFlow objects (tracks, then EFlow neutrals, in
+    output order) for the jet clustering: tracks with their smeared pT,
+    momentum direction and track energy; neutrals massless at the tower
+    centre with E = dE."""
+    o = objects(ref, ev)
+    t, n = o["track"], o["neutral"]
+    pt = np.concatenate([t["pt"], n["pt"]]).astype(np.float64)
+    eta = np.concatenate([t["eta"], n["eta"]]).astype(np.float64)
+    phi = np.concatenate([t["phi"], n["phi"]]).astype(np.float64)
+    e = np.concatenate([t["e"], n["e"]]).astype(np.float64)
+    return pt * np.cos(phi), pt * np.sin(phi), pt * np.sinh(eta), e
+
+
+INVISIBLE = (12, 14, 16)
+
+
+def truth_four_momenta(ev):
+    """(px, py, pz, E) of the generated particles except neutrinos, in input
+    order, E = sqrt(pT^2 cosh^2(eta) + m^2)."""
+    pdg = np.abs(np.asarray(ev["pdg"], np.int64))
+    sel = ~np.isin(pdg, INVISIBLE)
+    pt, eta, phi, m = (np.asarray(ev[k], np.float64)[sel] for k in ("pt", "eta", "phi", "mass"))
+    e = np.sqrt((pt * np.cosh(eta)) ** 2 + m * m)
+    return pt * np.cos(phi), pt * np.sin(phi), pt * np.sinh(eta), e

@@ -908,3 +908,101 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
   out[2] = sd;
   out[3] = sz;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Jet clustering: sequential recombination of the generalized-kT family   */
+/* (see oracle.h).  O(n^3): every step scans all active pairs.             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double px, py, pz, e, y, phi, kt2p;
+  int32_t nconst, active;
+} cl_obj;
+
+static void cl_derive(cl_obj* o, double p) {
+  const double pt2 = o->px * o->px + o->py * o->py;
+  o->phi = atan2(o->py, o->px);
+  o->y = 0.5 * log((o->e + o->pz) / (o->e - o->pz));
+  o->kt2p = pow(pt2, p); /* (pt^2)^p = pt^(2p) */
+}
+
+static double cl_dphi(double a, double b) {
+  double d = a - b;
+  while (d > M_PI) d -= 2.0 * M_PI;
+  while (d < -M_PI) d += 2.0 * M_PI;
+  return d;
+}
+
+int32_t oracle_cluster(int64_t n, const double* px, const double* py, const double* pz, const double* e,
+                       double p, double R, double pt_min, int32_t nconst_min, or_jet* jets, int32_t* n_marg) {
+  if (n < 0 || !(R > 0.0)) return -1;
+  *n_marg = 0;
+  if (n == 0) return 0;
+  cl_obj* o = (cl_obj*)calloc((size_t)n, sizeof(cl_obj));
+  if (!o) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    o[i].px = px[i]; o[i].py = py[i]; o[i].pz = pz[i]; o[i].e = e[i];
+    o[i].nconst = 1; o[i].active = 1;
+    cl_derive(&o[i], p);
+  }
+  const double R2 = R * R, eps = 1.0 / 8388608.0; /* 2^-23 */
+  int32_t nj = 0;
+  for (int64_t left = n; left > 0;) {
+    /* smallest distance; best / second: value and uncertainty */
+    double b = INFINITY, bu = 0.0, s2 = INFINITY, su = 0.0;
+    int64_t bi = -1, bj = -1;
+    for (int64_t i = 0; i < n; ++i) {
+      if (!o[i].active) continue;
+      const double diB = o[i].kt2p, uiB = 1e-6 * diB;
+      /* the beam distance first: it wins ties */
+      if (diB < b) { s2 = b; su = bu; b = diB; bu = uiB; bi = i; bj = -1; }
+      else if (diB < s2) { s2 = diB; su = uiB; }
+      for (int64_t j = i + 1; j < n; ++j) {
+        if (!o[j].active) continue;
+        const double dy = o[i].y - o[j].y, dp = cl_dphi(o[i].phi, o[j].phi);
+        const double kmin = fmin(o[i].kt2p, o[j].kt2p);
+        const double d = kmin * (dy * dy + dp * dp) / R2;
+        const double ey = eps * fmax(fmax(fabs(o[i].y), fabs(o[j].y)), 1.0), ep = eps * M_PI;
+        const double u = 1e-6 * d + kmin * (2.0 * fabs(dy) * ey + 2.0 * fabs(dp) * ep) / R2;
+        if (d < b) { s2 = b; su = bu; b = d; bu = u; bi = i; bj = j; }
+        else if (d < s2) { s2 = d; su = u; }
+      }
+    }
+    if (s2 - b <= bu + su) ++*n_marg;
+    if (bj < 0) {
+      /* i becomes a jet */
+      cl_obj* q = &o[bi];
+      q->active = 0;
+      --left;
+      const double pt = hypot(q->px, q->py);
+      if (pt >= pt_min && q->nconst >= nconst_min) {
+        or_jet* J = &jets[nj++];
+        J->px = q->px; J->py = q->py; J->pz = q->pz; J->e = q->e;
+        J->pt = pt;
+        J->eta = asinh(q->pz / pt);
+        J->phi = atan2(q->py, q->px);
+        const double m2 = q->e * q->e - (q->px * q->px + q->py * q->py + q->pz * q->pz);
+        J->mass = m2 > 0.0 ? sqrt(m2) : 0.0;
+        J->nconst = q->nconst;
+        J->pad = 0;
+      }
+    } else {
+      /* merge j into i (E-scheme) */
+      cl_obj* a = &o[bi];
+      cl_obj* c = &o[bj];
+      a->px += c->px; a->py += c->py; a->pz += c->pz; a->e += c->e;
+      a->nconst += c->nconst;
+      c->active = 0;
+      --left;
+      cl_derive(a, p);
+    }
+  }
+  free(o);
+  /* decreasing pT (insertion sort: stable, small counts) */
+  for (int32_t i = 1; i < nj; ++i) {
+    or_jet t = jets[i];
+    int32_t k = i - 1;
+    while (k >= 0 && jets[k].pt < t.pt) { jets[k + 1] = jets[k]; --k; }
+    jets[k + 1] = t;
+  }
+  return nj;
+}

@@ -257,6 +257,36 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
                              int32_t q, double x0, double y0, double z0, uint64_t seed, uint32_t event,
                              uint32_t idx, double out[4]);
 
+/* ---- jet clustering (Sec. 2.4: FastJet's generalized-kT family on the
+ * PFlow or truth collection; jet pT and constituent-count cuts) ----
+ * The sequential recombination written out (FastJet's algorithm is not
+ * copied; its definitions are textbook):
+ *   - objects i carry four-momenta (px, py, pz, E), rapidity
+ *     y = 0.5 ln((E + pz) / (E - pz)) and azimuth phi;
+ *   - d_iB = pt_i^(2p), d_ij = min(pt_i^(2p), pt_j^(2p)) dR_ij^2 / R^2 with
+ *     dR^2 = (y_i - y_j)^2 + dphi^2 (dphi wrapped into [-pi, pi]);
+ *     p = -1 anti-kT, 0 Cambridge/Aachen, 1 kT;
+ *   - repeatedly the smallest of all d_ij and d_iB over the active objects:
+ *     a d_ij merges i and j (E-scheme: four-momenta added), a d_iB makes i a
+ *     jet; ties go to the beam distance, then to the lower indices;
+ *   - jets with pT >= pt_min and at least nconst_min constituents are kept,
+ *     ordered by decreasing pT.
+ * A step is marginal when the runner-up distance (a different decision) lies
+ * within the float32 uncertainty of the two distances: 1e-6 relative, plus for
+ * pair distances min(pt^(2p)) (2 |dy| eps_y + 2 |dphi| eps_phi) / R^2 with
+ * eps_y = 2^-23 max(|y_i|, |y_j|, 1) and eps_phi = 2^-23 pi. */
+typedef struct or_jet {
+  double px, py, pz, e;
+  double pt, eta, phi, mass;
+  int32_t nconst, pad;
+} or_jet;
+
+/* Cluster n objects (four-momenta px, py, pz, e).  Writes the kept jets
+ * (at most n) and returns their number, or -1 for bad arguments; *n_marg
+ * counts the marginal steps. */
+int32_t oracle_cluster(int64_t n, const double* px, const double* py, const double* pz, const double* e,
+                       double p, double R, double pt_min, int32_t nconst_min, or_jet* jets, int32_t* n_marg);
+
 #ifdef __cplusplus
 }
 #endif

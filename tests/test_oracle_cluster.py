@@ -1,0 +1,126 @@
+"""Pins of the oracle's jet clustering (Sec. 2.4: FastJet's generalized-kT
+family, anti-kT by default, on the PFlow collection, with jet pT and
+constituent-count cuts).
+
+Expected values come from hand-worked events and from properties of the
+algorithms that do not restate the oracle's loop: four-momentum
+conservation, the kT algorithm with a radius spanning the whole acceptance
+(one jet: the event's total four-momentum), the anti-kT cone property
+(isolated hard particles absorb the soft particles around them), the
+Cambridge/Aachen two-particle threshold dR < R, and collinear safety.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _fm(pt, eta, phi, m=None):
+    pt, eta, phi = (np.asarray(x, np.float64) for x in (pt, eta, phi))
+    m = np.zeros_like(pt) if m is None else np.asarray(m, np.float64)
+    e = np.sqrt((pt * np.cosh(eta)) ** 2 + m ** 2)
+    return oracle.four_momenta(pt, eta, phi, e)
+
+
+def _random_event(rng, n):
+    pt = 0.5 * (1 - rng.random(n)) ** (-1 / 2.5)
+    eta = rng.uniform(-4, 4, n)
+    phi = rng.uniform(-math.pi, math.pi, n)
+    m = rng.choice([0.0, 0.13957, 0.49368], n)
+    return _fm(pt, eta, phi, m)
+
+
+def test_hand_worked_event():
+    """Two massless particles at dR = 0.1 (pT 10 and 20) and a third 2 units
+    away: anti-kT R = 0.4 gives the pair, then the loner.  The pair's mass is
+    sqrt(2 pT1 pT2 (cosh 0.1 - 1)) = 1.414803."""
+    jets, marg = oracle.cluster(*_fm([10, 20, 5], [0, 0.1, 2], [0, 0, 1]), p=-1, R=0.4)
+    assert marg == 0 and len(jets) == 2
+    assert jets[0]["pt"] == pytest.approx(30.0, abs=1e-12) and jets[0]["nconst"] == 2
+    assert jets[0]["mass"] == pytest.approx(math.sqrt(400 * (math.cosh(0.1) - 1)), rel=1e-9)
+    assert jets[0]["eta"] == pytest.approx(math.asinh(20 * math.sinh(0.1) / 30), rel=1e-12)
+    assert jets[1]["pt"] == pytest.approx(5.0, abs=1e-12) and jets[1]["eta"] == pytest.approx(2.0, abs=1e-12)
+    # pT and constituent cuts
+    assert len(oracle.cluster(*_fm([10, 20, 5], [0, 0.1, 2], [0, 0, 1]), p=-1, R=0.4, pt_min=6)[0]) == 1
+    assert len(oracle.cluster(*_fm([10, 20, 5], [0, 0.1, 2], [0, 0, 1]), p=-1, R=0.4, nconst_min=2)[0]) == 1
+
+
+@pytest.mark.parametrize("p", [-1.0, 0.0, 1.0])
+def test_four_momentum_is_conserved(p):
+    rng = np.random.default_rng(int(10 + p))
+    fm = _random_event(rng, 120)
+    jets, _ = oracle.cluster(*fm, p=p, R=0.5)
+    for k, key in enumerate(("px", "py", "pz", "e")):
+        assert jets[key].sum() == pytest.approx(fm[k].sum(), rel=1e-10, abs=1e-9)
+    assert jets["nconst"].sum() == 120
+    assert np.all(np.diff(jets["pt"]) <= 0)
+
+
+def test_kt_with_a_radius_spanning_everything_gives_one_jet():
+    """|y| < 4 and |dphi| <= pi: every dR^2 < 64 + pi^2 < R^2 for R = 9, so
+    d_ij < d_iB for every pair and all objects end in one jet."""
+    rng = np.random.default_rng(3)
+    fm = _random_event(rng, 60)
+    jets, _ = oracle.cluster(*fm, p=1.0, R=9.0)
+    assert len(jets) == 1 and jets[0]["nconst"] == 60
+    assert jets[0]["pt"] == pytest.approx(math.hypot(fm[0].sum(), fm[1].sum()), rel=1e-12)
+
+
+def test_anti_kt_cones_around_isolated_hard_particles():
+    """Hard particles (pT 100) 2 units apart; soft ones (pT <= 1) within
+    R / 2 of one hard particle each: every jet is one hard particle plus its
+    soft neighbours (the textbook cone property of anti-kT)."""
+    rng = np.random.default_rng(5)
+    hard_eta = np.array([-2.0, 0.0, 2.0])
+    hard_phi = np.array([0.0, 2.0, -2.0])
+    pt, eta, phi, owner = list(100.0 + 10 * np.arange(3)), list(hard_eta), list(hard_phi), [0, 1, 2]
+    for h in range(3):
+        for _ in range(15):
+            r, a = 0.2 * math.sqrt(rng.random()), rng.uniform(0, 2 * math.pi)
+            pt.append(rng.uniform(0.1, 1.0)); eta.append(hard_eta[h] + r * math.cos(a))
+            phi.append(hard_phi[h] + r * math.sin(a)); owner.append(h)
+    fm = _fm(pt, eta, phi)
+    jets, marg = oracle.cluster(*fm, p=-1.0, R=0.4)
+    assert len(jets) == 3 and marg == 0
+    owner = np.array(owner)
+    for h in range(3):
+        sel = owner == h
+        j = jets[2 - h]   # ordered by decreasing pT: the hardest seed is h = 2
+        assert j["nconst"] == 16
+        for k, key in enumerate(("px", "py", "pz", "e")):
+            assert j[key] == pytest.approx(fm[k][sel].sum(), rel=1e-12)
+
+
+def test_cambridge_pair_threshold():
+    """p = 0: d_ij = dR^2 / R^2 against d_iB = 1, so two particles merge iff
+    dR < R."""
+    for dr, merged in ((0.39, True), (0.41, False)):
+        jets, _ = oracle.cluster(*_fm([5, 7], [0.3, 0.3 + dr], [1.0, 1.0]), p=0.0, R=0.4)
+        assert (len(jets) == 1) == merged
+
+
+@pytest.mark.parametrize("p", [-1.0, 0.0, 1.0])
+def test_collinear_safety(p):
+    """Splitting one particle into two collinear halves leaves the jets."""
+    rng = np.random.default_rng(8)
+    pt = 0.5 * (1 - rng.random(40)) ** (-1 / 2.5)
+    eta = rng.uniform(-3, 3, 40)
+    phi = rng.uniform(-math.pi, math.pi, 40)
+    base, _ = oracle.cluster(*_fm(pt, eta, phi), p=p, R=0.5)
+    k = int(np.argmax(pt))
+    pt2 = np.concatenate([pt, [0.5 * pt[k]]])
+    pt2[k] *= 0.5
+    split, _ = oracle.cluster(*_fm(pt2, np.concatenate([eta, [eta[k]]]), np.concatenate([phi, [phi[k]]])),
+                              p=p, R=0.5)
+    assert len(split) == len(base)
+    for key in ("px", "py", "pz", "e"):
+        assert np.allclose(np.sort(split[key]), np.sort(base[key]), rtol=1e-10, atol=1e-9)
+
+
+def test_symmetric_configuration_is_marginal():
+    """Two equal particles at the same distance from a third: the first merge
+    is a tie, which the oracle reports as marginal."""
+    jets, marg = oracle.cluster(*_fm([10, 3, 3], [0.0, 0.2, -0.2], [0.0, 0.0, 0.0]), p=-1.0, R=0.4)
+    assert marg >= 1 and len(jets) == 1
