@@ -311,6 +311,8 @@ def bench_ours(args, dist, rank, ws):
     }
     if not args.no_track_ip:
         line["track_ip"] = bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts)
+    if not args.no_jets:
+        line["jets"] = bench_jets(args, B, ctx, bt, ob, n_ev, n_p, counts)
     if not args.no_postprocess:
         line["postprocess"] = bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts)
     if not args.no_serving and ws == 1:
@@ -414,6 +416,37 @@ def bench_serving(args, B, ctx):
             "per_request_p50_ms": float(np.percentile(lat, 50)), "per_request_p99_ms": float(np.percentile(lat, 99)),
             "per_request_particles_per_s": parts / span if span > 0 else None}
     return out
+
+
+def bench_jets(args, B, ctx, bt, ob, n_ev, n_p, counts):
+    """Anti-kT jets (R = 0.5, pT > 10 GeV, >= 2 constituents: the paper's
+    PFlowJetsAntiKt05 pipeline) of the response's PFlow objects."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    jets = torch.empty((n_p, 8), dtype=torch.float32, device="cuda")
+    jc = torch.empty((n_ev,), dtype=torch.int32, device="cuda")
+    prm = B.make_jet_params("pflow", "antikt", 0.5, 10.0, 2)
+    reps = max(2, args.steps // 5)
+    ctx.cluster_jets(bt, ob, prm, jets, jc)
+    torch.cuda.synchronize()
+    ctx.check()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.cluster_jets(bt, ob, prm, jets, jc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    ctx.check()
+    sec = statistics.mean(times)
+    n_obj = int(counts[:, 0].sum() + counts[:, 2].sum())
+    n_jets = int(jc.sum().item())
+    return {"algorithm": "anti-kT R = 0.5, pT >= 10 GeV, >= 2 constituents", "events": n_ev, "objects": n_obj,
+            "jets": n_jets, "ms": sec * 1e3, "events_per_s": n_ev / sec, "objects_per_s": n_obj / sec,
+            "bound": "issue (O(n^2) neighbour searches in shared memory per event; no DRAM roofline)",
+            "reps": reps}
 
 
 def bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts):
@@ -686,6 +719,7 @@ def main(argv=None):
     ap.add_argument("--no-pileup-merge", action="store_true")
     ap.add_argument("--no-postprocess", action="store_true")
     ap.add_argument("--no-track-ip", action="store_true")
+    ap.add_argument("--no-jets", action="store_true")
     ap.add_argument("--merge-only", action="store_true",
                     help="time only the pile-up merge (and the merged batch's response); prints that object")
     ap.add_argument("--pileup-events", type=int, default=10_000, help="hard events of the pile-up merge")

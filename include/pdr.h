@@ -439,6 +439,46 @@ typedef struct { float d0, z0, sigma_d0, sigma_z0; } pdr_ip;   /* m */
 int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_ip_params* params,
                  pdr_ip* ip, void* stream);
 
+/* ---------------------------------------------------------- jet clustering -- */
+/* Sec. 2.4: jets from the PFlow (or truth) collection with the generalized-kT
+ * family (anti-kT p = -1 by default, Cambridge/Aachen p = 0, kT p = 1, any
+ * p), jet radius R, and cuts pT >= pt_min and at least nconst_min
+ * constituents.  Sequential recombination: repeatedly the smallest of
+ * d_iB = pT_i^(2p) and d_ij = min(pT_i^(2p), pT_j^(2p)) dR_ij^2 / R^2
+ * (dR in rapidity and azimuth) over the remaining objects; a pair merges by
+ * four-momentum addition, a beam distance makes a jet.  Jets are ordered by
+ * decreasing pT.  PFlow objects are the energy-flow tracks (smeared pT,
+ * momentum direction, the generated particle's mass) and the energy-flow
+ * neutrals (massless, E = dE at the tower centre); truth objects are the
+ * generated particles except neutrinos (|pdg| 12, 14, 16). */
+#define PDR_JETS_PFLOW 0
+#define PDR_JETS_TRUTH 1
+
+typedef struct pdr_jet_params {
+  uint32_t collection;            /* PDR_JETS_*                               */
+  uint32_t nconst_min;            /* keep jets with at least this many objects */
+  double p;                       /* -1 anti-kT, 0 Cambridge/Aachen, 1 kT      */
+  double R;                       /* jet radius (> 0, <= 10)                   */
+  double pt_min;                  /* GeV                                       */
+} pdr_jet_params;
+
+typedef struct {
+  float pt, eta, phi, mass;       /* GeV, pseudorapidity, azimuth, GeV          */
+  float e;                        /* GeV                                        */
+  uint32_t nconst;
+  uint32_t pad[2];
+} pdr_jet;
+
+/* Clusters every event of `batch` (for PDR_JETS_PFLOW: the outputs `out` that
+ * pdr_run wrote from it; out may be NULL for truth).  jets: DEVICE, slot
+ * layout (event e's k-th jet at [offsets[e] + k]; at most as many jets as
+ * the event has particles); jet_counts [n_events] DEVICE.  Each event is
+ * clustered by one warp with its objects in shared memory; PDR_EOVERFLOW if
+ * an event has more objects than fit (about 3,800).  Synchronises `stream`
+ * once to size the shared memory, then runs asynchronously. */
+int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_jet_params* params,
+                     pdr_jet* jets, uint32_t* jet_counts, void* stream);
+
 /* ------------------------------------------------------- allocation-free run -- */
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that may not allocate device memory when they run the response:

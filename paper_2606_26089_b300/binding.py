@@ -144,6 +144,21 @@ def make_ip_params(resolution=IP_RESOLUTION, vx=None, vy=None) -> pdr_ip_params:
     return pdr_ip_params(*[float(x) for x in resolution], _ptr(vx), _ptr(vy))
 
 
+class pdr_jet_params(C.Structure):
+    _fields_ = [("collection", C.c_uint32), ("nconst_min", C.c_uint32), ("p", C.c_double), ("R", C.c_double),
+                ("pt_min", C.c_double)]
+
+
+JET_ALGORITHMS = {"antikt": -1.0, "cambridge": 0.0, "kt": 1.0}
+
+
+def make_jet_params(collection: str = "pflow", algorithm: str = "antikt", R: float = 0.5, pt_min: float = 0.0,
+                    nconst_min: int = 1, p: Optional[float] = None) -> pdr_jet_params:
+    """Clustering pipeline parameters (collection, algorithm or exponent p, dr, pt_min, nconst_min)."""
+    return pdr_jet_params({"pflow": 0, "truth": 1}[collection], int(nconst_min),
+                          float(JET_ALGORITHMS[algorithm] if p is None else p), float(R), float(pt_min))
+
+
 class pdr_features(C.Structure):
     _fields_ = [("ht", C.c_float), ("met_x", C.c_float), ("met_y", C.c_float), ("met", C.c_float)]
 
@@ -218,6 +233,8 @@ def lib():
             "pdr_pileup_merge": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(pdr_particles), P], I),
             "pdr_postprocess": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_filter), P, P], I),
             "pdr_track_ip": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_ip_params), P, P], I),
+            "pdr_cluster_jets": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_jet_params), P, P,
+                                  P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -479,6 +496,16 @@ class Context:
         float32 tensor [n_particles, 4], slot layout parallel to the tracks)."""
         self._check(self.L.pdr_track_ip(self.h, C.byref(batch), C.byref(out), C.byref(params), _ptr(ip),
                                         self._stream(stream)), "pdr_track_ip")
+
+    # ---- jet clustering
+    def cluster_jets(self, batch: pdr_batch, out: Optional[pdr_outputs], params: pdr_jet_params, jets, jet_counts,
+                     stream=None):
+        """Jets into `jets` (device float32 tensor [n_particles, 8]: pt, eta, phi,
+        mass, e, nconst (as uint32), pad, pad; slot layout) and `jet_counts`
+        (device int32 [n_events])."""
+        self._check(self.L.pdr_cluster_jets(self.h, C.byref(batch), C.byref(out) if out is not None else None,
+                                            C.byref(params), _ptr(jets), _ptr(jet_counts), self._stream(stream)),
+                    "pdr_cluster_jets")
 
     # ---- serving
     def serve_start(self, max_inflight_waves=0, max_wave_requests=0, max_wave_particles=0, use_graphs=1):

@@ -230,6 +230,31 @@ struct IPParams {
   uint32_t rk[20];                   // Philox round keys of the batch's seed
 };
 
+// Jet clustering.
+struct JetParams {
+  uint64_t n_events;
+  const uint64_t* offsets;
+  const float *pt, *eta, *phi, *mass;   // generated particles
+  const int32_t* pdg;
+  const pdr_track* tracks;              // PFlow
+  const pdr_eflow* eflow;
+  const uint32_t* counts;
+  const float2* centres;
+  uint32_t ntowers[2];
+  uint32_t collection, nconst_min;
+  uint32_t cap;                         // objects per warp workspace (multiple of 32)
+  uint32_t warps;                       // warps per block
+  float p, R2, inv_R2, pt_min;
+  pdr_jet* jets;
+  uint32_t* jet_counts;
+  uint32_t* err;
+};
+
+// Bytes of one warp's clustering workspace for `cap` objects: double px, py,
+// E + pz, E - pz; float y, phi, pT^2p, nearest-neighbour dR^2 and distance;
+// int nearest neighbour and constituent count.
+PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap) { return (uint64_t)cap * (4 * 8 + 5 * 4 + 2 * 4); }
+
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {
   uint64_t n_events;                 // all segments

@@ -1,0 +1,342 @@
+// Jet clustering (sm_103a; Sec. 2.4): the generalized-kT family by
+// sequential recombination, one warp per event with the event's objects in
+// shared memory.  The definitions are documented with pdr_cluster_jets in
+// the C header.
+//
+// Search: the smallest d_ij over all pairs is always reached at a pair whose
+// second member is a geometric nearest neighbour (in dR) of the first (if i's
+// nearest neighbour m is closer than j, then d_im <= pT_i^2p dR_im^2 / R^2 <
+// d_ij whenever pT_i^2p <= pT_j^2p), and a pair at dR >= R never beats the
+// beam distance of its member with the smaller pT^2p.  So each object keeps
+// its nearest neighbour within R and the distance min(d_iB, d_i,nn); a step
+// takes the smallest of those (a warp argmin), merges or makes a jet, and
+// re-searches only the objects whose neighbour was involved.
+//
+// Precision: four-momenta are kept as double (px, py, E + pz, E - pz); the
+// light-cone components are sums of positive terms, so the rapidity
+// y = ln((E + pz) / (E - pz)) / 2 of a merged object carries no cancellation
+// even far forward.  Distances are float32.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdr_internal.h"
+#include "pdr_math.cuh"
+
+namespace pdr {
+
+namespace {
+
+struct WS {
+  double *px, *py, *ap, *am;
+  float *y, *phi, *k2p, *nnr2, *dist;
+  int32_t *nn, *nc;   // nc > 0: active with nc constituents; < 0: a jet of -nc; 0: merged away
+};
+
+__device__ __forceinline__ WS carve(unsigned char* base, uint32_t cap) {
+  WS w;
+  double* d = reinterpret_cast<double*>(base);
+  w.px = d;
+  w.py = d + cap;
+  w.ap = d + 2 * cap;
+  w.am = d + 3 * cap;
+  float* f = reinterpret_cast<float*>(d + 4 * cap);
+  w.y = f;
+  w.phi = f + cap;
+  w.k2p = f + 2 * cap;
+  w.nnr2 = f + 3 * cap;
+  w.dist = f + 4 * cap;
+  int32_t* q = reinterpret_cast<int32_t*>(f + 5 * cap);
+  w.nn = q;
+  w.nc = q + cap;
+  return w;
+}
+
+__device__ __forceinline__ float kt2p_of(float pt2, float p) {
+  if (p == -1.0f) return 1.0f / pt2;
+  if (p == 0.0f) return 1.0f;
+  if (p == 1.0f) return pt2;
+  return powf(pt2, p);
+}
+
+__device__ __forceinline__ float dr2(const WS& w, uint32_t i, float yk, float pk) {
+  const float dy = w.y[i] - yk;
+  float dp = fabsf(w.phi[i] - pk);
+  if (dp > 3.14159265f) dp = 6.28318531f - dp;
+  return fmaf(dy, dy, dp * dp);
+}
+
+// min(d_iB, d_i,nn) of object k from its neighbour record (NaN read as +inf,
+// so that every comparison below is a total order).
+__device__ __forceinline__ float dist_of(const WS& w, uint32_t k, float inv_R2) {
+  const float dB = w.k2p[k];
+  const int32_t m = w.nn[k];
+  float d = dB;
+  if (m >= 0) {
+    const float dJ = fminf(dB, w.k2p[m]) * w.nnr2[k] * inv_R2;
+    d = dJ < dB ? dJ : dB;
+  }
+  return d <= INFINITY ? d : INFINITY;
+}
+
+// Nearest neighbour within R of object k, searched by the whole warp.
+__device__ __forceinline__ void rescan(const WS& w, uint32_t n, uint32_t k, float R2, uint32_t lane) {
+  const float yk = w.y[k], pk = w.phi[k];
+  float best = R2;
+  int32_t bi = -1;
+  for (uint32_t l = lane; l < n; l += 32u) {
+    if (l == k || w.nc[l] <= 0) continue;
+    const float d = dr2(w, l, yk, pk);
+    if (d < best) { best = d; bi = (int32_t)l; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float od = __shfl_xor_sync(PDR_FULL, best, o);
+    const int32_t oi = __shfl_xor_sync(PDR_FULL, bi, o);
+    if (od < best || (od == best && oi >= 0 && (bi < 0 || oi < bi))) { best = od; bi = oi; }
+  }
+  if (lane == 0) {
+    w.nn[k] = bi;
+    w.nnr2[k] = best;
+  }
+}
+
+// Loads the event's objects into the workspace; returns their number.
+__device__ __forceinline__ uint32_t load_objects(const JetParams& p, const WS& w, uint64_t a, uint64_t n_part,
+                                                 uint32_t c0, uint32_t c2, uint32_t lane) {
+  uint32_t n = 0;
+  auto put = [&](uint32_t k, float pt, float eta, float phi, float m) {
+    float sp, cp;
+    sincosf(phi, &sp, &cp);
+    const float mt = m > 0.0f ? sqrtf(fmaf(pt, pt, m * m)) : pt;
+    const float y = m > 0.0f ? asinhf(pt * sinhf(eta) / mt) : eta;
+    w.px[k] = (double)(pt * cp);
+    w.py[k] = (double)(pt * sp);
+    w.ap[k] = (double)(mt * expf(y));
+    w.am[k] = (double)(mt * expf(-y));
+    w.y[k] = y;
+    w.phi[k] = phi;
+    w.k2p[k] = kt2p_of(pt * pt, p.p);
+    w.nc[k] = 1;
+  };
+  if (p.collection == PDR_JETS_PFLOW) {
+    n = c0 + c2;
+    for (uint32_t k = lane; k < n; k += 32u) {
+      if (k < c0) {
+        const pdr_track t = p.tracks[a + k];
+        const float m = t.idx < n_part ? __ldg(p.mass + a + t.idx) : 0.0f;
+        put(k, t.pt, t.eta, t.phi, m);
+      } else {
+        const pdr_eflow f = p.eflow[a + (k - c0)];
+        const uint32_t calo = f.key >> 24, id = f.key & 0x00FFFFFFu;
+        float2 c = make_float2(0.0f, 0.0f);
+        if (calo <= 1 && id < p.ntowers[calo]) c = __ldg(p.centres + (calo ? p.ntowers[0] : 0u) + id);
+        else atomicOr(p.err, ERR_CSR);
+        put(k, f.et, c.x, c.y, 0.0f);
+      }
+    }
+  } else {
+    // generated particles except neutrinos, compacted in input order
+    for (uint64_t b = 0; b < n_part; b += 32u) {
+      const uint64_t i = b + lane;
+      bool vis = false;
+      if (i < n_part) {
+        const int32_t id = abs(__ldg(p.pdg + a + i));
+        vis = id != 12 && id != 14 && id != 16;
+      }
+      const uint32_t m = __ballot_sync(PDR_FULL, vis);
+      if (vis) {
+        const uint32_t k = n + __popc(m & ((1u << lane) - 1u));
+        put(k, __ldg(p.pt + a + i), __ldg(p.eta + a + i), __ldg(p.phi + a + i), __ldg(p.mass + a + i));
+      }
+      n += __popc(m);
+    }
+  }
+  return n;
+}
+
+__global__ void __launch_bounds__(256) cluster_kernel(const __grid_constant__ JetParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap), p.cap);
+  const uint64_t w0 = (uint64_t)blockIdx.x * p.warps + wib;
+  const uint64_t nw = (uint64_t)gridDim.x * p.warps;
+  const float R2 = p.R2, inv_R2 = p.inv_R2;
+  for (uint64_t e = w0; e < p.n_events; e += nw) {
+    const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
+    uint32_t c0 = 0, c2 = 0;
+    if (p.collection == PDR_JETS_PFLOW) {
+      c0 = p.counts[4 * e];
+      c2 = p.counts[4 * e + 2];
+    }
+    const uint64_t n_part = b - a;
+    const uint64_t n_obj = p.collection == PDR_JETS_PFLOW ? (uint64_t)c0 + c2 : n_part;
+    if (b < a || c0 > n_part || c2 > n_part || n_obj > p.cap) {
+      if (lane == 0) {
+        atomicOr(p.err, ERR_CSR);
+        p.jet_counts[e] = 0;
+      }
+      continue;
+    }
+    const uint32_t n = load_objects(p, w, a, n_part, c0, c2, lane);
+    __syncwarp();
+    // initial nearest neighbours (each lane searches for its own objects)
+    for (uint32_t k = lane; k < n; k += 32u) {
+      const float yk = w.y[k], pk = w.phi[k];
+      float best = R2;
+      int32_t bi = -1;
+      for (uint32_t l = 0; l < n; ++l) {
+        if (l == k) continue;
+        const float d = dr2(w, l, yk, pk);
+        if (d < best) { best = d; bi = (int32_t)l; }
+      }
+      w.nn[k] = bi;
+      w.nnr2[k] = best;
+    }
+    __syncwarp();
+    for (uint32_t k = lane; k < n; k += 32u) w.dist[k] = dist_of(w, k, inv_R2);
+    __syncwarp();
+    for (uint32_t left = n; left > 0; --left) {
+      // the smallest distance (ties: the lower index)
+      float bd = INFINITY;
+      int32_t bk = -1;
+      for (uint32_t k = lane; k < n; k += 32u)
+        if (w.nc[k] > 0 && (bk < 0 || w.dist[k] < bd)) { bd = w.dist[k]; bk = (int32_t)k; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float od = __shfl_xor_sync(PDR_FULL, bd, o);
+        const int32_t ok = __shfl_xor_sync(PDR_FULL, bk, o);
+        if (od < bd || (od == bd && ok >= 0 && (bk < 0 || ok < bk))) { bd = od; bk = ok; }
+      }
+      const uint32_t i = (uint32_t)bk;
+      const int32_t j = w.nn[i];
+      const float dB = w.k2p[i];
+      const bool merge = j >= 0 && fminf(dB, w.k2p[j]) * w.nnr2[i] * inv_R2 < dB;
+      const uint32_t ma = merge ? min(i, (uint32_t)j) : i, mb = merge ? max(i, (uint32_t)j) : i;
+      __syncwarp();
+      if (lane == 0) {
+        if (merge) {
+          w.px[ma] += w.px[mb];
+          w.py[ma] += w.py[mb];
+          w.ap[ma] += w.ap[mb];
+          w.am[ma] += w.am[mb];
+          w.nc[ma] += w.nc[mb];
+          w.nc[mb] = 0;
+          const double px = w.px[ma], py = w.py[ma];
+          w.y[ma] = 0.5f * logf((float)(w.ap[ma] / w.am[ma]));
+          w.phi[ma] = atan2f((float)py, (float)px);
+          w.k2p[ma] = kt2p_of((float)(px * px + py * py), p.p);
+        } else {
+          w.nc[i] = -w.nc[i];
+        }
+      }
+      __syncwarp();
+      if (left == 1) break;
+      // neighbour records: re-search the objects whose neighbour took part
+      for (uint32_t t = 0; t < n; t += 32u) {
+        const uint32_t k = t + lane;
+        bool need = false;
+        if (k < n && w.nc[k] > 0) {
+          const int32_t m = w.nn[k];
+          need = m == (int32_t)i || (merge && (m == j || k == ma));
+          if (!need && merge) {
+            const float d = dr2(w, ma, w.y[k], w.phi[k]);
+            if (d < w.nnr2[k]) {
+              w.nn[k] = (int32_t)ma;
+              w.nnr2[k] = d;
+            }
+            if (w.nn[k] == (int32_t)ma) w.dist[k] = dist_of(w, k, inv_R2);
+          }
+        }
+        uint32_t todo = __ballot_sync(PDR_FULL, need);
+        while (todo) {
+          const uint32_t kk = t + (uint32_t)(__ffs(todo) - 1);
+          todo &= todo - 1u;
+          rescan(w, n, kk, R2, lane);
+          __syncwarp();
+          if (lane == 0) w.dist[kk] = dist_of(w, kk, inv_R2);
+          __syncwarp();
+        }
+      }
+      __syncwarp();
+    }
+    // jets: the objects marked by a beam distance, cut, ordered by decreasing pT
+    uint32_t m = 0;
+    for (uint32_t t = 0; t < n; t += 32u) {
+      const uint32_t k = t + lane;
+      bool keep = false;
+      float pt = 0.0f;
+      if (k < n && w.nc[k] < 0) {
+        const double px = w.px[k], py = w.py[k];
+        pt = (float)sqrt(px * px + py * py);
+        keep = pt >= p.pt_min && (uint32_t)(-w.nc[k]) >= p.nconst_min;
+      }
+      const uint32_t mask = __ballot_sync(PDR_FULL, keep);
+      __syncwarp();
+      if (keep) {
+        const uint32_t slot = m + __popc(mask & ((1u << lane) - 1u));
+        w.nn[slot] = (int32_t)k;      // the neighbour array is free now: jet list
+        w.nnr2[slot] = pt;
+      }
+      m += __popc(mask);
+      __syncwarp();
+    }
+    __syncwarp();
+    for (uint32_t s = lane; s < m; s += 32u) {
+      const float pts = w.nnr2[s];
+      uint32_t rank = 0;
+      for (uint32_t o = 0; o < m; ++o) {
+        const float po = w.nnr2[o];
+        rank += (po > pts || (po == pts && o < s)) ? 1u : 0u;
+      }
+      const uint32_t k = (uint32_t)w.nn[s];
+      const double px = w.px[k], py = w.py[k], ap = w.ap[k], am = w.am[k];
+      const double pt = sqrt(px * px + py * py), pz = 0.5 * (ap - am), en = 0.5 * (ap + am);
+      const double m2 = ap * am - pt * pt;
+      pdr_jet J;
+      J.pt = (float)pt;
+      J.eta = (float)asinh(pz / pt);
+      J.phi = atan2f((float)py, (float)px);
+      J.mass = m2 > 0.0 ? (float)sqrt(m2) : 0.0f;
+      J.e = (float)en;
+      J.nconst = (uint32_t)(-w.nc[k]);
+      J.pad[0] = J.pad[1] = 0u;
+      if (rank < n_part) p.jets[a + rank] = J;   // the event's slots hold n_part records
+    }
+    if (lane == 0) {
+      if (m > n_part) atomicOr(p.err, ERR_OVERSIZE);
+      p.jet_counts[e] = (uint32_t)min((uint64_t)m, n_part);
+    }
+    __syncwarp();
+  }
+}
+
+// Largest number of clustering objects of an event.
+__global__ void jet_max_objects_kernel(JetParams p, uint32_t* out) {
+  uint32_t mx = 0;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < p.n_events;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t n = p.offsets[e + 1] - p.offsets[e];
+    const uint64_t v = p.collection == PDR_JETS_PFLOW ? (uint64_t)p.counts[4 * e] + p.counts[4 * e + 2] : n;
+    mx = max(mx, (uint32_t)min(v, (uint64_t)0xFFFFFFFFu));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(PDR_FULL, mx, o));
+  if ((threadIdx.x & 31u) == 0) atomicMax(out, mx);
+}
+
+}  // namespace
+
+cudaError_t launch_jet_max_objects(const JetParams& p, uint32_t* out, cudaStream_t s) {
+  const uint64_t blocks = p.n_events / 256 + 1;
+  jet_max_objects_kernel<<<(unsigned)(blocks < 1184 ? blocks : 1184), 256, 0, s>>>(p, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cluster(const JetParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cluster_kernel<<<grid, p.warps * 32u, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace pdr

@@ -32,6 +32,8 @@ cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_
 cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_postprocess(const PostParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_track_ip(const IPParams& p, int n_sms, cudaStream_t s);
+cudaError_t launch_jet_max_objects(const JetParams& p, uint32_t* out, cudaStream_t s);
+cudaError_t launch_cluster(const JetParams& p, uint32_t grid, size_t smem, cudaStream_t s);
 cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
                          uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
@@ -1806,5 +1808,60 @@ extern "C" int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs*
   p.a_z0 = (float)ipp->a_z0; p.b_z0 = (float)ipp->b_z0;
   fill_round_keys(p.rk, b->seed);
   PDR_CUDA(launch_track_ip(p, ctx->n_sms, (cudaStream_t)stream), "impact-parameter launch");
+  return PDR_OK;
+}
+
+// ============================================================ jet clustering
+extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_jet_params* jp,
+                                pdr_jet* jets, uint32_t* jet_counts, void* stream) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if (!jp || !jets || !jet_counts) return fail(PDR_EINVAL, "null parameters or jet arrays");
+  if (jp->collection > PDR_JETS_TRUTH) return fail(PDR_EINVAL, "unknown jet collection");
+  if (jp->collection == PDR_JETS_PFLOW && (!o || !o->tracks || !o->eflow || !o->counts))
+    return fail(PDR_EINVAL, "PFlow jets need the response's tracks, EFlow neutrals and counts");
+  if (!(jp->R > 0.0) || !(jp->R <= 10.0)) return fail(PDR_EINVAL, "jet radius must be in (0, 10]");
+  if (!std::isfinite(jp->p) || !(jp->pt_min >= 0.0) || !std::isfinite(jp->pt_min))
+    return fail(PDR_EINVAL, "bad clustering exponent or pT cut");
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (b->n_events == 0) return PDR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const CardEntry& ce = ctx->cards[b->card_id];
+  JetParams p;
+  std::memset(&p, 0, sizeof p);
+  p.n_events = b->n_events;
+  p.offsets = b->offsets;
+  p.pt = b->pt; p.eta = b->eta; p.phi = b->phi; p.mass = b->mass; p.pdg = b->pdg;
+  if (o) { p.tracks = o->tracks; p.eflow = o->eflow; p.counts = o->counts; }
+  p.centres = ce.centres;
+  p.ntowers[0] = ce.ntowers[0];
+  p.ntowers[1] = ce.ntowers[1];
+  p.collection = jp->collection;
+  p.nconst_min = jp->nconst_min;
+  p.p = (float)jp->p;
+  p.R2 = (float)(jp->R * jp->R);
+  p.inv_R2 = (float)(1.0 / (jp->R * jp->R));
+  p.pt_min = (float)jp->pt_min;
+  p.jets = jets;
+  p.jet_counts = jet_counts;
+  p.err = ctx->d_err;
+  // size the per-warp workspace from the largest event
+  PDR_CUDA(cudaMemsetAsync(ctx->d_word, 0, 4, s), "memset");
+  PDR_CUDA(launch_jet_max_objects(p, ctx->d_word, s), "jet sizing kernel");
+  PDR_CUDA(cudaMemcpyAsync(ctx->h_word, ctx->d_word, 4, cudaMemcpyDeviceToHost, s), "copy size");
+  PDR_CUDA(cudaStreamSynchronize(s), "sync");
+  const uint32_t max_n = *ctx->h_word;
+  const uint32_t cap = std::max<uint32_t>(32u, (max_n + 31u) & ~31u);
+  const uint64_t ws = jet_ws_bytes(cap);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+  if (ws > (uint64_t)smem_max) return fail(PDR_EOVERFLOW, "event has more clustering objects than fit in shared memory");
+  p.cap = cap;
+  p.warps = (uint32_t)std::min<uint64_t>(8, (uint64_t)smem_max / ws);
+  const size_t smem = (size_t)(p.warps * ws);
+  const uint64_t blocks = (b->n_events + p.warps - 1) / p.warps;
+  const uint64_t cap_blocks = (uint64_t)ctx->n_sms * 32;
+  PDR_CUDA(launch_cluster(p, (uint32_t)std::min(blocks, cap_blocks), smem, s), "clustering launch");
   return PDR_OK;
 }

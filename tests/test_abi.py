@@ -42,7 +42,7 @@ def test_abi_version(libpdr):
 
 STRUCTS = ("pdr_card", "pdr_batch", "pdr_outputs", "pdr_launch", "pdr_options", "pdr_result",
            "pdr_serve_options", "pdr_serve_stats", "pdr_pileup", "pdr_particles", "pdr_condition",
-           "pdr_filter", "pdr_features", "pdr_ip_params")
+           "pdr_filter", "pdr_features", "pdr_ip_params", "pdr_jet_params")
 
 
 def test_binding_structs_match_header_layout(tmp_path):
@@ -66,7 +66,7 @@ def test_binding_structs_match_header_layout(tmp_path):
             assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, (s, f)
     # record layouts the binding views as float32 columns
     for rec, size in (("pdr_track", 16), ("pdr_tower", 12), ("pdr_eflow", 12), ("pdr_cand", 16),
-                      ("pdr_iso", 8), ("pdr_debug", 16), ("pdr_ip", 16)):
+                      ("pdr_iso", 8), ("pdr_debug", 16), ("pdr_ip", 16), ("pdr_jet", 32)):
         probe = tmp_path / f"{rec}.c"
         probe.write_text(f'#include "pdr.h"\nint x[sizeof({rec}) == {size} ? 1 : -1];\n')
         subprocess.check_call(["gcc", "-c", "-I", os.path.join(ROOT, "include"), str(probe), "-o",
