@@ -474,8 +474,11 @@ typedef struct {
  * layout (event e's k-th jet at [offsets[e] + k]; at most as many jets as
  * the event has particles); jet_counts [n_events] DEVICE.  Each event is
  * clustered by one warp with its objects in shared memory; PDR_EOVERFLOW if
- * an event has more objects than fit (about 3,800).  Synchronises `stream`
- * once to size the shared memory, then runs asynchronously. */
+ * an event has more objects than fit (about 7,000).  Synchronises `stream`
+ * once to size the shared memory, then runs asynchronously.  Calls on one
+ * context share its clustering scratch (four-momenta in device memory, grown
+ * on demand): do not overlap two clusterings of one context on different
+ * streams. */
 int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_jet_params* params,
                      pdr_jet* jets, uint32_t* jet_counts, void* stream);
 

@@ -243,17 +243,26 @@ struct JetParams {
   uint32_t ntowers[2];
   uint32_t collection, nconst_min;
   uint32_t cap;                         // objects per warp workspace (multiple of 32)
+  uint32_t min_obj;                     // this launch clusters events with min_obj..cap objects
   uint32_t warps;                       // warps per block
   float p, R2, inv_R2, pt_min;
+  int32_t nty, ntp;                     // rapidity x azimuth tiles, each at least R wide
+  float y0, inv_wy, inv_wp;
   pdr_jet* jets;
   uint32_t* jet_counts;
   uint32_t* err;
+  double* scratch;                      // four-momenta: 4 x cap doubles for each warp of the grid
 };
 
-// Bytes of one warp's clustering workspace for `cap` objects: double px, py,
-// E + pz, E - pz; float y, phi, pT^2p, nearest-neighbour dR^2 and distance;
-// int nearest neighbour and constituent count.
-PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap) { return (uint64_t)cap * (4 * 8 + 5 * 4 + 2 * 4); }
+// Bytes of one warp's shared-memory clustering workspace for `cap` objects:
+// float y, phi, pT^2p, nearest-neighbour dR^2 and distance; int nearest
+// neighbour and constituent count; short tile and next-in-tile; then the
+// heads of the tile lists.  (The double four-momenta, touched once a step by
+// one lane, live in global scratch.)
+constexpr uint32_t PDR_JET_TILES = 1024;
+PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap) {
+  return (uint64_t)cap * (5 * 4 + 2 * 4 + 2 * 2) + 2 * PDR_JET_TILES;
+}
 
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {

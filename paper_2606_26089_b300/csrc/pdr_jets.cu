@@ -12,7 +12,8 @@
 // takes the smallest of those (a warp argmin), merges or makes a jet, and
 // re-searches only the objects whose neighbour was involved.
 //
-// Precision: four-momenta are kept as double (px, py, E + pz, E - pz); the
+// Precision: four-momenta are kept as double (px, py, E + pz, E - pz; in
+// global scratch, read and written once a step by one lane); the
 // light-cone components are sums of positive terms, so the rapidity
 // y = ln((E + pz) / (E - pz)) / 2 of a merged object carries no cancellation
 // even far forward.  Distances are float32.
@@ -30,16 +31,16 @@ struct WS {
   double *px, *py, *ap, *am;
   float *y, *phi, *k2p, *nnr2, *dist;
   int32_t *nn, *nc;   // nc > 0: active with nc constituents; < 0: a jet of -nc; 0: merged away
+  int16_t *tile, *next, *head;   // tile lists of the active objects
 };
 
-__device__ __forceinline__ WS carve(unsigned char* base, uint32_t cap) {
+__device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t cap) {
   WS w;
-  double* d = reinterpret_cast<double*>(base);
-  w.px = d;
-  w.py = d + cap;
-  w.ap = d + 2 * cap;
-  w.am = d + 3 * cap;
-  float* f = reinterpret_cast<float*>(d + 4 * cap);
+  w.px = mom;
+  w.py = mom + cap;
+  w.ap = mom + 2 * cap;
+  w.am = mom + 3 * cap;
+  float* f = reinterpret_cast<float*>(base);
   w.y = f;
   w.phi = f + cap;
   w.k2p = f + 2 * cap;
@@ -48,6 +49,10 @@ __device__ __forceinline__ WS carve(unsigned char* base, uint32_t cap) {
   int32_t* q = reinterpret_cast<int32_t*>(f + 5 * cap);
   w.nn = q;
   w.nc = q + cap;
+  int16_t* h = reinterpret_cast<int16_t*>(q + 2 * cap);
+  w.tile = h;
+  w.next = h + cap;
+  w.head = h + 2 * cap;
   return w;
 }
 
@@ -78,26 +83,96 @@ __device__ __forceinline__ float dist_of(const WS& w, uint32_t k, float inv_R2) 
   return d <= INFINITY ? d : INFINITY;
 }
 
-// Nearest neighbour within R of object k, searched by the whole warp.
-__device__ __forceinline__ void rescan(const WS& w, uint32_t n, uint32_t k, float R2, uint32_t lane) {
+// ---- tiles: nty x ntp cells in (rapidity, azimuth), each at least R wide,
+// so that every object within R of another lies in its cell or an adjacent
+// one (rapidity clamped at the ends, azimuth periodic; a single azimuth
+// column when 2 pi / R < 3).  A tile is ty << 5 | tp (both < 32).
+__device__ __forceinline__ int tile_of(const JetParams& p, float y, float phi) {
+  int ty = (int)floorf((y - p.y0) * p.inv_wy);
+  ty = min(max(ty, 0), p.nty - 1);
+  int tp = (int)floorf((phi + 3.14159265f) * p.inv_wp);
+  tp = min(max(tp, 0), p.ntp - 1);
+  return (ty << 5) | tp;
+}
+
+// Neighbour l (0..8) of tile t, or -1.
+__device__ __forceinline__ int neighbour(const JetParams& p, int t, int l) {
+  const int y2 = (t >> 5) + l / 3 - 1, dp = l % 3 - 1;
+  if (y2 < 0 || y2 >= p.nty) return -1;
+  int tp = t & 31;
+  if (p.ntp < 3) return dp == 0 ? (y2 << 5) | tp : -1;
+  tp += dp;
+  tp = tp < 0 ? tp + p.ntp : (tp >= p.ntp ? tp - p.ntp : tp);
+  return (y2 << 5) | tp;
+}
+
+__device__ __forceinline__ bool adjacent(const JetParams& p, int t1, int t2) {
+  if (abs((t1 >> 5) - (t2 >> 5)) > 1) return false;
+  if (p.ntp < 3) return true;
+  const int d = abs((t1 & 31) - (t2 & 31));
+  return d <= 1 || d == p.ntp - 1;
+}
+
+__device__ __forceinline__ void push(const WS& w, int t, uint32_t k) {
+  w.next[k] = w.head[t];
+  w.head[t] = (int16_t)k;
+  w.tile[k] = (int16_t)t;
+}
+
+// Unlinks k from its tile list (at most cap steps; a missing k sets the error word).
+__device__ __forceinline__ void unlink(const WS& w, uint32_t k, uint32_t cap, uint32_t* err) {
+  const int t = w.tile[k];
+  int q = w.head[t];
+  if (q == (int)k) {
+    w.head[t] = w.next[k];
+    return;
+  }
+  for (uint32_t it = 0; it < cap && q >= 0; ++it) {
+    const int nx = w.next[q];
+    if (nx == (int)k) {
+      w.next[q] = w.next[k];
+      return;
+    }
+    q = nx;
+  }
+  atomicOr(err, ERR_TABLE);
+}
+
+// Nearest neighbour within R of object k among the active objects of the
+// nine surrounding tiles (lanes 0..8 walk one tile each), as (dR^2, index).
+__device__ __forceinline__ void search(const JetParams& p, const WS& w, uint32_t k, uint32_t lane, float& best,
+                                       int32_t& bi) {
+  best = p.R2;
+  bi = -1;
   const float yk = w.y[k], pk = w.phi[k];
-  float best = R2;
-  int32_t bi = -1;
-  for (uint32_t l = lane; l < n; l += 32u) {
-    if (l == k || w.nc[l] <= 0) continue;
-    const float d = dr2(w, l, yk, pk);
-    if (d < best) { best = d; bi = (int32_t)l; }
+  if (lane < 9u) {
+    const int t = neighbour(p, w.tile[k], (int)lane);
+    if (t >= 0) {
+      int q = w.head[t];
+      for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
+        if (q != (int)k) {
+          const float d = dr2(w, (uint32_t)q, yk, pk);
+          if (d < best || (d == best && q < bi)) { best = d; bi = q; }
+        }
+        q = w.next[q];
+      }
+    }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float od = __shfl_xor_sync(PDR_FULL, best, o);
-    const int32_t oi = __shfl_xor_sync(PDR_FULL, bi, o);
-    if (od < best || (od == best && oi >= 0 && (bi < 0 || oi < bi))) { best = od; bi = oi; }
-  }
-  if (lane == 0) {
-    w.nn[k] = bi;
-    w.nnr2[k] = best;
-  }
+  // (dR^2, index) minimum: non-negative floats order as their bit patterns
+  const uint32_t key = bi < 0 ? 0xFFFFFFFFu : __float_as_uint(best);
+  const uint32_t mkey = __reduce_min_sync(PDR_FULL, key);
+  const uint32_t mi = __reduce_min_sync(PDR_FULL, key == mkey && bi >= 0 ? (uint32_t)bi : 0xFFFFFFFFu);
+  bi = mi == 0xFFFFFFFFu ? -1 : (int32_t)mi;
+  best = bi < 0 ? p.R2 : __uint_as_float(mkey);
+}
+
+// The warp's (distance, index) minimum over the lanes' candidates (a lane
+// without one holds index -1); distances are non-negative or +inf.
+__device__ __forceinline__ int32_t warp_argmin(float d, int32_t k) {
+  const uint32_t key = k < 0 ? 0xFFFFFFFFu : __float_as_uint(d);
+  const uint32_t mkey = __reduce_min_sync(PDR_FULL, key);
+  const uint32_t mi = __reduce_min_sync(PDR_FULL, key == mkey && k >= 0 ? (uint32_t)k : 0xFFFFFFFFu);
+  return mi == 0xFFFFFFFFu ? -1 : (int32_t)mi;
 }
 
 // Loads the event's objects into the workspace; returns their number.
@@ -154,13 +229,13 @@ __device__ __forceinline__ uint32_t load_objects(const JetParams& p, const WS& w
   return n;
 }
 
-__global__ void __launch_bounds__(256) cluster_kernel(const __grid_constant__ JetParams p) {
+__global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ JetParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap), p.cap);
   const uint64_t w0 = (uint64_t)blockIdx.x * p.warps + wib;
+  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap), p.scratch + w0 * 4u * p.cap, p.cap);
   const uint64_t nw = (uint64_t)gridDim.x * p.warps;
-  const float R2 = p.R2, inv_R2 = p.inv_R2;
+  const float inv_R2 = p.inv_R2;
   for (uint64_t e = w0; e < p.n_events; e += nw) {
     const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
     uint32_t c0 = 0, c2 = 0;
@@ -170,43 +245,41 @@ __global__ void __launch_bounds__(256) cluster_kernel(const __grid_constant__ Je
     }
     const uint64_t n_part = b - a;
     const uint64_t n_obj = p.collection == PDR_JETS_PFLOW ? (uint64_t)c0 + c2 : n_part;
-    if (b < a || c0 > n_part || c2 > n_part || n_obj > p.cap) {
-      if (lane == 0) {
+    if (b < a || c0 > n_part || c2 > n_part) {
+      if (lane == 0 && p.min_obj == 0) {
         atomicOr(p.err, ERR_CSR);
         p.jet_counts[e] = 0;
       }
       continue;
     }
+    if (n_obj < p.min_obj || n_obj > p.cap) continue;   // another launch's event
     const uint32_t n = load_objects(p, w, a, n_part, c0, c2, lane);
+    for (uint32_t t = lane; t < PDR_JET_TILES; t += 32u) w.head[t] = -1;
     __syncwarp();
-    // initial nearest neighbours (each lane searches for its own objects)
-    for (uint32_t k = lane; k < n; k += 32u) {
-      const float yk = w.y[k], pk = w.phi[k];
-      float best = R2;
-      int32_t bi = -1;
-      for (uint32_t l = 0; l < n; ++l) {
-        if (l == k) continue;
-        const float d = dr2(w, l, yk, pk);
-        if (d < best) { best = d; bi = (int32_t)l; }
+    if (lane == 0)
+      for (uint32_t k = 0; k < n; ++k) push(w, tile_of(p, w.y[k], w.phi[k]), k);
+    __syncwarp();
+    // initial nearest neighbours: the whole warp per object
+    for (uint32_t k = 0; k < n; ++k) {
+      float best;
+      int32_t bi;
+      search(p, w, k, lane, best, bi);
+      if (lane == 0) {
+        w.nn[k] = bi;
+        w.nnr2[k] = best;
       }
-      w.nn[k] = bi;
-      w.nnr2[k] = best;
     }
     __syncwarp();
-    for (uint32_t k = lane; k < n; k += 32u) w.dist[k] = dist_of(w, k, inv_R2);
-    __syncwarp();
+    float bd = INFINITY;
+    int32_t bk = -1;
+    for (uint32_t k = lane; k < n; k += 32u) {
+      const float d = dist_of(w, k, inv_R2);
+      w.dist[k] = d;
+      if (bk < 0 || d < bd) { bd = d; bk = (int32_t)k; }
+    }
     for (uint32_t left = n; left > 0; --left) {
       // the smallest distance (ties: the lower index)
-      float bd = INFINITY;
-      int32_t bk = -1;
-      for (uint32_t k = lane; k < n; k += 32u)
-        if (w.nc[k] > 0 && (bk < 0 || w.dist[k] < bd)) { bd = w.dist[k]; bk = (int32_t)k; }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float od = __shfl_xor_sync(PDR_FULL, bd, o);
-        const int32_t ok = __shfl_xor_sync(PDR_FULL, bk, o);
-        if (od < bd || (od == bd && ok >= 0 && (bk < 0 || ok < bk))) { bd = od; bk = ok; }
-      }
+      bk = warp_argmin(bd, bk);
       const uint32_t i = (uint32_t)bk;
       const int32_t j = w.nn[i];
       const float dB = w.k2p[i];
@@ -215,49 +288,69 @@ __global__ void __launch_bounds__(256) cluster_kernel(const __grid_constant__ Je
       __syncwarp();
       if (lane == 0) {
         if (merge) {
+          unlink(w, mb, p.cap, p.err);
+          unlink(w, ma, p.cap, p.err);
           w.px[ma] += w.px[mb];
           w.py[ma] += w.py[mb];
           w.ap[ma] += w.ap[mb];
           w.am[ma] += w.am[mb];
           w.nc[ma] += w.nc[mb];
           w.nc[mb] = 0;
-          const double px = w.px[ma], py = w.py[ma];
-          w.y[ma] = 0.5f * logf((float)(w.ap[ma] / w.am[ma]));
-          w.phi[ma] = atan2f((float)py, (float)px);
-          w.k2p[ma] = kt2p_of((float)(px * px + py * py), p.p);
+          const float fx = (float)w.px[ma], fy = (float)w.py[ma];
+          w.y[ma] = 0.5f * logf((float)w.ap[ma] / (float)w.am[ma]);
+          w.phi[ma] = atan2f(fy, fx);
+          w.k2p[ma] = kt2p_of(fmaf(fx, fx, fy * fy), p.p);
+          push(w, tile_of(p, w.y[ma], w.phi[ma]), ma);
         } else {
+          unlink(w, i, p.cap, p.err);
           w.nc[i] = -w.nc[i];
         }
       }
       __syncwarp();
       if (left == 1) break;
-      // neighbour records: re-search the objects whose neighbour took part
-      for (uint32_t t = 0; t < n; t += 32u) {
-        const uint32_t k = t + lane;
-        bool need = false;
-        if (k < n && w.nc[k] > 0) {
-          const int32_t m = w.nn[k];
-          need = m == (int32_t)i || (merge && (m == j || k == ma));
-          if (!need && merge) {
-            const float d = dr2(w, ma, w.y[k], w.phi[k]);
-            if (d < w.nnr2[k]) {
-              w.nn[k] = (int32_t)ma;
-              w.nnr2[k] = d;
-            }
-            if (w.nn[k] == (int32_t)ma) w.dist[k] = dist_of(w, k, inv_R2);
+      // neighbour records, in three passes: flag the objects whose neighbour
+      // took part (distance -1) and offer the merged object to those near it;
+      // re-search the flagged ones; take the next minimum
+      const int ta = w.tile[ma];
+      const float ya = w.y[ma], pa = w.phi[ma];
+#pragma unroll 4
+      for (uint32_t k = lane; k < n; k += 32u) {
+        if (w.nc[k] <= 0) continue;
+        const int32_t m = w.nn[k];
+        if (m == (int32_t)i || (merge && (m == j || k == ma))) {
+          w.dist[k] = -1.0f;
+        } else if (merge && adjacent(p, w.tile[k], ta)) {
+          const float d = dr2(w, k, ya, pa);
+          if (d < w.nnr2[k] || (d == w.nnr2[k] && (int32_t)ma < m)) {
+            w.nn[k] = (int32_t)ma;
+            w.nnr2[k] = d;
+            w.dist[k] = dist_of(w, k, inv_R2);
           }
-        }
-        uint32_t todo = __ballot_sync(PDR_FULL, need);
-        while (todo) {
-          const uint32_t kk = t + (uint32_t)(__ffs(todo) - 1);
-          todo &= todo - 1u;
-          rescan(w, n, kk, R2, lane);
-          __syncwarp();
-          if (lane == 0) w.dist[kk] = dist_of(w, kk, inv_R2);
-          __syncwarp();
         }
       }
       __syncwarp();
+      for (uint32_t t = 0; t < n; t += 32u) {
+        const uint32_t k = t + lane;
+        uint32_t todo = __ballot_sync(PDR_FULL, k < n && w.nc[k] > 0 && w.dist[k] < 0.0f);
+        while (todo) {
+          const uint32_t kk = t + (uint32_t)(__ffs(todo) - 1);
+          todo &= todo - 1u;
+          float best;
+          int32_t bi;
+          search(p, w, kk, lane, best, bi);
+          if (lane == 0) {
+            w.nn[kk] = bi;
+            w.nnr2[kk] = best;
+            w.dist[kk] = dist_of(w, kk, inv_R2);
+          }
+          __syncwarp();
+        }
+      }
+      bd = INFINITY;
+      bk = -1;
+#pragma unroll 4
+      for (uint32_t k = lane; k < n; k += 32u)
+        if (w.nc[k] > 0 && (bk < 0 || w.dist[k] < bd)) { bd = w.dist[k]; bk = (int32_t)k; }
     }
     // jets: the objects marked by a beam distance, cut, ordered by decreasing pT
     uint32_t m = 0;
@@ -330,6 +423,12 @@ cudaError_t launch_jet_max_objects(const JetParams& p, uint32_t* out, cudaStream
   const uint64_t blocks = p.n_events / 256 + 1;
   jet_max_objects_kernel<<<(unsigned)(blocks < 1184 ? blocks : 1184), 256, 0, s>>>(p, out);
   return cudaGetLastError();
+}
+
+cudaError_t occupancy_cluster(uint32_t threads, size_t smem, int* blocks) {
+  cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, cluster_kernel, (int)threads, smem);
 }
 
 cudaError_t launch_cluster(const JetParams& p, uint32_t grid, size_t smem, cudaStream_t s) {

@@ -34,6 +34,7 @@ cudaError_t launch_postprocess(const PostParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_track_ip(const IPParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_jet_max_objects(const JetParams& p, uint32_t* out, cudaStream_t s);
 cudaError_t launch_cluster(const JetParams& p, uint32_t grid, size_t smem, cudaStream_t s);
+cudaError_t occupancy_cluster(uint32_t threads, size_t smem, int* blocks);
 cudaError_t launch_pileup_fill(const PuParams& p, int n_sms, cudaStream_t s);
 cudaError_t launch_dense(const uint64_t* offsets, uint64_t n_events, const uint32_t* counts,
                          uint64_t* dense_off, uint64_t stride, unsigned long long* carry,
@@ -188,6 +189,9 @@ struct pdr_ctx {
   uint32_t pu_K = 0, pu_cap = 0;
   double pu_mean = -1.0;
   uint64_t* pu_hoff_total = nullptr;      // pinned: the merged total of a first pass
+  // jet clustering: per-warp four-momentum scratch (device)
+  double* jet_scratch = nullptr;
+  uint64_t jet_scratch_bytes = 0;
 };
 
 namespace {
@@ -668,6 +672,7 @@ int pdr_destroy(pdr_ctx* ctx) {
   if (ctx->h_tot) cudaFreeHost(ctx->h_tot);
   if (ctx->pu_T) cudaFree(ctx->pu_T);
   if (ctx->pu_hoff_total) cudaFreeHost(ctx->pu_hoff_total);
+  if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_word);
   delete ctx;
@@ -1843,6 +1848,15 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   p.R2 = (float)(jp->R * jp->R);
   p.inv_R2 = (float)(1.0 / (jp->R * jp->R));
   p.pt_min = (float)jp->pt_min;
+  // tiles at least R (plus a rounding margin) wide: rapidity [-6, 6]
+  // (clamped beyond), azimuth periodic; at most 32 x 32
+  const double rw = jp->R * 1.0001;
+  p.nty = (int32_t)std::min(32.0, std::max(1.0, std::floor(12.0 / rw)));
+  int32_t ntp = (int32_t)std::min(32.0, std::floor(2.0 * M_PI / rw));
+  p.ntp = ntp < 3 ? 1 : ntp;
+  p.y0 = -6.0f;
+  p.inv_wy = (float)(p.nty / 12.0);
+  p.inv_wp = (float)(p.ntp / (2.0 * M_PI));
   p.jets = jets;
   p.jet_counts = jet_counts;
   p.err = ctx->d_err;
@@ -1853,15 +1867,39 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   PDR_CUDA(cudaStreamSynchronize(s), "sync");
   const uint32_t max_n = *ctx->h_word;
   const uint32_t cap = std::max<uint32_t>(32u, (max_n + 31u) & ~31u);
-  const uint64_t ws = jet_ws_bytes(cap);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-  if (ws > (uint64_t)smem_max) return fail(PDR_EOVERFLOW, "event has more clustering objects than fit in shared memory");
-  p.cap = cap;
-  p.warps = (uint32_t)std::min<uint64_t>(8, (uint64_t)smem_max / ws);
-  const size_t smem = (size_t)(p.warps * ws);
-  const uint64_t blocks = (b->n_events + p.warps - 1) / p.warps;
-  const uint64_t cap_blocks = (uint64_t)ctx->n_sms * 32;
-  PDR_CUDA(launch_cluster(p, (uint32_t)std::min(blocks, cap_blocks), smem, s), "clustering launch");
+  if (jet_ws_bytes(cap) > (uint64_t)smem_max)
+    return fail(PDR_EOVERFLOW, "event has more clustering objects than fit in shared memory");
+  // The workspace of the largest event sets how many warps share an SM; so
+  // events up to 288 objects (most of a batch of a few hundred particles a
+  // event) run in a launch sized for them, and only the larger ones in a
+  // launch sized for the largest.
+  const uint32_t tier = 288;
+  const uint32_t caps[2] = {std::min(cap, tier), cap};
+  for (int k = 0; k < (cap > tier ? 2 : 1); ++k) {
+    p.cap = caps[k];
+    p.min_obj = k == 0 ? 0u : tier + 1u;
+    const uint64_t ws = jet_ws_bytes(p.cap);
+    // two blocks an SM where the shared memory allows (shorter tails)
+    p.warps = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, (uint64_t)smem_max / ws / 2));
+    const size_t smem = (size_t)(p.warps * ws);
+    int per_sm = 0;
+    PDR_CUDA(occupancy_cluster(p.warps * 32u, smem, &per_sm), "clustering occupancy");
+    const uint64_t blocks = std::min<uint64_t>((b->n_events + p.warps - 1) / p.warps,
+                                               (uint64_t)ctx->n_sms * (uint64_t)std::max(per_sm, 1));
+    // four-momentum scratch: 4 doubles per object for every warp of the grid
+    const uint64_t need = blocks * p.warps * (uint64_t)p.cap * 32u;
+    if (need > ctx->jet_scratch_bytes) {
+      PDR_CUDA(cudaDeviceSynchronize(), "sync");   // earlier clusterings may still use the scratch
+      if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);
+      ctx->jet_scratch = nullptr;
+      ctx->jet_scratch_bytes = 0;
+      PDR_CUDA(cudaMalloc((void**)&ctx->jet_scratch, need), "jet scratch");
+      ctx->jet_scratch_bytes = need;
+    }
+    p.scratch = ctx->jet_scratch;
+    PDR_CUDA(launch_cluster(p, (uint32_t)blocks, smem, s), "clustering launch");
+  }
   return PDR_OK;
 }
