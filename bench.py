@@ -445,7 +445,7 @@ def bench_jets(args, B, ctx, bt, ob, n_ev, n_p, counts):
     n_jets = int(jc.sum().item())
     return {"algorithm": "anti-kT R = 0.5, pT >= 10 GeV, >= 2 constituents", "events": n_ev, "objects": n_obj,
             "jets": n_jets, "ms": sec * 1e3, "events_per_s": n_ev / sec, "objects_per_s": n_obj / sec,
-            "bound": "issue (O(n^2) neighbour searches in shared memory per event; no DRAM roofline)",
+            "bound": "latency (a serial chain of clustering steps per event and warp; no DRAM or arithmetic roofline)",
             "reps": reps}
 
 
