@@ -503,7 +503,8 @@ def event_track_ip(card: Card, ip: IPParams, ev: dict, ref: "EventResult", seed:
 # jet clustering
 # ----------------------------------------------------------------------------
 JET = np.dtype([("px", "f8"), ("py", "f8"), ("pz", "f8"), ("e", "f8"), ("pt", "f8"), ("eta", "f8"),
-                ("phi", "f8"), ("mass", "f8"), ("nconst", "i4"), ("pad", "i4")])
+                ("phi", "f8"), ("mass", "f8"), ("e2", "f8"), ("e3", "f8"), ("c2", "f8"), ("d2", "f8"),
+                ("nconst", "i4"), ("pad", "i4")])
 ALGORITHM_P = {"antikt": -1.0, "cambridge": 0.0, "kt": 1.0}
 
 

@@ -915,7 +915,8 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
 /* ------------------------------------------------------------------------ */
 typedef struct {
   double px, py, pz, e, y, phi, kt2p;
-  int32_t nconst, active;
+  double pt0, y0, phi0;   /* the object as loaded (a constituent) */
+  int32_t nconst, active, parent;
 } cl_obj;
 
 static void cl_derive(cl_obj* o, double p) {
@@ -941,9 +942,15 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
   if (!o) return -1;
   for (int64_t i = 0; i < n; ++i) {
     o[i].px = px[i]; o[i].py = py[i]; o[i].pz = pz[i]; o[i].e = e[i];
-    o[i].nconst = 1; o[i].active = 1;
+    o[i].nconst = 1; o[i].active = 1; o[i].parent = -1;
     cl_derive(&o[i], p);
+    o[i].pt0 = hypot(px[i], py[i]);
+    o[i].y0 = o[i].y;
+    o[i].phi0 = o[i].phi;
   }
+  int64_t* jet_of = (int64_t*)malloc((size_t)n * sizeof(int64_t)); /* object -> jet slot, or -1 */
+  if (!jet_of) { free(o); return -1; }
+  for (int64_t i = 0; i < n; ++i) jet_of[i] = -1;
   const double R2 = R * R, eps = 1.0 / 8388608.0; /* 2^-23 */
   int32_t nj = 0;
   for (int64_t left = n; left > 0;) {
@@ -975,6 +982,7 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
       --left;
       const double pt = hypot(q->px, q->py);
       if (pt >= pt_min && q->nconst >= nconst_min) {
+        jet_of[bi] = nj;
         or_jet* J = &jets[nj++];
         J->px = q->px; J->py = q->py; J->pz = q->pz; J->e = q->e;
         J->pt = pt;
@@ -992,10 +1000,45 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
       a->px += c->px; a->py += c->py; a->pz += c->pz; a->e += c->e;
       a->nconst += c->nconst;
       c->active = 0;
+      c->parent = (int32_t)bi; /* j was merged into i */
       --left;
       cl_derive(a, p);
     }
   }
+  /* substructure: each constituent's jet is the end of its chain of merges */
+  for (int32_t k = 0; k < nj; ++k) { jets[k].e2 = jets[k].e3 = jets[k].c2 = jets[k].d2 = 0.0; }
+  int64_t* root = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  if (!root) { free(jet_of); free(o); return -1; }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t r = i;
+    while (o[r].parent >= 0) r = o[r].parent;
+    root[i] = jet_of[r];
+  }
+  for (int32_t k = 0; k < nj; ++k) {
+    double spt = 0.0;
+    for (int64_t i = 0; i < n; ++i) if (root[i] == k) spt += o[i].pt0;
+    double e2 = 0.0, e3 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (root[i] != k) continue;
+      for (int64_t j = i + 1; j < n; ++j) {
+        if (root[j] != k) continue;
+        const double dij = hypot(o[i].y0 - o[j].y0, cl_dphi(o[i].phi0, o[j].phi0));
+        e2 += o[i].pt0 * o[j].pt0 / (spt * spt) * dij;
+        for (int64_t l = j + 1; l < n; ++l) {
+          if (root[l] != k) continue;
+          const double dil = hypot(o[i].y0 - o[l].y0, cl_dphi(o[i].phi0, o[l].phi0));
+          const double djl = hypot(o[j].y0 - o[l].y0, cl_dphi(o[j].phi0, o[l].phi0));
+          e3 += o[i].pt0 * o[j].pt0 * o[l].pt0 / (spt * spt * spt) * dij * dil * djl;
+        }
+      }
+    }
+    jets[k].e2 = e2;
+    jets[k].e3 = e3;
+    jets[k].c2 = e2 > 0.0 ? e3 / (e2 * e2) : 0.0;
+    jets[k].d2 = e2 > 0.0 ? e3 / (e2 * e2 * e2) : 0.0;
+  }
+  free(root);
+  free(jet_of);
   free(o);
   /* decreasing pT (insertion sort: stable, small counts) */
   for (int32_t i = 1; i < nj; ++i) {

@@ -270,7 +270,12 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
  *     a d_ij merges i and j (E-scheme: four-momenta added), a d_iB makes i a
  *     jet; ties go to the beam distance, then to the lower indices;
  *   - jets with pT >= pt_min and at least nconst_min constituents are kept,
- *     ordered by decreasing pT.
+ *     ordered by decreasing pT;
+ *   - substructure (the output table of Sec. 2.5: D2 and C2): with the
+ *     energy correlation functions of the jet's constituents
+ *     e2 = sum_{i<j} z_i z_j dR_ij and e3 = sum_{i<j<k} z_i z_j z_k dR_ij dR_ik dR_jk
+ *     (z_i = pT_i / sum pT, dR in rapidity and azimuth, angular exponent
+ *     beta = 1), C2 = e3 / e2^2 and D2 = e3 / e2^3 (both 0 when e2 = 0).
  * A step is marginal when the runner-up distance (a different decision) lies
  * within the float32 uncertainty of the two distances: 1e-6 relative, plus for
  * pair distances min(pt^(2p)) (2 |dy| eps_y + 2 |dphi| eps_phi) / R^2 with
@@ -278,6 +283,7 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
 typedef struct or_jet {
   double px, py, pz, e;
   double pt, eta, phi, mass;
+  double e2, e3, c2, d2;
   int32_t nconst, pad;
 } or_jet;
 

@@ -7,7 +7,9 @@ algorithms that do not restate the oracle's loop: four-momentum
 conservation, the kT algorithm with a radius spanning the whole acceptance
 (one jet: the event's total four-momentum), the anti-kT cone property
 (isolated hard particles absorb the soft particles around them), the
-Cambridge/Aachen two-particle threshold dR < R, and collinear safety.
+Cambridge/Aachen two-particle threshold dR < R, and collinear safety; for
+the substructure C2 and D2, the two-prong closed form (e3 = 0), the
+equilateral three-prong jet (D2 = 1, C2 = a / 3) and rotation invariance.
 """
 import math
 
@@ -124,3 +126,39 @@ def test_symmetric_configuration_is_marginal():
     is a tie, which the oracle reports as marginal."""
     jets, marg = oracle.cluster(*_fm([10, 3, 3], [0.0, 0.2, -0.2], [0.0, 0.0, 0.0]), p=-1.0, R=0.4)
     assert marg >= 1 and len(jets) == 1
+
+
+def test_two_prong_energy_correlations():
+    """Two massless constituents at dR = 0.3 with pT 30 and 10: z = 3/4, 1/4,
+    e2 = (3/16) 0.3 = 0.05625, e3 = 0, C2 = D2 = 0."""
+    jets, _ = oracle.cluster(*_fm([30, 10], [0.5, 0.8], [1.0, 1.0]), p=-1.0, R=0.5)
+    assert len(jets) == 1
+    assert jets[0]["e2"] == pytest.approx(0.05625, rel=1e-12)
+    assert jets[0]["e3"] == 0.0 and jets[0]["c2"] == 0.0 and jets[0]["d2"] == 0.0
+
+
+def test_equilateral_three_prong_has_d2_one():
+    """Three equal-pT massless constituents on an equilateral triangle of side
+    a in (y, phi): z = 1/3, e2 = 3 a / 9, e3 = a^3 / 27, so C2 = a / 3 and
+    D2 = 1."""
+    a = 0.2
+    eta = [0.0, a, a / 2]
+    phi = [0.0, 0.0, a * math.sqrt(3) / 2]
+    jets, _ = oracle.cluster(*_fm([20, 20, 20], eta, phi), p=-1.0, R=0.5)
+    assert len(jets) == 1 and jets[0]["nconst"] == 3
+    assert jets[0]["e2"] == pytest.approx(a / 3, rel=1e-12)
+    assert jets[0]["e3"] == pytest.approx(a ** 3 / 27, rel=1e-12)
+    assert jets[0]["c2"] == pytest.approx(a / 3, rel=1e-12)
+    assert jets[0]["d2"] == pytest.approx(1.0, rel=1e-12)
+
+
+def test_substructure_is_rotation_invariant():
+    rng = np.random.default_rng(12)
+    pt = rng.uniform(1, 20, 30)
+    eta = rng.normal(0.3, 0.15, 30)
+    phi = rng.normal(1.0, 0.15, 30)
+    j0, _ = oracle.cluster(*_fm(pt, eta, phi), p=-1.0, R=0.6)
+    j1, _ = oracle.cluster(*_fm(pt, eta, phi + 1.7), p=-1.0, R=0.6)
+    assert len(j0) == len(j1)
+    for key in ("e2", "e3", "c2", "d2"):
+        assert np.allclose(j0[key], j1[key], rtol=1e-10, atol=1e-14)
