@@ -447,7 +447,11 @@ int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, c
  * d_iB = pT_i^(2p) and d_ij = min(pT_i^(2p), pT_j^(2p)) dR_ij^2 / R^2
  * (dR in rapidity and azimuth) over the remaining objects; a pair merges by
  * four-momentum addition, a beam distance makes a jet.  Jets are ordered by
- * decreasing pT.  PFlow objects are the energy-flow tracks (smeared pT,
+ * decreasing pT.  Substructure (the output table of Sec. 2.5): with the
+ * energy correlation functions of the jet's constituents
+ * e2 = sum_{i<j} z_i z_j dR_ij and e3 = sum_{i<j<k} z_i z_j z_k dR_ij dR_ik dR_jk
+ * (z = pT / sum pT of the constituents, angular exponent 1), C2 = e3 / e2^2
+ * and D2 = e3 / e2^3 (0 when e2 = 0).  PFlow objects are the energy-flow tracks (smeared pT,
  * momentum direction, the generated particle's mass) and the energy-flow
  * neutrals (massless, E = dE at the tower centre); truth objects are the
  * generated particles except neutrinos (|pdg| 12, 14, 16). */
@@ -466,7 +470,7 @@ typedef struct {
   float pt, eta, phi, mass;       /* GeV, pseudorapidity, azimuth, GeV          */
   float e;                        /* GeV                                        */
   uint32_t nconst;
-  uint32_t pad[2];
+  float c2, d2;                   /* substructure (below)                       */
 } pdr_jet;
 
 /* Clusters every event of `batch` (for PDR_JETS_PFLOW: the outputs `out` that

@@ -501,7 +501,7 @@ class Context:
     def cluster_jets(self, batch: pdr_batch, out: Optional[pdr_outputs], params: pdr_jet_params, jets, jet_counts,
                      stream=None):
         """Jets into `jets` (device float32 tensor [n_particles, 8]: pt, eta, phi,
-        mass, e, nconst (as uint32), pad, pad; slot layout) and `jet_counts`
+        mass, e, nconst (as uint32), C2, D2; slot layout) and `jet_counts`
         (device int32 [n_events])."""
         self._check(self.L.pdr_cluster_jets(self.h, C.byref(batch), C.byref(out) if out is not None else None,
                                             C.byref(params), _ptr(jets), _ptr(jet_counts), self._stream(stream)),

@@ -251,7 +251,7 @@ struct JetParams {
   pdr_jet* jets;
   uint32_t* jet_counts;
   uint32_t* err;
-  double* scratch;                      // four-momenta: 4 x cap doubles for each warp of the grid
+  double* scratch;                      // PDR_JET_SCRATCH_DOUBLES x cap doubles for each warp of the grid
 };
 
 // Bytes of one warp's shared-memory clustering workspace for `cap` objects:
@@ -261,8 +261,11 @@ struct JetParams {
 // one lane, live in global scratch.)
 constexpr uint32_t PDR_JET_TILES = 1024;
 PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap) {
-  return (uint64_t)cap * (5 * 4 + 2 * 4 + 2 * 2) + 2 * PDR_JET_TILES;
+  return (uint64_t)cap * (5 * 4 + 2 * 4 + 3 * 2) + 2 * PDR_JET_TILES;
 }
+// Global scratch of one warp, in doubles per object: px, py, E + pz, E - pz,
+// then float pT, y, phi of each object as loaded (two doubles' room).
+constexpr uint32_t PDR_JET_SCRATCH_DOUBLES = 6;
 
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {

@@ -32,6 +32,8 @@ struct WS {
   float *y, *phi, *k2p, *nnr2, *dist;
   int32_t *nn, *nc;   // nc > 0: active with nc constituents; < 0: a jet of -nc; 0: merged away
   int16_t *tile, *next, *head;   // tile lists of the active objects
+  int16_t* parent;               // the object a merged-away object went into, or -1
+  float *pt0, *y0, *phi0;        // each object as loaded (the jets' constituents; global scratch)
 };
 
 __device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t cap) {
@@ -40,6 +42,10 @@ __device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t c
   w.py = mom + cap;
   w.ap = mom + 2 * cap;
   w.am = mom + 3 * cap;
+  float* g = reinterpret_cast<float*>(mom + 4 * cap);
+  w.pt0 = g;
+  w.y0 = g + cap;
+  w.phi0 = g + 2 * cap;
   float* f = reinterpret_cast<float*>(base);
   w.y = f;
   w.phi = f + cap;
@@ -52,7 +58,8 @@ __device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t c
   int16_t* h = reinterpret_cast<int16_t*>(q + 2 * cap);
   w.tile = h;
   w.next = h + cap;
-  w.head = h + 2 * cap;
+  w.parent = h + 2 * cap;
+  w.head = h + 3 * cap;
   return w;
 }
 
@@ -66,6 +73,13 @@ __device__ __forceinline__ float kt2p_of(float pt2, float p) {
 __device__ __forceinline__ float dr2(const WS& w, uint32_t i, float yk, float pk) {
   const float dy = w.y[i] - yk;
   float dp = fabsf(w.phi[i] - pk);
+  if (dp > 3.14159265f) dp = 6.28318531f - dp;
+  return fmaf(dy, dy, dp * dp);
+}
+
+__device__ __forceinline__ float dr2_between(float y1, float p1, float y2, float p2) {
+  const float dy = y1 - y2;
+  float dp = fabsf(p1 - p2);
   if (dp > 3.14159265f) dp = 6.28318531f - dp;
   return fmaf(dy, dy, dp * dp);
 }
@@ -190,6 +204,10 @@ __device__ __forceinline__ uint32_t load_objects(const JetParams& p, const WS& w
     w.am[k] = (double)(mt * expf(-y));
     w.y[k] = y;
     w.phi[k] = phi;
+    w.pt0[k] = pt;
+    w.y0[k] = y;
+    w.phi0[k] = phi;
+    w.parent[k] = -1;
     w.k2p[k] = kt2p_of(pt * pt, p.p);
     w.nc[k] = 1;
   };
@@ -233,7 +251,8 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const uint64_t w0 = (uint64_t)blockIdx.x * p.warps + wib;
-  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap), p.scratch + w0 * 4u * p.cap, p.cap);
+  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap), p.scratch + w0 * (uint64_t)PDR_JET_SCRATCH_DOUBLES * p.cap,
+                     p.cap);
   const uint64_t nw = (uint64_t)gridDim.x * p.warps;
   const float inv_R2 = p.inv_R2;
   for (uint64_t e = w0; e < p.n_events; e += nw) {
@@ -296,6 +315,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
           w.am[ma] += w.am[mb];
           w.nc[ma] += w.nc[mb];
           w.nc[mb] = 0;
+          w.parent[mb] = (int16_t)ma;
           const float fx = (float)w.px[ma], fy = (float)w.py[ma];
           w.y[ma] = 0.5f * logf((float)w.ap[ma] / (float)w.am[ma]);
           w.phi[ma] = atan2f(fy, fx);
@@ -374,6 +394,69 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       __syncwarp();
     }
     __syncwarp();
+    // substructure of the kept jets: each object's jet is the end of its chain
+    // of merges (the jet list's slot, or -1), then the energy correlation
+    // functions e2, e3 (angular exponent 1) over the jet's constituents
+    for (uint32_t k = lane; k < n; k += 32u) w.next[k] = -1;
+    __syncwarp();
+    for (uint32_t s2 = lane; s2 < m; s2 += 32u) w.next[w.nn[s2]] = (int16_t)s2;
+    __syncwarp();
+    for (uint32_t k = lane; k < n; k += 32u) {
+      int r = (int)k;
+      for (uint32_t it = 0; it < n && w.parent[r] >= 0; ++it) r = w.parent[r];
+      w.tile[k] = w.next[r];   // the tile array is free now: the object's jet slot
+    }
+    __syncwarp();
+    int32_t* list = reinterpret_cast<int32_t*>(w.dist);   // free now: one jet's constituents
+    for (uint32_t s2 = 0; s2 < m; ++s2) {
+      uint32_t c = 0;
+      double spt = 0.0;
+      for (uint32_t t = 0; t < n; t += 32u) {
+        const uint32_t k = t + lane;
+        const bool in = k < n && w.tile[k] == (int16_t)s2;
+        const uint32_t mask = __ballot_sync(PDR_FULL, in);
+        if (in) {
+          list[c + __popc(mask & ((1u << lane) - 1u))] = (int32_t)k;
+          spt += (double)w.pt0[k];
+        }
+        c += __popc(mask);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) spt += __shfl_xor_sync(PDR_FULL, spt, o);
+      // distances in float (relative error ~1e-7), terms summed in double
+      double e2 = 0.0, e3 = 0.0;
+      for (uint32_t u = lane; u < c; u += 32u) {
+        const int32_t ki = list[u];
+        const float zi = w.pt0[ki], yi = w.y0[ki], fi = w.phi0[ki];
+        for (uint32_t v = u + 1; v < c; ++v) {
+          const int32_t kj = list[v];
+          const float zij = zi * w.pt0[kj];
+          const float dij = sqrtf(dr2_between(yi, fi, w.y0[kj], w.phi0[kj]));
+          e2 += (double)(zij * dij);
+          const float yj = w.y0[kj], fj = w.phi0[kj];
+          double s3 = 0.0;
+          for (uint32_t x = v + 1; x < c; ++x) {
+            const int32_t kl = list[x];
+            const float yl = w.y0[kl], fl = w.phi0[kl];
+            s3 += (double)(w.pt0[kl] * sqrtf(dr2_between(yi, fi, yl, fl)) * sqrtf(dr2_between(yj, fj, yl, fl)));
+          }
+          e3 += (double)(zij * dij) * s3;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(PDR_FULL, e2, o);
+        e3 += __shfl_xor_sync(PDR_FULL, e3, o);
+      }
+      if (lane == 0) {
+        e2 /= spt * spt;
+        e3 /= spt * spt * spt;
+        w.y[s2] = e2 > 0.0 ? (float)(e3 / (e2 * e2)) : 0.0f;       // C2 (y, phi are free now)
+        w.phi[s2] = e2 > 0.0 ? (float)(e3 / (e2 * e2 * e2)) : 0.0f;  // D2
+      }
+      __syncwarp();
+    }
     for (uint32_t s = lane; s < m; s += 32u) {
       const float pts = w.nnr2[s];
       uint32_t rank = 0;
@@ -392,7 +475,8 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       J.mass = m2 > 0.0 ? (float)sqrt(m2) : 0.0f;
       J.e = (float)en;
       J.nconst = (uint32_t)(-w.nc[k]);
-      J.pad[0] = J.pad[1] = 0u;
+      J.c2 = w.y[s];
+      J.d2 = w.phi[s];
       if (rank < n_part) p.jets[a + rank] = J;   // the event's slots hold n_part records
     }
     if (lane == 0) {

@@ -1889,7 +1889,7 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
     const uint64_t blocks = std::min<uint64_t>((b->n_events + p.warps - 1) / p.warps,
                                                (uint64_t)ctx->n_sms * (uint64_t)std::max(per_sm, 1));
     // four-momentum scratch: 4 doubles per object for every warp of the grid
-    const uint64_t need = blocks * p.warps * (uint64_t)p.cap * 32u;
+    const uint64_t need = blocks * p.warps * (uint64_t)p.cap * 8u * PDR_JET_SCRATCH_DOUBLES;
     if (need > ctx->jet_scratch_bytes) {
       PDR_CUDA(cudaDeviceSynchronize(), "sync");   // earlier clusterings may still use the scratch
       if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);

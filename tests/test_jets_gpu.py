@@ -11,7 +11,9 @@ HCAL neutrals, so they usually agree as well).  Agreement means: the
 same number, each oracle jet matched by a GPU jet with the same constituent
 count, pT within 4e-6 relative (each constituent carries the response's 2e-6
 and a float32 rounding; constituents within R are nearly collinear), eta and
-phi within 1e-5, mass squared within 1e-5 of m^2 + pT^2.
+phi within 1e-5, mass squared within 1e-5 of m^2 + pT^2, and the
+substructure C2 and D2 within 3e-4 relative (float32 constituent directions
+carry dR errors of a few 1e-7, amplified by the ratios of sums).
 """
 import numpy as np
 import pytest
@@ -80,6 +82,9 @@ def _compare(g, o):
         assert abs(g[k, 1] - j["eta"]) <= 1e-5 * max(1.0, abs(j["eta"])), (g[k], j)
         assert abs(np.angle(np.exp(1j * (g[k, 2] - j["phi"])))) <= 1e-5, (g[k], j)
         assert abs(g[k, 3] ** 2 - j["mass"] ** 2) <= 1e-5 * (j["mass"] ** 2 + j["pt"] ** 2) + 1e-6, (g[k], j)
+        # substructure: float32 constituent directions give dR errors of a few 1e-7
+        assert abs(g[k, 6] - j["c2"]) <= 3e-4 * abs(j["c2"]) + 1e-7, ("C2", g[k], j)
+        assert abs(g[k, 7] - j["d2"]) <= 3e-4 * abs(j["d2"]) + 1e-7, ("D2", g[k], j)
     # decreasing pT
     assert np.all(np.diff(g[:, 0]) <= 1e-6 * g[:-1, 0])
 
