@@ -155,7 +155,7 @@ def lib():
         _lib.oracle_track_ip_smeared.argtypes = [C.POINTER(Card), C.POINTER(IPParams), D, D, D, C.c_int32, D, D, D,
                                                  C.c_uint64, C.c_uint32, C.c_uint32, P]
         _lib.oracle_track_ip_smeared.restype = None
-        _lib.oracle_cluster.argtypes = [C.c_int64, P, P, P, P, D, D, D, C.c_int32, P, P]
+        _lib.oracle_cluster.argtypes = [C.c_int64, P, P, P, P, D, D, D, C.c_int32, C.c_int32, P, P]
         _lib.oracle_cluster.restype = C.c_int32
     return _lib
 
@@ -508,14 +508,16 @@ JET = np.dtype([("px", "f8"), ("py", "f8"), ("pz", "f8"), ("e", "f8"), ("pt", "f
 ALGORITHM_P = {"antikt": -1.0, "cambridge": 0.0, "kt": 1.0}
 
 
-def cluster(px, py, pz, e, p: float = -1.0, R: float = 0.5, pt_min: float = 0.0, nconst_min: int = 1):
-    """(jets structured array, marginal steps) of one event's objects (see oracle.h)."""
+def cluster(px, py, pz, e, p: float = -1.0, R: float = 0.5, pt_min: float = 0.0, nconst_min: int = 1,
+            ee: bool = False):
+    """(jets structured array, marginal steps) of one event's objects (see oracle.h);
+    ee: the e+e- generalized kT (energies and angles)."""
     arr = [np.ascontiguousarray(x, np.float64) for x in (px, py, pz, e)]
     n = arr[0].shape[0]
     jets = np.zeros(max(n, 1), JET)
     m = C.c_int32()
     k = lib().oracle_cluster(n, *[_ptr(a) for a in arr], float(p), float(R), float(pt_min), int(nconst_min),
-                             _ptr(jets), C.byref(m))
+                             int(bool(ee)), _ptr(jets), C.byref(m))
     if k < 0:
         raise ValueError("bad clustering arguments")
     return jets[:k].copy(), m.value

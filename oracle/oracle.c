@@ -915,15 +915,19 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
 /* ------------------------------------------------------------------------ */
 typedef struct {
   double px, py, pz, e, y, phi, kt2p;
+  double nx, ny, nz;      /* unit direction (e+e- distances) */
   double pt0, y0, phi0;   /* the object as loaded (a constituent) */
   int32_t nconst, active, parent;
 } cl_obj;
 
-static void cl_derive(cl_obj* o, double p) {
+static void cl_derive(cl_obj* o, double p, int32_t ee) {
   const double pt2 = o->px * o->px + o->py * o->py;
   o->phi = atan2(o->py, o->px);
   o->y = 0.5 * log((o->e + o->pz) / (o->e - o->pz));
-  o->kt2p = pow(pt2, p); /* (pt^2)^p = pt^(2p) */
+  const double pm = sqrt(pt2 + o->pz * o->pz);
+  o->nx = o->px / pm; o->ny = o->py / pm; o->nz = o->pz / pm;
+  /* pp: (pt^2)^p = pt^(2p); e+e-: E^(2p) */
+  o->kt2p = ee ? pow(o->e * o->e, p) : pow(pt2, p);
 }
 
 static double cl_dphi(double a, double b) {
@@ -934,8 +938,9 @@ static double cl_dphi(double a, double b) {
 }
 
 int32_t oracle_cluster(int64_t n, const double* px, const double* py, const double* pz, const double* e,
-                       double p, double R, double pt_min, int32_t nconst_min, or_jet* jets, int32_t* n_marg) {
-  if (n < 0 || !(R > 0.0)) return -1;
+                       double p, double R, double pt_min, int32_t nconst_min, int32_t ee, or_jet* jets,
+                       int32_t* n_marg) {
+  if (n < 0 || !(R > 0.0) || (ee && !(R <= M_PI))) return -1;
   *n_marg = 0;
   if (n == 0) return 0;
   cl_obj* o = (cl_obj*)calloc((size_t)n, sizeof(cl_obj));
@@ -943,7 +948,7 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
   for (int64_t i = 0; i < n; ++i) {
     o[i].px = px[i]; o[i].py = py[i]; o[i].pz = pz[i]; o[i].e = e[i];
     o[i].nconst = 1; o[i].active = 1; o[i].parent = -1;
-    cl_derive(&o[i], p);
+    cl_derive(&o[i], p, ee);
     o[i].pt0 = hypot(px[i], py[i]);
     o[i].y0 = o[i].y;
     o[i].phi0 = o[i].phi;
@@ -951,7 +956,8 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
   int64_t* jet_of = (int64_t*)malloc((size_t)n * sizeof(int64_t)); /* object -> jet slot, or -1 */
   if (!jet_of) { free(o); return -1; }
   for (int64_t i = 0; i < n; ++i) jet_of[i] = -1;
-  const double R2 = R * R, eps = 1.0 / 8388608.0; /* 2^-23 */
+  /* the distance normalisation: R^2, or 2 (1 - cos R) for e+e- (|n_i - n_j|^2 = 2 (1 - cos theta)) */
+  const double R2 = ee ? 2.0 * (1.0 - cos(R)) : R * R, eps = 1.0 / 8388608.0; /* 2^-23 */
   int32_t nj = 0;
   for (int64_t left = n; left > 0;) {
     /* smallest distance; best / second: value and uncertainty */
@@ -965,11 +971,19 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
       else if (diB < s2) { s2 = diB; su = uiB; }
       for (int64_t j = i + 1; j < n; ++j) {
         if (!o[j].active) continue;
-        const double dy = o[i].y - o[j].y, dp = cl_dphi(o[i].phi, o[j].phi);
         const double kmin = fmin(o[i].kt2p, o[j].kt2p);
-        const double d = kmin * (dy * dy + dp * dp) / R2;
-        const double ey = eps * fmax(fmax(fabs(o[i].y), fabs(o[j].y)), 1.0), ep = eps * M_PI;
-        const double u = 1e-6 * d + kmin * (2.0 * fabs(dy) * ey + 2.0 * fabs(dp) * ep) / R2;
+        double d, u;
+        if (ee) {
+          const double ax = o[i].nx - o[j].nx, ay = o[i].ny - o[j].ny, az = o[i].nz - o[j].nz;
+          const double dn2 = ax * ax + ay * ay + az * az;
+          d = kmin * dn2 / R2;
+          u = 1e-6 * d + kmin * 4.0 * sqrt(dn2) * (2.0 * eps) / R2;
+        } else {
+          const double dy = o[i].y - o[j].y, dp = cl_dphi(o[i].phi, o[j].phi);
+          d = kmin * (dy * dy + dp * dp) / R2;
+          const double ey = eps * fmax(fmax(fabs(o[i].y), fabs(o[j].y)), 1.0), ep = eps * M_PI;
+          u = 1e-6 * d + kmin * (2.0 * fabs(dy) * ey + 2.0 * fabs(dp) * ep) / R2;
+        }
         if (d < b) { s2 = b; su = bu; b = d; bu = u; bi = i; bj = j; }
         else if (d < s2) { s2 = d; su = u; }
       }
@@ -1002,7 +1016,7 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
       c->active = 0;
       c->parent = (int32_t)bi; /* j was merged into i */
       --left;
-      cl_derive(a, p);
+      cl_derive(a, p, ee);
     }
   }
   /* substructure: each constituent's jet is the end of its chain of merges */

@@ -276,10 +276,15 @@ void oracle_track_ip_smeared(const oracle_card* c, const oracle_ip_params* ip, d
  *     e2 = sum_{i<j} z_i z_j dR_ij and e3 = sum_{i<j<k} z_i z_j z_k dR_ij dR_ik dR_jk
  *     (z_i = pT_i / sum pT, dR in rapidity and azimuth, angular exponent
  *     beta = 1), C2 = e3 / e2^2 and D2 = e3 / e2^3 (both 0 when e2 = 0).
+ * With ee set (the e+e- generalized kT of the same family): d_iB = E_i^(2p),
+ * d_ij = min(E_i^(2p), E_j^(2p)) (1 - cos theta_ij) / (1 - cos R), R <= pi,
+ * with 1 - cos theta = |n_i - n_j|^2 / 2 for the unit directions n; pT cuts,
+ * ordering and substructure as above.
  * A step is marginal when the runner-up distance (a different decision) lies
  * within the float32 uncertainty of the two distances: 1e-6 relative, plus for
  * pair distances min(pt^(2p)) (2 |dy| eps_y + 2 |dphi| eps_phi) / R^2 with
- * eps_y = 2^-23 max(|y_i|, |y_j|, 1) and eps_phi = 2^-23 pi. */
+ * eps_y = 2^-23 max(|y_i|, |y_j|, 1) and eps_phi = 2^-23 pi (ee: the pair term
+ * min(E^2p) 4 |n_i - n_j| 2^-22 / (2 (1 - cos R))). */
 typedef struct or_jet {
   double px, py, pz, e;
   double pt, eta, phi, mass;
@@ -291,7 +296,8 @@ typedef struct or_jet {
  * (at most n) and returns their number, or -1 for bad arguments; *n_marg
  * counts the marginal steps. */
 int32_t oracle_cluster(int64_t n, const double* px, const double* py, const double* pz, const double* e,
-                       double p, double R, double pt_min, int32_t nconst_min, or_jet* jets, int32_t* n_marg);
+                       double p, double R, double pt_min, int32_t nconst_min, int32_t ee, or_jet* jets,
+                       int32_t* n_marg);
 
 #ifdef __cplusplus
 }

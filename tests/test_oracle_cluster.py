@@ -9,7 +9,9 @@ conservation, the kT algorithm with a radius spanning the whole acceptance
 (isolated hard particles absorb the soft particles around them), the
 Cambridge/Aachen two-particle threshold dR < R, and collinear safety; for
 the substructure C2 and D2, the two-prong closed form (e3 = 0), the
-equilateral three-prong jet (D2 = 1, C2 = a / 3) and rotation invariance.
+equilateral three-prong jet (D2 = 1, C2 = a / 3) and rotation invariance;
+for the e+e- variant, the opening-angle threshold of p = 0, back-to-back
+sprays, and invariance under 3D rotations.
 """
 import math
 
@@ -162,3 +164,63 @@ def test_substructure_is_rotation_invariant():
     assert len(j0) == len(j1)
     for key in ("e2", "e3", "c2", "d2"):
         assert np.allclose(j0[key], j1[key], rtol=1e-10, atol=1e-14)
+
+
+def _dir_fm(E, dirs):
+    """Massless four-momenta of energies E along unit vectors dirs."""
+    d = np.asarray(dirs, np.float64)
+    d = d / np.linalg.norm(d, axis=1)[:, None]
+    E = np.asarray(E, np.float64)
+    return E * d[:, 0], E * d[:, 1], E * d[:, 2], E
+
+
+@pytest.mark.parametrize("theta,merged", [(0.49, True), (0.51, False)])
+def test_ee_cambridge_angle_threshold(theta, merged):
+    """e+e- with p = 0: d_ij = (1 - cos theta) / (1 - cos R) against d_iB = 1,
+    so two particles merge iff their opening angle is below R."""
+    jets, _ = oracle.cluster(*_dir_fm([10, 7], [[1, 0, 0], [math.cos(theta), math.sin(theta), 0]]),
+                             p=0.0, R=0.5, ee=True)
+    assert (len(jets) == 1) == merged
+
+
+def test_ee_back_to_back_sprays_and_conservation():
+    """Two sprays around opposite directions (opening angles below R / 2):
+    the e+e- anti-kT gives two jets, each the sum of its spray; the
+    four-momentum of the event is conserved."""
+    rng = np.random.default_rng(21)
+    axis = np.array([0.3, -0.5, 0.8])
+    axis /= np.linalg.norm(axis)
+    dirs, E, owner = [], [], []
+    for side in (1.0, -1.0):
+        for _ in range(12):
+            v = side * axis + rng.normal(0, 0.08, 3)
+            dirs.append(v); E.append(rng.uniform(0.5, 8.0)); owner.append(side)
+    fm = _dir_fm(E, dirs)
+    jets, _ = oracle.cluster(*fm, p=-1.0, R=0.7, ee=True)
+    assert len(jets) == 2 and sorted(jets["nconst"]) == [12, 12]
+    owner = np.array(owner)
+    for j in jets:
+        side = 1.0 if j["px"] * axis[0] + j["py"] * axis[1] + j["pz"] * axis[2] > 0 else -1.0
+        sel = owner == side
+        assert j["e"] == pytest.approx(fm[3][sel].sum(), rel=1e-12)
+        assert j["px"] == pytest.approx(fm[0][sel].sum(), rel=1e-10, abs=1e-12)
+
+
+def test_ee_rotation_invariance():
+    """The e+e- distances depend on energies and opening angles only: a 3D
+    rotation of the event rotates the jets and keeps their energies."""
+    rng = np.random.default_rng(22)
+    n = 40
+    dirs = rng.normal(0, 1, (n, 3))
+    E = rng.exponential(4.0, n) + 0.2
+    fm = _dir_fm(E, dirs)
+    a, b = 0.7, -1.1
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(b), -math.sin(b)], [0, math.sin(b), math.cos(b)]])
+    rot = Rx @ Rz
+    p3 = np.stack(fm[:3], axis=1) @ rot.T
+    j0, _ = oracle.cluster(*fm, p=1.0, R=0.8, ee=True)
+    j1, _ = oracle.cluster(p3[:, 0], p3[:, 1], p3[:, 2], fm[3], p=1.0, R=0.8, ee=True)
+    assert len(j0) == len(j1)
+    assert np.allclose(np.sort(j0["e"]), np.sort(j1["e"]), rtol=1e-10)
+    assert sorted(j0["nconst"]) == sorted(j1["nconst"])
