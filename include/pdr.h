@@ -447,7 +447,9 @@ int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, c
  * d_iB = pT_i^(2p) and d_ij = min(pT_i^(2p), pT_j^(2p)) dR_ij^2 / R^2
  * (dR in rapidity and azimuth) over the remaining objects; a pair merges by
  * four-momentum addition, a beam distance makes a jet.  Jets are ordered by
- * decreasing pT.  Substructure (the output table of Sec. 2.5): with the
+ * decreasing pT.  The e+e- generalized kT (ee = 1) takes energies and
+ * opening angles instead: d_iB = E_i^(2p), d_ij = min(E_i^(2p), E_j^(2p))
+ * (1 - cos theta_ij) / (1 - cos R).  Substructure (the output table of Sec. 2.5): with the
  * energy correlation functions of the jet's constituents
  * e2 = sum_{i<j} z_i z_j dR_ij and e3 = sum_{i<j<k} z_i z_j z_k dR_ij dR_ik dR_jk
  * (z = pT / sum pT of the constituents, angular exponent 1), C2 = e3 / e2^2
@@ -462,8 +464,10 @@ typedef struct pdr_jet_params {
   uint32_t collection;            /* PDR_JETS_*                               */
   uint32_t nconst_min;            /* keep jets with at least this many objects */
   double p;                       /* -1 anti-kT, 0 Cambridge/Aachen, 1 kT      */
-  double R;                       /* jet radius (> 0, <= 10)                   */
+  double R;                       /* jet radius (> 0, <= 10; e+e-: <= pi)      */
   double pt_min;                  /* GeV                                       */
+  uint32_t ee;                    /* 1: the e+e- generalized kT (below)        */
+  uint32_t pad;
 } pdr_jet_params;
 
 typedef struct {

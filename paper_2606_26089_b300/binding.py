@@ -146,17 +146,22 @@ def make_ip_params(resolution=IP_RESOLUTION, vx=None, vy=None) -> pdr_ip_params:
 
 class pdr_jet_params(C.Structure):
     _fields_ = [("collection", C.c_uint32), ("nconst_min", C.c_uint32), ("p", C.c_double), ("R", C.c_double),
-                ("pt_min", C.c_double)]
+                ("pt_min", C.c_double), ("ee", C.c_uint32), ("pad", C.c_uint32)]
 
 
 JET_ALGORITHMS = {"antikt": -1.0, "cambridge": 0.0, "kt": 1.0}
 
 
 def make_jet_params(collection: str = "pflow", algorithm: str = "antikt", R: float = 0.5, pt_min: float = 0.0,
-                    nconst_min: int = 1, p: Optional[float] = None) -> pdr_jet_params:
-    """Clustering pipeline parameters (collection, algorithm or exponent p, dr, pt_min, nconst_min)."""
+                    nconst_min: int = 1, p: Optional[float] = None, ee: bool = False) -> pdr_jet_params:
+    """Clustering pipeline parameters (collection, algorithm or exponent p, dr, pt_min, nconst_min;
+    ee: the e+e- generalized kT, algorithm "ee-genkt" with p)."""
+    if algorithm == "ee-genkt":
+        ee = True
+        algorithm = "antikt" if p is None else algorithm
     return pdr_jet_params({"pflow": 0, "truth": 1}[collection], int(nconst_min),
-                          float(JET_ALGORITHMS[algorithm] if p is None else p), float(R), float(pt_min))
+                          float(JET_ALGORITHMS[algorithm] if p is None else p), float(R), float(pt_min),
+                          int(bool(ee)), 0)
 
 
 class pdr_features(C.Structure):

@@ -30,13 +30,14 @@ namespace {
 struct WS {
   double *px, *py, *ap, *am;
   float *y, *phi, *k2p, *nnr2, *dist;
+  float* nz;          // e+e-: (y, phi, nz) hold the unit direction instead
   int32_t *nn, *nc;   // nc > 0: active with nc constituents; < 0: a jet of -nc; 0: merged away
   int16_t *tile, *next, *head;   // tile lists of the active objects
   int16_t* parent;               // the object a merged-away object went into, or -1
   float *pt0, *y0, *phi0;        // each object as loaded (the jets' constituents; global scratch)
 };
 
-__device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t cap) {
+__device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t cap, bool ee) {
   WS w;
   w.px = mom;
   w.py = mom + cap;
@@ -52,7 +53,8 @@ __device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t c
   w.k2p = f + 2 * cap;
   w.nnr2 = f + 3 * cap;
   w.dist = f + 4 * cap;
-  int32_t* q = reinterpret_cast<int32_t*>(f + 5 * cap);
+  w.nz = ee ? f + 5 * cap : nullptr;
+  int32_t* q = reinterpret_cast<int32_t*>(f + (ee ? 6 : 5) * cap);
   w.nn = q;
   w.nc = q + cap;
   int16_t* h = reinterpret_cast<int16_t*>(q + 2 * cap);
@@ -75,6 +77,16 @@ __device__ __forceinline__ float dr2(const WS& w, uint32_t i, float yk, float pk
   float dp = fabsf(w.phi[i] - pk);
   if (dp > 3.14159265f) dp = 6.28318531f - dp;
   return fmaf(dy, dy, dp * dp);
+}
+
+// The pair metric of the clustering: dR^2 in (y, phi), or for e+e-
+// |n_i - n_j|^2 = 2 (1 - cos theta) of the unit directions.
+__device__ __forceinline__ float metric(const WS& w, bool ee, uint32_t i, float a, float b, float c) {
+  if (ee) {
+    const float dx = w.y[i] - a, dy = w.phi[i] - b, dz = w.nz[i] - c;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  }
+  return dr2(w, i, a, b);
 }
 
 __device__ __forceinline__ float dr2_between(float y1, float p1, float y2, float p2) {
@@ -158,14 +170,15 @@ __device__ __forceinline__ void search(const JetParams& p, const WS& w, uint32_t
                                        int32_t& bi) {
   best = p.R2;
   bi = -1;
-  const float yk = w.y[k], pk = w.phi[k];
+  const bool ee = p.ee != 0;
+  const float yk = w.y[k], pk = w.phi[k], zk = ee ? w.nz[k] : 0.0f;
   if (lane < 9u) {
     const int t = neighbour(p, w.tile[k], (int)lane);
     if (t >= 0) {
       int q = w.head[t];
       for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
         if (q != (int)k) {
-          const float d = dr2(w, (uint32_t)q, yk, pk);
+          const float d = metric(w, ee, (uint32_t)q, yk, pk, zk);
           if (d < best || (d == best && q < bi)) { best = d; bi = q; }
         }
         q = w.next[q];
@@ -208,7 +221,17 @@ __device__ __forceinline__ uint32_t load_objects(const JetParams& p, const WS& w
     w.y0[k] = y;
     w.phi0[k] = phi;
     w.parent[k] = -1;
-    w.k2p[k] = kt2p_of(pt * pt, p.p);
+    if (p.ee) {
+      // unit direction of the momentum and E^2p
+      const float ch = coshf(eta), ic = 1.0f / ch;
+      w.y[k] = cp * ic;
+      w.phi[k] = sp * ic;
+      w.nz[k] = tanhf(eta);
+      const float pc = pt * ch;
+      w.k2p[k] = kt2p_of(fmaf(pc, pc, m * m), p.p);
+    } else {
+      w.k2p[k] = kt2p_of(pt * pt, p.p);
+    }
     w.nc[k] = 1;
   };
   if (p.collection == PDR_JETS_PFLOW) {
@@ -251,8 +274,8 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const uint64_t w0 = (uint64_t)blockIdx.x * p.warps + wib;
-  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap), p.scratch + w0 * (uint64_t)PDR_JET_SCRATCH_DOUBLES * p.cap,
-                     p.cap);
+  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap, p.ee != 0),
+                     p.scratch + w0 * (uint64_t)PDR_JET_SCRATCH_DOUBLES * p.cap, p.cap, p.ee != 0);
   const uint64_t nw = (uint64_t)gridDim.x * p.warps;
   const float inv_R2 = p.inv_R2;
   for (uint64_t e = w0; e < p.n_events; e += nw) {
@@ -317,9 +340,20 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
           w.nc[mb] = 0;
           w.parent[mb] = (int16_t)ma;
           const float fx = (float)w.px[ma], fy = (float)w.py[ma];
-          w.y[ma] = 0.5f * logf((float)w.ap[ma] / (float)w.am[ma]);
-          w.phi[ma] = atan2f(fy, fx);
-          w.k2p[ma] = kt2p_of(fmaf(fx, fx, fy * fy), p.p);
+          if (p.ee) {
+            const double pz = 0.5 * (w.ap[ma] - w.am[ma]), en = 0.5 * (w.ap[ma] + w.am[ma]);
+            const float fz = (float)pz;
+            const float ip = rsqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
+            w.y[ma] = fx * ip;
+            w.phi[ma] = fy * ip;
+            w.nz[ma] = fz * ip;
+            const float fe = (float)en;
+            w.k2p[ma] = kt2p_of(fe * fe, p.p);
+          } else {
+            w.y[ma] = 0.5f * logf((float)w.ap[ma] / (float)w.am[ma]);
+            w.phi[ma] = atan2f(fy, fx);
+            w.k2p[ma] = kt2p_of(fmaf(fx, fx, fy * fy), p.p);
+          }
           push(w, tile_of(p, w.y[ma], w.phi[ma]), ma);
         } else {
           unlink(w, i, p.cap, p.err);
@@ -332,7 +366,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       // took part (distance -1) and offer the merged object to those near it;
       // re-search the flagged ones; take the next minimum
       const int ta = w.tile[ma];
-      const float ya = w.y[ma], pa = w.phi[ma];
+      const float ya = w.y[ma], pa = w.phi[ma], za = p.ee ? w.nz[ma] : 0.0f;
 #pragma unroll 4
       for (uint32_t k = lane; k < n; k += 32u) {
         if (w.nc[k] <= 0) continue;
@@ -340,7 +374,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
         if (m == (int32_t)i || (merge && (m == j || k == ma))) {
           w.dist[k] = -1.0f;
         } else if (merge && adjacent(p, w.tile[k], ta)) {
-          const float d = dr2(w, k, ya, pa);
+          const float d = metric(w, p.ee != 0, k, ya, pa, za);
           if (d < w.nnr2[k] || (d == w.nnr2[k] && (int32_t)ma < m)) {
             w.nn[k] = (int32_t)ma;
             w.nnr2[k] = d;

@@ -1826,6 +1826,7 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   if (jp->collection == PDR_JETS_PFLOW && (!o || !o->tracks || !o->eflow || !o->counts))
     return fail(PDR_EINVAL, "PFlow jets need the response's tracks, EFlow neutrals and counts");
   if (!(jp->R > 0.0) || !(jp->R <= 10.0)) return fail(PDR_EINVAL, "jet radius must be in (0, 10]");
+  if (jp->ee && !(jp->R <= M_PI)) return fail(PDR_EINVAL, "e+e- jet radius must be in (0, pi]");
   if (!std::isfinite(jp->p) || !(jp->pt_min >= 0.0) || !std::isfinite(jp->pt_min))
     return fail(PDR_EINVAL, "bad clustering exponent or pT cut");
   cudaSetDevice(ctx->device);
@@ -1845,14 +1846,18 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   p.collection = jp->collection;
   p.nconst_min = jp->nconst_min;
   p.p = (float)jp->p;
-  p.R2 = (float)(jp->R * jp->R);
-  p.inv_R2 = (float)(1.0 / (jp->R * jp->R));
+  p.ee = jp->ee ? 1u : 0u;
+  // the pair metric's normalisation: R^2, or |n_i - n_j|^2 at theta = R for e+e-
+  const double R2 = jp->ee ? 2.0 * (1.0 - std::cos(jp->R)) : jp->R * jp->R;
+  p.R2 = (float)R2;
+  p.inv_R2 = (float)(1.0 / R2);
   p.pt_min = (float)jp->pt_min;
   // tiles at least R (plus a rounding margin) wide: rapidity [-6, 6]
   // (clamped beyond), azimuth periodic; at most 32 x 32
+  // (e+e-: one tile; the neighbour searches then walk every object)
   const double rw = jp->R * 1.0001;
-  p.nty = (int32_t)std::min(32.0, std::max(1.0, std::floor(12.0 / rw)));
-  int32_t ntp = (int32_t)std::min(32.0, std::floor(2.0 * M_PI / rw));
+  p.nty = jp->ee ? 1 : (int32_t)std::min(32.0, std::max(1.0, std::floor(12.0 / rw)));
+  int32_t ntp = jp->ee ? 1 : (int32_t)std::min(32.0, std::floor(2.0 * M_PI / rw));
   p.ntp = ntp < 3 ? 1 : ntp;
   p.y0 = -6.0f;
   p.inv_wy = (float)(p.nty / 12.0);
@@ -1869,7 +1874,7 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   const uint32_t cap = std::max<uint32_t>(32u, (max_n + 31u) & ~31u);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-  if (jet_ws_bytes(cap) > (uint64_t)smem_max)
+  if (jet_ws_bytes(cap, jp->ee != 0) > (uint64_t)smem_max)
     return fail(PDR_EOVERFLOW, "event has more clustering objects than fit in shared memory");
   // The workspace of the largest event sets how many warps share an SM; so
   // events up to 288 objects (most of a batch of a few hundred particles a
@@ -1880,7 +1885,7 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   for (int k = 0; k < (cap > tier ? 2 : 1); ++k) {
     p.cap = caps[k];
     p.min_obj = k == 0 ? 0u : tier + 1u;
-    const uint64_t ws = jet_ws_bytes(p.cap);
+    const uint64_t ws = jet_ws_bytes(p.cap, p.ee != 0);
     // two blocks an SM where the shared memory allows (shorter tails)
     p.warps = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, (uint64_t)smem_max / ws / 2));
     const size_t smem = (size_t)(p.warps * ws);

@@ -156,3 +156,36 @@ def test_bad_parameters_are_rejected(B, ctx, pflow):
         ctx.cluster_jets(b, B.make_outputs(out), B.make_jet_params(R=0.0), jets, counts)
     with pytest.raises(B.PdrError):
         ctx.cluster_jets(b, None, B.make_jet_params("pflow"), jets, counts)
+
+
+def test_ee_genkt_on_ee_events(B, ctx):
+    """e+e- generalized kT (energies, opening angles) on the e+e- workload's
+    PFlow objects (ALEPH-like card): anti-kT-like p = -1 with R = 0.7 and the
+    Durham-like p = 1 with R = pi."""
+    from paper_2606_26089_b300 import synth
+    batch = synth.make_ee(60, seed=47)
+    cid = ctx.card_load("ee_like")
+    card = oracle.load_card("ee_like")
+    dev = B.batch_to_device(batch)
+    out = B.alloc_outputs(batch.n_events, batch.n_particles, debug=True)
+    host = P.run_gpu(ctx, cid, batch, SEED, dev=dev, outs=out)
+    stats = P.Stats()
+    refs = [P.compare_event(card, batch.event(e), P.gpu_event(host, batch, e), SEED, e, stats)
+            for e in range(batch.n_events)]
+    for p_, R in ((-1.0, 0.7), (1.0, np.pi)):
+        params = B.make_jet_params("pflow", "ee-genkt", R, 0.0, 1, p=p_)
+        g, gc = _gpu_jets(B, ctx, batch, dev, cid, out, params)
+        skipped = n_jets = 0
+        for e in range(batch.n_events):
+            fm = OF.pflow_four_momenta(refs[e], batch.event(e))
+            o, marg = oracle.cluster(*fm, p=p_, R=R, pt_min=0.0, nconst_min=1, ee=True)
+            a = int(batch.offsets[e])
+            try:
+                _compare(g[a:a + gc[e]], o)
+            except AssertionError:
+                if not marg:
+                    raise
+                skipped += 1
+                continue
+            n_jets += len(o)
+        assert skipped <= 6 and n_jets >= batch.n_events   # (R = pi merges each event into one jet)
