@@ -257,13 +257,14 @@ struct JetParams {
 
 // Bytes of one warp's shared-memory clustering workspace for `cap` objects:
 // float y, phi, pT^2p, nearest-neighbour dR^2 and distance, and for e+e- a
-// third direction component (y, phi, nz then hold the unit direction); int nearest
-// neighbour and constituent count; short tile and next-in-tile; then the
-// heads of the tile lists.  (The double four-momenta, touched once a step by
-// one lane, live in global scratch.)
+// third direction component (y, phi, nz then hold the unit direction); int
+// nearest neighbour and constituent count; short tile, next-in-tile, parent
+// and a step's re-search list; then the heads of the tile lists and a
+// counter.  (The double four-momenta, touched once a step by one lane, live
+// in global scratch.)
 constexpr uint32_t PDR_JET_TILES = 1024;
 PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap, bool ee) {
-  return (uint64_t)cap * ((ee ? 6 : 5) * 4 + 2 * 4 + 3 * 2) + 2 * PDR_JET_TILES;
+  return (uint64_t)cap * ((ee ? 6 : 5) * 4 + 2 * 4 + 4 * 2) + 2 * PDR_JET_TILES + 16;
 }
 // Global scratch of one warp, in doubles per object: px, py, E + pz, E - pz,
 // then float pT, y, phi of each object as loaded (two doubles' room).

@@ -34,6 +34,8 @@ struct WS {
   int32_t *nn, *nc;   // nc > 0: active with nc constituents; < 0: a jet of -nc; 0: merged away
   int16_t *tile, *next, *head;   // tile lists of the active objects
   int16_t* parent;               // the object a merged-away object went into, or -1
+  int16_t* todo;                 // a step's objects to re-search
+  int32_t* ntodo;
   float *pt0, *y0, *phi0;        // each object as loaded (the jets' constituents; global scratch)
 };
 
@@ -61,7 +63,9 @@ __device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t c
   w.tile = h;
   w.next = h + cap;
   w.parent = h + 2 * cap;
-  w.head = h + 3 * cap;
+  w.todo = h + 3 * cap;
+  w.head = h + 4 * cap;
+  w.ntodo = reinterpret_cast<int32_t*>(w.head + PDR_JET_TILES);
   return w;
 }
 
@@ -130,13 +134,6 @@ __device__ __forceinline__ int neighbour(const JetParams& p, int t, int l) {
   tp += dp;
   tp = tp < 0 ? tp + p.ntp : (tp >= p.ntp ? tp - p.ntp : tp);
   return (y2 << 5) | tp;
-}
-
-__device__ __forceinline__ bool adjacent(const JetParams& p, int t1, int t2) {
-  if (abs((t1 >> 5) - (t2 >> 5)) > 1) return false;
-  if (p.ntp < 3) return true;
-  const int d = abs((t1 & 31) - (t2 & 31));
-  return d <= 1 || d == p.ntp - 1;
 }
 
 __device__ __forceinline__ void push(const WS& w, int t, uint32_t k) {
@@ -327,6 +324,8 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       const float dB = w.k2p[i];
       const bool merge = j >= 0 && fminf(dB, w.k2p[j]) * w.nnr2[i] * inv_R2 < dB;
       const uint32_t ma = merge ? min(i, (uint32_t)j) : i, mb = merge ? max(i, (uint32_t)j) : i;
+      const int ti = w.tile[i], tj = merge ? w.tile[j] : -1;   // cells before the step
+      if (lane == 0) *w.ntodo = 0;
       __syncwarp();
       if (lane == 0) {
         if (merge) {
@@ -362,43 +361,49 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       }
       __syncwarp();
       if (left == 1) break;
-      // neighbour records, in three passes: flag the objects whose neighbour
-      // took part (distance -1) and offer the merged object to those near it;
-      // re-search the flagged ones; take the next minimum
+      // neighbour records.  Every object's neighbour lies within R of it, so
+      // the objects whose neighbour was i or j are in the cells around i's and
+      // j's cells, and those the merged object may now be nearest to are in
+      // the cells around its new cell: lanes 0-26 walk those 27 cells, listing
+      // (once each) the objects to re-search and offering the merged object
+      // to the others; then the listed objects are re-searched
       const int ta = w.tile[ma];
       const float ya = w.y[ma], pa = w.phi[ma], za = p.ee ? w.nz[ma] : 0.0f;
-#pragma unroll 4
-      for (uint32_t k = lane; k < n; k += 32u) {
-        if (w.nc[k] <= 0) continue;
-        const int32_t m = w.nn[k];
-        if (m == (int32_t)i || (merge && (m == j || k == ma))) {
-          w.dist[k] = -1.0f;
-        } else if (merge && adjacent(p, w.tile[k], ta)) {
-          const float d = metric(w, p.ee != 0, k, ya, pa, za);
-          if (d < w.nnr2[k] || (d == w.nnr2[k] && (int32_t)ma < m)) {
-            w.nn[k] = (int32_t)ma;
-            w.nnr2[k] = d;
-            w.dist[k] = dist_of(w, k, inv_R2);
+      const int grp = (int)(lane / 9u);
+      if (lane < 27u && (grp == 0 || merge)) {
+        const int t = neighbour(p, grp == 0 ? ti : (grp == 1 ? tj : ta), (int)(lane - 9u * grp));
+        if (t >= 0) {
+          int q = w.head[t];
+          for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
+            const int32_t m = w.nn[q];
+            if (m == (int32_t)i || (merge && (m == j || q == (int)ma))) {
+              const int prev = atomicExch(reinterpret_cast<int*>(w.dist + q), __float_as_int(-1.0f));
+              if (prev != __float_as_int(-1.0f)) w.todo[atomicAdd(w.ntodo, 1)] = (int16_t)q;
+            } else if (grp == 2) {
+              const float d = metric(w, p.ee != 0, (uint32_t)q, ya, pa, za);
+              if (d < w.nnr2[q] || (d == w.nnr2[q] && (int32_t)ma < m)) {
+                w.nn[q] = (int32_t)ma;
+                w.nnr2[q] = d;
+                w.dist[q] = dist_of(w, (uint32_t)q, inv_R2);
+              }
+            }
+            q = w.next[q];
           }
         }
       }
       __syncwarp();
-      for (uint32_t t = 0; t < n; t += 32u) {
-        const uint32_t k = t + lane;
-        uint32_t todo = __ballot_sync(PDR_FULL, k < n && w.nc[k] > 0 && w.dist[k] < 0.0f);
-        while (todo) {
-          const uint32_t kk = t + (uint32_t)(__ffs(todo) - 1);
-          todo &= todo - 1u;
-          float best;
-          int32_t bi;
-          search(p, w, kk, lane, best, bi);
-          if (lane == 0) {
-            w.nn[kk] = bi;
-            w.nnr2[kk] = best;
-            w.dist[kk] = dist_of(w, kk, inv_R2);
-          }
-          __syncwarp();
+      const int32_t nt = *w.ntodo;
+      for (int32_t c = 0; c < nt; ++c) {
+        const uint32_t kk = (uint32_t)w.todo[c];
+        float best;
+        int32_t bi;
+        search(p, w, kk, lane, best, bi);
+        if (lane == 0) {
+          w.nn[kk] = bi;
+          w.nnr2[kk] = best;
+          w.dist[kk] = dist_of(w, kk, inv_R2);
         }
+        __syncwarp();
       }
       bd = INFINITY;
       bk = -1;
