@@ -298,12 +298,27 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
     if (lane == 0)
       for (uint32_t k = 0; k < n; ++k) push(w, tile_of(p, w.y[k], w.phi[k]), k);
     __syncwarp();
-    // initial nearest neighbours: the whole warp per object
-    for (uint32_t k = 0; k < n; ++k) {
-      float best;
-      int32_t bi;
-      search(p, w, k, lane, best, bi);
-      if (lane == 0) {
+    // initial nearest neighbours: each lane walks the cells around its own
+    // objects (ties: the lower index, as in the warp search)
+    {
+      const bool ee = p.ee != 0;
+      for (uint32_t k = lane; k < n; k += 32u) {
+        const float yk = w.y[k], pk = w.phi[k], zk = ee ? w.nz[k] : 0.0f;
+        const int tk = w.tile[k];
+        float best = p.R2;
+        int32_t bi = -1;
+        for (int l = 0; l < 9; ++l) {
+          const int t = neighbour(p, tk, l);
+          if (t < 0) continue;
+          int q = w.head[t];
+          for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
+            if (q != (int)k) {
+              const float d = metric(w, ee, (uint32_t)q, yk, pk, zk);
+              if (d < best || (d == best && q < bi)) { best = d; bi = q; }
+            }
+            q = w.next[q];
+          }
+        }
         w.nn[k] = bi;
         w.nnr2[k] = best;
       }
