@@ -309,11 +309,12 @@ def bench_ours(args, dist, rank, ws):
         "clocks": clk,
         "gpu_launches": args.steps,
     }
-    if not args.no_track_ip:
+    # the steps around the response, each timed in its own region (one GPU)
+    if not args.no_track_ip and ws == 1:
         line["track_ip"] = bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts)
-    if not args.no_jets:
+    if not args.no_jets and ws == 1:
         line["jets"] = bench_jets(args, B, ctx, bt, ob, n_ev, n_p, counts)
-    if not args.no_postprocess:
+    if not args.no_postprocess and ws == 1:
         line["postprocess"] = bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts)
     if not args.no_serving and ws == 1:
         line["serving"] = bench_serving(args, B, ctx)

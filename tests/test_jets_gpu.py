@@ -189,3 +189,21 @@ def test_ee_genkt_on_ee_events(B, ctx):
                 continue
             n_jets += len(o)
         assert skipped <= 6 and n_jets >= batch.n_events   # (R = pi merges each event into one jet)
+
+
+def test_event_beyond_the_shared_memory_workspace_is_refused(B, ctx):
+    """An event with more clustering objects than one warp's shared-memory
+    workspace holds is refused on the host (no launch)."""
+    from paper_2606_26089_b300 import synth
+    rng = np.random.default_rng(3)
+    n = 9000
+    rows = list(zip(rng.uniform(0.5, 5.0, n), rng.uniform(-4, 4, n), rng.uniform(-np.pi, np.pi, n),
+                    np.full(n, 0.13957), np.full(n, 211), np.ones(n, int), np.zeros(n)))
+    batch = synth.from_particles([rows])
+    cid = ctx.card_load("cms_like")
+    dev = B.batch_to_device(batch)
+    jets = torch.empty((batch.n_particles, 8), device="cuda")
+    counts = torch.empty((1,), dtype=torch.int32, device="cuda")
+    with pytest.raises(B.PdrError, match="shared memory"):
+        ctx.cluster_jets(B.make_batch(dev, cid, SEED), None, B.make_jet_params("truth"), jets, counts)
+    ctx.check()
