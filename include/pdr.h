@@ -3,7 +3,7 @@
  *
  * The library applies a Delphes-style parametric detector response to every
  * truth particle of every event in a batch: the TorchDelphes module chain of
- * the paper (Sec. 2.2 "parametric backend"; App. C.1): particle propagation in
+ * the paper (Sec. 2.2 "parametric backend"; App. D.1): particle propagation in
  * the solenoid field, tracking / lepton / photon efficiencies, momentum and
  * energy smearing, ECAL/HCAL eta-phi towers with smearing and thresholds,
  * energy-flow track subtraction (Towers and EFlowObjects), and the cone
@@ -65,7 +65,7 @@ typedef enum {
 
 /*
  * Detector card: raw parameters (GeV, m, T), as the paper's cards give the
- * per-module parameters (App. C.1).  The library expands them into device
+ * per-module parameters (App. D.1).  The library expands them into device
  * tables at pdr_card_load; the caller keeps ownership of the struct.
  *
  * Calorimeter grids: each side of eta = 0 is cut into nseg segments; segment

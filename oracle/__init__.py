@@ -6,7 +6,7 @@ its binding) never does, and this package imports nothing from the product: it
 parses the detector card JSON itself and has its own C implementation of every
 step of the method.
 
-The C oracle follows the paper's TorchDelphes module chain (Sec. 2.2, App. C)
+The C oracle follows the paper's TorchDelphes module chain (Sec. 2.2, App. D)
 and the isolation definition of Sec. 2.4 (Eq. 1); see ``oracle.h``.
 """
 

@@ -5,10 +5,10 @@
  * may load this library; the product path never does.  See oracle.h for the
  * contract.  Every function below names the part of the method it follows:
  *
- *   Sec. 2.2 / App. C.1  TorchDelphes module chain: propagation, tracking
+ *   Sec. 2.2 / App. D.1  TorchDelphes module chain: propagation, tracking
  *                        efficiency, momentum smearing, calorimeter response,
  *                        energy-flow merging (Towers, EFlowObjects).
- *   App. C.2             PropagatedParticle (deterministic intermediate).
+ *   App. D.2             PropagatedParticle (deterministic intermediate).
  *   Sec. 2.4, Eq. 1      lepton isolation: cone sum of charged, neutral and
  *                        photon pT, excluding the lepton itself, over pT.
  *
@@ -311,7 +311,7 @@ static int phi_decide(or_dctx* d, uint32_t id, int calo, int nphi, double v) {
 
 /* ------------------------------------------------------------------------ */
 /* Propagation to the calorimeter cylinder (radius R, half-length L) in a     */
-/* uniform field B along z (App. C.2 PropagatedParticle).  The particle starts */
+/* uniform field B along z (App. D.2 PropagatedParticle).  The particle starts */
 /* at (0, 0, vz).  Neutral particles (or B = 0) move on a straight line.       */
 /* Charged ones move on a helix of radius r = pT / (0.299792458 |q| |B|); the  */
 /* momentum azimuth turns by -h s / r over transverse arc length s, with        */

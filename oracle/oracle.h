@@ -9,7 +9,7 @@
  * precision in the order the method defines.
  *
  * The method is the paper's parametric backend (TorchDelphes, Sec. 2.2 and
- * App. C.1): particle propagation in the solenoid field, tracking efficiency,
+ * App. D.1): particle propagation in the solenoid field, tracking efficiency,
  * momentum smearing, calorimeter response (towers), energy-flow merging, and
  * the lepton isolation of Sec. 2.4 (Eq. 1).  The paper prints no formulas for
  * the TorchDelphes modules; the readings used here (helix geometry, log-normal

@@ -153,9 +153,10 @@ JET_ALGORITHMS = {"antikt": -1.0, "cambridge": 0.0, "kt": 1.0}
 
 
 def make_jet_params(collection: str = "pflow", algorithm: str = "antikt", R: float = 0.5, pt_min: float = 0.0,
-                    nconst_min: int = 1, p: Optional[float] = None, ee: bool = False) -> pdr_jet_params:
+                    nconst_min: int = 2, p: Optional[float] = None, ee: bool = False) -> pdr_jet_params:
     """Clustering pipeline parameters (collection, algorithm or exponent p, dr, pt_min, nconst_min;
-    ee: the e+e- generalized kT, algorithm "ee-genkt" with p)."""
+    ee: the e+e- generalized kT, algorithm "ee-genkt" with p).  The defaults are the
+    clustering pipeline's (App. C: pflow, antikt, dr 0.5, pt_min 0, nconst_min 2)."""
     if algorithm == "ee-genkt":
         ee = True
         algorithm = "antikt" if p is None else algorithm
@@ -607,12 +608,14 @@ def event_records(out_host: dict, counts: np.ndarray, offsets: np.ndarray, e: in
 # ---------------------------------------------------------------------------
 # pile-up merging helpers
 # ---------------------------------------------------------------------------
-# vertex-time width and truncation defaults of the pile-up block (Sec. 2.2)
+# defaults of the pile-up block (Sec. 2.2; App. C, parametric pile-up fields)
+SIGMA_Z = 0.053
+MAX_Z = 0.25
 SIGMA_T = 160e-12
 MAX_T = 800e-12
 
 
-def make_pileup(pool_dev: dict, mean: float, sigma_z: float, max_z: float, smear_hs: bool,
+def make_pileup(pool_dev: dict, mean: float, sigma_z: float = SIGMA_Z, max_z: float = MAX_Z, smear_hs: bool = True,
                 sigma_t: float = SIGMA_T, max_t: float = MAX_T) -> pdr_pileup:
     """pdr_pileup over a device pool (batch_to_device of the minimum-bias batch)."""
     p = pdr_pileup()

@@ -2,7 +2,7 @@
 //
 // One persistent launch walks a ragged CSR batch.  A "team" of TEAM threads
 // (a warp ... a whole CTA) owns one event at a time and runs the TorchDelphes
-// chain of the paper (Sec. 2.2, App. C.1) plus the isolation of Sec. 2.4:
+// chain of the paper (Sec. 2.2, App. D.1) plus the isolation of Sec. 2.4:
 //
 //   phase 1, per particle (chunks of TEAM particles, coalesced SoA loads):
 //     S0 classify, S1 propagate to the calorimeter surface, S2 tracking

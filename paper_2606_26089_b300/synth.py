@@ -1,7 +1,7 @@
 """Seeded synthetic truth events shaped like the paper's workloads.
 
 The paper's samples (Pythia8 H->ZZ->4l, ttW and ee->ZZ->qq HepMC files, and the
-MinBias pile-up file; Sec. 3 performance table and App. C validation) are not
+MinBias pile-up file; Sec. 3 performance table and App. D validation) are not
 available, so these generators stand in for them.  They only draw truth-level
 particles; nothing here computes any part of the detector response, so both the
 CUDA path and the CPU oracle can take their inputs from this module.

@@ -1,4 +1,4 @@
-"""Pins for the oracle's propagation step (App. C.2, PropagatedParticle).
+"""Pins for the oracle's propagation step (App. D.2, PropagatedParticle).
 
 The oracle uses the closed-form helix/cylinder intersection.  These tests pin
 it to things other than that formula:
