@@ -293,6 +293,7 @@ enum : uint32_t {
   ERR_TABLE = 4u,      // tower table full (cannot happen when sized as documented)
   ERR_PILEUP = 8u,     // pile-up merge: an event's size differs from the offsets given
   ERR_VERTEX = 16u,    // pile-up merge: no vertex inside the truncation in 1024 draws
+  ERR_JETS = 32u,      // jet clustering: more jets than the event's slots, or an inconsistent cell list
 };
 
 // Bytes of a team's event workspace: the tower table (keys, owner, esum, etrk

@@ -158,7 +158,7 @@ __device__ __forceinline__ void unlink(const WS& w, uint32_t k, uint32_t cap, ui
     }
     q = nx;
   }
-  atomicOr(err, ERR_TABLE);
+  atomicOr(err, ERR_JETS);
 }
 
 // Nearest neighbour within R of object k among the active objects of the
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       if (rank < n_part) p.jets[a + rank] = J;   // the event's slots hold n_part records
     }
     if (lane == 0) {
-      if (m > n_part) atomicOr(p.err, ERR_OVERSIZE);
+      if (m > n_part) atomicOr(p.err, ERR_JETS);
       p.jet_counts[e] = (uint32_t)min((uint64_t)m, n_part);
     }
     __syncwarp();
