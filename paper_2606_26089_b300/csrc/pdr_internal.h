@@ -285,6 +285,8 @@ struct KParams {
   uint64_t g_team_bytes;
   uint32_t* err;                     // device error word (bit flags below)
   KSeg seg[PDR_LAUNCH_SEGS];
+  uint32_t smem_may_overflow;        // 1: the shared table is sized below the particle count (an event
+                                     // whose towers overflow it is redone with the global table)
 };
 
 enum : uint32_t {

@@ -396,6 +396,10 @@ struct Tbl {
   __device__ __forceinline__ uint32_t* jobs() const { return pinfo() + nmax; }
 };
 
+// Set when the block's shared table fills up, in kernels built for a shared
+// table sized below the particle count (one team a block); see process_event.
+__shared__ uint32_t s_table_full;
+
 __device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32_t nmax) {
   Tbl t;
   t.base = base;
@@ -409,6 +413,7 @@ __device__ __forceinline__ Tbl carve(unsigned char* base, uint32_t slots, uint32
 // its own deposit, track energy and index with plain stores (before the team
 // barrier that precedes any accumulation); every other depositor adds with
 // atomics after that barrier.  Returns the slot; *claimed tells which case.
+template <bool OVF>
 __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uint32_t i,
                                                  unsigned long long e_fp, unsigned long long t_fp,
                                                  bool* claimed, uint32_t* err) {
@@ -427,7 +432,10 @@ __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uin
     if (prev == key) return h;
     h = h + 1 == T.nslots ? 0u : h + 1;
   }
-  atomicOr(err, ERR_TABLE);
+  // full: OVF flags it for the block (read after the particle phase, which
+  // then hands the event to a larger table); otherwise it is an error
+  if constexpr (OVF) s_table_full = 1u;
+  else atomicOr(err, ERR_TABLE);
   return PDR_EMPTY;
 }
 
@@ -497,10 +505,15 @@ __device__ __forceinline__ void iso_object(const HotCard& K, float4 obj, uint32_
 //       candidates' cones (S8)
 //   3   isolation results; candidates beyond the staged ones loop over all
 //       EFlow objects
-template <int TEAM>
-__device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
-                                              const Tbl& T, TeamTail& tt, const TeamCtx<TEAM>& tc,
-                                              uint64_t e, uint64_t a, uint32_t n) {
+// OVF: the table is a shared table sized below the particle count.  One that
+// fills up sets s_table_full, and the function returns false after the
+// particle phase, having written nothing but debug records, so that the
+// caller redoes the event with a larger table.  (Otherwise a full table, which
+// sizing by particle count rules out, reports an error.)
+template <int TEAM, bool OVF>
+__device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
+                                              const Tbl& T, TeamTail& tt, const TeamCtx<TEAM>& tc, uint64_t e,
+                                              uint64_t a, uint32_t n) {
   const uint32_t event = S.event_base + (uint32_t)e;
   const bool dbg = S.debug != nullptr;
   uint32_t n_trk = 0, n_cand = 0, flip = 0;
@@ -516,7 +529,7 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     uint32_t slot = PDR_EMPTY;
     bool claimed = false;
     const unsigned long long e_fp = to_fp(o.E);
-    if (valid && o.key != PDR_NO_KEY) slot = table_insert(T, o.key, i, e_fp, 0ull, &claimed, err);
+    if (valid && o.key != PDR_NO_KEY) slot = table_insert<OVF>(T, o.key, i, e_fp, 0ull, &claimed, err);
     if (valid) T.pinfo()[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
     const bool has_job = o.job != PDR_EMPTY;
     uint32_t tot;
@@ -533,6 +546,9 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
     n_job += tot & 0xFFFFu;
   }
   tc.sync();
+  if constexpr (OVF) {
+    if (s_table_full) return false;   // every thread reads it after the barrier
+  }
 
   // ---- 1b: smearing jobs (S2, S3, S4) in particle order
   for (uint32_t j0 = 0; j0 < n_job; j0 += TEAM) {
@@ -690,12 +706,13 @@ __device__ __forceinline__ void process_event(const KSeg& S, uint32_t* err, cons
   tc.sync();
   if (tc.tid == 0)
     reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
+  return true;
 }
 
 // The persistent event loop of one team.  ONE: the launch holds a single
 // batch, whose fields the compiler then reads straight from the parameter
 // block (no per-event segment lookup).
-template <int TEAM, int BLOCK, bool ONE>
+template <int TEAM, int BLOCK, bool ONE, bool OVF>
 __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem, const TeamCtx<TEAM>& tc,
                                            const Tbl& st, TeamTail& tt) {
   constexpr int NT = BLOCK / TEAM;
@@ -723,12 +740,24 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
       continue;
     }
     if (n <= p.nmax_smem) {
-      process_event<TEAM>(S, p.err, K, KD, st, tt, tc, e, a, n);
-    } else if (p.gscratch != nullptr && n <= p.g_nmax) {
+      if constexpr (!OVF) {
+        process_event<TEAM, false>(S, p.err, K, KD, st, tt, tc, e, a, n);
+        continue;
+      } else {
+        if (process_event<TEAM, true>(S, p.err, K, KD, st, tt, tc, e, a, n)) continue;
+        // the shared table (sized below the particle count) filled up: reset
+        // the flag, empty the table and redo the event with the global table
+        tc.sync();
+        if (tc.tid == 0) s_table_full = 0u;
+        for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys()[s] = PDR_EMPTY;
+        tc.sync();
+      }
+    }
+    if (p.gscratch != nullptr && n <= p.g_nmax) {
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_nmax);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys()[s] = PDR_EMPTY;
       tc.sync();
-      process_event<TEAM>(S, p.err, K, KD, gt, tt, tc, e, a, n);
+      process_event<TEAM, false>(S, p.err, K, KD, gt, tt, tc, e, a, n);
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);
@@ -744,9 +773,10 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
 // Register cap: at most 64 registers a thread (1024 / BLOCK resident CTAs).
 // The launch covers up to PDR_LAUNCH_SEGS batches (each with its own card,
 // inputs, outputs and seed) as one launch-wide sequence of events.
-template <int TEAM, int BLOCK>
+template <int TEAM, int BLOCK, bool OVF>
 __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1)
     fused_kernel(const __grid_constant__ KParams p) {
+  static_assert(!OVF || TEAM == BLOCK, "the table-full flag is one per block");
   extern __shared__ __align__(16) unsigned char smem[];
   for (uint32_t c = 0; c < p.n_cards; ++c)
     for (uint32_t k = threadIdx.x; k < p.hot_bytes[c] / 16; k += BLOCK)
@@ -761,9 +791,12 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
   TeamTail& tt = *reinterpret_cast<TeamTail*>(tail);
   for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys()[s] = PDR_EMPTY;
   if ((uint32_t)tc.tid < PDR_CMAX) tt.csum[tc.tid] = 0ull;
+  if constexpr (OVF) {
+    if (tc.tid == 0) s_table_full = 0u;
+  }
   __syncthreads();
-  if (p.n_segs == 1) event_loop<TEAM, BLOCK, true>(p, smem, tc, st, tt);
-  else event_loop<TEAM, BLOCK, false>(p, smem, tc, st, tt);
+  if (p.n_segs == 1) event_loop<TEAM, BLOCK, true, OVF>(p, smem, tc, st, tt);
+  else event_loop<TEAM, BLOCK, false, OVF>(p, smem, tc, st, tt);
 }
 
 // ------------------------------------------------------- auxiliary kernels
@@ -837,24 +870,26 @@ __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64
 }
 
 // ------------------------------------------------------- launch helpers
-template <int TEAM, int BLOCK>
+template <int TEAM, int BLOCK, bool OVF>
 static cudaError_t launch_t(const KParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
-  auto fn = fused_kernel<TEAM, BLOCK>;
+  auto fn = fused_kernel<TEAM, BLOCK, OVF>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, BLOCK, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int TEAM, int BLOCK>
+template <int TEAM, int BLOCK, bool OVF>
 static cudaError_t occupancy_t(int* blocks, size_t smem) {
-  auto fn = fused_kernel<TEAM, BLOCK>;
+  auto fn = fused_kernel<TEAM, BLOCK, OVF>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, BLOCK, smem);
 }
 
 #define PDR_SHAPES(X) X(32, 128) X(32, 256) X(64, 256) X(128, 128) X(128, 256) X(256, 256) X(512, 512) X(1024, 1024)
+// shapes also built with a shared table sized below the particle count (large events)
+#define PDR_OVF_SHAPES(X) X(512, 512) X(1024, 1024)
 
 bool shape_supported(uint32_t team, uint32_t block) {
 #define PDR_SUP(T, B) if (team == T && block == B) return true;
@@ -863,16 +898,36 @@ bool shape_supported(uint32_t team, uint32_t block) {
   return false;
 }
 
+bool shape_supports_overflow(uint32_t team, uint32_t block) {
+#define PDR_SUP(T, B) if (team == T && block == B) return true;
+  PDR_OVF_SHAPES(PDR_SUP)
+#undef PDR_SUP
+  return false;
+}
+
 cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
                          cudaStream_t s) {
-#define PDR_L(T, B) if (team == T && block == B) return launch_t<T, B>(p, grid, smem, s);
+  if (p.smem_may_overflow) {
+#define PDR_LO(T, B) if (team == T && block == B) return launch_t<T, B, true>(p, grid, smem, s);
+    PDR_OVF_SHAPES(PDR_LO)
+#undef PDR_LO
+    return cudaErrorInvalidValue;
+  }
+#define PDR_L(T, B) if (team == T && block == B) return launch_t<T, B, false>(p, grid, smem, s);
   PDR_SHAPES(PDR_L)
 #undef PDR_L
   return cudaErrorInvalidValue;
 }
 
+cudaError_t occupancy_fused_ovf(uint32_t team, uint32_t block, size_t smem, int* blocks) {
+#define PDR_OO(T, B) if (team == T && block == B) return occupancy_t<T, B, true>(blocks, smem);
+  PDR_OVF_SHAPES(PDR_OO)
+#undef PDR_OO
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks) {
-#define PDR_O(T, B) if (team == T && block == B) return occupancy_t<T, B>(blocks, smem);
+#define PDR_O(T, B) if (team == T && block == B) return occupancy_t<T, B, false>(blocks, smem);
   PDR_SHAPES(PDR_O)
 #undef PDR_O
   return cudaErrorInvalidValue;

@@ -27,6 +27,8 @@ bool shape_supported(uint32_t team, uint32_t block);
 cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
                          cudaStream_t s);
 cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks);
+cudaError_t occupancy_fused_ovf(uint32_t team, uint32_t block, size_t smem, int* blocks);
+bool shape_supports_overflow(uint32_t team, uint32_t block);
 cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
                              cudaStream_t s);
 cudaError_t launch_pileup_count(const PuParams& p, int n_sms, cudaStream_t s);
@@ -393,6 +395,7 @@ int expand_card(const pdr_card* c, DevCard& D) {
 struct Shape {
   uint32_t team, block, slots, nmax, grid;
   size_t smem;
+  bool may_overflow = false;   // shared table sized below the particle count (see optimistic_shape)
 };
 
 const uint32_t kTeams[] = {32, 64, 128, 256, 512, 1024};
@@ -426,6 +429,35 @@ int make_shape(pdr_ctx* ctx, uint32_t team, uint32_t block, uint32_t want_slots,
   if (per_sm < 1) return fail(PDR_EINVAL, "launch shape cannot be resident");
   S.grid = grid ? grid : (uint32_t)(per_sm * ctx->n_sms);
   return PDR_OK;
+}
+
+// For events larger than a table sized by particle count allows in shared
+// memory: keep every particle's entries on chip and give the tower table the
+// rest.  An event has far fewer distinct towers than particles (pile-up
+// events of 5,500 particles hit a few thousand), so the table rarely fills;
+// an event that fills it is redone by the kernel with the global table.  Not
+// worth it when the table would get fewer slots than half the particles.
+bool optimistic_shape(pdr_ctx* ctx, uint32_t max_n, uint32_t hot_bytes, uint32_t grid, Shape& S) {
+  const uint32_t nt = S.block / S.team;
+  if (!shape_supports_overflow(S.team, S.block) || max_n > 65535u || hot_bytes + 16u >= ctx->smem_optin)
+    return false;
+  // per team; 16 bytes stay free for the kernel's static shared flag
+  const uint64_t budget = (uint64_t)(ctx->smem_optin - hot_bytes - 16u) / nt;
+  const uint64_t fixed = sizeof(TeamTail) + (uint64_t)max_n * 8u;
+  if (budget <= fixed) return false;
+  const uint64_t slots = std::min<uint64_t>(((budget - fixed) / 24u) & ~31ull, 65536u);
+  if (slots < 64 || slots < max_n / 2) return false;
+  Shape T = S;
+  T.slots = (uint32_t)slots;
+  T.nmax = max_n;
+  T.smem = (size_t)(hot_bytes + nt * team_smem_bytes(S.team, T.slots, T.nmax));
+  if (T.smem + 16u > ctx->smem_optin) return false;
+  int per_sm = 0;
+  if (occupancy_fused_ovf(S.team, S.block, T.smem, &per_sm) != cudaSuccess || per_sm < 1) return false;
+  T.grid = grid ? grid : (uint32_t)(per_sm * ctx->n_sms);
+  T.may_overflow = true;
+  S = T;
+  return true;
 }
 
 pdr_launch default_launch(uint32_t max_n) {
@@ -520,8 +552,9 @@ void fill_seg(KSeg& g, const pdr_batch* b, const pdr_outputs* o, uint64_t start,
 int set_tables(pdr_ctx* ctx, KParams& p, const Shape& S, uint32_t max_n) {
   p.table_slots = S.slots;
   p.nmax_smem = S.nmax;
+  p.smem_may_overflow = S.may_overflow ? 1u : 0u;
   p.err = ctx->d_err;
-  if (max_n > S.nmax) {
+  if (max_n > S.nmax || S.may_overflow) {   // the global table: larger events, or the redo of an overflow
     const uint32_t gs = slots_for(max_n);
     if (gs > 65536) return fail(PDR_EOVERFLOW, "event larger than 49152 particles");
     p.g_slots = gs;
@@ -561,6 +594,7 @@ int prepare_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* c
   p.n_events = start;
   int rc = make_shape(ctx, P.team, P.block, P.want_slots, P.grid, p.hot_total, S);
   if (rc) return rc;
+  if (max_n > S.nmax) optimistic_shape(ctx, max_n, p.hot_total, P.grid, S);
   return set_tables(ctx, p, S, max_n);
 }
 

@@ -426,3 +426,28 @@ def test_full_size_ee(B, ctx, cards, synth):
 
 def test_full_size_pileup(B, ctx, cards, synth):
     _full(B, ctx, cards, synth, "pileup", seed=3, sample=6, count_check=False)
+
+
+def test_large_events_in_shared_tables_and_the_overflow_redo(B, ctx, cards, synth):
+    """Events too large for a table sized by particle count keep their
+    particles on chip with a tower table sized below it: pile-up events fit;
+    an event of 8,000 photons spread over the fine ECAL grid hits more towers
+    than the table holds and is redone with the global table.  Both against
+    the oracle, and bitwise equal to the same events run with global tables
+    only (a smaller team shape)."""
+    rng = np.random.default_rng(9)
+    n = 8000
+    spread = list(zip(rng.uniform(1.0, 20.0, n), rng.uniform(-1.4, 1.4, n), rng.uniform(-np.pi, np.pi, n),
+                      np.zeros(n), np.full(n, 22), np.zeros(n, int)))
+    pile = synth.make("pileup", n_events=2)
+    rows = []
+    for e in range(2):
+        ev = pile.event(e)
+        rows.append(list(zip(ev["pt"], ev["eta"], ev["phi"], ev["mass"], ev["pdg"], ev["charge"], ev["vz"])))
+    small = synth.make("batched", n_events=2)
+    ev_small = [list(zip(*(small.event(e)[k] for k in ("pt", "eta", "phi", "mass", "pdg", "charge"))))
+                for e in range(2)]
+    b = synth.from_particles([ev_small[0], rows[0], spread, rows[1], ev_small[1]])
+    h1, _ = _check_all(ctx, cards, "cms_like", b, seed=21, launch=_launch(B, 1024, 1024))
+    h2, _ = _check_all(ctx, cards, "cms_like", b, seed=21, launch=_launch(B, 256, 256))
+    _same(h1, h2, b)
