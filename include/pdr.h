@@ -482,7 +482,7 @@ typedef struct {
  * layout (event e's k-th jet at [offsets[e] + k]; at most as many jets as
  * the event has particles); jet_counts [n_events] DEVICE.  Each event is
  * clustered by one warp with its objects in shared memory; PDR_EOVERFLOW if
- * an event has more objects than fit (about 6,700; 6,000 for e+e-).  Synchronises `stream`
+ * an event has more objects than fit (about 9,600; 8,200 for e+e-).  Synchronises `stream`
  * once to size the shared memory, then runs asynchronously.  Calls on one
  * context share its clustering scratch (four-momenta in device memory, grown
  * on demand): do not overlap two clusterings of one context on different

@@ -248,6 +248,7 @@ struct JetParams {
   uint32_t warps;                       // warps per block
   float p, R2, inv_R2, pt_min;
   int32_t nty, ntp;                     // rapidity x azimuth tiles, each at least R wide
+  uint32_t ntiles;                      // nty * ntp
   float y0, inv_wy, inv_wp;
   pdr_jet* jets;
   uint32_t* jet_counts;
@@ -255,20 +256,20 @@ struct JetParams {
   double* scratch;                      // PDR_JET_SCRATCH_DOUBLES x cap doubles for each warp of the grid
 };
 
-// Bytes of one warp's shared-memory clustering workspace for `cap` objects:
-// float y, phi, pT^2p, nearest-neighbour dR^2 and distance, and for e+e- a
-// third direction component (y, phi, nz then hold the unit direction); int
-// nearest neighbour and constituent count; short tile, next-in-tile, parent
-// and a step's re-search list; then the heads of the tile lists and a
-// counter.  (The double four-momenta, touched once a step by one lane, live
-// in global scratch.)
-constexpr uint32_t PDR_JET_TILES = 1024;
-PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap, bool ee) {
-  return (uint64_t)cap * ((ee ? 6 : 5) * 4 + 2 * 4 + 4 * 2) + 2 * PDR_JET_TILES + 16;
+// Bytes of one warp's shared-memory clustering workspace for `cap` objects
+// (a multiple of 32) and `ntiles` tiles: float y, phi, pT^2p and distance,
+// and for e+e- a third direction component (y, phi, nz then hold the unit
+// direction); short nearest neighbour, tile, next-in-tile and a step's
+// re-search list; then the heads of the tile lists and a counter.  (The
+// double four-momenta, constituent counts and merge parents, touched once a
+// step by one lane, live in global scratch.)
+PDR_HD inline uint64_t jet_ws_bytes(uint32_t cap, bool ee, uint32_t ntiles) {
+  return (uint64_t)cap * ((ee ? 5 : 4) * 4 + 4 * 2) + 2 * (uint64_t)((ntiles + 7u) & ~7u) + 16;
 }
 // Global scratch of one warp, in doubles per object: px, py, E + pz, E - pz,
-// then float pT, y, phi of each object as loaded (two doubles' room).
-constexpr uint32_t PDR_JET_SCRATCH_DOUBLES = 6;
+// then float pT, y, phi of each object as loaded, int constituent count and
+// short merge parent (50 of the 56 bytes).
+constexpr uint32_t PDR_JET_SCRATCH_DOUBLES = 7;
 
 // Kernel parameter block (passed by value, read through __grid_constant__).
 struct KParams {

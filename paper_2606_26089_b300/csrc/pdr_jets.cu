@@ -17,6 +17,15 @@
 // light-cone components are sums of positive terms, so the rapidity
 // y = ln((E + pz) / (E - pz)) / 2 of a merged object carries no cancellation
 // even far forward.  Distances are float32.
+//
+// Occupancy: a step is a serial chain of dependent shared-memory accesses, so
+// the time follows the number of events (warps) an SM holds, which the
+// shared workspace limits.  It holds per object only what the step chain
+// reads (24 bytes: y, phi, pT^2p, the distance, and 16-bit neighbour, tile,
+// list and work-list entries); an object's neighbour dR^2 is recomputed from
+// the two positions when needed (bitwise the value the search found), and the
+// constituent counts and merge parents live in global scratch with the
+// four-momenta.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,19 +36,28 @@ namespace pdr {
 
 namespace {
 
+// dist holds, besides the distances (non-negative or +inf), these bit
+// patterns; as unsigned keys all of them order after every distance
+constexpr uint32_t KEY_MERGED = 0xFFFFFFFFu;   // merged away
+constexpr uint32_t KEY_JET = 0xFFFFFFFEu;      // a jet (removed with its beam distance)
+constexpr uint32_t KEY_TODO = 0xBF800000u;     // (-1.0f) listed for a re-search this step
+
 struct WS {
+  // global scratch
   double *px, *py, *ap, *am;
-  float *y, *phi, *k2p, *nnr2, *dist;
-  float* nz;          // e+e-: (y, phi, nz) hold the unit direction instead
-  int32_t *nn, *nc;   // nc > 0: active with nc constituents; < 0: a jet of -nc; 0: merged away
-  int16_t *tile, *next, *head;   // tile lists of the active objects
+  float *pt0, *y0, *phi0;        // each object as loaded (the jets' constituents)
+  int32_t* nc;                   // constituents of each object
   int16_t* parent;               // the object a merged-away object went into, or -1
+  // shared
+  float *y, *phi, *k2p, *dist;
+  float* nz;                     // e+e-: (y, phi, nz) hold the unit direction instead
+  int16_t* nn;                   // nearest neighbour within R, or -1
+  int16_t *tile, *next, *head;   // tile lists of the active objects
   int16_t* todo;                 // a step's objects to re-search
   int32_t* ntodo;
-  float *pt0, *y0, *phi0;        // each object as loaded (the jets' constituents; global scratch)
 };
 
-__device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t cap, bool ee) {
+__device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t cap, bool ee, uint32_t ntiles) {
   WS w;
   w.px = mom;
   w.py = mom + cap;
@@ -49,23 +67,21 @@ __device__ __forceinline__ WS carve(unsigned char* base, double* mom, uint32_t c
   w.pt0 = g;
   w.y0 = g + cap;
   w.phi0 = g + 2 * cap;
+  w.nc = reinterpret_cast<int32_t*>(g + 3 * cap);
+  w.parent = reinterpret_cast<int16_t*>(w.nc + cap);
   float* f = reinterpret_cast<float*>(base);
   w.y = f;
   w.phi = f + cap;
   w.k2p = f + 2 * cap;
-  w.nnr2 = f + 3 * cap;
-  w.dist = f + 4 * cap;
-  w.nz = ee ? f + 5 * cap : nullptr;
-  int32_t* q = reinterpret_cast<int32_t*>(f + (ee ? 6 : 5) * cap);
-  w.nn = q;
-  w.nc = q + cap;
-  int16_t* h = reinterpret_cast<int16_t*>(q + 2 * cap);
-  w.tile = h;
-  w.next = h + cap;
-  w.parent = h + 2 * cap;
+  w.dist = f + 3 * cap;
+  w.nz = ee ? f + 4 * cap : nullptr;
+  int16_t* h = reinterpret_cast<int16_t*>(f + (ee ? 5 : 4) * cap);
+  w.nn = h;
+  w.tile = h + cap;
+  w.next = h + 2 * cap;
   w.todo = h + 3 * cap;
   w.head = h + 4 * cap;
-  w.ntodo = reinterpret_cast<int32_t*>(w.head + PDR_JET_TILES);
+  w.ntodo = reinterpret_cast<int32_t*>(w.head + ((ntiles + 7u) & ~7u));
   return w;
 }
 
@@ -100,14 +116,13 @@ __device__ __forceinline__ float dr2_between(float y1, float p1, float y2, float
   return fmaf(dy, dy, dp * dp);
 }
 
-// min(d_iB, d_i,nn) of object k from its neighbour record (NaN read as +inf,
-// so that every comparison below is a total order).
-__device__ __forceinline__ float dist_of(const WS& w, uint32_t k, float inv_R2) {
-  const float dB = w.k2p[k];
-  const int32_t m = w.nn[k];
+// min(d_iB, d_i,nn) of an object with beam distance dB, neighbour m (or -1)
+// at pair metric r2 (NaN read as +inf, so that every comparison below is a
+// total order).
+__device__ __forceinline__ float dist_of(const WS& w, float dB, int32_t m, float r2, float inv_R2) {
   float d = dB;
   if (m >= 0) {
-    const float dJ = fminf(dB, w.k2p[m]) * w.nnr2[k] * inv_R2;
+    const float dJ = fminf(dB, w.k2p[m]) * r2 * inv_R2;
     d = dJ < dB ? dJ : dB;
   }
   return d <= INFINITY ? d : INFINITY;
@@ -125,6 +140,11 @@ __device__ __forceinline__ int tile_of(const JetParams& p, float y, float phi) {
   return (ty << 5) | tp;
 }
 
+// The list head of tile t (heads stored densely, nty x ntp).
+__device__ __forceinline__ int16_t& head(const JetParams& p, const WS& w, int t) {
+  return w.head[(t >> 5) * p.ntp + (t & 31)];
+}
+
 // Neighbour l (0..8) of tile t, or -1.
 __device__ __forceinline__ int neighbour(const JetParams& p, int t, int l) {
   const int y2 = (t >> 5) + l / 3 - 1, dp = l % 3 - 1;
@@ -136,21 +156,22 @@ __device__ __forceinline__ int neighbour(const JetParams& p, int t, int l) {
   return (y2 << 5) | tp;
 }
 
-__device__ __forceinline__ void push(const WS& w, int t, uint32_t k) {
-  w.next[k] = w.head[t];
-  w.head[t] = (int16_t)k;
+__device__ __forceinline__ void push(const JetParams& p, const WS& w, int t, uint32_t k) {
+  int16_t& h = head(p, w, t);
+  w.next[k] = h;
+  h = (int16_t)k;
   w.tile[k] = (int16_t)t;
 }
 
 // Unlinks k from its tile list (at most cap steps; a missing k sets the error word).
-__device__ __forceinline__ void unlink(const WS& w, uint32_t k, uint32_t cap, uint32_t* err) {
-  const int t = w.tile[k];
-  int q = w.head[t];
+__device__ __forceinline__ void unlink(const JetParams& p, const WS& w, uint32_t k, uint32_t* err) {
+  int16_t& h = head(p, w, w.tile[k]);
+  int q = h;
   if (q == (int)k) {
-    w.head[t] = w.next[k];
+    h = w.next[k];
     return;
   }
-  for (uint32_t it = 0; it < cap && q >= 0; ++it) {
+  for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
     const int nx = w.next[q];
     if (nx == (int)k) {
       w.next[q] = w.next[k];
@@ -172,7 +193,7 @@ __device__ __forceinline__ void search(const JetParams& p, const WS& w, uint32_t
   if (lane < 9u) {
     const int t = neighbour(p, w.tile[k], (int)lane);
     if (t >= 0) {
-      int q = w.head[t];
+      int q = head(p, w, t);
       for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
         if (q != (int)k) {
           const float d = metric(w, ee, (uint32_t)q, yk, pk, zk);
@@ -190,13 +211,23 @@ __device__ __forceinline__ void search(const JetParams& p, const WS& w, uint32_t
   best = bi < 0 ? p.R2 : __uint_as_float(mkey);
 }
 
-// The warp's (distance, index) minimum over the lanes' candidates (a lane
-// without one holds index -1); distances are non-negative or +inf.
-__device__ __forceinline__ int32_t warp_argmin(float d, int32_t k) {
-  const uint32_t key = k < 0 ? 0xFFFFFFFFu : __float_as_uint(d);
-  const uint32_t mkey = __reduce_min_sync(PDR_FULL, key);
-  const uint32_t mi = __reduce_min_sync(PDR_FULL, key == mkey && k >= 0 ? (uint32_t)k : 0xFFFFFFFFu);
+// The warp's (key, index) minimum over the lanes' candidates (a lane without
+// one holds index -1); returns the index, the key in *mkey.
+__device__ __forceinline__ int32_t warp_argmin(uint32_t key, int32_t k, uint32_t* mkey) {
+  key = k < 0 ? 0xFFFFFFFFu : key;
+  *mkey = __reduce_min_sync(PDR_FULL, key);
+  const uint32_t mi = __reduce_min_sync(PDR_FULL, key == *mkey && k >= 0 ? (uint32_t)k : 0xFFFFFFFFu);
   return mi == 0xFFFFFFFFu ? -1 : (int32_t)mi;
+}
+
+// The current pair metric of object q and its neighbour m (or R^2 without
+// one): recomputed from the two positions in the operand order the searches
+// use, so it is bitwise the value the search found (neither object has
+// moved since, or q would have been re-searched).
+__device__ __forceinline__ float nn_metric(const JetParams& p, const WS& w, uint32_t q, int32_t m) {
+  if (m < 0) return p.R2;
+  const bool ee = p.ee != 0;
+  return metric(w, ee, (uint32_t)m, w.y[q], w.phi[q], ee ? w.nz[q] : 0.0f);
 }
 
 // Loads the event's objects into the workspace; returns their number.
@@ -218,6 +249,7 @@ __device__ __forceinline__ uint32_t load_objects(const JetParams& p, const WS& w
     w.y0[k] = y;
     w.phi0[k] = phi;
     w.parent[k] = -1;
+    w.nc[k] = 1;
     if (p.ee) {
       // unit direction of the momentum and E^2p
       const float ch = coshf(eta), ic = 1.0f / ch;
@@ -229,7 +261,6 @@ __device__ __forceinline__ uint32_t load_objects(const JetParams& p, const WS& w
     } else {
       w.k2p[k] = kt2p_of(pt * pt, p.p);
     }
-    w.nc[k] = 1;
   };
   if (p.collection == PDR_JETS_PFLOW) {
     n = c0 + c2;
@@ -271,8 +302,9 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const uint64_t w0 = (uint64_t)blockIdx.x * p.warps + wib;
-  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap, p.ee != 0),
-                     p.scratch + w0 * (uint64_t)PDR_JET_SCRATCH_DOUBLES * p.cap, p.cap, p.ee != 0);
+  const bool ee = p.ee != 0;
+  const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap, ee, p.ntiles),
+                     p.scratch + w0 * (uint64_t)PDR_JET_SCRATCH_DOUBLES * p.cap, p.cap, ee, p.ntiles);
   const uint64_t nw = (uint64_t)gridDim.x * p.warps;
   const float inv_R2 = p.inv_R2;
   for (uint64_t e = w0; e < p.n_events; e += nw) {
@@ -293,69 +325,67 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
     }
     if (n_obj < p.min_obj || n_obj > p.cap) continue;   // another launch's event
     const uint32_t n = load_objects(p, w, a, n_part, c0, c2, lane);
-    for (uint32_t t = lane; t < PDR_JET_TILES; t += 32u) w.head[t] = -1;
+    for (uint32_t t = lane; t < p.ntiles; t += 32u) w.head[t] = -1;
     __syncwarp();
     if (lane == 0)
-      for (uint32_t k = 0; k < n; ++k) push(w, tile_of(p, w.y[k], w.phi[k]), k);
+      for (uint32_t k = 0; k < n; ++k) push(p, w, tile_of(p, w.y[k], w.phi[k]), k);
     __syncwarp();
-    // initial nearest neighbours: each lane walks the cells around its own
-    // objects (ties: the lower index, as in the warp search)
-    {
-      const bool ee = p.ee != 0;
-      for (uint32_t k = lane; k < n; k += 32u) {
-        const float yk = w.y[k], pk = w.phi[k], zk = ee ? w.nz[k] : 0.0f;
-        const int tk = w.tile[k];
-        float best = p.R2;
-        int32_t bi = -1;
-        for (int l = 0; l < 9; ++l) {
-          const int t = neighbour(p, tk, l);
-          if (t < 0) continue;
-          int q = w.head[t];
-          for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
-            if (q != (int)k) {
-              const float d = metric(w, ee, (uint32_t)q, yk, pk, zk);
-              if (d < best || (d == best && q < bi)) { best = d; bi = q; }
-            }
-            q = w.next[q];
-          }
-        }
-        w.nn[k] = bi;
-        w.nnr2[k] = best;
-      }
-    }
-    __syncwarp();
-    float bd = INFINITY;
+    // initial nearest neighbours and distances: each lane walks the cells
+    // around its own objects (ties: the lower index, as in the warp search)
+    uint32_t bkey = 0xFFFFFFFFu;
     int32_t bk = -1;
     for (uint32_t k = lane; k < n; k += 32u) {
-      const float d = dist_of(w, k, inv_R2);
+      const float yk = w.y[k], pk = w.phi[k], zk = ee ? w.nz[k] : 0.0f;
+      const int tk = w.tile[k];
+      float best = p.R2;
+      int32_t bi = -1;
+      for (int l = 0; l < 9; ++l) {
+        const int t = neighbour(p, tk, l);
+        if (t < 0) continue;
+        int q = head(p, w, t);
+        for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
+          if (q != (int)k) {
+            const float d = metric(w, ee, (uint32_t)q, yk, pk, zk);
+            if (d < best || (d == best && q < bi)) { best = d; bi = q; }
+          }
+          q = w.next[q];
+        }
+      }
+      w.nn[k] = (int16_t)bi;
+      const float d = dist_of(w, w.k2p[k], bi, best, inv_R2);
       w.dist[k] = d;
-      if (bk < 0 || d < bd) { bd = d; bk = (int32_t)k; }
+      if (__float_as_uint(d) < bkey) { bkey = __float_as_uint(d); bk = (int32_t)k; }
     }
+    __syncwarp();
     for (uint32_t left = n; left > 0; --left) {
       // the smallest distance (ties: the lower index)
-      bk = warp_argmin(bd, bk);
+      uint32_t mkey;
+      bk = warp_argmin(bkey, bk, &mkey);
       const uint32_t i = (uint32_t)bk;
       const int32_t j = w.nn[i];
       const float dB = w.k2p[i];
-      const bool merge = j >= 0 && fminf(dB, w.k2p[j]) * w.nnr2[i] * inv_R2 < dB;
+      // (d_i,j < d_iB exactly when the distance taken is the pair's)
+      const bool merge = j >= 0 && __uint_as_float(mkey) < dB;
       const uint32_t ma = merge ? min(i, (uint32_t)j) : i, mb = merge ? max(i, (uint32_t)j) : i;
       const int ti = w.tile[i], tj = merge ? w.tile[j] : -1;   // cells before the step
       if (lane == 0) *w.ntodo = 0;
       __syncwarp();
       if (lane == 0) {
         if (merge) {
-          unlink(w, mb, p.cap, p.err);
-          unlink(w, ma, p.cap, p.err);
-          w.px[ma] += w.px[mb];
-          w.py[ma] += w.py[mb];
-          w.ap[ma] += w.ap[mb];
-          w.am[ma] += w.am[mb];
+          unlink(p, w, mb, p.err);
+          unlink(p, w, ma, p.err);
+          const double px = w.px[ma] + w.px[mb], py = w.py[ma] + w.py[mb];
+          const double ap = w.ap[ma] + w.ap[mb], am = w.am[ma] + w.am[mb];
+          w.px[ma] = px;
+          w.py[ma] = py;
+          w.ap[ma] = ap;
+          w.am[ma] = am;
           w.nc[ma] += w.nc[mb];
-          w.nc[mb] = 0;
           w.parent[mb] = (int16_t)ma;
-          const float fx = (float)w.px[ma], fy = (float)w.py[ma];
-          if (p.ee) {
-            const double pz = 0.5 * (w.ap[ma] - w.am[ma]), en = 0.5 * (w.ap[ma] + w.am[ma]);
+          w.dist[mb] = __uint_as_float(KEY_MERGED);
+          const float fx = (float)px, fy = (float)py;
+          if (ee) {
+            const double pz = 0.5 * (ap - am), en = 0.5 * (ap + am);
             const float fz = (float)pz;
             const float ip = rsqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz)));
             w.y[ma] = fx * ip;
@@ -364,14 +394,15 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
             const float fe = (float)en;
             w.k2p[ma] = kt2p_of(fe * fe, p.p);
           } else {
-            w.y[ma] = 0.5f * logf((float)w.ap[ma] / (float)w.am[ma]);
-            w.phi[ma] = atan2f(fy, fx);
+            const float ym = 0.5f * logf((float)ap / (float)am), pm = atan2f(fy, fx);
+            w.y[ma] = ym;
+            w.phi[ma] = pm;
             w.k2p[ma] = kt2p_of(fmaf(fx, fx, fy * fy), p.p);
           }
-          push(w, tile_of(p, w.y[ma], w.phi[ma]), ma);
+          push(p, w, tile_of(p, w.y[ma], w.phi[ma]), ma);
         } else {
-          unlink(w, i, p.cap, p.err);
-          w.nc[i] = -w.nc[i];
+          unlink(p, w, i, p.err);
+          w.dist[i] = __uint_as_float(KEY_JET);
         }
       }
       __syncwarp();
@@ -383,23 +414,25 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       // (once each) the objects to re-search and offering the merged object
       // to the others; then the listed objects are re-searched
       const int ta = w.tile[ma];
-      const float ya = w.y[ma], pa = w.phi[ma], za = p.ee ? w.nz[ma] : 0.0f;
+      const float ya = w.y[ma], pa = w.phi[ma], za = ee ? w.nz[ma] : 0.0f;
       const int grp = (int)(lane / 9u);
       if (lane < 27u && (grp == 0 || merge)) {
         const int t = neighbour(p, grp == 0 ? ti : (grp == 1 ? tj : ta), (int)(lane - 9u * grp));
         if (t >= 0) {
-          int q = w.head[t];
+          int q = head(p, w, t);
           for (uint32_t it = 0; it < p.cap && q >= 0; ++it) {
             const int32_t m = w.nn[q];
             if (m == (int32_t)i || (merge && (m == j || q == (int)ma))) {
-              const int prev = atomicExch(reinterpret_cast<int*>(w.dist + q), __float_as_int(-1.0f));
-              if (prev != __float_as_int(-1.0f)) w.todo[atomicAdd(w.ntodo, 1)] = (int16_t)q;
+              const uint32_t prev = atomicExch(reinterpret_cast<unsigned int*>(w.dist + q), KEY_TODO);
+              if (prev != KEY_TODO) w.todo[atomicAdd(w.ntodo, 1)] = (int16_t)q;
             } else if (grp == 2) {
-              const float d = metric(w, p.ee != 0, (uint32_t)q, ya, pa, za);
-              if (d < w.nnr2[q] || (d == w.nnr2[q] && (int32_t)ma < m)) {
-                w.nn[q] = (int32_t)ma;
-                w.nnr2[q] = d;
-                w.dist[q] = dist_of(w, (uint32_t)q, inv_R2);
+              const float d = metric(w, ee, (uint32_t)q, ya, pa, za);
+              if (d < p.R2) {   // (a neighbour record's metric is below R^2, or R^2 without one)
+                const float r = nn_metric(p, w, (uint32_t)q, m);
+                if (d < r || (d == r && (int32_t)ma < m)) {
+                  w.nn[q] = (int16_t)ma;
+                  w.dist[q] = dist_of(w, w.k2p[q], (int32_t)ma, d, inv_R2);
+                }
               }
             }
             q = w.next[q];
@@ -414,35 +447,38 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
         int32_t bi;
         search(p, w, kk, lane, best, bi);
         if (lane == 0) {
-          w.nn[kk] = bi;
-          w.nnr2[kk] = best;
-          w.dist[kk] = dist_of(w, kk, inv_R2);
+          w.nn[kk] = (int16_t)bi;
+          w.dist[kk] = dist_of(w, w.k2p[kk], bi, best, inv_R2);
         }
         __syncwarp();
       }
-      bd = INFINITY;
+      bkey = 0xFFFFFFFFu;
       bk = -1;
 #pragma unroll 4
-      for (uint32_t k = lane; k < n; k += 32u)
-        if (w.nc[k] > 0 && (bk < 0 || w.dist[k] < bd)) { bd = w.dist[k]; bk = (int32_t)k; }
+      for (uint32_t k = lane; k < n; k += 32u) {
+        const uint32_t kk = __float_as_uint(w.dist[k]);
+        if (kk < bkey) { bkey = kk; bk = (int32_t)k; }
+      }
     }
-    // jets: the objects marked by a beam distance, cut, ordered by decreasing pT
+    // jets: the objects removed with their beam distance, cut, ordered by
+    // decreasing pT.  The pair arrays are free now: nn holds the jet list,
+    // k2p the jets' pT
     uint32_t m = 0;
     for (uint32_t t = 0; t < n; t += 32u) {
       const uint32_t k = t + lane;
       bool keep = false;
       float pt = 0.0f;
-      if (k < n && w.nc[k] < 0) {
+      if (k < n && __float_as_uint(w.dist[k]) == KEY_JET) {
         const double px = w.px[k], py = w.py[k];
         pt = (float)sqrt(px * px + py * py);
-        keep = pt >= p.pt_min && (uint32_t)(-w.nc[k]) >= p.nconst_min;
+        keep = pt >= p.pt_min && (uint32_t)w.nc[k] >= p.nconst_min;
       }
       const uint32_t mask = __ballot_sync(PDR_FULL, keep);
       __syncwarp();
       if (keep) {
         const uint32_t slot = m + __popc(mask & ((1u << lane) - 1u));
-        w.nn[slot] = (int32_t)k;      // the neighbour array is free now: jet list
-        w.nnr2[slot] = pt;
+        w.nn[slot] = (int16_t)k;
+        w.k2p[slot] = pt;
       }
       m += __popc(mask);
       __syncwarp();
@@ -451,13 +487,16 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
     // substructure of the kept jets: each object's jet is the end of its chain
     // of merges (the jet list's slot, or -1), then the energy correlation
     // functions e2, e3 (angular exponent 1) over the jet's constituents
-    for (uint32_t k = lane; k < n; k += 32u) w.next[k] = -1;
+    for (uint32_t k = lane; k < n; k += 32u) {
+      w.next[k] = -1;
+      w.todo[k] = w.parent[k];   // the merge parents, into shared memory
+    }
     __syncwarp();
     for (uint32_t s2 = lane; s2 < m; s2 += 32u) w.next[w.nn[s2]] = (int16_t)s2;
     __syncwarp();
     for (uint32_t k = lane; k < n; k += 32u) {
       int r = (int)k;
-      for (uint32_t it = 0; it < n && w.parent[r] >= 0; ++it) r = w.parent[r];
+      for (uint32_t it = 0; it < n && w.todo[r] >= 0; ++it) r = w.todo[r];
       w.tile[k] = w.next[r];   // the tile array is free now: the object's jet slot
     }
     __syncwarp();
@@ -478,7 +517,9 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       __syncwarp();
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) spt += __shfl_xor_sync(PDR_FULL, spt, o);
-      // distances in float (relative error ~1e-7), terms summed in double
+      // distances in float (relative error ~1e-7); the innermost sums (at
+      // most one term a constituent, all positive) in float, the pair terms
+      // in double
       double e2 = 0.0, e3 = 0.0;
       for (uint32_t u = lane; u < c; u += 32u) {
         const int32_t ki = list[u];
@@ -486,16 +527,16 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
         for (uint32_t v = u + 1; v < c; ++v) {
           const int32_t kj = list[v];
           const float zij = zi * w.pt0[kj];
-          const float dij = sqrtf(dr2_between(yi, fi, w.y0[kj], w.phi0[kj]));
-          e2 += (double)(zij * dij);
           const float yj = w.y0[kj], fj = w.phi0[kj];
-          double s3 = 0.0;
+          const float dij = sqrtf(dr2_between(yi, fi, yj, fj));
+          e2 += (double)(zij * dij);
+          float s3 = 0.0f;
           for (uint32_t x = v + 1; x < c; ++x) {
             const int32_t kl = list[x];
             const float yl = w.y0[kl], fl = w.phi0[kl];
-            s3 += (double)(w.pt0[kl] * sqrtf(dr2_between(yi, fi, yl, fl)) * sqrtf(dr2_between(yj, fj, yl, fl)));
+            s3 = fmaf(w.pt0[kl] * sqrtf(dr2_between(yi, fi, yl, fl)), sqrtf(dr2_between(yj, fj, yl, fl)), s3);
           }
-          e3 += (double)(zij * dij) * s3;
+          e3 += (double)(zij * dij) * (double)s3;
         }
       }
 #pragma unroll
@@ -512,10 +553,10 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       __syncwarp();
     }
     for (uint32_t s = lane; s < m; s += 32u) {
-      const float pts = w.nnr2[s];
+      const float pts = w.k2p[s];
       uint32_t rank = 0;
       for (uint32_t o = 0; o < m; ++o) {
-        const float po = w.nnr2[o];
+        const float po = w.k2p[o];
         rank += (po > pts || (po == pts && o < s)) ? 1u : 0u;
       }
       const uint32_t k = (uint32_t)w.nn[s];
@@ -528,7 +569,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       J.phi = atan2f((float)py, (float)px);
       J.mass = m2 > 0.0 ? (float)sqrt(m2) : 0.0f;
       J.e = (float)en;
-      J.nconst = (uint32_t)(-w.nc[k]);
+      J.nconst = (uint32_t)w.nc[k];
       J.c2 = w.y[s];
       J.d2 = w.phi[s];
       if (rank < n_part) p.jets[a + rank] = J;   // the event's slots hold n_part records

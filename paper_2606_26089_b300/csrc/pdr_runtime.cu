@@ -1894,6 +1894,7 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   p.nty = jp->ee ? 1 : (int32_t)std::min(32.0, std::max(1.0, std::floor(12.0 / rw)));
   int32_t ntp = jp->ee ? 1 : (int32_t)std::min(32.0, std::floor(2.0 * M_PI / rw));
   p.ntp = ntp < 3 ? 1 : ntp;
+  p.ntiles = (uint32_t)(p.nty * p.ntp);
   p.y0 = -6.0f;
   p.inv_wy = (float)(p.nty / 12.0);
   p.inv_wp = (float)(p.ntp / (2.0 * M_PI));
@@ -1907,9 +1908,14 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   PDR_CUDA(cudaStreamSynchronize(s), "sync");
   const uint32_t max_n = *ctx->h_word;
   const uint32_t cap = std::max<uint32_t>(32u, (max_n + 31u) & ~31u);
-  int smem_max = 0;
+  int smem_max = 0, smem_sm = 0, smem_rsv = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-  if (jet_ws_bytes(cap, jp->ee != 0) > (uint64_t)smem_max)
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+  cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device);
+  // dynamic shared memory of each of two blocks on one SM
+  const uint64_t half_sm = std::min<uint64_t>((uint64_t)smem_max,
+                                              (uint64_t)std::max(0, smem_sm / 2 - smem_rsv));
+  if (cap > 32767u || jet_ws_bytes(cap, jp->ee != 0, p.ntiles) > (uint64_t)smem_max)
     return fail(PDR_EOVERFLOW, "event has more clustering objects than fit in shared memory");
   // The workspace of the largest event sets how many warps share an SM; so
   // events up to 288 objects (most of a batch of a few hundred particles a
@@ -1920,9 +1926,9 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   for (int k = 0; k < (cap > tier ? 2 : 1); ++k) {
     p.cap = caps[k];
     p.min_obj = k == 0 ? 0u : tier + 1u;
-    const uint64_t ws = jet_ws_bytes(p.cap, p.ee != 0);
+    const uint64_t ws = jet_ws_bytes(p.cap, p.ee != 0, p.ntiles);
     // two blocks an SM where the shared memory allows (shorter tails)
-    p.warps = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, (uint64_t)smem_max / ws / 2));
+    p.warps = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, half_sm / ws));
     const size_t smem = (size_t)(p.warps * ws);
     int per_sm = 0;
     PDR_CUDA(occupancy_cluster(p.warps * 32u, smem, &per_sm), "clustering occupancy");

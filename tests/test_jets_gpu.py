@@ -196,7 +196,7 @@ def test_event_beyond_the_shared_memory_workspace_is_refused(B, ctx):
     workspace holds is refused on the host (no launch)."""
     from paper_2606_26089_b300 import synth
     rng = np.random.default_rng(3)
-    n = 9000
+    n = 11000
     rows = list(zip(rng.uniform(0.5, 5.0, n), rng.uniform(-4, 4, n), rng.uniform(-np.pi, np.pi, n),
                     np.full(n, 0.13957), np.full(n, 211), np.ones(n, int), np.zeros(n)))
     batch = synth.from_particles([rows])
