@@ -369,13 +369,21 @@ def bench_serving(args, B, ctx):
         tickets = []
         done = th.Event()
 
+        failed = []
+
         def releaser():
+            # a failed request is released too (its pool memory would otherwise
+            # block admission and the server would never drain)
             i = 0
             while not (done.is_set() and i >= len(tickets)):
                 if i < len(tickets):
-                    if ctx.wait(tickets[i], 120_000) != 0:
-                        raise RuntimeError("serving request failed")
-                    ctx.release(tickets[i])
+                    rc = ctx.wait(tickets[i], 120_000)
+                    if rc != 0:
+                        failed.append((i, rc))
+                    try:
+                        ctx.release(tickets[i])
+                    except B.PdrError:
+                        failed.append((i, "release"))
                     i += 1
                 else:
                     time.sleep(0.0005)
@@ -391,6 +399,8 @@ def bench_serving(args, B, ctx):
         rt.join()
         st = ctx.serve_stats()
         ctx.serve_stop()
+        if failed:
+            raise RuntimeError(f"{len(failed)} serving requests failed (first: {failed[0]})")
         # ---- baseline: one request at a time, one plain launch each (H2D, run, sync)
         lat = []
         t0 = time.perf_counter()

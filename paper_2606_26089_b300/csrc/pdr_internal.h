@@ -119,6 +119,7 @@ struct alignas(16) HotCard {
 
 #define PDR_HOT_MAX_BYTES (40u * 1024u)   // shared-memory card cache limit
 
+#define PDR_MAX_DEVICES 64   // device ordinals the library tracks per-device state for
 #define PDR_LAUNCH_SEGS 32   // batches in one fused launch
 #define PDR_LAUNCH_CARDS 4   // distinct cards in one fused launch
 

@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pdr_internal.h"
 #include "pdr_math.cuh"
 
@@ -870,21 +872,37 @@ __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64
 }
 
 // ------------------------------------------------------- launch helpers
+// A kernel's dynamic shared-memory limit only ever grows (per device): a
+// captured graph replays its launch with the shared memory it was captured
+// with, which a later smaller launch must not take away.
+template <int TEAM, int BLOCK, bool OVF>
+static cudaError_t allow_smem(size_t smem) {
+  static std::mutex mu;
+  static int allowed[PDR_MAX_DEVICES] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= PDR_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)smem <= allowed[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(fused_kernel<TEAM, BLOCK, OVF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) allowed[dev] = (int)smem;
+  return e;
+}
+
 template <int TEAM, int BLOCK, bool OVF>
 static cudaError_t launch_t(const KParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
-  auto fn = fused_kernel<TEAM, BLOCK, OVF>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem<TEAM, BLOCK, OVF>(smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, BLOCK, smem, s>>>(p);
+  fused_kernel<TEAM, BLOCK, OVF><<<grid, BLOCK, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 template <int TEAM, int BLOCK, bool OVF>
 static cudaError_t occupancy_t(int* blocks, size_t smem) {
-  auto fn = fused_kernel<TEAM, BLOCK, OVF>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem<TEAM, BLOCK, OVF>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fn, BLOCK, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fused_kernel<TEAM, BLOCK, OVF>, BLOCK, smem);
 }
 
 #define PDR_SHAPES(X) X(32, 128) X(32, 256) X(64, 256) X(128, 128) X(128, 256) X(256, 256) X(512, 512) X(1024, 1024)

@@ -1250,7 +1250,9 @@ struct Server {
   std::deque<Wave> inflight;
   bool stop = false;
   cudaStream_t s_copy = nullptr, s_comp = nullptr, s_cap = nullptr;
-  std::map<std::tuple<uint32_t, uint32_t, uint32_t, size_t>, GraphSlot> graphs;
+  // keyed by the launch shape and the kernel variant (shared table sized
+  // below the particle count or not)
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t, size_t, bool>, GraphSlot> graphs;
   std::vector<double> lat_ms;
   uint64_t requests_done = 0, events_done = 0, particles_done = 0, waves = 0, admission_waits = 0,
            graph_launches = 0;
@@ -1316,7 +1318,7 @@ void serve_admit(pdr_ctx* ctx, Server& sv, ServeReq* r) {
 
 // Launch a prepared parameter block through a captured graph of its shape.
 cudaError_t graph_launch(Server& sv, const KParams& p, const Shape& S) {
-  const auto key = std::make_tuple(S.team, S.block, S.grid, S.smem);
+  const auto key = std::make_tuple(S.team, S.block, S.grid, S.smem, S.may_overflow);
   auto it = sv.graphs.find(key);
   if (it == sv.graphs.end()) {
     GraphSlot g;

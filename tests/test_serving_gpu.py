@@ -121,3 +121,36 @@ def test_bounded_wait_times_out_instead_of_hanging(B, synth):
         ctx.serve_stop()
     finally:
         ctx.close()
+
+
+def test_graph_replay_keeps_its_shared_memory(B, synth):
+    """Large events (whose shared tower tables are sized to fill the shared
+    memory, so each event size gives its own launch shape): waves replayed
+    from captured graphs after direct launches of the same kernel with other
+    shared-memory sizes still run, and match the direct results."""
+    ctx = B.Context(0, pool_bytes=1 << 30, max_tickets=64)
+    try:
+        cid = ctx.card_load("cms_like")
+        batches = [synth.make_pileup(n_events=1, seed=40 + k, n_vertices=v)
+                   for k, v in enumerate((100, 115, 130, 145, 160, 175))]
+        ctx.serve_start(use_graphs=1)
+
+        def serve(b):
+            hb, keep = B.pinned_host_batch(b, cid, 9, 0)
+            t = ctx.serve_submit(hb)
+            assert ctx.wait(t, 60_000) == 0
+            h = B.result_to_host(ctx.fetch(t))
+            ctx.release(t)
+            return h
+
+        first = [serve(b) for b in batches]                     # each wave captures a graph
+        alone = [_alone(B, ctx, cid, b, 9, 0) for b in batches]  # direct launches in between
+        for b, f, a in zip(batches, first, alone):
+            _compare(a, f, b)
+        for b, a in zip(batches, alone):                         # the graphs replayed
+            _compare(a, serve(b), b)
+        st = ctx.serve_stats()
+        assert st["graph_launches"] == st["waves"] == 2 * len(batches)
+        ctx.serve_stop()
+    finally:
+        ctx.close()
