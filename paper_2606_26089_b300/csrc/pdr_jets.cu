@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pdr_internal.h"
 #include "pdr_math.cuh"
 
@@ -604,14 +606,30 @@ cudaError_t launch_jet_max_objects(const JetParams& p, uint32_t* out, cudaStream
   return cudaGetLastError();
 }
 
+// The kernel's dynamic shared-memory limit only ever grows (per device), so
+// calls from other threads or contexts never lower it under a launch.
+static cudaError_t allow_cluster_smem(size_t smem) {
+  static std::mutex mu;
+  static int allowed[PDR_MAX_DEVICES] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= PDR_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)smem <= allowed[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) allowed[dev] = (int)smem;
+  return e;
+}
+
 cudaError_t occupancy_cluster(uint32_t threads, size_t smem, int* blocks) {
-  cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_cluster_smem(smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, cluster_kernel, (int)threads, smem);
 }
 
 cudaError_t launch_cluster(const JetParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_cluster_smem(smem);
   if (e != cudaSuccess) return e;
   cluster_kernel<<<grid, p.warps * 32u, smem, s>>>(p);
   return cudaGetLastError();
