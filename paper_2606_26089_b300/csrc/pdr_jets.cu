@@ -213,6 +213,14 @@ __device__ __forceinline__ void search(const JetParams& p, const WS& w, uint32_t
   best = bi < 0 ? p.R2 : __uint_as_float(mkey);
 }
 
+// Square root by the PTX approximate instruction (relative error about one
+// float32 ulp; the substructure's tolerance is far coarser); sqrt(0) = 0.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // The warp's (key, index) minimum over the lanes' candidates (a lane without
 // one holds index -1); returns the index, the key in *mkey.
 __device__ __forceinline__ int32_t warp_argmin(uint32_t key, int32_t k, uint32_t* mkey) {
@@ -487,8 +495,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
     }
     __syncwarp();
     // substructure of the kept jets: each object's jet is the end of its chain
-    // of merges (the jet list's slot, or -1), then the energy correlation
-    // functions e2, e3 (angular exponent 1) over the jet's constituents
+    // of merges (the jet list's slot, or -1)
     for (uint32_t k = lane; k < n; k += 32u) {
       w.next[k] = -1;
       w.todo[k] = w.parent[k];   // the merge parents, into shared memory
@@ -502,58 +509,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       w.tile[k] = w.next[r];   // the tile array is free now: the object's jet slot
     }
     __syncwarp();
-    int32_t* list = reinterpret_cast<int32_t*>(w.dist);   // free now: one jet's constituents
-    for (uint32_t s2 = 0; s2 < m; ++s2) {
-      uint32_t c = 0;
-      double spt = 0.0;
-      for (uint32_t t = 0; t < n; t += 32u) {
-        const uint32_t k = t + lane;
-        const bool in = k < n && w.tile[k] == (int16_t)s2;
-        const uint32_t mask = __ballot_sync(PDR_FULL, in);
-        if (in) {
-          list[c + __popc(mask & ((1u << lane) - 1u))] = (int32_t)k;
-          spt += (double)w.pt0[k];
-        }
-        c += __popc(mask);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) spt += __shfl_xor_sync(PDR_FULL, spt, o);
-      // distances in float (relative error ~1e-7); the innermost sums (at
-      // most one term a constituent, all positive) in float, the pair terms
-      // in double
-      double e2 = 0.0, e3 = 0.0;
-      for (uint32_t u = lane; u < c; u += 32u) {
-        const int32_t ki = list[u];
-        const float zi = w.pt0[ki], yi = w.y0[ki], fi = w.phi0[ki];
-        for (uint32_t v = u + 1; v < c; ++v) {
-          const int32_t kj = list[v];
-          const float zij = zi * w.pt0[kj];
-          const float yj = w.y0[kj], fj = w.phi0[kj];
-          const float dij = sqrtf(dr2_between(yi, fi, yj, fj));
-          e2 += (double)(zij * dij);
-          float s3 = 0.0f;
-          for (uint32_t x = v + 1; x < c; ++x) {
-            const int32_t kl = list[x];
-            const float yl = w.y0[kl], fl = w.phi0[kl];
-            s3 = fmaf(w.pt0[kl] * sqrtf(dr2_between(yi, fi, yl, fl)), sqrtf(dr2_between(yj, fj, yl, fl)), s3);
-          }
-          e3 += (double)(zij * dij) * (double)s3;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        e2 += __shfl_xor_sync(PDR_FULL, e2, o);
-        e3 += __shfl_xor_sync(PDR_FULL, e3, o);
-      }
-      if (lane == 0) {
-        e2 /= spt * spt;
-        e3 /= spt * spt * spt;
-        w.y[s2] = e2 > 0.0 ? (float)(e3 / (e2 * e2)) : 0.0f;       // C2 (y, phi are free now)
-        w.phi[s2] = e2 > 0.0 ? (float)(e3 / (e2 * e2 * e2)) : 0.0f;  // D2
-      }
-      __syncwarp();
-    }
+    // the kept jets' records, in decreasing pT (C2 and D2 are added below)
     for (uint32_t s = lane; s < m; s += 32u) {
       const float pts = w.k2p[s];
       uint32_t rank = 0;
@@ -572,9 +528,71 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
       J.mass = m2 > 0.0 ? (float)sqrt(m2) : 0.0f;
       J.e = (float)en;
       J.nconst = (uint32_t)w.nc[k];
-      J.c2 = w.y[s];
-      J.d2 = w.phi[s];
+      J.c2 = 0.0f;
+      J.d2 = 0.0f;
       if (rank < n_part) p.jets[a + rank] = J;   // the event's slots hold n_part records
+      w.todo[s] = (int16_t)min(rank, 32767u);     // (the parents' copy is free now)
+    }
+    __syncwarp();
+    // then the energy correlation functions e2, e3 (angular exponent 1) over
+    // each jet's constituents, staged as (y, phi, pT) in the free y, phi and
+    // pT^2p arrays.  Distances in float (relative error ~1e-7; the triples'
+    // by the approximate square root), the innermost sums (at most one term a
+    // constituent, all positive) in float, the pair terms in double
+    float* sy = w.y;
+    float* sf = w.phi;
+    float* sz = w.k2p;
+    for (uint32_t s2 = 0; s2 < m; ++s2) {
+      uint32_t c = 0;
+      double spt = 0.0;
+      for (uint32_t t = 0; t < n; t += 32u) {
+        const uint32_t k = t + lane;
+        const bool in = k < n && w.tile[k] == (int16_t)s2;
+        const uint32_t mask = __ballot_sync(PDR_FULL, in);
+        if (in) {
+          const uint32_t x = c + __popc(mask & ((1u << lane) - 1u));
+          const float z = w.pt0[k];
+          sy[x] = w.y0[k];
+          sf[x] = w.phi0[k];
+          sz[x] = z;
+          spt += (double)z;
+        }
+        c += __popc(mask);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) spt += __shfl_xor_sync(PDR_FULL, spt, o);
+      double e2 = 0.0, e3 = 0.0;
+      for (uint32_t u = lane; u < c; u += 32u) {
+        const float zi = sz[u], yi = sy[u], fi = sf[u];
+        for (uint32_t v = u + 1; v < c; ++v) {
+          const float zij = zi * sz[v];
+          const float yj = sy[v], fj = sf[v];
+          const float dij = sqrtf(dr2_between(yi, fi, yj, fj));
+          e2 += (double)(zij * dij);
+          float s3 = 0.0f;
+          for (uint32_t x = v + 1; x < c; ++x) {
+            const float yl = sy[x], fl = sf[x];
+            s3 = fmaf(sz[x] * sqrt_approx(dr2_between(yi, fi, yl, fl)), sqrt_approx(dr2_between(yj, fj, yl, fl)), s3);
+          }
+          e3 += (double)(zij * dij) * (double)s3;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(PDR_FULL, e2, o);
+        e3 += __shfl_xor_sync(PDR_FULL, e3, o);
+      }
+      if (lane == 0) {
+        const uint32_t rank = (uint32_t)w.todo[s2];
+        e2 /= spt * spt;
+        e3 /= spt * spt * spt;
+        if (rank < n_part) {
+          p.jets[a + rank].c2 = e2 > 0.0 ? (float)(e3 / (e2 * e2)) : 0.0f;
+          p.jets[a + rank].d2 = e2 > 0.0 ? (float)(e3 / (e2 * e2 * e2)) : 0.0f;
+        }
+      }
+      __syncwarp();
     }
     if (lane == 0) {
       if (m > n_part) atomicOr(p.err, ERR_JETS);
