@@ -255,6 +255,7 @@ struct JetParams {
   uint32_t* jet_counts;
   uint32_t* err;
   double* scratch;                      // PDR_JET_SCRATCH_DOUBLES x cap doubles for each warp of the grid
+  uint32_t* next_event;                 // work counter (zero at launch): warps take events in turn
 };
 
 // Bytes of one warp's shared-memory clustering workspace for `cap` objects

@@ -315,9 +315,14 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
   const bool ee = p.ee != 0;
   const WS w = carve(smem + (uint64_t)wib * jet_ws_bytes(p.cap, ee, p.ntiles),
                      p.scratch + w0 * (uint64_t)PDR_JET_SCRATCH_DOUBLES * p.cap, p.cap, ee, p.ntiles);
-  const uint64_t nw = (uint64_t)gridDim.x * p.warps;
   const float inv_R2 = p.inv_R2;
-  for (uint64_t e = w0; e < p.n_events; e += nw) {
+  // events are taken from a work counter as warps become free (their
+  // clustering times vary), not in a fixed round-robin
+  for (;;) {
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(p.next_event, 1u);
+    const uint64_t e = __shfl_sync(PDR_FULL, next, 0);
+    if (e >= p.n_events) break;
     const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
     uint32_t c0 = 0, c2 = 0;
     if (p.collection == PDR_JETS_PFLOW) {

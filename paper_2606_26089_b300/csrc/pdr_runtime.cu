@@ -168,6 +168,7 @@ struct pdr_ctx {
   size_t smem_optin = 0;
   uint32_t* d_err = nullptr;      // device error word
   uint32_t* d_word = nullptr;     // small device word for reductions
+  uint32_t* d_next = nullptr;     // device work counter of the clustering launches
   uint32_t* h_word = nullptr;     // pinned host word
   std::map<uint32_t, CardEntry> cards;
   uint32_t next_card = 1;
@@ -663,11 +664,12 @@ int pdr_create(pdr_ctx** out, int cuda_device, const pdr_options* opt) {
   }
   ctx->n_sms = prop.multiProcessorCount;
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
-  if (cudaMalloc((void**)&ctx->d_err, 16) != cudaSuccess || cudaMemset(ctx->d_err, 0, 16) != cudaSuccess) {
+  if (cudaMalloc((void**)&ctx->d_err, 32) != cudaSuccess || cudaMemset(ctx->d_err, 0, 32) != cudaSuccess) {
     delete ctx;
     return fail(PDR_ENOMEM, "cannot allocate the device error word");
   }
   ctx->d_word = ctx->d_err + 2;
+  ctx->d_next = ctx->d_err + 4;
   if (cudaMallocHost((void**)&ctx->h_word, 16) != cudaSuccess) {
     cudaFree(ctx->d_err);
     delete ctx;
@@ -1947,6 +1949,8 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
       ctx->jet_scratch_bytes = need;
     }
     p.scratch = ctx->jet_scratch;
+    p.next_event = ctx->d_next;
+    PDR_CUDA(cudaMemsetAsync(ctx->d_next, 0, 4, s), "memset");
     PDR_CUDA(launch_cluster(p, (uint32_t)blocks, smem, s), "clustering launch");
   }
   return PDR_OK;
