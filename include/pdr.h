@@ -206,7 +206,12 @@ int pdr_card_towers(pdr_ctx* ctx, uint32_t card_id, int calo, uint32_t* n);
  * the context pool (allocated on first need, outside any stream capture).
  * Returns PDR_EINVAL for malformed arguments (checked on the host: non-null
  * pointers, n_events < 2^31; the CSR itself is checked on the device and a bad
- * one sets the device error word). */
+ * one sets the device error word).  The launch hands events to its teams
+ * from a work counter that the context keeps per stream (launches on one
+ * stream run in order, and each leaves its counter at zero): a launch
+ * captured into a graph keeps the counter of the stream it was captured on,
+ * so do not run two replays of it, or a replay and a launch on that stream,
+ * at the same time. */
 int pdr_run(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,
             const pdr_launch* launch, void* stream);
 

@@ -290,7 +290,11 @@ struct KParams {
   KSeg seg[PDR_LAUNCH_SEGS];
   uint32_t smem_may_overflow;        // 1: the shared table is sized below the particle count (an event
                                      // whose towers overflow it is redone with the global table)
+  uint32_t* work;                    // (events handed out, teams done), zero at launch and reset by the
+                                     // launch's last team; null: a fixed round-robin of events
 };
+
+#define PDR_WORK_STREAMS 1024   // streams per context with their own fused-launch work counter
 
 enum : uint32_t {
   ERR_CSR = 1u,        // offsets not monotone
@@ -313,6 +317,7 @@ PDR_HD inline uint64_t table_bytes(uint32_t slots, uint32_t nmax) {
 // the staged isolation candidates (eta, phi, pT', particle index; own tower
 // key; record info word; fixed-point cone sums).
 struct TeamTail {
+  uint32_t next[4];                  // the team's next events, double-buffered (work counter)
   uint32_t wbuf[2 * 32];
   float4 cf[PDR_CMAX];
   uint32_t ckey[PDR_CMAX];

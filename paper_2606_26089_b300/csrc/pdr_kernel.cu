@@ -721,7 +721,16 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
   const uint64_t gteam = (uint64_t)blockIdx.x * NT + tc.tix;
   const uint64_t nteams = (uint64_t)gridDim.x * NT;
   uint32_t sg = 0;  // segment cursor: a team's events only move forward
-  for (uint64_t ge = gteam; ge < p.n_events; ge += nteams) {
+  // A team's first event is its own index; with a work counter the later ones
+  // are handed out as teams become free (event times vary, so a fixed
+  // round-robin leaves a tail of teams with the slowest events).  The team's
+  // next index is fetched when an event starts and passed to the team in a
+  // double-buffered shared word: every event has a team barrier after the
+  // write and before the reads, and one between the reads and the write two
+  // events later.
+  uint32_t turn = 0;
+  for (uint64_t ge = gteam; ge < p.n_events; ge = p.work ? (uint64_t)tt.next[(turn++) & 1u] : ge + nteams) {
+    if (p.work && tc.tid == 0) tt.next[turn & 1u] = (uint32_t)nteams + atomicAdd(p.work, 1u);
     if (!ONE)
       while (sg + 1 < p.n_segs && ge >= p.seg[sg + 1].event_start) ++sg;
     const KSeg& S = p.seg[ONE ? 0 : sg];
@@ -734,11 +743,13 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
         atomicOr(p.err, ERR_CSR);
         reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
       }
+      if (p.work) tc.sync();
       continue;
     }
     const uint32_t n = (uint32_t)(b - a);
-    if (n == 0) {  // nothing to do (and no team synchronisation for an empty event)
+    if (n == 0) {  // nothing to do (a team barrier only for the work counter's hand-over)
       if (tc.tid == 0) reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
+      if (p.work) tc.sync();
       continue;
     }
     if (n <= p.nmax_smem) {
@@ -765,6 +776,17 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
         atomicOr(p.err, ERR_OVERSIZE);
         reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
       }
+      if (p.work) tc.sync();
+    }
+  }
+  // the launch's last team to finish resets the counter for the next launch
+  // on this stream (every team's last fetch precedes its count of finished
+  // teams)
+  if (p.work && tc.tid == 0) {
+    __threadfence();
+    if (atomicAdd(p.work + 1, 1u) == (uint32_t)nteams - 1u) {
+      atomicExch(p.work, 0u);
+      atomicExch(p.work + 1, 0u);
     }
   }
 }

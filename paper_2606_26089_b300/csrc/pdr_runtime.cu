@@ -169,6 +169,11 @@ struct pdr_ctx {
   uint32_t* d_err = nullptr;      // device error word
   uint32_t* d_word = nullptr;     // small device word for reductions
   uint32_t* d_next = nullptr;     // device work counter of the clustering launches
+  // fused-launch work counters, one pair a stream (launches on one stream run
+  // in order; each launch leaves its counter at zero)
+  uint32_t* d_work = nullptr;
+  void* work_stream[PDR_WORK_STREAMS] = {};
+  bool work_used[PDR_WORK_STREAMS] = {};
   uint32_t* h_word = nullptr;     // pinned host word
   std::map<uint32_t, CardEntry> cards;
   uint32_t next_card = 1;
@@ -490,6 +495,24 @@ int ensure_gscratch(pdr_ctx* ctx, uint64_t bytes) {
   return PDR_OK;
 }
 
+// The work counter of fused launches on stream s (caller holds ctx->mu), or
+// null when every slot belongs to another stream (the launch then hands out
+// its events in a fixed round-robin).
+uint32_t* work_counter(pdr_ctx* ctx, cudaStream_t s) {
+  if (!ctx->d_work) return nullptr;
+  const uintptr_t h = (uintptr_t)s;
+  uint32_t k = (uint32_t)((h >> 4) ^ (h >> 17)) % PDR_WORK_STREAMS;
+  for (uint32_t probe = 0; probe < PDR_WORK_STREAMS; ++probe, k = (k + 1) % PDR_WORK_STREAMS) {
+    if (ctx->work_used[k] && ctx->work_stream[k] == (void*)s) return ctx->d_work + 2 * k;
+    if (!ctx->work_used[k]) {
+      ctx->work_used[k] = true;
+      ctx->work_stream[k] = (void*)s;
+      return ctx->d_work + 2 * k;
+    }
+  }
+  return nullptr;
+}
+
 int check_batch(pdr_ctx* ctx, const pdr_batch* b) {
   if (!ctx || !b) return fail(PDR_EINVAL, "null context or batch");
   if (b->n_events >= (1ull << 31)) return fail(PDR_EINVAL, "n_events must be < 2^31");
@@ -606,6 +629,7 @@ int launch_group(pdr_ctx* ctx, const pdr_batch* const* bs, const pdr_outputs* co
   int rc = prepare_group(ctx, bs, os, n, P, max_n, p, S);
   if (rc) return rc;
   if (p.n_events == 0) return PDR_OK;
+  p.work = work_counter(ctx, s);
   PDR_CUDA(launch_fused(S.team, S.block, p, S.grid, S.smem, s), "fused kernel launch");
   return PDR_OK;
 }
@@ -670,14 +694,23 @@ int pdr_create(pdr_ctx** out, int cuda_device, const pdr_options* opt) {
   }
   ctx->d_word = ctx->d_err + 2;
   ctx->d_next = ctx->d_err + 4;
+  // work counters (optional: without them launches use a fixed round-robin)
+  if (cudaMalloc((void**)&ctx->d_work, 8ull * PDR_WORK_STREAMS) != cudaSuccess ||
+      cudaMemset(ctx->d_work, 0, 8ull * PDR_WORK_STREAMS) != cudaSuccess) {
+    if (ctx->d_work) cudaFree(ctx->d_work);
+    ctx->d_work = nullptr;
+    cudaGetLastError();
+  }
   if (cudaMallocHost((void**)&ctx->h_word, 16) != cudaSuccess) {
     cudaFree(ctx->d_err);
+    if (ctx->d_work) cudaFree(ctx->d_work);
     delete ctx;
     return fail(PDR_ENOMEM, "cannot allocate pinned host word");
   }
   const uint64_t pool = opt && opt->pool_bytes ? opt->pool_bytes : (1ull << 30);
   if (ctx->pool.init(pool) != PDR_OK) {
     cudaFree(ctx->d_err);
+    if (ctx->d_work) cudaFree(ctx->d_work);
     cudaFreeHost(ctx->h_word);
     delete ctx;
     return fail(PDR_ENOMEM, "cannot allocate the device pool");
@@ -709,6 +742,7 @@ int pdr_destroy(pdr_ctx* ctx) {
   if (ctx->pu_T) cudaFree(ctx->pu_T);
   if (ctx->pu_hoff_total) cudaFreeHost(ctx->pu_hoff_total);
   if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);
+  if (ctx->d_work) cudaFree(ctx->d_work);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_word);
   delete ctx;
@@ -1389,6 +1423,7 @@ bool serve_launch_wave(pdr_ctx* ctx, Server& sv) {
   Shape S;
   const Plan P = plan_launch(ctx, reqs[0]->hb.card_id, max_n, nullptr);
   int rc = prepare_group(ctx, bs.data(), os.data(), (uint32_t)bs.size(), P, max_n, p, S);
+  p.work = work_counter(ctx, sv.s_comp);   // (the graphs run on the compute stream)
   cudaError_t e = cudaSuccess;
   if (rc == PDR_OK && p.n_events > 0)
     e = sv.opt.use_graphs ? graph_launch(sv, p, S) : launch_fused(S.team, S.block, p, S.grid, S.smem, sv.s_comp);

@@ -231,6 +231,27 @@ def test_rerun_and_per_event_form_are_bitwise_identical(ctx, cards, synth):
     _same(h1, h3, b)
 
 
+def test_concurrent_launches_on_two_streams(B, ctx, cards, synth):
+    """Launches on two streams at once (each stream has its own work counter)
+    and several launches in a row on one stream (each leaves its counter at
+    zero for the next) all give the bits of a single launch."""
+    cid, _ = cards["cms_like"]
+    b = synth.make("batched", n_events=3000)
+    ref = P.run_gpu(ctx, cid, b, seed=8, debug=False)
+    dev = B.batch_to_device(b)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    outs = []
+    for k in range(6):
+        o = B.alloc_outputs(b.n_events, b.n_particles, debug=False)
+        ctx.run(B.make_batch(dev, cid, 8), B.make_outputs(o), stream=(s1, s2)[k % 2])
+        outs.append(o)
+    torch.cuda.synchronize()
+    ctx.check()
+    for o in outs:
+        _same(ref, _host(o, b.n_events), b)
+
+
 def _host(o, n_events):
     h = {k: (v.cpu().numpy() if v is not None else None) for k, v in o.items()}
     h["counts"] = h["counts"].view(np.uint32)[:n_events]
