@@ -75,7 +75,10 @@ __global__ void __launch_bounds__(256) track_ip_kernel(const __grid_constant__ I
 
 cudaError_t launch_track_ip(const IPParams& p, int n_sms, cudaStream_t s) {
   const uint64_t blocks = (p.n_events + 7) / 8;
-  const uint64_t cap = (uint64_t)n_sms * 16;
+  // one warp an event and no persistent cap: the block scheduler balances
+  // events of different sizes (a capped grid left warps with one event more
+  // than others)
+  const uint64_t cap = (uint64_t)n_sms * 4096;
   track_ip_kernel<<<(unsigned)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
