@@ -211,7 +211,8 @@ int pdr_card_towers(pdr_ctx* ctx, uint32_t card_id, int calo, uint32_t* n);
  * stream run in order, and each leaves its counter at zero): a launch
  * captured into a graph keeps the counter of the stream it was captured on,
  * so do not run two replays of it, or a replay and a launch on that stream,
- * at the same time. */
+ * at the same time; likewise let a stream's launches finish before
+ * destroying it if a new stream might receive the same handle. */
 int pdr_run(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out,
             const pdr_launch* launch, void* stream);
 
