@@ -25,7 +25,8 @@
 // list and work-list entries); an object's neighbour dR^2 is recomputed from
 // the two positions when needed (bitwise the value the search found), and the
 // constituent counts and merge parents live in global scratch with the
-// four-momenta.
+// four-momenta.  A warp takes its next event from a work counter when it
+// becomes free, as clustering times vary with the event.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
