@@ -186,7 +186,8 @@ __device__ __forceinline__ uint32_t pu_interactions_block(const PuParams& p, uin
 }
 
 __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_constant__ PuParams p) {
-  __shared__ uint64_t s_src[PU_BLOCK], s_off[PU_BLOCK];
+  __shared__ uint64_t s_src[PU_BLOCK];
+  __shared__ uint32_t s_off[PU_BLOCK];   // offsets within the chunk (32-bit: the search compares stay narrow)
   __shared__ float s_z[PU_BLOCK], s_t[PU_BLOCK];
   __shared__ uint64_t s_wsum[PU_BLOCK / 32];
   const uint32_t tid = threadIdx.x;
@@ -230,21 +231,26 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
         z = pu_truncated_normal(p, p.sigma_z, p.max_z, k, event, 6u);
         if (p.ovt) t = pu_truncated_normal(p, p.sigma_t, p.max_t, k, event, 7u);
       }
-      uint64_t chunk;
-      const uint64_t off = pu_block_scan(len, s_wsum, &chunk);
+      uint64_t chunk64;
+      const uint64_t off = pu_block_scan(len, s_wsum, &chunk64);
+      if (chunk64 >= (1ull << 31)) {   // (256 pool events beyond 2^31 particles: 32-bit indices below)
+        if (tid == 0) atomicOr(p.err, ERR_PILEUP);
+        break;
+      }
+      const uint32_t chunk = (uint32_t)chunk64;
       s_src[tid] = src;
-      s_off[tid] = off;
+      s_off[tid] = (uint32_t)off;
       s_z[tid] = z;
       s_t[tid] = t;
       __syncthreads();
       const uint32_t nk = min((uint32_t)PU_BLOCK, n_int - k0);
-      for (uint64_t i0 = 0; i0 < chunk; i0 += (uint64_t)PU_UNROLL * PU_BLOCK) {
+      for (uint32_t i0 = 0; i0 < chunk; i0 += (uint32_t)PU_UNROLL * PU_BLOCK) {
         float pt[PU_UNROLL], eta[PU_UNROLL], phi[PU_UNROLL], m[PU_UNROLL], vz[PU_UNROLL], vt[PU_UNROLL];
         int32_t pdg[PU_UNROLL];
         int8_t q[PU_UNROLL];
 #pragma unroll
         for (int u = 0; u < PU_UNROLL; ++u) {
-          const uint64_t i = i0 + (uint64_t)u * PU_BLOCK + tid;
+          const uint32_t i = i0 + (uint32_t)u * PU_BLOCK + tid;
           if (i < chunk) {
             // the last interaction whose range starts at or before i
             uint32_t lo = 0, hi = nk - 1;
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
               if (s_off[mid] <= i) lo = mid;
               else hi = mid - 1;
             }
-            const uint64_t x = s_src[lo] + (i - s_off[lo]);
+            const uint64_t x = s_src[lo] + (uint64_t)(i - s_off[lo]);
             pt[u] = __ldg(p.ppt + x); eta[u] = __ldg(p.peta + x); phi[u] = __ldg(p.pphi + x);
             m[u] = __ldg(p.pmass + x); pdg[u] = __ldg(p.ppdg + x); q[u] = __ldg(p.pcharge + x);
             vz[u] = s_z[lo];
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
         }
 #pragma unroll
         for (int u = 0; u < PU_UNROLL; ++u) {
-          const uint64_t i = i0 + (uint64_t)u * PU_BLOCK + tid;
+          const uint32_t i = i0 + (uint32_t)u * PU_BLOCK + tid;
           if (i < chunk) {
             const uint64_t d = pos + i;
             p.opt[d] = pt[u]; p.oeta[d] = eta[u]; p.ophi[d] = phi[u]; p.omass[d] = m[u];
