@@ -188,8 +188,9 @@ def bench_ours(args, dist, rank, ws):
     bt = B.make_batch(dev, cid, args.seed, event_base=base)
     if args.launch:
         best = B.pdr_launch()
-        best.team, best.block = (int(x) for x in args.launch.split(","))
-        best.table_slots, best.grid = 0, 0
+        f = [int(x) for x in args.launch.split(",")]
+        best.team, best.block = f[0], f[1]
+        best.table_slots, best.grid = (f[2] if len(f) > 2 else 0), 0
     else:
         best = ctx.autotune(bt, ob)
     stream = torch.cuda.current_stream()
@@ -720,7 +721,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--per-event-events", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--launch", default=None, help="fixed launch shape 'team,block' (skips autotuning)")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shape 'team,block[,table_slots]' (skips autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[50, 100, 200, 500])
