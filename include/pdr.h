@@ -203,7 +203,9 @@ int pdr_card_towers(pdr_ctx* ctx, uint32_t card_id, int calo, uint32_t* n);
  * caller must keep inputs and outputs alive until the stream has finished.
  * launch may be NULL (the context's tuned or default shape is used).  Events
  * larger than the launch's shared-memory table use a global-memory table from
- * the context pool (allocated on first need, outside any stream capture).
+ * the context pool (allocated on first need, outside any stream capture);
+ * launches of one context that use it share it, so do not overlap such
+ * launches on different streams.
  * Returns PDR_EINVAL for malformed arguments (checked on the host: non-null
  * pointers, n_events < 2^31; the CSR itself is checked on the device and a bad
  * one sets the device error word).  The launch hands events to its teams
