@@ -168,7 +168,7 @@ struct pdr_ctx {
   size_t smem_optin = 0;
   uint32_t* d_err = nullptr;      // device error word
   uint32_t* d_word = nullptr;     // small device word for reductions
-  uint32_t* d_next = nullptr;     // device work counter of the clustering launches
+  uint32_t* d_next = nullptr;     // device work counters of the clustering launches (one a size tier)
   // fused-launch work counters, one pair a stream (launches on one stream run
   // in order; each launch leaves its counter at zero)
   uint32_t* d_work = nullptr;
@@ -200,6 +200,8 @@ struct pdr_ctx {
   // jet clustering: per-warp four-momentum scratch (device)
   double* jet_scratch = nullptr;
   uint64_t jet_scratch_bytes = 0;
+  cudaStream_t s_jet = nullptr;   // side stream of the clustering's second size tier
+  cudaEvent_t ev_jfork = nullptr, ev_jjoin = nullptr;
 };
 
 namespace {
@@ -742,6 +744,9 @@ int pdr_destroy(pdr_ctx* ctx) {
   if (ctx->pu_T) cudaFree(ctx->pu_T);
   if (ctx->pu_hoff_total) cudaFreeHost(ctx->pu_hoff_total);
   if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);
+  if (ctx->s_jet) cudaStreamDestroy(ctx->s_jet);
+  if (ctx->ev_jfork) cudaEventDestroy(ctx->ev_jfork);
+  if (ctx->ev_jjoin) cudaEventDestroy(ctx->ev_jjoin);
   if (ctx->d_work) cudaFree(ctx->d_work);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_word);
@@ -1962,31 +1967,56 @@ extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outp
   // launch sized for the largest.
   const uint32_t tier = 288;
   const uint32_t caps[2] = {std::min(cap, tier), cap};
-  for (int k = 0; k < (cap > tier ? 2 : 1); ++k) {
-    p.cap = caps[k];
-    p.min_obj = k == 0 ? 0u : tier + 1u;
-    const uint64_t ws = jet_ws_bytes(p.cap, p.ee != 0, p.ntiles);
+  const int n_tiers = cap > tier ? 2 : 1;
+  JetParams tp[2];
+  uint64_t blocks[2] = {0, 0}, need[2] = {0, 0};
+  size_t smem[2] = {0, 0};
+  for (int k = 0; k < n_tiers; ++k) {
+    tp[k] = p;
+    tp[k].cap = caps[k];
+    tp[k].min_obj = k == 0 ? 0u : tier + 1u;
+    const uint64_t ws = jet_ws_bytes(tp[k].cap, p.ee != 0, p.ntiles);
     // two blocks an SM where the shared memory allows (shorter tails)
-    p.warps = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, half_sm / ws));
-    const size_t smem = (size_t)(p.warps * ws);
+    tp[k].warps = (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, half_sm / ws));
+    smem[k] = (size_t)(tp[k].warps * ws);
     int per_sm = 0;
-    PDR_CUDA(occupancy_cluster(p.warps * 32u, smem, &per_sm), "clustering occupancy");
-    const uint64_t blocks = std::min<uint64_t>((b->n_events + p.warps - 1) / p.warps,
-                                               (uint64_t)ctx->n_sms * (uint64_t)std::max(per_sm, 1));
-    // four-momentum scratch: 4 doubles per object for every warp of the grid
-    const uint64_t need = blocks * p.warps * (uint64_t)p.cap * 8u * PDR_JET_SCRATCH_DOUBLES;
-    if (need > ctx->jet_scratch_bytes) {
-      PDR_CUDA(cudaDeviceSynchronize(), "sync");   // earlier clusterings may still use the scratch
-      if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);
-      ctx->jet_scratch = nullptr;
-      ctx->jet_scratch_bytes = 0;
-      PDR_CUDA(cudaMalloc((void**)&ctx->jet_scratch, need), "jet scratch");
-      ctx->jet_scratch_bytes = need;
-    }
-    p.scratch = ctx->jet_scratch;
-    p.next_event = ctx->d_next;
-    PDR_CUDA(cudaMemsetAsync(ctx->d_next, 0, 4, s), "memset");
-    PDR_CUDA(launch_cluster(p, (uint32_t)blocks, smem, s), "clustering launch");
+    PDR_CUDA(occupancy_cluster(tp[k].warps * 32u, smem[k], &per_sm), "clustering occupancy");
+    blocks[k] = std::min<uint64_t>((b->n_events + tp[k].warps - 1) / tp[k].warps,
+                                   (uint64_t)ctx->n_sms * (uint64_t)std::max(per_sm, 1));
+    // four-momentum scratch: PDR_JET_SCRATCH_DOUBLES per object for every warp of the grid
+    need[k] = blocks[k] * tp[k].warps * (uint64_t)tp[k].cap * 8u * PDR_JET_SCRATCH_DOUBLES;
+  }
+  if (need[0] + need[1] > ctx->jet_scratch_bytes) {
+    PDR_CUDA(cudaDeviceSynchronize(), "sync");   // earlier clusterings may still use the scratch
+    if (ctx->jet_scratch) cudaFree(ctx->jet_scratch);
+    ctx->jet_scratch = nullptr;
+    ctx->jet_scratch_bytes = 0;
+    PDR_CUDA(cudaMalloc((void**)&ctx->jet_scratch, need[0] + need[1]), "jet scratch");
+    ctx->jet_scratch_bytes = need[0] + need[1];
+  }
+  // The two tiers run on two streams (the caller's and the context's side
+  // stream, forked before and joined after), so the larger events' blocks
+  // start as the smaller events' blocks drain instead of after the last one.
+  if (n_tiers == 2 && !ctx->s_jet) {
+    if (cudaStreamCreateWithFlags(&ctx->s_jet, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_jfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_jjoin, cudaEventDisableTiming) != cudaSuccess)
+      return fail(PDR_EDEVICE, "cannot create the clustering side stream");
+  }
+  if (n_tiers == 2) {
+    PDR_CUDA(cudaEventRecord(ctx->ev_jfork, s), "fork");
+    PDR_CUDA(cudaStreamWaitEvent(ctx->s_jet, ctx->ev_jfork, 0), "fork");
+  }
+  for (int k = 0; k < n_tiers; ++k) {
+    cudaStream_t sk = k == 0 ? s : ctx->s_jet;
+    tp[k].scratch = ctx->jet_scratch + (k == 0 ? 0 : need[0] / 8);
+    tp[k].next_event = ctx->d_next + k;
+    PDR_CUDA(cudaMemsetAsync(tp[k].next_event, 0, 4, sk), "memset");
+    PDR_CUDA(launch_cluster(tp[k], (uint32_t)blocks[k], smem[k], sk), "clustering launch");
+  }
+  if (n_tiers == 2) {
+    PDR_CUDA(cudaEventRecord(ctx->ev_jjoin, ctx->s_jet), "join");
+    PDR_CUDA(cudaStreamWaitEvent(s, ctx->ev_jjoin, 0), "join");
   }
   return PDR_OK;
 }
