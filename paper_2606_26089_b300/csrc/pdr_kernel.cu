@@ -711,6 +711,16 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
   return true;
 }
 
+// The event on a global-memory table (events beyond the shared table, or
+// the redo of an overflow): rare, so kept out of line, which keeps the
+// kernel's hot code small for the instruction cache.
+template <int TEAM>
+__device__ __noinline__ void process_event_global(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
+                                                  const Tbl& T, TeamTail& tt, const TeamCtx<TEAM>& tc, uint64_t e,
+                                                  uint64_t a, uint32_t n) {
+  process_event<TEAM, false>(S, err, K, KD, T, tt, tc, e, a, n);
+}
+
 // The persistent event loop of one team.  ONE: the launch holds a single
 // batch, whose fields the compiler then reads straight from the parameter
 // block (no per-event segment lookup).
@@ -770,7 +780,7 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_nmax);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys()[s] = PDR_EMPTY;
       tc.sync();
-      process_event<TEAM, false>(S, p.err, K, KD, gt, tt, tc, e, a, n);
+      process_event_global<TEAM>(S, p.err, K, KD, gt, tt, tc, e, a, n);
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);
