@@ -512,16 +512,21 @@ int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* ou
  * which every GPU that loads the library holds until the process exits.
  *
  * The first call on a device looks up that array's device address (a one-time
- * set-up with the device current); make that first call before any stream
- * capture.  Calls share the array and it keeps the previous call's contents:
- * each call re-stages the card, clears the error word and re-initialises the
- * tables it uses, but calls whose work overlaps on the GPU race and must not
- * be issued.  The call returns after the work on `stream` has finished (it
- * synchronises the stream) and reports device-side errors directly:
- * PDR_EDEVICE for malformed CSR offsets, PDR_EOVERFLOW when an event has more
- * than 49152 particles or its tower tables do not fit in the static array,
- * PDR_EINVAL / PDR_ECARD for bad arguments or cards.  No context is needed;
- * messages go to pdr_last_error(NULL). */
+ * set-up with the device current).  With CUDA's lazy module loading (the
+ * default) the array's device memory is committed at that first call, not
+ * when the library is loaded (CUDA_MODULE_LOADING=EAGER commits it at load):
+ * a caller that gives the remaining device memory to its own allocator makes
+ * one warm-up call first - a batch with n_events = 0 does the set-up and
+ * nothing else.  Calls share the array and it keeps the previous call's
+ * contents: each call re-stages the card, clears the error word and
+ * re-initialises the tables it uses, but calls whose work overlaps on the GPU
+ * race and must not be issued.  Every call copies the error word back and
+ * synchronises `stream` before it returns, so it cannot be issued on a stream
+ * that is being captured into a CUDA graph.  Device-side errors are reported
+ * directly: PDR_EDEVICE for malformed CSR offsets, PDR_EOVERFLOW when an
+ * event has more than 49152 particles or its tower tables do not fit in the
+ * static array, PDR_EINVAL / PDR_ECARD for bad arguments or cards.  No context
+ * is needed; messages go to pdr_last_error(NULL). */
 #define PDR_NOALLOC_SCRATCH_BYTES (32ull << 20)
 int pdr_run_noalloc(const pdr_card* card, const pdr_batch* batch, const pdr_outputs* out, void* stream);
 

@@ -149,6 +149,10 @@ def lib():
         _lib.oracle_pileup_draws.argtypes = [C.POINTER(PileUp), P, C.c_int32, C.c_uint64, C.c_uint64,
                                              C.c_uint32, C.c_double, P, P, P, P, C.c_int32, P, P]
         _lib.oracle_pileup_draws.restype = C.c_int32
+        _lib.oracle_pileup_draws_forced.argtypes = [C.POINTER(PileUp), P, C.c_int32, C.c_uint64, C.c_uint64,
+                                                    C.c_uint32, C.c_double, P, P, P, P, C.c_int32, P, P,
+                                                    P, C.c_int32, P, C.c_int32]
+        _lib.oracle_pileup_draws_forced.restype = C.c_int32
         D = C.c_double
         _lib.oracle_track_ip.argtypes = [C.POINTER(Card), D, D, D, C.c_int32, D, D, D, P, P, P]
         _lib.oracle_track_ip.restype = None
@@ -157,6 +161,9 @@ def lib():
         _lib.oracle_track_ip_smeared.restype = None
         _lib.oracle_cluster.argtypes = [C.c_int64, P, P, P, P, D, D, D, C.c_int32, C.c_int32, P, P]
         _lib.oracle_cluster.restype = C.c_int32
+        _lib.oracle_cluster_forced.argtypes = [C.c_int64, P, P, P, P, D, D, D, C.c_int32, C.c_int32, P, P,
+                                               P, C.c_int32, P, C.c_int32]
+        _lib.oracle_cluster_forced.restype = C.c_int32
     return _lib
 
 
@@ -392,32 +399,44 @@ def poisson_thresholds(mean: float, kmax: int = 8192) -> np.ndarray:
 
 
 def pileup_draws(pu: PileUp, T: np.ndarray, n_pool: int, seed: int, event: int, g: float = DEFAULT_G,
-                 cap: int = 65536):
+                 cap: int = 65536, flips: Sequence[tuple] = (), marginal_out: Optional[list] = None):
     """(n, pool indices, vertex z [m], vertex t [s], hard vertex shift z_hs [m],
-    hard vertex time t_hs [s], marginal count) of one hard event."""
+    hard vertex time t_hs [s], marginal count) of one hard event.  flips lists
+    truncation decisions (purpose, slot, attempt) to take the other way (each
+    must be marginal: else ValueError); marginal_out, if given, receives the
+    (purpose, slot, attempt) triples of the run's marginal decisions."""
     n = C.c_int32()
     zhs, ths = C.c_double(), C.c_double()
     idx = np.zeros(cap, np.uint32)
     z = np.zeros(cap, np.float64)
     t = np.zeros(cap, np.float64)
     T = np.ascontiguousarray(T, np.uint64)
-    m = lib().oracle_pileup_draws(C.byref(pu), _ptr(T), int(T.shape[0]), int(n_pool), int(seed) & (2**64 - 1),
-                                  int(event) & 0xFFFFFFFF, float(g), C.byref(n), _ptr(idx), _ptr(z), _ptr(t),
-                                  int(cap), C.byref(zhs), C.byref(ths))
+    fl = np.ascontiguousarray(np.asarray(list(flips) or [(0, 0, 0)], np.uint32).reshape(-1, 3))
+    mcap = 4096
+    mo = np.zeros((mcap, 3), np.uint32)
+    m = lib().oracle_pileup_draws_forced(C.byref(pu), _ptr(T), int(T.shape[0]), int(n_pool), int(seed) & (2**64 - 1),
+                                         int(event) & 0xFFFFFFFF, float(g), C.byref(n), _ptr(idx), _ptr(z), _ptr(t),
+                                         int(cap), C.byref(zhs), C.byref(ths), _ptr(fl), len(flips), _ptr(mo), mcap)
+    if m == -2:
+        raise ValueError("a forced truncation decision is not marginal or does not occur")
     if m < 0:
         raise ValueError("more interactions than cap")
+    if marginal_out is not None:
+        marginal_out.extend(tuple(int(x) for x in r) for r in mo[:min(m, mcap)])
     k = n.value
     return k, idx[:k].copy(), z[:k].copy(), t[:k].copy(), zhs.value, ths.value, m
 
 
 def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs: bool, seed: int,
-                 event_base: int = 0, g: float = DEFAULT_G, sigma_t: float = SIGMA_T, max_t: float = MAX_T) -> dict:
+                 event_base: int = 0, g: float = DEFAULT_G, sigma_t: float = SIGMA_T, max_t: float = MAX_T,
+                 flips: Optional[dict] = None) -> dict:
     """The merged batch: per hard event its own particles (vertex z plus the hard
     shift), then the pool events of its interactions in draw order, each at its
     interaction's vertex z and time (the hard particles at time t_hs).  Returns
     the merged CSR arrays (vz and vt in float64), the
-    draws, the number of marginal truncation decisions and the events holding
-    them."""
+    draws, the number of marginal truncation decisions, the events holding
+    them and, per such event, its marginal decisions.  flips maps an event
+    to the truncation decisions to force the other way (see pileup_draws)."""
     pu = PileUp(float(mean), float(sigma_z), float(max_z), float(sigma_t), float(max_t), int(bool(smear_hs)), 0)
     T = poisson_thresholds(mean)
     po = np.asarray(pool.offsets, np.int64)
@@ -427,11 +446,15 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
     draws = []
     n_marg = 0
     marg_events = []
+    marg_decisions = {}
     for e in range(hard.n_events):
-        k, idx, z, t, zhs, ths, m = pileup_draws(pu, T, pool.n_events, seed, event_base + e, g)
+        mlist = []
+        k, idx, z, t, zhs, ths, m = pileup_draws(pu, T, pool.n_events, seed, event_base + e, g,
+                                                 flips=(flips or {}).get(e, ()), marginal_out=mlist)
         n_marg += m
         if m:
             marg_events.append(e)
+            marg_decisions[e] = mlist
         draws.append((k, idx, z, t, zhs, ths))
         starts.append(ho[e]); lens.append(ho[e + 1] - ho[e]); zs.append(zhs); ts.append(ths); srcs.append(0)
         for j in range(k):
@@ -462,6 +485,7 @@ def pileup_merge(hard, pool, mean: float, sigma_z: float, max_z: float, smear_hs
     out["draws"] = draws
     out["marginal"] = n_marg
     out["marginal_events"] = marg_events
+    out["marginal_decisions"] = marg_decisions
     return out
 
 
@@ -521,6 +545,27 @@ def cluster(px, py, pz, e, p: float = -1.0, R: float = 0.5, pt_min: float = 0.0,
     if k < 0:
         raise ValueError("bad clustering arguments")
     return jets[:k].copy(), m.value
+
+
+def cluster_forced(px, py, pz, e, p: float = -1.0, R: float = 0.5, pt_min: float = 0.0, nconst_min: int = 1,
+                   ee: bool = False, flips: Sequence[int] = ()):
+    """(jets, indices of the marginal steps) of one event, taking the runner-up
+    decision at each listed step (steps counted from 0 in recombination order);
+    raises ValueError if a listed step is not marginal."""
+    arr = [np.ascontiguousarray(x, np.float64) for x in (px, py, pz, e)]
+    n = arr[0].shape[0]
+    jets = np.zeros(max(n, 1), JET)
+    m = C.c_int32()
+    fl = np.ascontiguousarray(list(flips) or [0], np.int32)
+    cap = max(n, 1)
+    steps = np.zeros(cap, np.int32)
+    k = lib().oracle_cluster_forced(n, *[_ptr(a) for a in arr], float(p), float(R), float(pt_min), int(nconst_min),
+                                    int(bool(ee)), _ptr(jets), C.byref(m), _ptr(fl), len(flips), _ptr(steps), cap)
+    if k == -2:
+        raise ValueError("a forced step is not marginal")
+    if k < 0:
+        raise ValueError("bad clustering arguments")
+    return jets[:k].copy(), steps[:min(m.value, cap)].tolist()
 
 
 def four_momenta(pt, eta, phi, e):

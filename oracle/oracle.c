@@ -818,37 +818,82 @@ int32_t oracle_poisson_thresholds(double mean, uint64_t* T, int32_t kmax) {
 /* sigma times a standard normal, redrawn until |v| <= bound (decided on the
  * float32 value): a Gaussian truncated at +-bound.  *marg counts decisions
  * within the band g of the bound. */
+/* The parity protocol's forced branches of the truncation decisions: a
+ * decision (purpose, slot, attempt) listed in fl is taken the other way -
+ * only if it is marginal (else *refused is set).  Marginal decisions are
+ * recorded as (purpose, slot, attempt) triples in mo (up to mcap of them). */
+typedef struct pu_force {
+  const uint32_t* fl;
+  int32_t nfl;
+  uint32_t* mo;
+  int32_t mcap;
+  int32_t used;   /* forced decisions met */
+  int refused;
+} pu_force;
+
+static int pu_listed(const pu_force* f, uint32_t purpose, uint32_t slot, uint32_t a) {
+  for (int32_t k = 0; f && k < f->nfl; ++k)
+    if (f->fl[3 * k] == purpose && f->fl[3 * k + 1] == slot && f->fl[3 * k + 2] == a) return 1;
+  return 0;
+}
+
 static double truncated_normal(double sigma, double bound, uint64_t seed, uint32_t slot, uint32_t event,
-                               uint32_t purpose, double g, int32_t* marg) {
+                               uint32_t purpose, double g, int32_t* marg, pu_force* f) {
   for (uint32_t a = 0;; ++a) {
     uint32_t w[4];
     uint32_t ctr[4] = {slot, event, purpose, a};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     oracle_philox4x32_10(ctr, key, w);
     double v = sigma * oracle_normal(w[1], w[2]);
-    if (fabs(fabs(v) - bound) <= g * fmax(fabs(v), bound)) ++*marg;
-    if (fabsf((float)v) <= (float)bound) return v;
+    const int marginal = fabs(fabs(v) - bound) <= g * fmax(fabs(v), bound);
+    if (marginal) {
+      if (f && *marg < f->mcap) {
+        f->mo[3 * *marg] = purpose;
+        f->mo[3 * *marg + 1] = slot;
+        f->mo[3 * *marg + 2] = a;
+      }
+      ++*marg;
+    }
+    int accept = fabsf((float)v) <= (float)bound;
+    if (pu_listed(f, purpose, slot, a)) {
+      if (!marginal) f->refused = 1;
+      accept = !accept;
+      ++f->used;
+    }
+    if (accept) return v;
   }
 }
 
 int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K, uint64_t n_pool,
                             uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
                             double* z, double* t, int32_t cap, double* z_hs, double* t_hs) {
+  return oracle_pileup_draws_forced(p, T, K, n_pool, seed, event, g, n, idx, z, t, cap, z_hs, t_hs,
+                                    NULL, 0, NULL, 0);
+}
+
+int32_t oracle_pileup_draws_forced(const oracle_pileup* p, const uint64_t* T, int32_t K, uint64_t n_pool,
+                                   uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
+                                   double* z, double* t, int32_t cap, double* z_hs, double* t_hs,
+                                   const uint32_t* flips, int32_t n_flips, uint32_t* marg_out, int32_t marg_cap) {
   int32_t marg = 0;
+  pu_force force = {flips, n_flips, marg_out, marg_out ? marg_cap : 0, 0, 0};
+  pu_force* f = (flips || marg_out) ? &force : NULL;
   uint32_t w[4];
   draw(seed, 0u, event, 5u, w);
   int32_t N = 0;
   while (N < K - 1 && (uint64_t)w[0] >= T[N]) ++N;  /* smallest N with w0 < T[N] */
   *n = N;
-  *z_hs = p->smear_hs ? truncated_normal(p->sigma_z, p->max_z, seed, 0u, event, 5u, g, &marg) : 0.0;
-  *t_hs = p->smear_hs ? truncated_normal(p->sigma_t, p->max_t, seed, 0u, event, 8u, g, &marg) : 0.0;
+  *z_hs = p->smear_hs ? truncated_normal(p->sigma_z, p->max_z, seed, 0u, event, 5u, g, &marg, f) : 0.0;
+  *t_hs = p->smear_hs ? truncated_normal(p->sigma_t, p->max_t, seed, 0u, event, 8u, g, &marg, f) : 0.0;
   if (N > cap) return -1;
   for (int32_t k = 0; k < N; ++k) {
     draw(seed, (uint32_t)k, event, 6u, w);
     idx[k] = (uint32_t)(((uint64_t)w[0] * n_pool) >> 32);
-    z[k] = truncated_normal(p->sigma_z, p->max_z, seed, (uint32_t)k, event, 6u, g, &marg);
-    t[k] = truncated_normal(p->sigma_t, p->max_t, seed, (uint32_t)k, event, 7u, g, &marg);
+    z[k] = truncated_normal(p->sigma_z, p->max_z, seed, (uint32_t)k, event, 6u, g, &marg, f);
+    t[k] = truncated_normal(p->sigma_t, p->max_t, seed, (uint32_t)k, event, 7u, g, &marg, f);
   }
+  /* every forced decision must be met, and be marginal */
+  if (f && (force.refused || force.used != n_flips)) return -2;
   return marg;
 }
 
@@ -940,6 +985,19 @@ static double cl_dphi(double a, double b) {
 int32_t oracle_cluster(int64_t n, const double* px, const double* py, const double* pz, const double* e,
                        double p, double R, double pt_min, int32_t nconst_min, int32_t ee, or_jet* jets,
                        int32_t* n_marg) {
+  return oracle_cluster_forced(n, px, py, pz, e, p, R, pt_min, nconst_min, ee, jets, n_marg, NULL, 0, NULL, 0);
+}
+
+static int cl_listed(const int32_t* v, int32_t nv, int32_t x) {
+  for (int32_t k = 0; k < nv; ++k)
+    if (v[k] == x) return 1;
+  return 0;
+}
+
+int32_t oracle_cluster_forced(int64_t n, const double* px, const double* py, const double* pz, const double* e,
+                              double p, double R, double pt_min, int32_t nconst_min, int32_t ee, or_jet* jets,
+                              int32_t* n_marg, const int32_t* flips, int32_t n_flips, int32_t* marg_steps,
+                              int32_t marg_cap) {
   if (n < 0 || !(R > 0.0) || (ee && !(R <= M_PI))) return -1;
   *n_marg = 0;
   if (n == 0) return 0;
@@ -959,16 +1017,18 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
   /* the distance normalisation: R^2, or 2 (1 - cos R) for e+e- (|n_i - n_j|^2 = 2 (1 - cos theta)) */
   const double R2 = ee ? 2.0 * (1.0 - cos(R)) : R * R, eps = 1.0 / 8388608.0; /* 2^-23 */
   int32_t nj = 0;
-  for (int64_t left = n; left > 0;) {
-    /* smallest distance; best / second: value and uncertainty */
+  int32_t step = 0;
+  for (int64_t left = n; left > 0; ++step) {
+    /* smallest distance; best / second: value, uncertainty and decision
+     * (object i with object j, or with the beam: j = -1) */
     double b = INFINITY, bu = 0.0, s2 = INFINITY, su = 0.0;
-    int64_t bi = -1, bj = -1;
+    int64_t bi = -1, bj = -1, si = -1, sj = -1;
     for (int64_t i = 0; i < n; ++i) {
       if (!o[i].active) continue;
       const double diB = o[i].kt2p, uiB = 1e-6 * diB;
       /* the beam distance first: it wins ties */
-      if (diB < b) { s2 = b; su = bu; b = diB; bu = uiB; bi = i; bj = -1; }
-      else if (diB < s2) { s2 = diB; su = uiB; }
+      if (diB < b) { s2 = b; su = bu; si = bi; sj = bj; b = diB; bu = uiB; bi = i; bj = -1; }
+      else if (diB < s2) { s2 = diB; su = uiB; si = i; sj = -1; }
       for (int64_t j = i + 1; j < n; ++j) {
         if (!o[j].active) continue;
         const double kmin = fmin(o[i].kt2p, o[j].kt2p);
@@ -984,11 +1044,21 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
           const double ey = eps * fmax(fmax(fabs(o[i].y), fabs(o[j].y)), 1.0), ep = eps * M_PI;
           u = 1e-6 * d + kmin * (2.0 * fabs(dy) * ey + 2.0 * fabs(dp) * ep) / R2;
         }
-        if (d < b) { s2 = b; su = bu; b = d; bu = u; bi = i; bj = j; }
-        else if (d < s2) { s2 = d; su = u; }
+        if (d < b) { s2 = b; su = bu; si = bi; sj = bj; b = d; bu = u; bi = i; bj = j; }
+        else if (d < s2) { s2 = d; su = u; si = i; sj = j; }
       }
     }
-    if (s2 - b <= bu + su) ++*n_marg;
+    const int marginal = s2 - b <= bu + su;
+    if (marginal) {
+      if (*n_marg < marg_cap && marg_steps) marg_steps[*n_marg] = step;
+      ++*n_marg;
+    }
+    if (flips && cl_listed(flips, n_flips, step)) {
+      /* take the runner-up decision: only at a marginal step */
+      if (!marginal || si < 0) { free(jet_of); free(o); return -2; }
+      bi = si;
+      bj = sj;
+    }
     if (bj < 0) {
       /* i becomes a jet */
       cl_obj* q = &o[bi];
@@ -1019,6 +1089,9 @@ int32_t oracle_cluster(int64_t n, const double* px, const double* py, const doub
       cl_derive(a, p, ee);
     }
   }
+  /* a forced step that never came is refused too */
+  for (int32_t k = 0; flips && k < n_flips; ++k)
+    if (flips[k] < 0 || flips[k] >= step) { free(jet_of); free(o); return -2; }
   /* substructure: each constituent's jet is the end of its chain of merges */
   for (int32_t k = 0; k < nj; ++k) { jets[k].e2 = jets[k].e3 = jets[k].c2 = jets[k].d2 = 0.0; }
   int64_t* root = (int64_t*)malloc((size_t)n * sizeof(int64_t));

@@ -226,6 +226,18 @@ int32_t oracle_pileup_draws(const oracle_pileup* p, const uint64_t* T, int32_t K
                             uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
                             double* z, double* t, int32_t cap, double* z_hs, double* t_hs);
 
+/* The same with the parity protocol's forced branches: each (purpose, slot,
+ * attempt) triple of flips[3 n_flips] names a truncation decision (purpose 5
+ * hard vertex z, 8 hard vertex time, 6 interaction z, 7 interaction time;
+ * slot the interaction; attempt the draw's counter word 3) to be taken the
+ * other way.  Every listed decision must occur and be marginal, else the
+ * call refuses and returns -2.  The triples of this run's marginal decisions
+ * go to marg_out[3 marg_cap] (may be NULL). */
+int32_t oracle_pileup_draws_forced(const oracle_pileup* p, const uint64_t* T, int32_t K, uint64_t n_pool,
+                                   uint64_t seed, uint32_t event, double g, int32_t* n, uint32_t* idx,
+                                   double* z, double* t, int32_t cap, double* z_hs, double* t_hs,
+                                   const uint32_t* flips, int32_t n_flips, uint32_t* marg_out, int32_t marg_cap);
+
 /* ---- track impact parameters (the paper's output table: d0, z0 and their
  * errors for charged particles; Sec. 2.5) ----
  * Readings (the paper gives no formula):
@@ -298,6 +310,16 @@ typedef struct or_jet {
 int32_t oracle_cluster(int64_t n, const double* px, const double* py, const double* pz, const double* e,
                        double p, double R, double pt_min, int32_t nconst_min, int32_t ee, or_jet* jets,
                        int32_t* n_marg);
+
+/* The same, with the parity protocol's forced branches: at every step whose
+ * index (0, 1, ... in recombination order) is listed in flips[n_flips] the
+ * runner-up decision is taken instead of the smallest distance - only where
+ * that step is marginal and exists (else the call refuses and returns -2).  The indices of
+ * the marginal steps of this run go to marg_steps (up to marg_cap of them). */
+int32_t oracle_cluster_forced(int64_t n, const double* px, const double* py, const double* pz, const double* e,
+                              double p, double R, double pt_min, int32_t nconst_min, int32_t ee, or_jet* jets,
+                              int32_t* n_marg, const int32_t* flips, int32_t n_flips, int32_t* marg_steps,
+                              int32_t marg_cap);
 
 #ifdef __cplusplus
 }

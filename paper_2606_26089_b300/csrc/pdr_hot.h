@@ -2,6 +2,8 @@
 // expanded DevCard.  Writes into caller storage; allocates nothing.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "pdr_internal.h"
@@ -87,6 +89,18 @@ inline size_t build_hot_card(const DevCard& D, unsigned char* out, size_t cap) {
   std::memcpy(H.s_min, D.s_min, sizeof H.s_min);
   H.cand_ptmin = D.cand_ptmin; H.dr2max = D.dr2max; H.dr2min = D.dr2min;
   H.iso_ptmin = D.iso_ptmin; H.imax = D.imax;
+  {
+    // (a cone radius that is not a finite number puts every object in one bin)
+    const double dr = std::sqrt((double)D.dr2max);
+    if (std::isfinite(dr)) {
+      const double w = std::max(1.001 * dr, 16.0 / PDR_ISO_BINS);
+      H.iso_inv_w = (float)(1.0 / w);
+      H.iso_nbin = std::max(1, std::min(PDR_ISO_BINS, (int)std::ceil(16.0 / w)));
+    } else {
+      H.iso_inv_w = 0.0f;
+      H.iso_nbin = 1;
+    }
+  }
   const size_t used = nf;
   nf = (nf + 3) & ~size_t(3);  // 16-byte multiple
   if (nf > max_floats) return 0;

@@ -114,6 +114,11 @@ struct alignas(16) HotCard {
   unsigned long long id_T[3][PDR_MAXEDGE];
   float e_min[2], s_min[2];
   float cand_ptmin, dr2max, dr2min, iso_ptmin, imax;
+  // isolation pre-selection: eta bins of width w >= 1.001 dR over [-8, 8]
+  // (eta outside clamps to the end bins), so an object within the cone of a
+  // candidate lies in the candidate's bin or a neighbouring one
+  float iso_inv_w;
+  int32_t iso_nbin;
   int32_t data_floats;
 };
 
@@ -305,17 +310,26 @@ enum : uint32_t {
   ERR_JETS = 32u,      // jet clustering: more jets than the event's slots, or an inconsistent cell list
 };
 
+// An event's CSR range [a, b) is usable iff a <= b <= end, end = offsets[n_events]
+// (the particle and output arrays hold `end` entries).  Checking b < a alone
+// is not enough: a non-monotone interior offset past the end gives an earlier
+// event a range that reads and writes beyond the arrays.
+PDR_HD inline bool csr_ok(uint64_t a, uint64_t b, uint64_t end) { return a <= b && b <= end; }
+
+#define PDR_PART_BYTES 8     // per particle: info word, smearing-job entry
+#define PDR_ISO_BINS 64      // eta bins of the isolation pre-selection
+
 // Bytes of a team's event workspace: the tower table (keys, owner, esum, etrk
 // per slot), then per particle an info word and a smearing-job entry
 // (16-byte multiple).
 PDR_HD inline uint64_t table_bytes(uint32_t slots, uint32_t nmax) {
-  const uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * (4 + 4);
+  const uint64_t b = (uint64_t)slots * (4 + 4 + 8 + 8) + (uint64_t)nmax * PDR_PART_BYTES;
   return (b + 15) & ~15ull;
 }
 
 // A team's shared scratch after its table: scan buffers (double-buffered),
 // the staged isolation candidates (eta, phi, pT', particle index; own tower
-// key; record info word; fixed-point cone sums).
+// key; record info word; fixed-point cone sums) and their eta-bin masks.
 struct TeamTail {
   uint32_t next[4];                  // the team's next events, double-buffered (work counter)
   uint32_t wbuf[2 * 32];
@@ -323,12 +337,15 @@ struct TeamTail {
   uint32_t ckey[PDR_CMAX];
   uint32_t cinfo[PDR_CMAX];
   unsigned long long csum[PDR_CMAX];
+  uint32_t binmask[PDR_ISO_BINS];    // bit c: staged candidate c lies in this eta bin or a neighbour
 };
+
+PDR_HD inline uint64_t tail_bytes(uint32_t) { return (sizeof(TeamTail) + 15) & ~15ull; }
 
 // Shared-memory bytes needed by one team of a launch shape (the card cache is
 // counted separately, once per CTA).
 PDR_HD inline uint64_t team_smem_bytes(uint32_t team, uint32_t slots, uint32_t nmax) {
-  return table_bytes(slots, nmax) + sizeof(TeamTail);
+  return table_bytes(slots, nmax) + tail_bytes(team);
 }
 
 PDR_HD inline uint64_t global_team_bytes(uint32_t slots, uint32_t nmax) {

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) track_ip_kernel(const __grid_constant__ I
   for (uint64_t e = w0; e < p.n_events; e += nw) {
     const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
     const uint32_t nt = p.counts[4 * e];
-    if (b < a || nt > b - a) {
+    if (!csr_ok(a, b, p.offsets[p.n_events]) || nt > b - a) {
       if (lane == 0) atomicOr(p.err, ERR_CSR);
       continue;
     }

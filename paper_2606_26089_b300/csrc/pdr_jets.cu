@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(const __grid_constant__ Je
     }
     const uint64_t n_part = b - a;
     const uint64_t n_obj = p.collection == PDR_JETS_PFLOW ? (uint64_t)c0 + c2 : n_part;
-    if (b < a || c0 > n_part || c2 > n_part) {
+    if (!csr_ok(a, b, p.offsets[p.n_events]) || c0 > n_part || c2 > n_part) {
       if (lane == 0 && p.min_obj == 0) {
         atomicOr(p.err, ERR_CSR);
         p.jet_counts[e] = 0;
@@ -613,7 +613,8 @@ __global__ void jet_max_objects_kernel(JetParams p, uint32_t* out) {
   uint32_t mx = 0;
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < p.n_events;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t n = p.offsets[e + 1] - p.offsets[e];
+    const uint64_t a = p.offsets[e], b = p.offsets[e + 1];
+    const uint64_t n = csr_ok(a, b, p.offsets[p.n_events]) ? b - a : 0;  // bad ranges are flagged by the clustering
     const uint64_t v = p.collection == PDR_JETS_PFLOW ? (uint64_t)p.counts[4 * e] + p.counts[4 * e + 2] : n;
     mx = max(mx, (uint32_t)min(v, (uint64_t)0xFFFFFFFFu));
   }

@@ -375,6 +375,18 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
   }
 }
 
+// Adds v to the 64-bit fixed-point sum at p with two native 32-bit atomics (a
+// 64-bit shared-memory atomic add is a compare-and-swap loop): the low word,
+// then the high word plus the carry out of the low word.  Every term's carry
+// is added exactly once, so the sum is exact in any order.
+__device__ __forceinline__ void fp_add(unsigned long long* p, unsigned long long v) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(p);
+  const uint32_t lo = (uint32_t)v;
+  const uint32_t old = atomicAdd(w, lo);
+  const uint32_t hi = (uint32_t)(v >> 32) + (old + lo < old ? 1u : 0u);
+  if (hi != 0u) atomicAdd(w + 1, hi);
+}
+
 // ------------------------------------------------------------ tower table
 // Per-team open-addressing table (linear probing, multiplicative hash) keyed
 // by tower key; per particle an info word (slot | ring << 16, or empty); the
@@ -477,23 +489,37 @@ __device__ __forceinline__ void tower_stage(const HotCard& K, const float* KD, u
 // ------------------------------------------------------------ isolation
 #define PDR_ISO_TRACK 0x80000000u    // object tag: a track (particle index), else a tower key
 
-// Adds an object's fixed-point pT to every staged candidate whose cone holds it.
-__device__ __forceinline__ void iso_object(const HotCard& K, float4 obj, uint32_t gn, TeamTail& tt) {
+// Staged candidates mark their eta bin and both neighbours in a bit mask per
+// bin (bins at least 1.001 cone radii wide, over [-8, 8], the ends clamped), so
+// an object only tests the candidates of its own bin's mask - usually none.
+__device__ __forceinline__ int iso_bin(const HotCard& K, float eta) {
+  const int b = (int)((eta + 8.0f) * K.iso_inv_w);
+  return min(max(b, 0), K.iso_nbin - 1);
+}
+
+// Adds an object's fixed-point pT to every staged candidate whose cone
+// ΔR_min <= ΔR < ΔR_max holds it, skipping the object built from the
+// candidate itself (its own track, by particle index, or the EFlow neutral of
+// its own tower, by key).
+__device__ __forceinline__ void iso_object(const HotCard& K, float4 obj, TeamTail& tt) {
+  uint32_t m = tt.binmask[iso_bin(K, obj.x)];
+  if (m == 0u) return;
   const uint32_t tag = __float_as_uint(obj.w);
   const bool is_trk = (tag & PDR_ISO_TRACK) != 0u;
   const uint32_t oid = tag & ~PDR_ISO_TRACK;
   const unsigned long long wgt = to_fp(obj.z);
-  for (uint32_t c = 0; c < gn; ++c) {
+  do {
+    const uint32_t c = __ffs(m) - 1;
+    m &= m - 1u;
     const float4 cv = tt.cf[c];
-    // the candidate's own track / own tower
     if (is_trk ? (oid == __float_as_uint(cv.w)) : (oid == tt.ckey[c])) continue;
     const float de = obj.x - cv.x;
     float dp = obj.y - cv.y;
     if (dp >= PI_F) dp -= TWO_PI_F;
     else if (dp < -PI_F) dp += TWO_PI_F;
     const float dr2 = fmaf(de, de, dp * dp);
-    if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&tt.csum[c], wgt);
-  }
+    if (dr2 < K.dr2max && dr2 >= K.dr2min) fp_add(&tt.csum[c], wgt);
+  } while (m != 0u);
 }
 
 // ------------------------------------------------------------- one event
@@ -538,7 +564,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     const uint32_t pre = team_scan2<TEAM>(has_job, false, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (slot != PDR_EMPTY && !claimed) {  // after the barrier that orders the claimers' stores
-      atomicAdd(&T.esum()[slot], e_fp);
+      fp_add(&T.esum()[slot], e_fp);
       atomicMin(&T.owner()[slot], i);
     }
     if (has_job) T.jobs()[n_job + (pre & 0xFFFFu)] = o.job;
@@ -564,7 +590,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       run_job(S, K, a, job, event, r);
       if (r.tracked) {
         const uint32_t pi = T.pinfo()[i];
-        if (pi != PDR_EMPTY) atomicAdd(&T.etrk()[pi & 0xFFFFu], to_fp(r.etrk));
+        if (pi != PDR_EMPTY) fp_add(&T.etrk()[pi & 0xFFFFu], to_fp(r.etrk));
       }
       if (dbg && (r.tracked || r.cand))
         reinterpret_cast<uint32_t*>(S.debug + a + i)[3] |=
@@ -590,6 +616,11 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
           tt.cf[jc] = make_float4(eta, phi, r.cpt, __uint_as_float(i));
           tt.ckey[jc] = key;
           tt.cinfo[jc] = i | ((uint32_t)r.cc << 28);
+          const int b = iso_bin(K, eta);
+          const uint32_t bit = 1u << jc;
+          if (b > 0) atomicOr(&tt.binmask[b - 1], bit);
+          atomicOr(&tt.binmask[b], bit);
+          if (b + 1 < K.iso_nbin) atomicOr(&tt.binmask[b + 1], bit);
         }
       }
     }
@@ -618,7 +649,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
             const int calo = (int)(key >> 24), ring = (int)(pi >> 16);
             const float oe = ring_rec(K, KD, calo, ring).x;
             iso_object(K, make_float4(oe, tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring), to.det,
-                                      __uint_as_float(key)), gn0, tt);
+                                      __uint_as_float(key)), tt);
           }
         }
       }
@@ -626,7 +657,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     if (gn0 > 0 && i < n_trk) {
       const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + i];
       if (t.x > K.iso_ptmin)
-        iso_object(K, make_float4(t.y, t.z, t.x, __uint_as_float(__float_as_uint(t.w) | PDR_ISO_TRACK)), gn0, tt);
+        iso_object(K, make_float4(t.y, t.z, t.x, __uint_as_float(__float_as_uint(t.w) | PDR_ISO_TRACK)), tt);
     }
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, tt.wbuf + 32 * flip, tot, tc);
@@ -647,6 +678,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
   // object's pT during 2 (its last team scan orders those sums before this
   // read); further groups of PDR_CMAX candidates loop over all EFlow objects.
   if (gn0 > 0) {
+    for (uint32_t k = tc.tid; k < PDR_ISO_BINS; k += TEAM) tt.binmask[k] = 0u;  // read only during 2
     if ((uint32_t)tc.tid < gn0) {
       const uint32_t c = tc.tid;
       const float s = from_fp(tt.csum[c]);
@@ -691,7 +723,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
         if (dp >= PI_F) dp -= TWO_PI_F;
         else if (dp < -PI_F) dp += TWO_PI_F;
         const float dr2 = fmaf(de, de, dp * dp);
-        if (dr2 < K.dr2max && dr2 >= K.dr2min) atomicAdd(&tt.csum[c], wgt);
+        if (dr2 < K.dr2max && dr2 >= K.dr2min) fp_add(&tt.csum[c], wgt);
       }
     }
     tc.sync();
@@ -748,7 +780,7 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
     const HotCard& K = *reinterpret_cast<const HotCard*>(smem + p.hot_off[S.card]);
     const float* KD = reinterpret_cast<const float*>(smem + p.hot_off[S.card] + sizeof(HotCard));
     const uint64_t a = S.offsets[e], b = S.offsets[e + 1];
-    if (b < a || b - a >= (1ull << 28)) {
+    if (!csr_ok(a, b, S.offsets[S.n_events]) || b - a >= (1ull << 28)) {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_CSR);
         reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
@@ -825,6 +857,7 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
   TeamTail& tt = *reinterpret_cast<TeamTail*>(tail);
   for (uint32_t s = tc.tid; s < p.table_slots; s += TEAM) st.keys()[s] = PDR_EMPTY;
   if ((uint32_t)tc.tid < PDR_CMAX) tt.csum[tc.tid] = 0ull;
+  for (uint32_t k = tc.tid; k < PDR_ISO_BINS; k += TEAM) tt.binmask[k] = 0u;
   if constexpr (OVF) {
     if (tc.tid == 0) s_table_full = 0u;
   }
@@ -840,7 +873,7 @@ __global__ void max_event_kernel(const uint64_t* __restrict__ offsets, uint64_t 
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n_events;
        e += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t a = offsets[e], b = offsets[e + 1];
-    if (b < a) atomicOr(err, ERR_CSR);
+    if (!csr_ok(a, b, offsets[n_events])) atomicOr(err, ERR_CSR);
     else m = max(m, (uint32_t)min(b - a, (uint64_t)0xFFFFFFFFu));
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(PDR_FULL, m, o));

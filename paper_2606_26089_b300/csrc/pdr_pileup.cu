@@ -51,18 +51,20 @@ __device__ __forceinline__ float pu_truncated_normal(const PuParams& p, float si
 __device__ __forceinline__ uint64_t pu_event_size(const PuParams& p, uint64_t e, uint32_t event, uint32_t lane,
                                                   uint32_t n_int, bool& ok) {
   const uint64_t a = p.hoff[e], b = p.hoff[e + 1];
+  const uint64_t pool_end = __ldg(p.poff + p.n_pool);
   uint64_t sum = 0;
   bool bad = false;
   for (uint32_t k = lane; k < n_int; k += 32u) {
     const uint64_t q = pu_pool_event(p, k, event);
     const uint64_t q0 = __ldg(p.poff + q), q1 = __ldg(p.poff + q + 1);
-    bad |= q1 < q0 || q1 - q0 >= (1ull << 32);
+    bad |= !csr_ok(q0, q1, pool_end) || q1 - q0 >= (1ull << 32);
     sum += q1 - q0;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(PDR_FULL, sum, o);
-  ok = b >= a && !__any_sync(PDR_FULL, bad);
-  return (b >= a ? b - a : 0) + sum;
+  const bool hard_ok = csr_ok(a, b, p.hoff[p.n_events]);
+  ok = hard_ok && !__any_sync(PDR_FULL, bad);
+  return (hard_ok ? b - a : 0) + sum;
 }
 
 // First pass: one warp per hard event writes the event's merged size.
@@ -195,24 +197,25 @@ __global__ void __launch_bounds__(PU_BLOCK, 4) pu_fill_kernel(const __grid_const
     const uint32_t event = p.event_base + (uint32_t)e;
     const uint32_t n_int = pu_interactions_block(p, event);
     const uint64_t a = p.hoff[e], b = p.hoff[e + 1];
+    const uint64_t pool_end = __ldg(p.poff + p.n_pool);
     // the merged size, recomputed
     uint64_t part = 0;
     bool bad = false;
     for (uint32_t k = tid; k < n_int; k += PU_BLOCK) {
       const uint64_t q = pu_pool_event(p, k, event);
       const uint64_t q0 = __ldg(p.poff + q), q1 = __ldg(p.poff + q + 1);
-      bad |= q1 < q0 || q1 - q0 >= (1ull << 32);
+      bad |= !csr_ok(q0, q1, pool_end) || q1 - q0 >= (1ull << 32);
       part += q1 - q0;
     }
     const int any_bad = __syncthreads_or(bad);
     uint64_t pool_size;
     (void)pu_block_scan(part, s_wsum, &pool_size);
     const uint64_t m0 = p.moff[e], m1 = p.moff[e + 1];
-    if (any_bad || b < a) {
+    if (any_bad || !csr_ok(a, b, p.hoff[p.n_events])) {
       if (tid == 0) atomicOr(p.err, ERR_CSR);
       continue;
     }
-    if (m1 < m0 || m1 - m0 != (b - a) + pool_size) {  // other arguments than the first pass
+    if (!csr_ok(m0, m1, p.moff[p.n_events]) || m1 - m0 != (b - a) + pool_size) {  // other arguments than the first pass
       if (tid == 0) atomicOr(p.err, ERR_PILEUP);
       continue;
     }

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) postprocess_kernel(const __grid_constant_
     const uint64_t a = p.offsets[e], n = p.offsets[e + 1] - a;
     const uint32_t c0 = p.counts[4 * e], c1 = p.counts[4 * e + 1], c2 = p.counts[4 * e + 2],
                    c3 = p.counts[4 * e + 3];
-    if (p.offsets[e + 1] < a || c0 > n || c1 > n || c2 > n || c3 > n) {
+    if (!csr_ok(a, p.offsets[e + 1], p.offsets[p.n_events]) || c0 > n || c1 > n || c2 > n || c3 > n) {
       if (lane == 0) atomicOr(p.err, ERR_CSR);
       continue;
     }

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "pdr.h"
+#include "pdr_card.h"
 #include "pdr_hot.h"
 #include "pdr_internal.h"
 
@@ -206,199 +207,6 @@ struct pdr_ctx {
 
 namespace {
 
-// ------------------------------------------------------------ card expansion
-int expand_calo(const pdr_card* c, int calo, DevCalo& D, float* pool, int& pool_used,
-                std::vector<std::pair<int, int>>& phi_tables) {
-  const int nseg = c->nseg[calo];
-  if (nseg < 1 || nseg > PDR_MAXSEG) return fail(PDR_ECARD, "calorimeter needs 1..4 eta segments");
-  std::vector<double> p(1, 0.0);
-  std::vector<int> pn;
-  double lo = 0.0;
-  std::memset(&D, 0, sizeof D);
-  D.nseg = nseg;
-  for (int s = 0; s < nseg; ++s) {
-    const double hi = c->seg_eta_hi[calo][s];
-    const int n = c->seg_neta[calo][s];
-    const int nphi = c->seg_nphi[calo][s];
-    if (!(hi > lo) || n < 1 || nphi < 1 || nphi > PDR_MAXPHI)
-      return fail(PDR_ECARD, "bad calorimeter segment (eta_hi must increase, n_eta >= 1, 1 <= n_phi <= 1024)");
-    D.seg_lo[s] = (float)lo;
-    D.seg_hi[s] = (float)hi;
-    D.seg_scale[s] = (float)(n / (hi - lo));
-    D.seg_n[s] = n;
-    D.seg_first[s] = (int)pn.size();
-    for (int k = 1; k <= n; ++k) {
-      p.push_back(k == n ? hi : lo + ((hi - lo) * (double)k) / (double)n);
-      pn.push_back(nphi);
-    }
-    lo = hi;
-  }
-  const int m = (int)pn.size();
-  if (2 * m > PDR_MAXRING) return fail(PDR_ECARD, "too many eta rings (max 512)");
-  D.nring = 2 * m;
-  std::vector<double> edge(2 * m + 1);
-  for (int j = 0; j <= m; ++j) {
-    edge[m + j] = p[j];
-    edge[m - j] = -p[j];
-  }
-  edge[m] = 0.0;
-  std::vector<int> nphi(2 * m);
-  for (int r = 0; r < m; ++r) {
-    nphi[m + r] = pn[r];
-    nphi[m - 1 - r] = pn[r];
-  }
-  for (int j = 0; j <= 2 * m; ++j) D.edge[j] = (float)edge[j];
-  for (int j = 0; j < 2 * m; ++j)
-    if (!(D.edge[j] < D.edge[j + 1])) return fail(PDR_ECARD, "eta ring edges not increasing in float32");
-  int base = 0;
-  for (int r = 0; r < 2 * m; ++r) {
-    D.base[r] = base;
-    D.nphi[r] = nphi[r];
-    base += nphi[r];
-    // phi table shared by rings with the same number of bins
-    int off = -1;
-    for (auto& t : phi_tables)
-      if (t.first == nphi[r]) off = t.second;
-    if (off < 0) {
-      const int np = nphi[r];
-      if (pool_used + 2 * np + 1 > PDR_PHIPOOL) return fail(PDR_ECARD, "phi table pool exhausted");
-      off = pool_used;
-      for (int k = 0; k <= np; ++k) {
-        const double e = k == 0 ? -M_PI : (k == np ? M_PI : -M_PI + (2.0 * M_PI * (double)k) / (double)np);
-        pool[off + k] = (float)e;
-      }
-      for (int k = 0; k < np; ++k) {
-        const double e0 = k == 0 ? -M_PI : -M_PI + (2.0 * M_PI * (double)k) / (double)np;
-        const double e1 = k + 1 == np ? M_PI : -M_PI + (2.0 * M_PI * (double)(k + 1)) / (double)np;
-        pool[off + np + 1 + k] = (float)(0.5 * (e0 + e1));
-      }
-      pool_used += 2 * np + 1;
-      phi_tables.push_back({np, off});
-    }
-    D.phioff[r] = off;
-    D.phi_scale[r] = (float)(nphi[r] / (2.0 * M_PI));
-    const double ec = 0.5 * (edge[r] + edge[r + 1]);
-    D.eta_c[r] = (float)ec;
-    D.inv_cosh_c[r] = (float)(1.0 / std::cosh(ec));
-  }
-  D.ntowers = base;
-  // ring groups in ring order: negative-side segments outermost first, then
-  // positive-side segments innermost first
-  D.ngroup = 2 * nseg;
-  for (int s = 0; s < nseg; ++s) {
-    const int gn = nseg - 1 - s, gp = nseg + s;
-    D.grp_first[gn] = m - D.seg_first[s] - D.seg_n[s];
-    D.grp_first[gp] = m + D.seg_first[s];
-    D.grp_nphi[gn] = D.grp_nphi[gp] = c->seg_nphi[calo][s];
-    D.grp_base[gn] = D.base[D.grp_first[gn]];
-    D.grp_base[gp] = D.base[D.grp_first[gp]];
-  }
-  if (base >= (1 << 24)) return fail(PDR_ECARD, "too many towers (max 2^24 per calorimeter)");
-  return PDR_OK;
-}
-
-int lookup_res_bin(const pdr_card* c, int comp, float x) {
-  int k = -1;
-  for (int j = 0; j < c->res_n[comp]; ++j)
-    if ((float)c->res_edges[comp][j] <= x) k = j;
-  return k < 0 ? 0 : k;
-}
-
-unsigned long long eff_threshold(double eff) {
-  if (eff >= 1.0) return 4294967296ull;
-  if (!(eff > 0.0)) return 0ull;
-  return (unsigned long long)std::floor(eff * 4294967296.0);
-}
-
-bool increasing(const double* v, int n) {
-  for (int i = 0; i + 1 < n; ++i)
-    if (!((float)v[i] < (float)v[i + 1])) return false;
-  return true;
-}
-
-int expand_card(const pdr_card* c, DevCard& D) {
-  std::memset(&D, 0, sizeof D);
-  if (!(c->R > 0.0) || !(c->L > 0.0) || !std::isfinite(c->B)) return fail(PDR_ECARD, "need R > 0, L > 0, finite B");
-  int pool_used = 0;
-  std::vector<std::pair<int, int>> tables;
-  for (int calo = 0; calo < 2; ++calo) {
-    std::vector<std::pair<int, int>> t;  // phi tables are per calorimeter
-    int rc = expand_calo(c, calo, D.calo[calo], D.phi_pool, pool_used, t);
-    if (rc) return rc;
-  }
-  D.R = (float)c->R;
-  D.L = (float)c->L;
-  D.kB = (float)(0.299792458 * std::fabs(c->B));
-  D.Bsign = c->B > 0.0 ? 1 : -1;
-  D.has_field = c->B != 0.0;
-  for (int q = 1; q <= PDR_MAXQ; ++q) {
-    const double kq = 0.299792458 * std::fabs((double)q) * std::fabs(c->B);
-    const double cR = kq * c->R;
-    D.cR_hi[q] = (float)cR;
-    D.cR_lo[q] = (float)(cR - (double)D.cR_hi[q]);
-  }
-  // efficiencies
-  if (c->trk_npt < 1 || c->trk_npt > PDR_MAXEDGE || c->trk_neta < 1 || c->trk_neta > PDR_MAXEDGE ||
-      c->id_n < 1 || c->id_n > PDR_MAXEDGE)
-    return fail(PDR_ECARD, "efficiency tables need 1..8 edges per axis");
-  if (!increasing(c->trk_pt_edges, c->trk_npt) || !increasing(c->trk_eta_edges, c->trk_neta) ||
-      !increasing(c->id_edges, c->id_n))
-    return fail(PDR_ECARD, "efficiency table edges must increase");
-  D.trk_npt = c->trk_npt;
-  D.trk_neta = c->trk_neta;
-  for (int k = 0; k < PDR_MAXEDGE; ++k) {
-    D.trk_pt_edges[k] = D.trk_eta_edges[k] = D.id_edges[k] = INFINITY;
-    for (int comp = 0; comp < 4; ++comp) D.res_edges[comp][k] = INFINITY;
-  }
-  for (int k = 0; k < c->trk_npt; ++k) D.trk_pt_edges[k] = (float)c->trk_pt_edges[k];
-  for (int k = 0; k < c->trk_neta; ++k) D.trk_eta_edges[k] = (float)c->trk_eta_edges[k];
-  for (int t = 0; t < 3; ++t)
-    for (int i = 0; i < c->trk_npt; ++i)
-      for (int j = 0; j < c->trk_neta; ++j) {
-        const double e = c->trk_eff[t][i][j];
-        if (!(e >= 0.0 && e <= 1.0)) return fail(PDR_ECARD, "tracking efficiency outside [0, 1]");
-        D.trk_T[t][i][j] = eff_threshold(e);
-      }
-  D.id_n = c->id_n;
-  for (int k = 0; k < c->id_n; ++k) D.id_edges[k] = (float)c->id_edges[k];
-  for (int t = 0; t < 3; ++t)
-    for (int k = 0; k < c->id_n; ++k) {
-      const double e = c->id_eff[t][k];
-      if (!(e >= 0.0 && e <= 1.0)) return fail(PDR_ECARD, "identification efficiency outside [0, 1]");
-      D.id_T[t][k] = eff_threshold(e);
-    }
-  // resolutions
-  for (int comp = 0; comp < 4; ++comp) {
-    const int n = c->res_n[comp];
-    if (n < 1 || n > PDR_MAXEDGE || !increasing(c->res_edges[comp], n))
-      return fail(PDR_ECARD, "resolution tables need 1..8 increasing |eta| edges");
-    D.res_n[comp] = n;
-    for (int k = 0; k < n; ++k) {
-      D.res_edges[comp][k] = (float)c->res_edges[comp][k];
-      const double a = c->res_abcd[comp][k][0], b = c->res_abcd[comp][k][1];
-      const double cc = c->res_abcd[comp][k][2], d = c->res_abcd[comp][k][3];
-      if (!(a >= 0 && b >= 0 && cc >= 0 && d >= 0)) return fail(PDR_ECARD, "negative resolution coefficient");
-      D.res_a2[comp][k] = (float)(a * a);
-      D.res_b2[comp][k] = (float)(b * b);
-      D.res_c2[comp][k] = (float)(cc * cc);
-      D.res_d2[comp][k] = (float)(d * d);
-    }
-  }
-  for (int calo = 0; calo < 2; ++calo) {
-    DevCalo& C = D.calo[calo];
-    const int comp = calo == 0 ? RES_ECAL : RES_HCAL;
-    for (int r = 0; r < C.nring; ++r) C.resbin[r] = lookup_res_bin(c, comp, std::fabs(C.eta_c[r]));
-    D.e_min[calo] = (float)c->e_min[calo];
-    D.s_min[calo] = (float)c->s_min[calo];
-  }
-  D.cand_ptmin = (float)c->cand_ptmin;
-  D.dr2max = (float)(c->iso_dr * c->iso_dr);
-  D.dr2min = (float)(c->iso_drmin * c->iso_drmin);
-  D.iso_ptmin = (float)c->iso_ptmin;
-  D.imax = (float)c->iso_imax;
-  return PDR_OK;
-}
-
 // ------------------------------------------------------------ launch shapes
 struct Shape {
   uint32_t team, block, slots, nmax, grid;
@@ -451,7 +259,7 @@ bool optimistic_shape(pdr_ctx* ctx, uint32_t max_n, uint32_t hot_bytes, uint32_t
     return false;
   // per team; 16 bytes stay free for the kernel's static shared flag
   const uint64_t budget = (uint64_t)(ctx->smem_optin - hot_bytes - 16u) / nt;
-  const uint64_t fixed = sizeof(TeamTail) + (uint64_t)max_n * 8u;
+  const uint64_t fixed = tail_bytes(S.team) + (uint64_t)max_n * PDR_PART_BYTES;
   if (budget <= fixed) return false;
   const uint64_t slots = std::min<uint64_t>(((budget - fixed) / 24u) & ~31ull, 65536u);
   if (slots < 64 || slots < max_n / 2) return false;

@@ -224,3 +224,47 @@ def test_ee_rotation_invariance():
     assert len(j0) == len(j1)
     assert np.allclose(np.sort(j0["e"]), np.sort(j1["e"]), rtol=1e-10)
     assert sorted(j0["nconst"]) == sorted(j1["nconst"])
+
+
+def test_forced_runner_up_at_a_tie():
+    """The parity protocol's forced branch.  Two soft particles at equal
+    distance 0.35 on either side of a hard one, with R = 0.5 anti-kT, and a
+    third soft particle 0.65 from the hard one: the first step is a tie
+    between merging the left and the right soft particle (d = pT_hard^-2
+    0.35^2 / R^2 for both).  Unforced, the lower index wins; forced, the other
+    pair is merged first.  Both runs end in the same jets (the cone around
+    the hard particle takes both soft particles; the third stays a jet of its
+    own), while a step that is not a tie cannot be forced.  Without forced
+    steps the result equals the plain call."""
+    fm = _fm([100.0, 2.0, 2.0, 1.0], [0.0, -0.35, 0.35, 0.65], [0.0, 0.0, 0.0, 0.0])
+    plain, m0 = oracle.cluster(*fm, p=-1.0, R=0.5)
+    j0, steps = oracle.cluster_forced(*fm, p=-1.0, R=0.5)
+    assert np.array_equal(plain, j0) and m0 == len(steps) >= 1 and steps[0] == 0
+    j1, steps1 = oracle.cluster_forced(*fm, p=-1.0, R=0.5, flips=[0])
+    assert len(j1) == len(j0) == 2 and list(j0["nconst"]) == [3, 1] == list(j1["nconst"])
+    for k in ("px", "py", "pz", "e"):
+        assert j1[0][k] == pytest.approx(j0[0][k], rel=1e-12, abs=1e-12)
+    with pytest.raises(ValueError):
+        oracle.cluster_forced(*fm, p=-1.0, R=0.5, flips=[len(fm[0]) - 1 + 5])  # beyond the last step
+    # a clear (non-marginal) step refuses to be forced
+    clear = _fm([100.0, 2.0, 2.0], [0.0, 0.1, 0.4], [0.0, 0.0, 0.0])
+    _, st = oracle.cluster_forced(*clear, p=-1.0, R=0.5)
+    assert 0 not in st
+    with pytest.raises(ValueError):
+        oracle.cluster_forced(*clear, p=-1.0, R=0.5, flips=[0])
+
+
+def test_forced_runner_up_changes_a_split():
+    """Where the tie decides the result: three equal-pT particles on a line at
+    spacing 0.4 with Cambridge/Aachen R = 0.5.  The first step merges the left
+    pair (lower indices win the tie); the merged axis then lies 0.6 from the
+    third, so two jets: (left pair) + right.  Forcing the runner-up merges the
+    right pair first: (right pair) + left.  The jets' constituent counts are
+    both (2, 1) but the 2-constituent jet sits on the other side, mirrored."""
+    fm = _fm([5.0, 5.0, 5.0], [-0.4, 0.0, 0.4], [0.0, 0.0, 0.0])
+    j0, steps = oracle.cluster_forced(*fm, p=0.0, R=0.5)
+    assert 0 in steps
+    j1, _ = oracle.cluster_forced(*fm, p=0.0, R=0.5, flips=[0])
+    two0 = j0[j0["nconst"] == 2][0]
+    two1 = j1[j1["nconst"] == 2][0]
+    assert two0["eta"] < -0.19 and two1["eta"] == pytest.approx(-two0["eta"], rel=1e-12)

@@ -156,3 +156,39 @@ def test_merging_does_not_depend_on_batching():
     a, b = int(whole["offsets"][3]), int(whole["offsets"][8])
     for key in ("pt", "eta", "pdg", "vz", "vt"):
         assert np.array_equal(part[key], whole[key][a:b])
+
+
+def test_forced_truncation_decision():
+    """The parity protocol's forced branch of a truncation decision: with the
+    bound set to exactly |v| of interaction 0's first vertex-z draw, that
+    decision (|v| <= bound, taken in float32) is marginal and accepts; forced
+    the other way, the draw is rejected and the vertex z is the next accepted
+    attempt's value (attempt words recomputed from Philox here).  A decision
+    that is not marginal, or one that never occurs, refuses to be forced."""
+    sigma = 0.053
+    T = oracle.poisson_thresholds(30.0)
+    ev = 0
+    for ev in range(50):  # an event with at least one interaction
+        if oracle.pileup_draws(_pu(30.0), T, 100, SEED, ev)[0] > 0:
+            break
+    w0 = _words(0, ev, 6, 0)
+    v0 = sigma * oracle.normal(int(w0[1]), int(w0[2]))
+    bound = abs(v0)
+    pu = _pu(30.0, smear=False, sigma_z=sigma, max_z=bound)
+    marg = []
+    k, _, z, _, _, _, m = oracle.pileup_draws(pu, T, 100, SEED, ev, marginal_out=marg)
+    assert k > 0 and z[0] == v0 and (6, 0, 0) in marg
+    _, _, zf, _, _, _, _ = oracle.pileup_draws(pu, T, 100, SEED, ev, flips=[(6, 0, 0)])
+    nxt = None
+    for a in range(1, 1000):
+        w = _words(0, ev, 6, a)
+        v = sigma * oracle.normal(int(w[1]), int(w[2]))
+        if abs(np.float32(v)) <= np.float32(bound):
+            nxt = v
+            break
+    assert zf[0] == nxt and zf[0] != z[0]
+    assert np.array_equal(zf[1:], z[1:])  # other interactions untouched
+    with pytest.raises(ValueError):
+        oracle.pileup_draws(pu, T, 100, SEED, ev, flips=[(6, 1, 0)])       # interaction 1's first z: not marginal
+    with pytest.raises(ValueError):
+        oracle.pileup_draws(pu, T, 100, SEED, ev, flips=[(6, 0, 999999)])  # never drawn

@@ -208,6 +208,39 @@ def test_malformed_csr_sets_device_error(B, ctx, cards, synth):
     ctx.check()  # the error word was cleared
 
 
+@pytest.mark.parametrize("sized", [True, False])
+def test_offset_past_the_end_is_rejected(B, ctx, cards, synth, sized):
+    """An interior offset past offsets[n_events] gives an earlier event a range
+    beyond the batch (each event alone still has b >= a).  The kernel must flag
+    it (PDR_EDEVICE, CSR) and touch neither inputs nor outputs outside the
+    batch.  The arrays hold a fifth event beyond the four-event batch, so even
+    the bad range stays inside memory the test owns; that tail must come back
+    unwritten."""
+    cid, _ = cards["cms_like"]
+    b5 = synth.make("tiny", n_events=5)
+    dev = B.batch_to_device(b5)
+    end4 = int(b5.offsets[4])
+    spare = b5.n_particles - end4
+    assert spare > 10
+    off = dev["offsets"][:5].clone()
+    off[1] = end4 + spare // 2          # past the end of the 4-event batch
+    dev["offsets"] = off
+    dev["n_events"] = 4
+    o = B.alloc_outputs(5, b5.n_particles)
+    sentinel = -12345.0
+    for k in ("tracks", "towers", "eflow", "cands", "iso"):
+        o[k].fill_(sentinel)
+    ctx.run(B.make_batch(dev, cid, 0, max_event_size=b5.n_particles if sized else 0), B.make_outputs(o))
+    with pytest.raises(B.PdrError) as ei:
+        ctx.check()
+    assert ei.value.code == -5 and "CSR" in str(ei.value)
+    ctx.check()
+    counts = o["counts"].cpu().numpy()
+    assert (counts[:2] == 0).all()      # events 0 and 1 are the malformed ones
+    for k in ("tracks", "towers", "eflow", "cands", "iso"):
+        assert bool((o[k][end4:] == sentinel).all()), f"{k} written beyond the batch"
+
+
 def test_bad_card_is_rejected(B, ctx):
     c = B.card_from_json("cms_like")
     c.trk_eff[0][1][0] = 1.5
@@ -386,8 +419,8 @@ def test_tickets_submit_wait_fetch_release(B, ctx, cards, synth):
 
 
 # ------------------------------------------------------------ full-size runs
-def _full(B, ctx, cards, synth, name, seed, sample, count_check=False):
-    cid, ocard = cards[synth.card_for(name)]
+def _full(B, ctx, cards, synth, name, seed, sample, count_check=False, card=None):
+    cid, ocard = cards[card or synth.card_for(name)]
     b = synth.make(name)
     dev = B.batch_to_device(b)
     o = B.alloc_outputs(b.n_events, b.n_particles, debug=False)
@@ -426,19 +459,31 @@ def _full(B, ctx, cards, synth, name, seed, sample, count_check=False):
 
     for e in picks:
         P.compare_event(ocard, b.event(e), P.gpu_event(event_host(e), b, e), seed, int(e), stats)
+    n_diff = 0
     if count_check:
         oc = oracle.run_batch(ocard, b, seed)
         diff = np.flatnonzero(np.any(oc != counts, axis=1))
-        # events whose counts differ must be explained by marginal decisions
-        assert len(diff) <= max(5, b.n_events // 1000), f"{len(diff)} events with different counts"
-        for e in diff[:50]:
+        n_diff = len(diff)
+        # every event whose counts differ must be explained by marginal decisions
+        for e in diff:
             P.compare_event(ocard, b.event(e), P.gpu_event(event_host(e), b, e), seed, int(e), stats)
-    print(name, best.as_dict(), stats)
+    print(f"{name} ({card or synth.card_for(name)}) {best.as_dict()}: {stats.events} events compared in full, "
+          f"{stats.particles} particles; marginal decisions {stats.marginal} "
+          f"({stats.marginal / max(stats.particles, 1):.2e} per particle), flipped {stats.flips} "
+          f"({stats.flips / max(stats.particles, 1):.2e} per particle); "
+          f"{n_diff} of {b.n_events} events with counts differing from the oracle's unflipped run "
+          f"(each explained); max rel {stats.max_rel}")
     return stats
 
 
 def test_full_size_batched(B, ctx, cards, synth):
     _full(B, ctx, cards, synth, "batched", seed=1, sample=100, count_check=True)
+
+
+def test_full_size_batched_atlas_card(B, ctx, cards, synth):
+    """The batched workload through the ATLAS-like card (B = 2 T, R = 1.5 m),
+    the third card of the serving mix, at full size."""
+    _full(B, ctx, cards, synth, "batched", seed=4, sample=100, count_check=True, card="atlas_like")
 
 
 def test_full_size_ee(B, ctx, cards, synth):
