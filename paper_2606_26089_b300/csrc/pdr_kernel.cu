@@ -578,7 +578,13 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     if (s_table_full) return false;   // every thread reads it after the barrier
   }
 
-  // ---- 1b: smearing jobs (S2, S3, S4) in particle order
+  // ---- 1b: smearing jobs (S2, S3, S4) in particle order.  The last chunk's
+  // tracks stay in registers (lt_*) and add to the cones once every candidate
+  // is staged, after the barrier below; earlier chunks' tracks (events with
+  // more jobs than the team has threads) do so in 2, from their records.
+  uint32_t trk_reg0 = 0;   // first track of the last chunk
+  float4 lt_obj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  bool lt_has = false;
   for (uint32_t j0 = 0; j0 < n_job; j0 += TEAM) {
     const uint32_t j = j0 + (uint32_t)tc.tid;
     JobOut r;
@@ -599,11 +605,16 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(r.tracked, r.cand, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
+    trk_reg0 = n_trk;
+    lt_has = false;
     if (r.tracked || r.cand) {
       const float eta = __ldg(S.eta + a + i), phi = __ldg(S.phi + a + i);
-      if (r.tracked)
+      if (r.tracked) {
         reinterpret_cast<float4*>(S.tracks)[a + n_trk + (pre & 0xFFFFu)] =
             make_float4(r.ptp, eta, phi, __uint_as_float(i));
+        lt_has = r.ptp > K.iso_ptmin;
+        lt_obj = make_float4(eta, phi, r.ptp, __uint_as_float(i | PDR_ISO_TRACK));
+      }
       if (r.cand) {
         const uint32_t jc = n_cand + (pre >> 16);
         const uint32_t pi = T.pinfo()[i];
@@ -628,10 +639,12 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     n_cand += tot >> 16;
   }
   tc.sync();
-  // ---- 2: towers (S6, S7), each by its lowest-index depositing particle;
-  // EFlow neutrals and tracks add their pT to the staged candidates' cones (S8)
-  uint32_t n_twr = 0, n_ef = 0;
   const uint32_t gn0 = min(n_cand, (uint32_t)PDR_CMAX);
+  if (lt_has && gn0 > 0) iso_object(K, lt_obj, tt);
+  // ---- 2: towers (S6, S7), each by its lowest-index depositing particle;
+  // EFlow neutrals and the earlier chunks' tracks add their pT to the staged
+  // candidates' cones (S8)
+  uint32_t n_twr = 0, n_ef = 0;
   for (uint32_t c0 = 0; c0 < n; c0 += TEAM) {
     const uint32_t i = c0 + (uint32_t)tc.tid;
     TowerOut to;
@@ -648,13 +661,14 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
           if (to.ef && gn0 > 0 && to.det > K.iso_ptmin) {
             const int calo = (int)(key >> 24), ring = (int)(pi >> 16);
             const float oe = ring_rec(K, KD, calo, ring).x;
-            iso_object(K, make_float4(oe, tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring), to.det,
-                                      __uint_as_float(key)), tt);
+            if (tt.binmask[iso_bin(K, oe)] != 0u)  // else no staged candidate is near in eta
+              iso_object(K, make_float4(oe, tower_phi_c(K, KD, calo, key & 0xFFFFFFu, ring), to.det,
+                                        __uint_as_float(key)), tt);
           }
         }
       }
     }
-    if (gn0 > 0 && i < n_trk) {
+    if (gn0 > 0 && i < trk_reg0) {
       const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + i];
       if (t.x > K.iso_ptmin)
         iso_object(K, make_float4(t.y, t.z, t.x, __uint_as_float(__float_as_uint(t.w) | PDR_ISO_TRACK)), tt);
