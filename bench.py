@@ -135,10 +135,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh"),
+KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh", "pdr_ip.cuh"),
                   "pu_fill_kernel": ("pdr_pileup.cu", "pdr_math.cuh"),
                   "postprocess_kernel": ("pdr_postprocess.cu", "pdr_math.cuh"),
-                  "track_ip_kernel": ("pdr_ip.cu", "pdr_math.cuh")}
+                  "track_ip_kernel": ("pdr_ip.cu", "pdr_math.cuh", "pdr_ip.cuh")}
 
 
 def kernel_fingerprint(kernel: str = "fused_kernel") -> str:
@@ -312,7 +312,8 @@ def bench_ours(args, dist, rank, ws):
     }
     # the steps around the response, each timed in its own region (one GPU)
     if not args.no_track_ip and ws == 1:
-        line["track_ip"] = bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts)
+        line["track_ip"] = bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts, launch=best,
+                                          response_ms=avg_launch_s * 1e3)
     if not args.no_jets and ws == 1:
         line["jets"] = bench_jets(args, B, ctx, bt, ob, n_ev, n_p, counts)
     if not args.no_postprocess and ws == 1:
@@ -323,13 +324,19 @@ def bench_ours(args, dist, rank, ws):
         line["pileup_merge"] = bench_pileup_merge(args, B, ctx)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, card_name, args.seed, args.cpu_seconds)
+        line["cpu_baseline"]["parity_sample"] = parity_sample(ctx, cid, batch, card_name, args.seed, base)
     ctx.close()
     return line
 
 
 def bench_serving(args, B, ctx):
     """Continuous-batching serving loop vs one plain launch per request, on the
-    same Poisson arrival schedules; latency = submit -> results on the device."""
+    same Poisson arrival schedules (at most --serving-max-requests a rate, so
+    the highest rates saturate both forms).  Latency to device: submit ->
+    results in device memory (the library's clock); to host: submit -> the
+    request's counts and records (slot layout) copied back to pinned host
+    memory, on a stream of the caller's."""
+    import ctypes
     import threading as th
 
     import torch
@@ -343,6 +350,12 @@ def bench_serving(args, B, ctx):
         pinned[g] = {k: (None if getattr(pb, k) is None else
                          torch.from_numpy(np.ascontiguousarray(getattr(pb, k))).pin_memory())
                      for k in ("pt", "eta", "phi", "mass", "pdg", "charge", "vz")}
+    cudart = ctypes.CDLL("libcudart.so.13")
+    cudart.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                       ctypes.c_void_p]
+    d2h_stream = torch.cuda.Stream()
+    REC = (("counts", 16, True), ("tracks", 16, False), ("towers", 12, False), ("eflow", 12, False),
+           ("cands", 16, False), ("iso", 8, False))
 
     def host_batch(r):
         pb = pools[r.generator]
@@ -358,19 +371,37 @@ def bench_serving(args, B, ctx):
         hb.max_event_size = int(np.diff(off).max()) if r.n_events else 0
         return hb, o, a0, int(off[-1])
 
+    def d2h(ptrs, n_ev, n_p, host):
+        """Counts and every record array of one request (device pointers) into `host`."""
+        off = 0
+        for (name, size, per_event), p in zip(REC, ptrs):
+            nb = size * (n_ev if per_event else n_p)
+            if nb:
+                rc = cudart.cudaMemcpyAsync(host.data_ptr() + off, p, nb, 2, d2h_stream.cuda_stream)
+                if rc:
+                    raise RuntimeError(f"cudaMemcpyAsync failed ({rc})")
+            off += nb
+        d2h_stream.synchronize()
+
     out = {"workload": "Poisson arrivals; requests of log-uniform(1, 5000) events from the batched, "
                        "e+e- and pile-up generators, card uniform among CMS-like, ATLAS-like, e+e-",
-           "duration_s": args.serving_seconds, "rates": {}}
+           "duration_s": args.serving_seconds, "max_requests_per_rate": args.serving_max_requests, "rates": {}}
     for rate in args.serving_rates:
-        sched = synth.serving_schedule(rate, args.serving_seconds, args.serving_pool)
+        sched = synth.serving_schedule(rate, args.serving_seconds, args.serving_pool)[:args.serving_max_requests]
+        if not sched:
+            continue
         reqs = [host_batch(r) for r in sched]
         parts = sum(x[3] for x in reqs)
-        # ---- served: submit at arrival times, a helper thread releases finished tickets
+        max_b = max(16 * r.n_events + 64 * x[3] for r, x in zip(sched, reqs))
+        host = torch.empty(max_b, dtype=torch.uint8).pin_memory()
+        # ---- served: submit at arrival times; a helper thread waits for each
+        # ticket, copies its results to the host and releases it
         ctx.serve_start()
-        tickets = []
+        tickets, t_sub = [], []
+        lat_host = []
         done = th.Event()
-
         failed = []
+        t_last = [0.0]
 
         def releaser():
             # a failed request is released too (its pool memory would otherwise
@@ -381,20 +412,28 @@ def bench_serving(args, B, ctx):
                     rc = ctx.wait(tickets[i], 120_000)
                     if rc != 0:
                         failed.append((i, rc))
+                    else:
+                        r = ctx.fetch(tickets[i])
+                        d2h([r.counts, r.tracks, r.towers, r.eflow, r.cands, r.iso], r.n_events, r.n_particles,
+                            host)
+                        now = time.perf_counter()
+                        lat_host.append((now - t_sub[i]) * 1e3)
+                        t_last[0] = now
                     try:
                         ctx.release(tickets[i])
                     except B.PdrError:
                         failed.append((i, "release"))
                     i += 1
                 else:
-                    time.sleep(0.0005)
+                    time.sleep(0.0002)
 
         rt = th.Thread(target=releaser)
         rt.start()
         t0 = time.perf_counter()
         for r, (hb, o, a0, np_) in zip(sched, reqs):
             while time.perf_counter() - t0 < r.t_arrival:
-                time.sleep(0.0002)
+                time.sleep(0.0001)
+            t_sub.append(time.perf_counter())
             tickets.append(ctx.serve_submit(hb))
         done.set()
         rt.join()
@@ -402,14 +441,15 @@ def bench_serving(args, B, ctx):
         ctx.serve_stop()
         if failed:
             raise RuntimeError(f"{len(failed)} serving requests failed (first: {failed[0]})")
-        # ---- baseline: one request at a time, one plain launch each (H2D, run, sync)
-        lat = []
+        served_span = t_last[0] - (t0 + sched[0].t_arrival)
+        # ---- baseline: one request at a time, one plain launch each (H2D, run,
+        # sync), then the same copies back
+        lat_dev, lat_h = [], []
         t0 = time.perf_counter()
         s = torch.cuda.current_stream()
         for r, (hb, o, a0, np_) in zip(sched, reqs):
             while time.perf_counter() - t0 < r.t_arrival:
-                time.sleep(0.0002)
-            pb = pools[r.generator]
+                time.sleep(0.0001)
             dev = {"offsets": o.to("cuda", non_blocking=True)}
             for k, t in pinned[r.generator].items():
                 dev[k] = None if t is None else t[a0:a0 + np_].to("cuda", non_blocking=True)
@@ -417,16 +457,28 @@ def bench_serving(args, B, ctx):
             outb = B.alloc_outputs(r.n_events, np_)
             ctx.run(B.make_batch(dev, cards[r.card], r.seed), B.make_outputs(outb))
             s.synchronize()
-            lat.append((time.perf_counter() - t0 - r.t_arrival) * 1e3)
-        span = time.perf_counter() - t0 - sched[0].t_arrival if sched else 1.0
-        lat = np.array(lat) if lat else np.zeros(1)
+            lat_dev.append((time.perf_counter() - t0 - r.t_arrival) * 1e3)
+            d2h([outb[k].data_ptr() for k, _, _ in REC], r.n_events, np_, host)
+            lat_h.append((time.perf_counter() - t0 - r.t_arrival) * 1e3)
+        span = time.perf_counter() - t0 - sched[0].t_arrival
+        lat_dev = np.array(lat_dev)
+        lat_h = np.array(lat_h)
+        lh = np.array(lat_host) if lat_host else np.zeros(1)
+        served_ps = parts / served_span if served_span > 0 else None
+        per_req_ps = parts / span if span > 0 else None
         out["rates"][str(rate)] = {
-            "requests": len(sched), "particles": parts,
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "particles_per_s": st["particles_done"] / st["span_s"] if st["span_s"] > 0 else None,
-            "waves": st["waves"], "admission_waits": st["admission_waits"],
-            "per_request_p50_ms": float(np.percentile(lat, 50)), "per_request_p99_ms": float(np.percentile(lat, 99)),
-            "per_request_particles_per_s": parts / span if span > 0 else None}
+            "requests": len(sched), "particles": parts, "offered_s": sched[-1].t_arrival,
+            "waves": st["waves"], "requests_per_wave": len(sched) / max(st["waves"], 1),
+            "admission_waits": st["admission_waits"],
+            "served": {"p50_ms_device": st["p50_ms"], "p99_ms_device": st["p99_ms"],
+                       "p50_ms_host": float(np.percentile(lh, 50)), "p99_ms_host": float(np.percentile(lh, 99)),
+                       "particles_per_s_device": st["particles_done"] / st["span_s"] if st["span_s"] > 0 else None,
+                       "particles_per_s_host": served_ps},
+            "per_request": {"p50_ms_device": float(np.percentile(lat_dev, 50)),
+                            "p99_ms_device": float(np.percentile(lat_dev, 99)),
+                            "p50_ms_host": float(np.percentile(lat_h, 50)), "p99_ms_host": float(np.percentile(lat_h, 99)),
+                            "particles_per_s_host": per_req_ps},
+            "served_over_per_request_throughput": (served_ps / per_req_ps) if served_ps and per_req_ps else None}
     return out
 
 
@@ -461,7 +513,7 @@ def bench_jets(args, B, ctx, bt, ob, n_ev, n_p, counts):
             "reps": reps}
 
 
-def bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts):
+def bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts, launch=None, response_ms=None):
     """Track impact parameters (d0, z0 and their errors) of every track of the
     response's outputs, vertices on the axis (the workload has none off it)."""
     import torch
@@ -490,11 +542,27 @@ def bench_track_ip(args, B, ctx, bt, ob, n_ev, n_p, counts):
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     achieved = alg / sec / 1e9
+    # the fused form: the response writes each track's record beside the track
+    # (pdr_run_ip); its cost is its launch time minus the plain response's
+    for _ in range(3):
+        ctx.run_ip(bt, ob, prm, ip, launch=launch)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.run_ip(bt, ob, prm, ip, launch=launch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    fused = e0.elapsed_time(e1) / reps
+    fused_out = {"ms_response_with_ip": fused, "ms_response": response_ms,
+                 "ms_added": (fused - response_ms) if response_ms is not None else None,
+                 "algorithmic_bytes_added": int(16 * nt),
+                 "note": "the generated particles are read once, by the response"}
     return {"tracks": nt, "ms": sec * 1e3, "tracks_per_s": nt / sec,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": _traffic_from_profile("batched", "track_ip_kernel"),
                          "algorithmic_bytes_per_launch": int(alg), "kernel": "pdr::track_ip_kernel"},
-            "reps": reps}
+            "fused": fused_out, "reps": reps}
 
 
 def bench_postprocess(args, B, ctx, bt, ob, out, n_ev, counts):
@@ -669,6 +737,26 @@ def cpu_baseline(batch, card_name, seed, target_s):
                       f"{dt:.1f} s on {cores} threads"}
 
 
+def parity_sample(ctx, cid, batch, card_name, seed, event_base, n_events=200):
+    """Marginal decisions of the parity protocol on a sample of the workload:
+    the first n_events run again with debug records and compared with the
+    oracle event by event (decisions within the oracle's band of their
+    threshold are marginal; a flip is one the GPU took the other way)."""
+    import oracle
+    from tests import parity as P
+
+    sub = batch.slice_events(0, min(n_events, batch.n_events))
+    card = oracle.load_card(card_name)
+    host = P.run_gpu(ctx, cid, sub, seed, event_base=event_base, debug=True)
+    st = P.Stats()
+    for e in range(sub.n_events):
+        P.compare_event(card, sub.event(e), P.gpu_event(host, sub, e), seed, event_base + e, st)
+    return {"events": st.events, "particles": st.particles, "marginal": st.marginal, "flips": st.flips,
+            "marginal_per_particle": st.marginal / max(st.particles, 1),
+            "flips_per_particle": st.flips / max(st.particles, 1),
+            "max_rel": st.max_rel, "band": P.G_BAND}
+
+
 def bench_reference(args, rank):
     """The reference arm: the FP64 oracle on the host cores, bounded samples."""
     from paper_2606_26089_b300 import synth
@@ -725,7 +813,8 @@ def main(argv=None):
                     help="fixed launch shape 'team,block[,table_slots]' (skips autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-rates", type=float, nargs="+", default=[50, 100, 200, 500])
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[50, 100, 200, 500, 1000, 2000, 5000])
+    ap.add_argument("--serving-max-requests", type=int, default=300)
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-pool", type=int, default=5000)
     ap.add_argument("--no-per-event", action="store_true")

@@ -447,6 +447,17 @@ typedef struct { float d0, z0, sigma_d0, sigma_z0; } pdr_ip;   /* m */
 int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_ip_params* params,
                  pdr_ip* ip, void* stream);
 
+/* pdr_run with the tracks' impact parameters computed in the same fused
+ * launch: each accepted track's pdr_ip record is written beside its track
+ * record, from the generated particle the smearing job already holds (ip:
+ * DEVICE, slot layout parallel to out->tracks, like pdr_track_ip).  The
+ * results are those of pdr_run followed by pdr_track_ip, bit for bit, without
+ * a second pass over the generated particles.  Same launch shapes, errors
+ * and asynchrony as pdr_run, plus PDR_EINVAL for a null ip or negative
+ * resolutions. */
+int pdr_run_ip(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_ip_params* params,
+               pdr_ip* ip, const pdr_launch* launch, void* stream);
+
 /* ---------------------------------------------------------- jet clustering -- */
 /* Sec. 2.4: jets from the PFlow (or truth) collection with the generalized-kT
  * family (anti-kT p = -1 by default, Cambridge/Aachen p = 0, kT p = 1, any

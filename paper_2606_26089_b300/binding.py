@@ -239,6 +239,8 @@ def lib():
             "pdr_pileup_merge": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_pileup), P, C.POINTER(pdr_particles), P], I),
             "pdr_postprocess": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_filter), P, P], I),
             "pdr_track_ip": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_ip_params), P, P], I),
+            "pdr_run_ip": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_ip_params), P,
+                            C.POINTER(pdr_launch), P], I),
             "pdr_cluster_jets": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_jet_params), P, P,
                                   P], I),
         }
@@ -502,6 +504,14 @@ class Context:
         float32 tensor [n_particles, 4], slot layout parallel to the tracks)."""
         self._check(self.L.pdr_track_ip(self.h, C.byref(batch), C.byref(out), C.byref(params), _ptr(ip),
                                         self._stream(stream)), "pdr_track_ip")
+
+    def run_ip(self, batch: pdr_batch, out: pdr_outputs, params: pdr_ip_params, ip,
+               launch: Optional[pdr_launch] = None, stream=None):
+        """pdr_run with the tracks' impact parameters computed in the same
+        launch, into `ip` (device float32 [n_particles, 4], parallel to the tracks)."""
+        self._check(self.L.pdr_run_ip(self.h, C.byref(batch), C.byref(out), C.byref(params), _ptr(ip),
+                                      C.byref(launch) if launch is not None else None, self._stream(stream)),
+                    "pdr_run_ip")
 
     # ---- jet clustering
     def cluster_jets(self, batch: pdr_batch, out: Optional[pdr_outputs], params: pdr_jet_params, jets, jet_counts,

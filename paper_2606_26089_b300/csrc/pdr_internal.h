@@ -128,6 +128,13 @@ struct alignas(16) HotCard {
 #define PDR_LAUNCH_SEGS 32   // batches in one fused launch
 #define PDR_LAUNCH_CARDS 4   // distinct cards in one fused launch
 
+// Field and resolutions of the impact-parameter smearing.
+struct IPConst {
+  float kB;                          // 0.299792458 |B|
+  int32_t bsign, has_field;
+  float a_d0, b_d0, a_z0, b_z0;      // sigma = sqrt(a^2 + (b / pT)^2)
+};
+
 // One batch of a launch: its inputs, outputs, randomness and card.
 struct KSeg {
   uint64_t event_start;              // first launch-wide event index of the batch
@@ -145,6 +152,10 @@ struct KSeg {
   pdr_iso* iso;
   uint32_t* counts;
   pdr_debug* debug;                  // null: no debug records
+  // impact parameters of the tracks (kernels built for them only)
+  pdr_ip* ip;
+  const float *vx, *vy;              // transverse production vertex, or null (0)
+  IPConst ipc;
 };
 
 // Philox4x32-10 round keys of a 64-bit seed: round r uses key (lo + r W0,
@@ -229,10 +240,8 @@ struct IPParams {
   const uint32_t* counts;
   pdr_ip* ip;
   uint32_t* err;
-  float kB;                          // 0.299792458 |B|
-  int32_t bsign, has_field;
+  IPConst c;
   uint32_t event_base;
-  float a_d0, b_d0, a_z0, b_z0;
   uint32_t rk[20];                   // Philox round keys of the batch's seed
 };
 

@@ -33,6 +33,7 @@
 #include <mutex>
 
 #include "pdr_internal.h"
+#include "pdr_ip.cuh"
 #include "pdr_math.cuh"
 
 namespace pdr {
@@ -538,7 +539,7 @@ __device__ __forceinline__ void iso_object(const HotCard& K, float4 obj, TeamTai
 // particle phase, having written nothing but debug records, so that the
 // caller redoes the event with a larger table.  (Otherwise a full table, which
 // sizing by particle count rules out, reports an error.)
-template <int TEAM, bool OVF>
+template <int TEAM, bool OVF, bool IP>
 __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
                                               const Tbl& T, TeamTail& tt, const TeamCtx<TEAM>& tc, uint64_t e,
                                               uint64_t a, uint32_t n) {
@@ -612,6 +613,13 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       if (r.tracked) {
         reinterpret_cast<float4*>(S.tracks)[a + n_trk + (pre & 0xFFFFu)] =
             make_float4(r.ptp, eta, phi, __uint_as_float(i));
+        if constexpr (IP) {  // the track's impact parameters, parallel to its record
+          const uint64_t g = a + i;
+          const float x0 = S.vx ? __ldg(S.vx + g) : 0.0f, y0 = S.vy ? __ldg(S.vy + g) : 0.0f;
+          const float zv = S.vz ? __ldg(S.vz + g) : 0.0f;
+          S.ip[a + n_trk + (pre & 0xFFFFu)] =
+              track_ip_of(__ldg(S.pt + g), eta, phi, (int)__ldg(S.charge + g), x0, y0, zv, i, event, S.rk, S.ipc);
+        }
         lt_has = r.ptp > K.iso_ptmin;
         lt_obj = make_float4(eta, phi, r.ptp, __uint_as_float(i | PDR_ISO_TRACK));
       }
@@ -760,17 +768,17 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
 // The event on a global-memory table (events beyond the shared table, or
 // the redo of an overflow): rare, so kept out of line, which keeps the
 // kernel's hot code small for the instruction cache.
-template <int TEAM>
+template <int TEAM, bool IP>
 __device__ __noinline__ void process_event_global(const KSeg& S, uint32_t* err, const HotCard& K, const float* KD,
                                                   const Tbl& T, TeamTail& tt, const TeamCtx<TEAM>& tc, uint64_t e,
                                                   uint64_t a, uint32_t n) {
-  process_event<TEAM, false>(S, err, K, KD, T, tt, tc, e, a, n);
+  process_event<TEAM, false, IP>(S, err, K, KD, T, tt, tc, e, a, n);
 }
 
 // The persistent event loop of one team.  ONE: the launch holds a single
 // batch, whose fields the compiler then reads straight from the parameter
 // block (no per-event segment lookup).
-template <int TEAM, int BLOCK, bool ONE, bool OVF>
+template <int TEAM, int BLOCK, bool ONE, bool OVF, bool IP>
 __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem, const TeamCtx<TEAM>& tc,
                                            const Tbl& st, TeamTail& tt) {
   constexpr int NT = BLOCK / TEAM;
@@ -810,10 +818,10 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
     }
     if (n <= p.nmax_smem) {
       if constexpr (!OVF) {
-        process_event<TEAM, false>(S, p.err, K, KD, st, tt, tc, e, a, n);
+        process_event<TEAM, false, IP>(S, p.err, K, KD, st, tt, tc, e, a, n);
         continue;
       } else {
-        if (process_event<TEAM, true>(S, p.err, K, KD, st, tt, tc, e, a, n)) continue;
+        if (process_event<TEAM, true, IP>(S, p.err, K, KD, st, tt, tc, e, a, n)) continue;
         // the shared table (sized below the particle count) filled up: reset
         // the flag, empty the table and redo the event with the global table
         tc.sync();
@@ -826,7 +834,7 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
       const Tbl gt = carve(p.gscratch + gteam * p.g_team_bytes, p.g_slots, p.g_nmax);
       for (uint32_t s = tc.tid; s < p.g_slots; s += TEAM) gt.keys()[s] = PDR_EMPTY;
       tc.sync();
-      process_event_global<TEAM>(S, p.err, K, KD, gt, tt, tc, e, a, n);
+      process_event_global<TEAM, IP>(S, p.err, K, KD, gt, tt, tc, e, a, n);
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);
@@ -853,7 +861,8 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
 // Register cap: at most 64 registers a thread (1024 / BLOCK resident CTAs).
 // The launch covers up to PDR_LAUNCH_SEGS batches (each with its own card,
 // inputs, outputs and seed) as one launch-wide sequence of events.
-template <int TEAM, int BLOCK, bool OVF>
+// IP: also the impact parameters of every accepted track (pdr_run_ip).
+template <int TEAM, int BLOCK, bool OVF, bool IP>
 __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1)
     fused_kernel(const __grid_constant__ KParams p) {
   static_assert(!OVF || TEAM == BLOCK, "the table-full flag is one per block");
@@ -876,8 +885,8 @@ __global__ void __launch_bounds__(BLOCK, (1024 / BLOCK) > 0 ? (1024 / BLOCK) : 1
     if (tc.tid == 0) s_table_full = 0u;
   }
   __syncthreads();
-  if (p.n_segs == 1) event_loop<TEAM, BLOCK, true, OVF>(p, smem, tc, st, tt);
-  else event_loop<TEAM, BLOCK, false, OVF>(p, smem, tc, st, tt);
+  if (p.n_segs == 1) event_loop<TEAM, BLOCK, true, OVF, IP>(p, smem, tc, st, tt);
+  else event_loop<TEAM, BLOCK, false, OVF, IP>(p, smem, tc, st, tt);
 }
 
 // ------------------------------------------------------- auxiliary kernels
@@ -954,7 +963,7 @@ __global__ void gather_dense_kernel(const uint64_t* __restrict__ offsets, uint64
 // A kernel's dynamic shared-memory limit only ever grows (per device): a
 // captured graph replays its launch with the shared memory it was captured
 // with, which a later smaller launch must not take away.
-template <int TEAM, int BLOCK, bool OVF>
+template <int TEAM, int BLOCK, bool OVF, bool IP>
 static cudaError_t allow_smem(size_t smem) {
   static std::mutex mu;
   static int allowed[PDR_MAX_DEVICES] = {};
@@ -964,24 +973,24 @@ static cudaError_t allow_smem(size_t smem) {
   if (dev < 0 || dev >= PDR_MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(mu);
   if ((int)smem <= allowed[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(fused_kernel<TEAM, BLOCK, OVF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(fused_kernel<TEAM, BLOCK, OVF, IP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess) allowed[dev] = (int)smem;
   return e;
 }
 
-template <int TEAM, int BLOCK, bool OVF>
+template <int TEAM, int BLOCK, bool OVF, bool IP>
 static cudaError_t launch_t(const KParams& p, uint32_t grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = allow_smem<TEAM, BLOCK, OVF>(smem);
+  cudaError_t e = allow_smem<TEAM, BLOCK, OVF, IP>(smem);
   if (e != cudaSuccess) return e;
-  fused_kernel<TEAM, BLOCK, OVF><<<grid, BLOCK, smem, s>>>(p);
+  fused_kernel<TEAM, BLOCK, OVF, IP><<<grid, BLOCK, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 template <int TEAM, int BLOCK, bool OVF>
 static cudaError_t occupancy_t(int* blocks, size_t smem) {
-  cudaError_t e = allow_smem<TEAM, BLOCK, OVF>(smem);
+  cudaError_t e = allow_smem<TEAM, BLOCK, OVF, false>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fused_kernel<TEAM, BLOCK, OVF>, BLOCK, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, fused_kernel<TEAM, BLOCK, OVF, false>, BLOCK, smem);
 }
 
 #define PDR_SHAPES(X) X(32, 128) X(32, 256) X(64, 256) X(128, 128) X(128, 256) X(256, 256) X(512, 512) X(1024, 1024)
@@ -1002,15 +1011,20 @@ bool shape_supports_overflow(uint32_t team, uint32_t block) {
   return false;
 }
 
+// ip: the kernel that also writes the tracks' impact parameters (the
+// parameter block's segments carry the ip arrays); its occupancy is taken
+// to be the plain kernel's (same shared memory, same register cap).
 cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool ip) {
   if (p.smem_may_overflow) {
-#define PDR_LO(T, B) if (team == T && block == B) return launch_t<T, B, true>(p, grid, smem, s);
+#define PDR_LO(T, B) if (team == T && block == B) return ip ? launch_t<T, B, true, true>(p, grid, smem, s) \
+                                                                : launch_t<T, B, true, false>(p, grid, smem, s);
     PDR_OVF_SHAPES(PDR_LO)
 #undef PDR_LO
     return cudaErrorInvalidValue;
   }
-#define PDR_L(T, B) if (team == T && block == B) return launch_t<T, B, false>(p, grid, smem, s);
+#define PDR_L(T, B) if (team == T && block == B) return ip ? launch_t<T, B, false, true>(p, grid, smem, s) \
+                                                           : launch_t<T, B, false, false>(p, grid, smem, s);
   PDR_SHAPES(PDR_L)
 #undef PDR_L
   return cudaErrorInvalidValue;

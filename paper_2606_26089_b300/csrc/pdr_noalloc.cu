@@ -37,7 +37,7 @@
 namespace pdr {
 bool shape_supported(uint32_t team, uint32_t block);
 cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
-                         cudaStream_t s);
+                         cudaStream_t s, bool ip = false);
 cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks);
 cudaError_t launch_max_event(const uint64_t* offsets, uint64_t n_events, uint32_t* out, uint32_t* err,
                              cudaStream_t s);

@@ -26,7 +26,7 @@
 namespace pdr {
 bool shape_supported(uint32_t team, uint32_t block);
 cudaError_t launch_fused(uint32_t team, uint32_t block, const KParams& p, uint32_t grid, size_t smem,
-                         cudaStream_t s);
+                         cudaStream_t s, bool ip = false);
 cudaError_t occupancy_fused(uint32_t team, uint32_t block, size_t smem, int* blocks);
 cudaError_t occupancy_fused_ovf(uint32_t team, uint32_t block, size_t smem, int* blocks);
 bool shape_supports_overflow(uint32_t team, uint32_t block);
@@ -1669,14 +1669,59 @@ extern "C" int pdr_postprocess(pdr_ctx* ctx, const pdr_batch* b, const pdr_outpu
 }
 
 // ============================================================ impact parameters
+namespace {
+IPConst ip_const(const CardEntry& ce, const pdr_ip_params* ipp) {
+  IPConst c;
+  c.kB = ce.kB;
+  c.bsign = ce.bsign;
+  c.has_field = ce.has_field;
+  c.a_d0 = (float)ipp->a_d0; c.b_d0 = (float)ipp->b_d0;
+  c.a_z0 = (float)ipp->a_z0; c.b_z0 = (float)ipp->b_z0;
+  return c;
+}
+
+int check_ip_params(const pdr_ip_params* ipp) {
+  if (!ipp) return fail(PDR_EINVAL, "null impact-parameter parameters");
+  const double r[4] = {ipp->a_d0, ipp->b_d0, ipp->a_z0, ipp->b_z0};
+  for (double v : r)
+    if (!(v >= 0.0) || !std::isfinite(v)) return fail(PDR_EINVAL, "impact-parameter resolutions must be >= 0");
+  return PDR_OK;
+}
+}  // namespace
+
+extern "C" int pdr_run_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_ip_params* ipp,
+                          pdr_ip* ip, const pdr_launch* l, void* stream) {
+  int rc = check_batch(ctx, b);
+  if (rc) return rc;
+  if ((rc = check_outputs(o))) return rc;
+  if (!ip) return fail(PDR_EINVAL, "null ip array");
+  if ((rc = check_ip_params(ipp))) return rc;
+  cudaSetDevice(ctx->device);
+  std::lock_guard<std::mutex> g(ctx->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t max_n = 0;
+  if ((rc = batch_max_n(ctx, b, s, &max_n))) return rc;
+  static thread_local KParams p;
+  Shape S;
+  const pdr_batch* bs[1] = {b};
+  const pdr_outputs* os[1] = {o};
+  if ((rc = prepare_group(ctx, bs, os, 1, plan_launch(ctx, b->card_id, max_n, l), max_n, p, S))) return rc;
+  if (p.n_events == 0) return PDR_OK;
+  p.seg[0].ip = ip;
+  p.seg[0].vx = ipp->vx;
+  p.seg[0].vy = ipp->vy;
+  p.seg[0].ipc = ip_const(ctx->cards[b->card_id], ipp);
+  p.work = work_counter(ctx, s);
+  PDR_CUDA(launch_fused(S.team, S.block, p, S.grid, S.smem, s, true), "fused kernel launch (impact parameters)");
+  return PDR_OK;
+}
+
 extern "C" int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_ip_params* ipp,
                             pdr_ip* ip, void* stream) {
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if (!o || !o->tracks || !o->counts || !ipp || !ip) return fail(PDR_EINVAL, "null track, count or ip array");
-  const double r[4] = {ipp->a_d0, ipp->b_d0, ipp->a_z0, ipp->b_z0};
-  for (double v : r)
-    if (!(v >= 0.0) || !std::isfinite(v)) return fail(PDR_EINVAL, "impact-parameter resolutions must be >= 0");
+  if ((rc = check_ip_params(ipp))) return rc;
   cudaSetDevice(ctx->device);
   std::lock_guard<std::mutex> g(ctx->mu);
   if (b->n_events == 0) return PDR_OK;
@@ -1692,12 +1737,8 @@ extern "C" int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs*
   p.counts = o->counts;
   p.ip = ip;
   p.err = ctx->d_err;
-  p.kB = ce.kB;
-  p.bsign = ce.bsign;
-  p.has_field = ce.has_field;
+  p.c = ip_const(ce, ipp);
   p.event_base = b->event_index_base;
-  p.a_d0 = (float)ipp->a_d0; p.b_d0 = (float)ipp->b_d0;
-  p.a_z0 = (float)ipp->a_z0; p.b_z0 = (float)ipp->b_z0;
   fill_round_keys(p.rk, b->seed);
   PDR_CUDA(launch_track_ip(p, ctx->n_sms, (cudaStream_t)stream), "impact-parameter launch");
   return PDR_OK;

@@ -126,3 +126,39 @@ def test_bad_resolutions_are_rejected(B, ctx):
     ip = torch.empty((batch.n_particles, 4), device="cuda")
     with pytest.raises(B.PdrError):
         ctx.track_ip(B.make_batch(dev, cid, SEED), B.make_outputs(out), B.make_ip_params((-1.0, 0, 0, 0)), ip)
+
+
+def test_fused_form_equals_the_separate_pass(B, ctx):
+    """pdr_run_ip (impact parameters written by the response kernel's smearing
+    jobs) gives the records of pdr_run followed by pdr_track_ip bit for bit,
+    for every launch shape family (one-warp teams, CTA teams, the large-event
+    path with optimistic shared tables) and with vertex arrays absent."""
+    from paper_2606_26089_b300 import synth
+    batch, vx, vy = _displaced_batch(60, 37)
+    big = synth.make("pileup", n_events=2)
+    for b, tvx, tvy in ((batch, vx, vy), (big, None, None)):
+        cid = ctx.card_load("cms_like")
+        dev = B.batch_to_device(b)
+        txy = [None if v is None else torch.from_numpy(v).cuda() for v in (tvx, tvy)]
+        prm = B.make_ip_params(RES, *txy)
+        for team, block in ((32, 256), (256, 256), (1024, 1024)):
+            l = B.pdr_launch()
+            l.team, l.block, l.table_slots, l.grid = team, block, 0, 0
+            o1 = B.alloc_outputs(b.n_events, b.n_particles)
+            ip1 = torch.full((b.n_particles, 4), float("nan"), device="cuda")
+            bt = B.make_batch(dev, cid, SEED)
+            ctx.run(bt, B.make_outputs(o1), launch=l)
+            ctx.track_ip(bt, B.make_outputs(o1), prm, ip1)
+            o2 = B.alloc_outputs(b.n_events, b.n_particles)
+            ip2 = torch.full((b.n_particles, 4), float("nan"), device="cuda")
+            ctx.run_ip(bt, B.make_outputs(o2), prm, ip2, launch=l)
+            torch.cuda.synchronize()
+            ctx.check()
+            assert torch.equal(o1["counts"], o2["counts"])
+            counts = o1["counts"].cpu().numpy().view(np.uint32)
+            for e in range(b.n_events):
+                a, nt = int(b.offsets[e]), int(counts[e][0])
+                assert torch.equal(o1["tracks"][a:a + nt].view(torch.int32), o2["tracks"][a:a + nt].view(torch.int32))
+                assert torch.equal(ip1[a:a + nt].view(torch.int32), ip2[a:a + nt].view(torch.int32)), (team, e)
+    with pytest.raises(B.PdrError):
+        ctx.run_ip(bt, B.make_outputs(o2), B.make_ip_params((-1.0, 0, 0, 0)), ip2)
