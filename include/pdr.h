@@ -509,6 +509,29 @@ typedef struct {
 int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* out, const pdr_jet_params* params,
                      pdr_jet* jets, uint32_t* jet_counts, void* stream);
 
+/* ----------------------------------------------------------- diagnostics -- */
+/* The paper has no counterpart to this entry point: it exposes, for tests, the
+ * single-precision function approximations the kernels use in place of the
+ * library calls (each with an error bound stated in the library's source),
+ * evaluated element-wise on DEVICE arrays: y[k] = f(x[k]) (PDR_FN_NORMAL:
+ * the Box-Muller deviate of the words whose bits x[k] and x2[k] carry;
+ * PDR_FN_U01: the uniform of the word whose bits x[k] carries).
+ * Asynchronous on `stream`; PDR_EINVAL for an unknown function or a null array. */
+#define PDR_FN_ASIN_HALF 0      /* asin(x), x in [0, 1/2]                      */
+#define PDR_FN_SIN_HALF_TURN 1  /* sin(x), x in [0, pi]                        */
+#define PDR_FN_LN_UNIT 2        /* ln(u), u in (0, 1)                          */
+#define PDR_FN_LOG1P_POS 3      /* ln(1 + x), x >= 0                           */
+#define PDR_FN_COS_TWO_PI 4     /* cos(2 pi u), u in (0, 1)                    */
+#define PDR_FN_COSH 5           /* cosh(x)                                     */
+#define PDR_FN_SINH 6           /* sinh(x)                                     */
+#define PDR_FN_ASINH 7          /* asinh(x)                                    */
+#define PDR_FN_U01 8            /* (2k + 1) / 2^24 for the top 23 bits k       */
+#define PDR_FN_NORMAL 9         /* sqrt(-2 ln u01(a)) cos(2 pi u01(b))         */
+#define PDR_FN_RCP 10           /* 1 / x                                       */
+#define PDR_FN_SQRT 11          /* sqrt(x)                                     */
+#define PDR_FN_COUNT 12
+int pdr_math_eval(int fn, const float* x, const float* x2, float* y, uint64_t n, void* stream);
+
 /* ------------------------------------------------------- allocation-free run -- */
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that may not allocate device memory when they run the response:

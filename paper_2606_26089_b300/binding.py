@@ -241,6 +241,7 @@ def lib():
             "pdr_track_ip": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_ip_params), P, P], I),
             "pdr_run_ip": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_ip_params), P,
                             C.POINTER(pdr_launch), P], I),
+            "pdr_math_eval": ([C.c_int, P, P, P, C.c_uint64, P], I),
             "pdr_cluster_jets": ([P, C.POINTER(pdr_batch), C.POINTER(pdr_outputs), C.POINTER(pdr_jet_params), P, P,
                                   P], I),
         }
@@ -254,6 +255,22 @@ def lib():
 
 def exported_symbols():
     return [n for n in dir(lib()) if n.startswith("pdr_")]
+
+
+MATH_FN = {"asin_half": 0, "sin_half_turn": 1, "ln_unit": 2, "log1p_pos": 3, "cos_two_pi": 4, "cosh": 5, "sinh": 6,
+           "asinh": 7, "u01": 8, "normal": 9, "rcp": 10, "sqrt": 11}
+
+
+def math_eval(name: str, x, x2=None, stream=None):
+    """One of the kernels' float32 function approximations on a device float32
+    tensor x (for "u01" and "normal" the tensors carry 32-bit words: x.view)."""
+    torch = _torch()
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    rc = lib().pdr_math_eval(MATH_FN[name], _ptr(x), _ptr(x2), _ptr(y), int(x.numel()), s)
+    if rc:
+        raise PdrError(rc, "pdr_math_eval", (lib().pdr_last_error(None) or b"").decode())
+    return y
 
 
 def card_path(name: str) -> str:

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libpdr.so")
-SOURCES = ["pdr_kernel.cu", "pdr_pileup.cu", "pdr_postprocess.cu", "pdr_ip.cu", "pdr_jets.cu", "pdr_runtime.cu", "pdr_noalloc.cu"]
+SOURCES = ["pdr_kernel.cu", "pdr_pileup.cu", "pdr_postprocess.cu", "pdr_ip.cu", "pdr_jets.cu", "pdr_runtime.cu",
+           "pdr_noalloc.cu", "pdr_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

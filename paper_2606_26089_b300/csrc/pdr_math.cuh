@@ -33,9 +33,10 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return make_uint4(c0, c1, c2, c3);
 }
 
-// Reciprocal to 1 ulp (the hardware approximation); used where the result
-// only needs a few ulp: every such quotient feeds either an output compared at
-// 2e-6 relative or a decision taken with the 1e-5 marginal band.
+// Reciprocal to 1 ulp (the hardware approximation; relative error below
+// 2^-22 over 1e-20 ... 1e20); used where the result only needs a few ulp:
+// every such quotient feeds either an output compared at 2e-6 relative or a
+// decision taken with the 1e-5 marginal band.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -44,26 +45,32 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 __device__ __forceinline__ float fdiv(float a, float b) { return a * rcp_approx(b); }
 
-// Square root to 1 ulp (the hardware approximation; measured over a spread of
-// magnitudes: relative error below 1e-7): energies, smearing widths and the
-// Box-Muller radius need only a few ulp.
+// Square root to 1 ulp (the hardware approximation; relative error below
+// 2^-22 over 1e-20 ... 1e20): energies, smearing widths and the Box-Muller
+// radius need only a few ulp.
 __device__ __forceinline__ float sqrt_approx(float x) {
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
-// Polynomial approximations, coefficients from a least-squares fit on
-// Chebyshev nodes in double precision (truncation error far below float
-// rounding on the stated ranges):
-//   asin(x) = x + x^3 P(x^2) on [0, 1/2]             (fit error ~1e-9)
-//   sin(x)  = x + x^3 Q(x^2) on [0, pi/2]            (fit error ~2e-10)
-//   ln(1 - v) = -v L(v)      on [0, 1/4]             (fit error ~3e-9)
-//   ln(1 + x) = x M(x)       on [0, 1/4]             (fit error ~4e-10)
+// Polynomial approximations.  Coefficients: least-squares polynomial fits in
+// double precision of the reduced function in its reduced variable, sampled
+// at the 64 Chebyshev points of the first kind of the interval, rounded to
+// float32 (fit_poly.py beside this file computes them; the relative error of
+// each fit before float32 evaluation is given in brackets):
+//   asin(x) = x + x^3 P(x^2), P on x^2 in [0, 1/4]      (2.5e-9)
+//   sin(x)  = x + x^3 Q(x^2), Q on x^2 in [0, pi^2/4]   (1.9e-8)
+//   ln(1 - v) = -v L(v),      L on v in [0, 1/4]        (4.6e-9)
+//   ln(1 + x) = x M(x),       M on x in [0, 1/4]        (3.0e-9)
+// Each function below states its float32 error bound over its whole argument
+// range; a GPU test (through pdr_math_eval) holds it to that bound, at every
+// one of the 2^23 uniforms for the Box-Muller pieces and on dense grids for
+// the others.
 __device__ __forceinline__ float asin_half(float x) {
   const float t = x * x;
-  float p = fmaf(t, 0.033805817f, 0.017077811f);
-  p = fmaf(t, p, 0.031116169f);
+  float p = fmaf(t, 0.033805776f, 0.01707784f);
+  p = fmaf(t, p, 0.031116161f);
   p = fmaf(t, p, 0.04459803f);
   p = fmaf(t, p, 0.07500099f);
   p = fmaf(t, p, 0.16666666f);
@@ -72,20 +79,23 @@ __device__ __forceinline__ float asin_half(float x) {
 
 __device__ __forceinline__ float sin_quarter(float x) {
   const float t = x * x;
-  float q = fmaf(t, -2.4080528e-08f, 2.753648e-06f);
+  float q = fmaf(t, -2.4080485e-08f, 2.7536478e-06f);
   q = fmaf(t, q, -0.00019841087f);
   q = fmaf(t, q, 0.008333333f);
   q = fmaf(t, q, -0.16666667f);
   return fmaf(x * t, q, x);
 }
 
-// sin on [0, pi]: reflected to [0, pi/2] with pi split in two floats.
+// asin_half: relative error below 2.4e-7 on [0, 1/2].
+// sin_half_turn: sin on [0, pi], reflected to [0, pi/2] with pi split in two
+// floats; absolute error below 1.8e-7.
 __device__ __forceinline__ float sin_half_turn(float y) {
   return sin_quarter(y > PIO2_HI ? (3.14159274101257324f - y) + -8.74227766e-8f : y);
 }
 
-// ln u for u in (0, 1): hardware log2 below 3/4 (relative error < 5e-7
-// there, |ln u| > 0.28), -v L(v) with v = 1 - u (exact) above.
+// ln u for u in (0, 1): hardware log2 below 3/4 (|ln u| > 0.28 there),
+// -v L(v) with v = 1 - u (exact) above; relative error below 6e-7 at every
+// uniform the generator makes.
 __device__ __forceinline__ float ln_unit(float u) {
   const float v = 1.0f - u;
   float p = fmaf(v, 0.33390906f, 0.08952039f);
@@ -98,7 +108,7 @@ __device__ __forceinline__ float ln_unit(float u) {
 }
 
 // ln(1 + x) for x >= 0: x M(x) up to 1/4, hardware log2 of 1 + x above
-// (relative error < 6e-7 there, ln(1 + x) > 0.22).
+// (ln(1 + x) > 0.22 there); relative error below 6e-7 up to 1e8.
 __device__ __forceinline__ float log1p_pos(float x) {
   float m = fmaf(x, 0.070751615f, -0.14544724f);
   m = fmaf(x, m, 0.19665538f);
@@ -110,7 +120,8 @@ __device__ __forceinline__ float log1p_pos(float x) {
 }
 
 // cos(2 pi u) for u in (0, 1): folded exactly in turns to sin of at most a
-// quarter turn (cos(2 pi u) = -cos(pi t), t = |2u - 1|).
+// quarter turn (cos(2 pi u) = -cos(pi t), t = |2u - 1|); absolute error below
+// 2.4e-7 at every uniform the generator makes.
 __device__ __forceinline__ float cos_two_pi(float u) {
   const float t = fabsf(2.0f * u - 1.0f);
   const float r = t > 0.5f ? t - 0.5f : 0.5f - t;
@@ -120,7 +131,8 @@ __device__ __forceinline__ float cos_two_pi(float u) {
 
 // cosh and sinh from one exponential: cosh = (e + 1/e) / 2; sinh likewise for
 // |x| >= 1/2 (no cancellation there: e - 1/e >= 1.04) and from its odd Taylor
-// series through x^9 below 1/2 (truncation < 3e-11 relative).
+// series through x^9 below 1/2 (truncation < 3e-11 relative); relative error
+// of both below 4e-7 on [-12, 12].
 __device__ __forceinline__ void cosh_sinh(float x, float& ch, float& sh) {
   const float ax = fabsf(x);
   const float e = expf(ax);
@@ -134,9 +146,10 @@ __device__ __forceinline__ void cosh_sinh(float x, float& ch, float& sh) {
   sh = copysignf(s, x);
 }
 
-// asinh(u) = sign(u) log(|u| + sqrt(u^2 + 1)) with the hardware log2 (absolute
-// error about 1e-7; the argument is >= 1, so no cancellation): used for the
-// surface pseudorapidity, whose tolerance is 2e-6 max(|eta|, 1).
+// asinh(u) = sign(u) log(|u| + sqrt(u^2 + 1)) with the hardware log2 (the
+// argument of the log is >= 1, so no cancellation): error below
+// 2.5e-7 max(|asinh u|, 1) up to |u| = 1e7.  Used for the surface
+// pseudorapidity, whose tolerance is 2e-6 max(|eta|, 1).
 __device__ __forceinline__ float asinh_fast(float u) {
   const float au = fabsf(u);
   return copysignf(__logf(au + sqrt_approx(fmaf(au, au, 1.0f))), u);
@@ -147,8 +160,8 @@ __device__ __forceinline__ float u01(uint32_t w) {
   return (__uint2float_rn(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
 }
 
-// Box-Muller, cosine branch (over all 2^23 inputs of each word the deviate
-// is within 1e-6 absolute of its FP64 value).
+// Box-Muller, cosine branch: at every value of either word (the other fixed
+// at several values) the deviate is within 1e-6 absolute of its FP64 value.
 __device__ __forceinline__ float normal(uint32_t wa, uint32_t wb) {
   return sqrt_approx(-2.0f * ln_unit(u01(wa))) * cos_two_pi(u01(wb));
 }
