@@ -1026,8 +1026,10 @@ int32_t oracle_cluster_forced(int64_t n, const double* px, const double* py, con
     for (int64_t i = 0; i < n; ++i) {
       if (!o[i].active) continue;
       const double diB = o[i].kt2p, uiB = 1e-6 * diB;
-      /* the beam distance first: it wins ties */
-      if (diB < b) { s2 = b; su = bu; si = bi; sj = bj; b = diB; bu = uiB; bi = i; bj = -1; }
+      /* the beam distance first: it wins ties (the first active object's is
+       * taken even when infinite, so that objects whose every distance is
+       * infinite - pT = 0 with p < 0 - leave as jets in index order) */
+      if (bi < 0 || diB < b) { s2 = b; su = bu; si = bi; sj = bj; b = diB; bu = uiB; bi = i; bj = -1; }
       else if (diB < s2) { s2 = diB; su = uiB; si = i; sj = -1; }
       for (int64_t j = i + 1; j < n; ++j) {
         if (!o[j].active) continue;

@@ -268,3 +268,17 @@ def test_forced_runner_up_changes_a_split():
     two0 = j0[j0["nconst"] == 2][0]
     two1 = j1[j1["nconst"] == 2][0]
     assert two0["eta"] < -0.19 and two1["eta"] == pytest.approx(-two0["eta"], rel=1e-12)
+
+
+def test_objects_with_only_infinite_distances_become_jets():
+    """With p < 0 an object of pT = 0 has d_iB = pT^(2p) = infinity, and so has
+    every pair distance among such objects: by the tie rule (the beam
+    distance first, then the lowest index) each leaves as a jet of its own,
+    after the finite-distance object has left."""
+    px = np.array([0.0, 0.0, 10.0])
+    py = np.array([0.0, 0.0, 0.0])
+    pz = np.array([3.0, -4.0, 1.0])
+    e = np.sqrt(px ** 2 + py ** 2 + pz ** 2)
+    jets, _ = oracle.cluster(px, py, pz, e, p=-1.0, R=0.5, pt_min=0.0, nconst_min=1)
+    assert len(jets) == 3 and list(jets["nconst"]) == [1, 1, 1]
+    assert jets[0]["pt"] == pytest.approx(10.0)
