@@ -18,7 +18,8 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpdr.so")
+# PDR_LIB_VARIANT=bounds loads the bounds-checking debug build (libpdr_bounds.so)
+LIB_PATH = os.path.join(HERE, "libpdr_bounds.so" if os.environ.get("PDR_LIB_VARIANT") == "bounds" else "libpdr.so")
 CARD_DIR = os.path.join(HERE, "cards")
 
 MAXSEG, MAXEDGE = 4, 8

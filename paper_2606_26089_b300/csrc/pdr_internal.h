@@ -317,6 +317,7 @@ enum : uint32_t {
   ERR_PILEUP = 8u,     // pile-up merge: an event's size differs from the offsets given
   ERR_VERTEX = 16u,    // pile-up merge: no vertex inside the truncation in 1024 draws
   ERR_JETS = 32u,      // jet clustering: more jets than the event's slots, or an inconsistent cell list
+  ERR_BOUNDS = 64u,    // bounds-checking build (PDR_BOUNDS): an index out of its array; the access was skipped
 };
 
 // An event's CSR range [a, b) is usable iff a <= b <= end, end = offsets[n_events]

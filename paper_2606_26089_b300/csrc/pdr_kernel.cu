@@ -38,6 +38,31 @@
 
 namespace pdr {
 
+// ---------------------------------------------------- bounds-checking build
+// Built with -DPDR_BOUNDS (libpdr_bounds.so, a debug build of the library):
+// every index into a batch array (inputs, outputs, debug records) is checked
+// against the batch's end offsets[n_events], every event index against
+// n_events and every table index against the table's size.  An index out of
+// range sets a sticky flag and is replaced by 0 (an index inside the array),
+// so the access never leaves the arrays; each team ORs the flag into the
+// launch's error word (ERR_BOUNDS) when it finishes.  In the normal build the
+// checks are the identity.
+#ifdef PDR_BOUNDS
+__device__ uint32_t g_bounds_flag;
+__device__ __forceinline__ uint64_t bchk(uint64_t i, uint64_t n) {
+  if (i < n) return i;
+  atomicOr(&g_bounds_flag, 1u);
+  return 0;
+}
+#define PDR_B(S, i) bchk((uint64_t)(i), (S).offsets[(S).n_events])
+#define PDR_BE(S, e) bchk((uint64_t)(e), (S).n_events)
+#define PDR_BT(i, n) ((uint32_t)bchk((uint64_t)(i), (uint64_t)(n)))
+#else
+#define PDR_B(S, i) (i)
+#define PDR_BE(S, e) (e)
+#define PDR_BT(i, n) (i)
+#endif
+
 // Log-normal with mean x and relative variance rel2 = (sigma/x)^2.
 __device__ __forceinline__ float lognormal(float x, float rel2, float z) {
   const float s2 = log1p_pos(rel2);
@@ -266,6 +291,7 @@ struct PartA {
 
 __device__ __forceinline__ void particle_stage_a(const KSeg& S, const HotCard& K, const float* KD,
                                                  uint64_t g, uint32_t i, PartA& o) {
+  g = PDR_B(S, g);
   const float PT = __ldg(S.pt + g), ETA = __ldg(S.eta + g), PHI = __ldg(S.phi + g);
   const float M = __ldg(S.mass + g);
   const int32_t PDG = __ldg(S.pdg + g);
@@ -324,7 +350,8 @@ __device__ __forceinline__ void run_job(const KSeg& S, const HotCard& K, uint64_
                                         uint32_t event, JobOut& r) {
   const uint32_t i = job & 0xFFFFu;
   const bool photon = (job & PDR_JOB_PHOTON) != 0u;
-  const float PT = __ldg(S.pt + a + i), ETA = __ldg(S.eta + a + i), M = __ldg(S.mass + a + i);
+  const uint64_t g = PDR_B(S, a + i);
+  const float PT = __ldg(S.pt + g), ETA = __ldg(S.eta + g), M = __ldg(S.mass + g);
   const float aeta = fabsf(ETA);
   float ch, sh;
   cosh_sinh(ETA, ch, sh);
@@ -433,7 +460,7 @@ __device__ __forceinline__ uint32_t table_insert(const Tbl& T, uint32_t key, uin
                                                  unsigned long long e_fp, unsigned long long t_fp,
                                                  bool* claimed, uint32_t* err) {
   // multiplicative hash scaled to [0, nslots): the high word of h * nslots
-  uint32_t h = __umulhi(key * 0x9E3779B1u, T.nslots);
+  uint32_t h = PDR_BT(__umulhi(key * 0x9E3779B1u, T.nslots), T.nslots);
   *claimed = false;
   for (uint32_t probe = 0; probe < T.nslots; ++probe) {
     const uint32_t prev = atomicCAS(&T.keys()[h], PDR_EMPTY, key);
@@ -559,7 +586,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     bool claimed = false;
     const unsigned long long e_fp = to_fp(o.E);
     if (valid && o.key != PDR_NO_KEY) slot = table_insert<OVF>(T, o.key, i, e_fp, 0ull, &claimed, err);
-    if (valid) T.pinfo()[i] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
+    if (valid) T.pinfo()[PDR_BT(i, T.nmax)] = slot == PDR_EMPTY ? PDR_EMPTY : (slot | (o.ring << 16));
     const bool has_job = o.job != PDR_EMPTY;
     uint32_t tot;
     const uint32_t pre = team_scan2<TEAM>(has_job, false, tt.wbuf + 32 * flip, tot, tc);
@@ -568,9 +595,9 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       fp_add(&T.esum()[slot], e_fp);
       atomicMin(&T.owner()[slot], i);
     }
-    if (has_job) T.jobs()[n_job + (pre & 0xFFFFu)] = o.job;
+    if (has_job) T.jobs()[PDR_BT(n_job + (pre & 0xFFFFu), T.nmax)] = o.job;
     if (dbg && valid)
-      reinterpret_cast<float4*>(S.debug)[a + i] =
+      reinterpret_cast<float4*>(S.debug)[PDR_B(S, a + i)] =
           make_float4(__uint_as_float(o.key), o.eta_pos, o.phi_pos, __uint_as_float(o.flags));
     n_job += tot & 0xFFFFu;
   }
@@ -592,15 +619,15 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     r.tracked = false; r.cand = false;
     uint32_t i = 0;
     if (j < n_job) {
-      const uint32_t job = T.jobs()[j];
+      const uint32_t job = T.jobs()[PDR_BT(j, T.nmax)];
       i = job & 0xFFFFu;
       run_job(S, K, a, job, event, r);
       if (r.tracked) {
-        const uint32_t pi = T.pinfo()[i];
-        if (pi != PDR_EMPTY) fp_add(&T.etrk()[pi & 0xFFFFu], to_fp(r.etrk));
+        const uint32_t pi = T.pinfo()[PDR_BT(i, T.nmax)];
+        if (pi != PDR_EMPTY) fp_add(&T.etrk()[PDR_BT(pi & 0xFFFFu, T.nslots)], to_fp(r.etrk));
       }
       if (dbg && (r.tracked || r.cand))
-        reinterpret_cast<uint32_t*>(S.debug + a + i)[3] |=
+        reinterpret_cast<uint32_t*>(S.debug + PDR_B(S, a + i))[3] |=
             (r.tracked ? PDR_F_TRACKED : 0u) | (r.cand ? PDR_F_CAND : 0u);
     }
     uint32_t tot;
@@ -609,15 +636,15 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     trk_reg0 = n_trk;
     lt_has = false;
     if (r.tracked || r.cand) {
-      const float eta = __ldg(S.eta + a + i), phi = __ldg(S.phi + a + i);
+      const float eta = __ldg(S.eta + PDR_B(S, a + i)), phi = __ldg(S.phi + PDR_B(S, a + i));
       if (r.tracked) {
-        reinterpret_cast<float4*>(S.tracks)[a + n_trk + (pre & 0xFFFFu)] =
+        reinterpret_cast<float4*>(S.tracks)[PDR_B(S, a + n_trk + (pre & 0xFFFFu))] =
             make_float4(r.ptp, eta, phi, __uint_as_float(i));
         if constexpr (IP) {  // the track's impact parameters, parallel to its record
-          const uint64_t g = a + i;
+          const uint64_t g = PDR_B(S, a + i);
           const float x0 = S.vx ? __ldg(S.vx + g) : 0.0f, y0 = S.vy ? __ldg(S.vy + g) : 0.0f;
           const float zv = S.vz ? __ldg(S.vz + g) : 0.0f;
-          S.ip[a + n_trk + (pre & 0xFFFFu)] =
+          S.ip[PDR_B(S, a + n_trk + (pre & 0xFFFFu))] =
               track_ip_of(__ldg(S.pt + g), eta, phi, (int)__ldg(S.charge + g), x0, y0, zv, i, event, S.rk, S.ipc);
         }
         lt_has = r.ptp > K.iso_ptmin;
@@ -625,12 +652,12 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       }
       if (r.cand) {
         const uint32_t jc = n_cand + (pre >> 16);
-        const uint32_t pi = T.pinfo()[i];
-        const uint32_t key = pi == PDR_EMPTY ? PDR_NO_KEY : T.keys()[pi & 0xFFFFu];
-        reinterpret_cast<float4*>(S.cands)[a + jc] =
+        const uint32_t pi = T.pinfo()[PDR_BT(i, T.nmax)];
+        const uint32_t key = pi == PDR_EMPTY ? PDR_NO_KEY : T.keys()[PDR_BT(pi & 0xFFFFu, T.nslots)];
+        reinterpret_cast<float4*>(S.cands)[PDR_B(S, a + jc)] =
             make_float4(r.cpt, eta, phi, __uint_as_float(i | ((uint32_t)r.cc << 28)));
         // own tower key, read back by the isolation of candidates beyond the staged ones
-        reinterpret_cast<float2*>(S.iso)[a + jc] = make_float2(__uint_as_float(key), 0.0f);
+        reinterpret_cast<float2*>(S.iso)[PDR_B(S, a + jc)] = make_float2(__uint_as_float(key), 0.0f);
         if (jc < PDR_CMAX) {  // staged for the isolation
           tt.cf[jc] = make_float4(eta, phi, r.cpt, __uint_as_float(i));
           tt.ckey[jc] = key;
@@ -659,9 +686,9 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     to.kept = false; to.ef = false;
     uint32_t key = PDR_NO_KEY;
     if (i < n) {
-      const uint32_t pi = T.pinfo()[i];
+      const uint32_t pi = T.pinfo()[PDR_BT(i, T.nmax)];
       if (pi != PDR_EMPTY) {
-        const uint32_t slot = pi & 0xFFFFu;
+        const uint32_t slot = PDR_BT(pi & 0xFFFFu, T.nslots);
         if (T.owner()[slot] == i) {
           key = T.keys()[slot];
           tower_stage(K, KD, key, pi >> 16, T.esum()[slot], T.etrk()[slot], event, S.rk, to);
@@ -677,7 +704,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       }
     }
     if (gn0 > 0 && i < trk_reg0) {
-      const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + i];
+      const float4 t = reinterpret_cast<const float4*>(S.tracks)[PDR_B(S, a + i)];
       if (t.x > K.iso_ptmin)
         iso_object(K, make_float4(t.y, t.z, t.x, __uint_as_float(__float_as_uint(t.w) | PDR_ISO_TRACK)), tt);
     }
@@ -685,11 +712,11 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     const uint32_t pre = team_scan2<TEAM>(to.kept, to.ef, tt.wbuf + 32 * flip, tot, tc);
     flip ^= 1u;
     if (to.kept) {
-      pdr_tower* r = S.towers + a + n_twr + (pre & 0xFFFFu);
+      pdr_tower* r = S.towers + PDR_B(S, a + n_twr + (pre & 0xFFFFu));
       r->key = key; r->e = to.e; r->et = to.et;
     }
     if (to.ef) {
-      pdr_eflow* r = S.eflow + a + n_ef + (pre >> 16);
+      pdr_eflow* r = S.eflow + PDR_B(S, a + n_ef + (pre >> 16));
       r->key = key; r->e = to.de; r->et = to.det;
     }
     n_twr += tot & 0xFFFFu;
@@ -706,8 +733,8 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       const float s = from_fp(tt.csum[c]);
       tt.csum[c] = 0ull;  // clean for the next group / event
       const float rel = s / tt.cf[c].z;
-      reinterpret_cast<float2*>(S.iso)[a + c] = make_float2(s, rel);
-      reinterpret_cast<uint32_t*>(S.cands + a + c)[3] = tt.cinfo[c] | (rel < K.imax ? 0x80000000u : 0u);
+      reinterpret_cast<float2*>(S.iso)[PDR_B(S, a + c)] = make_float2(s, rel);
+      reinterpret_cast<uint32_t*>(S.cands + PDR_B(S, a + c))[3] = tt.cinfo[c] | (rel < K.imax ? 0x80000000u : 0u);
     }
   }
   for (uint32_t g0 = PDR_CMAX; g0 < n_cand; g0 += PDR_CMAX) {
@@ -715,7 +742,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     const uint32_t n_obj = n_trk + n_ef;
     tc.sync();
     if ((uint32_t)tc.tid < gn) {  // candidates beyond the staged ones
-      const uint64_t j = a + g0 + tc.tid;
+      const uint64_t j = PDR_B(S, a + g0 + tc.tid);
       const float4 c = reinterpret_cast<const float4*>(S.cands)[j];
       tt.cf[tc.tid] = make_float4(c.y, c.z, c.x, __uint_as_float(__float_as_uint(c.w) & 0x0FFFFFFFu));
       tt.ckey[tc.tid] = __float_as_uint(reinterpret_cast<const float2*>(S.iso)[j].x);
@@ -727,10 +754,10 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
       uint32_t oid;
       bool is_trk;
       if (j < n_trk) {
-        const float4 t = reinterpret_cast<const float4*>(S.tracks)[a + j];
+        const float4 t = reinterpret_cast<const float4*>(S.tracks)[PDR_B(S, a + j)];
         opt = t.x; oe = t.y; op = t.z; oid = __float_as_uint(t.w); is_trk = true;
       } else {
-        const pdr_eflow f = S.eflow[a + (j - n_trk)];
+        const pdr_eflow f = S.eflow[PDR_B(S, a + (j - n_trk))];
         int r;
         tower_decode(K, KD, (int)(f.key >> 24), f.key & 0xFFFFFFu, r, oe, op);
         opt = f.et; oid = f.key; is_trk = false;
@@ -750,7 +777,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     }
     tc.sync();
     if ((uint32_t)tc.tid < gn) {
-      const uint64_t j = a + g0 + tc.tid;
+      const uint64_t j = PDR_B(S, a + g0 + tc.tid);
       const float s = from_fp(tt.csum[tc.tid]);
       tt.csum[tc.tid] = 0ull;
       const float rel = s / tt.cf[tc.tid].z;
@@ -761,7 +788,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
   // the next event reuses the table, the staged candidates and the buffers
   tc.sync();
   if (tc.tid == 0)
-    reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(n_trk, n_twr, n_ef, n_cand);
+    reinterpret_cast<uint4*>(S.counts)[PDR_BE(S, e)] = make_uint4(n_trk, n_twr, n_ef, n_cand);
   return true;
 }
 
@@ -805,14 +832,14 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
     if (!csr_ok(a, b, S.offsets[S.n_events]) || b - a >= (1ull << 28)) {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_CSR);
-        reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(S.counts)[PDR_BE(S, e)] = make_uint4(0, 0, 0, 0);
       }
       if (p.work) tc.sync();
       continue;
     }
     const uint32_t n = (uint32_t)(b - a);
     if (n == 0) {  // nothing to do (a team barrier only for the work counter's hand-over)
-      if (tc.tid == 0) reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
+      if (tc.tid == 0) reinterpret_cast<uint4*>(S.counts)[PDR_BE(S, e)] = make_uint4(0, 0, 0, 0);
       if (p.work) tc.sync();
       continue;
     }
@@ -838,11 +865,14 @@ __device__ __forceinline__ void event_loop(const KParams& p, unsigned char* smem
     } else {
       if (tc.tid == 0) {
         atomicOr(p.err, ERR_OVERSIZE);
-        reinterpret_cast<uint4*>(S.counts)[e] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4*>(S.counts)[PDR_BE(S, e)] = make_uint4(0, 0, 0, 0);
       }
       if (p.work) tc.sync();
     }
   }
+#ifdef PDR_BOUNDS
+  if (tc.tid == 0 && *(volatile uint32_t*)&g_bounds_flag) atomicOr(p.err, ERR_BOUNDS);
+#endif
   // the launch's last team to finish resets the counter for the next launch
   // on this stream (every team's last fetch precedes its count of finished
   // teams)

@@ -728,6 +728,7 @@ int pdr_check(pdr_ctx* ctx, void* stream) {
     if (w & ERR_PILEUP) m += " pile-up merge arguments differ from the first pass;";
     if (w & ERR_VERTEX) m += " no pile-up vertex inside the truncation in 1024 draws;";
     if (w & ERR_JETS) m += " jet clustering: more jets than the event's slots (the rest dropped) or a bookkeeping error;";
+    if (w & ERR_BOUNDS) m += " index out of bounds (bounds-checking build);";
     return fail(PDR_EDEVICE, m);
   }
   return PDR_OK;
