@@ -18,6 +18,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pdr.h"
 #include "pdr_card.h"
 #include "pdr_hot.h"
@@ -49,6 +51,18 @@ using namespace pdr;
 namespace {
 
 thread_local std::string t_err;
+
+// NVTX range for the duration of a scope: the host-side stages of each entry
+// point show up in a timeline tool (Nsight Systems, ncu's NVTX filter).  The
+// response's device stages S0-S9 run inside one fused kernel, so they have no
+// ranges of their own.  NVTX3 is header-only: without an attached tool a range
+// costs a check of a null pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int fail(int code, const std::string& msg) {
   t_err = msg;
@@ -563,6 +577,7 @@ int pdr_destroy(pdr_ctx* ctx) {
 }
 
 int pdr_card_load(pdr_ctx* ctx, const pdr_card* card, uint32_t* card_id) {
+  NvtxRange nvtx_range("pdr_card_load");
   if (!ctx || !card || !card_id) return fail(PDR_EINVAL, "null argument");
   std::lock_guard<std::mutex> g(ctx->mu);
   DevCard* host = new DevCard();
@@ -644,6 +659,7 @@ int pdr_max_event_size(pdr_ctx* ctx, const pdr_batch* b, void* stream, uint32_t*
 }
 
 int pdr_run(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_launch* l, void* stream) {
+  NvtxRange nvtx_range("pdr_run");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if ((rc = check_outputs(o))) return rc;
@@ -656,6 +672,7 @@ int pdr_run(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_la
 
 int pdr_run_multi(pdr_ctx* ctx, const pdr_batch* bs, uint32_t n, const pdr_outputs* os, const pdr_launch* l,
                   void* stream) {
+  NvtxRange nvtx_range("pdr_run_multi");
   if (!ctx || (n > 0 && (!bs || !os))) return fail(PDR_EINVAL, "null argument");
   for (uint32_t k = 0; k < n; ++k) {
     int rc = check_batch(ctx, &bs[k]);
@@ -677,6 +694,7 @@ int pdr_run_multi(pdr_ctx* ctx, const pdr_batch* bs, uint32_t n, const pdr_outpu
 }
 
 int pdr_run_per_event(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* stream) {
+  NvtxRange nvtx_range("pdr_run_per_event");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if ((rc = check_outputs(o))) return rc;
@@ -735,6 +753,7 @@ int pdr_check(pdr_ctx* ctx, void* stream) {
 }
 
 int pdr_autotune(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* stream, pdr_launch* best) {
+  NvtxRange nvtx_range("pdr_autotune");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if ((rc = check_outputs(o))) return rc;
@@ -787,6 +806,7 @@ int pdr_autotune(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, void* s
 }
 
 int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const pdr_launch* l, void* stream) {
+  NvtxRange nvtx_range("pdr_run_host");
   int rc = check_batch(ctx, hb);
   if (rc) return rc;
   if (!ho || !ho->tracks || !ho->towers || !ho->eflow || !ho->cands || !ho->iso || !ho->counts)
@@ -940,6 +960,7 @@ int pdr_run_host(pdr_ctx* ctx, const pdr_batch* hb, const pdr_outputs* ho, const
 
 // ---------------------------------------------------------------- tickets
 int pdr_submit(pdr_ctx* ctx, const pdr_batch* b, void* stream, uint64_t* ticket) {
+  NvtxRange nvtx_range("pdr_submit");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if (!ticket) return fail(PDR_EINVAL, "null ticket");
@@ -1114,6 +1135,7 @@ namespace {
 
 // Carve a request's device memory and queue its input copies (ctx->mu held).
 void serve_admit(pdr_ctx* ctx, Server& sv, ServeReq* r) {
+  NvtxRange nvtx_range("serve: admit");
   unsigned char* m = r->mem;
   auto carve = [&](uint64_t bytes) {
     unsigned char* q = m;
@@ -1208,6 +1230,7 @@ void fail_wave(pdr_ctx* ctx, std::vector<ServeReq*>& reqs) {
 
 // One wave: the first admitted requests (up to the limits), one fused launch.
 bool serve_launch_wave(pdr_ctx* ctx, Server& sv) {
+  NvtxRange nvtx_range("serve: wave");
   std::vector<ServeReq*> reqs;
   std::vector<uint32_t> cards;
   uint64_t particles = 0;
@@ -1349,6 +1372,7 @@ int pdr_serve_start(pdr_ctx* ctx, const pdr_serve_options* opt) {
 }
 
 int pdr_serve_submit(pdr_ctx* ctx, const pdr_batch* hb, uint64_t* ticket) {
+  NvtxRange nvtx_range("pdr_serve_submit");
   int rc = check_batch(ctx, hb);
   if (rc) return rc;
   if (!ticket) return fail(PDR_EINVAL, "null ticket");
@@ -1546,6 +1570,7 @@ extern "C" {
 
 int pdr_pileup_offsets(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, uint64_t* merged_offsets,
                        uint64_t* total, void* stream) {
+  NvtxRange nvtx_range("pdr_pileup_offsets");
   int rc = pileup_args(ctx, h, pu);
   if (rc) return rc;
   if (!merged_offsets || !total) return fail(PDR_EINVAL, "null offsets or total");
@@ -1570,6 +1595,7 @@ int pdr_pileup_offsets(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, u
 
 int pdr_pileup_merge(pdr_ctx* ctx, const pdr_batch* h, const pdr_pileup* pu, const uint64_t* merged_offsets,
                      const pdr_particles* out, void* stream) {
+  NvtxRange nvtx_range("pdr_pileup_merge");
   int rc = pileup_args(ctx, h, pu);
   if (rc) return rc;
   if (!merged_offsets || !out || !out->pt || !out->eta || !out->phi || !out->mass || !out->vz || !out->pdg ||
@@ -1637,6 +1663,7 @@ int post_conditions(const pdr_filter* f, PostParams& p) {
 
 extern "C" int pdr_postprocess(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_filter* f,
                                pdr_features* features, void* stream) {
+  NvtxRange nvtx_range("pdr_postprocess");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if ((rc = check_outputs(o))) return rc;
@@ -1692,6 +1719,7 @@ int check_ip_params(const pdr_ip_params* ipp) {
 
 extern "C" int pdr_run_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_ip_params* ipp,
                           pdr_ip* ip, const pdr_launch* l, void* stream) {
+  NvtxRange nvtx_range("pdr_run_ip");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if ((rc = check_outputs(o))) return rc;
@@ -1719,6 +1747,7 @@ extern "C" int pdr_run_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o
 
 extern "C" int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_ip_params* ipp,
                             pdr_ip* ip, void* stream) {
+  NvtxRange nvtx_range("pdr_track_ip");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if (!o || !o->tracks || !o->counts || !ipp || !ip) return fail(PDR_EINVAL, "null track, count or ip array");
@@ -1748,6 +1777,7 @@ extern "C" int pdr_track_ip(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs*
 // ============================================================ jet clustering
 extern "C" int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* b, const pdr_outputs* o, const pdr_jet_params* jp,
                                 pdr_jet* jets, uint32_t* jet_counts, void* stream) {
+  NvtxRange nvtx_range("pdr_cluster_jets");
   int rc = check_batch(ctx, b);
   if (rc) return rc;
   if (!jp || !jets || !jet_counts) return fail(PDR_EINVAL, "null parameters or jet arrays");
