@@ -135,7 +135,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh", "pdr_ip.cuh"),
+KERNEL_SOURCES = {"fused_kernel": ("pdr_kernel.cu", "pdr_math.cuh", "pdr_ip.cuh", "pdr_ff.cuh", "pdr_internal.h"),
                   "pu_fill_kernel": ("pdr_pileup.cu", "pdr_math.cuh"),
                   "postprocess_kernel": ("pdr_postprocess.cu", "pdr_math.cuh"),
                   "track_ip_kernel": ("pdr_ip.cu", "pdr_math.cuh", "pdr_ip.cuh")}

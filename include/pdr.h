@@ -529,7 +529,11 @@ int pdr_cluster_jets(pdr_ctx* ctx, const pdr_batch* batch, const pdr_outputs* ou
 #define PDR_FN_NORMAL 9         /* sqrt(-2 ln u01(a)) cos(2 pi u01(b))         */
 #define PDR_FN_RCP 10           /* 1 / x                                       */
 #define PDR_FN_SQRT 11          /* sqrt(x)                                     */
-#define PDR_FN_COUNT 12
+#define PDR_FN_EXP_FF_HI 12     /* e^x, x in [0, 88], float-float: hi part     */
+#define PDR_FN_EXP_FF_LO 13     /*   ... and lo part (e^x ~ hi + lo)           */
+#define PDR_FN_SINH_FF_HI 14    /* sinh(x), x >= 0, float-float: hi part       */
+#define PDR_FN_SINH_FF_LO 15    /*   ... and lo part                           */
+#define PDR_FN_COUNT 16
 int pdr_math_eval(int fn, const float* x, const float* x2, float* y, uint64_t n, void* stream);
 
 /* ------------------------------------------------------- allocation-free run -- */

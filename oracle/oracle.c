@@ -253,10 +253,8 @@ static int decide(or_dctx* d, uint32_t kind, uint32_t id, uint32_t aux, uint32_t
   return res;
 }
 
-/* Eta-ring lookup with decision report: ring index, or -1 outside coverage.
- * extra: an absolute widening of the marginal band (conditioning of v). */
-static int ring_decide(or_dctx* d, uint32_t id, int calo, const or_grid* g, double v,
-                       double extra) {
+/* Eta-ring lookup with decision report: ring index, or -1 outside coverage. */
+static int ring_decide(or_dctx* d, uint32_t id, int calo, const or_grid* g, double v) {
   int m = g->nring;
   float vf = (float)v;
   int k = -1;
@@ -271,7 +269,7 @@ static int ring_decide(or_dctx* d, uint32_t id, int calo, const or_grid* g, doub
   }
   int below = jn - 1 >= 0 ? jn - 1 : -1;
   int above = jn < m ? jn : -1;
-  int marginal = isfinite(v) && dn <= d->g * fmax(fabs(v), 1.0) + extra &&
+  int marginal = isfinite(v) && dn <= d->g * fmax(fabs(v), 1.0) &&
                  (ring == below || ring == above);
   int alt = (ring == above) ? below : above;
   if (d->nflips > 0 && find_flip(d, OR_K_ETA, id, (uint32_t)calo, 0)) {
@@ -406,7 +404,7 @@ uint32_t oracle_tower_key(const oracle_card* c, int calo, double eta_pos, double
   or_dctx d;
   memset(&d, 0, sizeof d);
   d.cap = -1;
-  int ring = ring_decide(&d, 0, calo, &g, eta_pos, 0.0);
+  int ring = ring_decide(&d, 0, calo, &g, eta_pos);
   if (ring < 0) return OR_NO_KEY;
   int iphi = phi_decide(&d, 0, calo, g.nphi[ring], phi_pos);
   return ((uint32_t)calo << 24) | (uint32_t)(g.base[ring] + iphi);
@@ -499,22 +497,19 @@ static int run_event_impl(const oracle_card* c, const or_grid grid[2], int64_t n
     P->eta_pos = ep;
     P->phi_pos = pp;
     P->cond = cond;
-    /* float32 carries the turning angle to a few units of 2^-24 relative; the
-     * ring decisions on eta_pos are marginal within that error times cond */
-    const double cband = 16.0 * 5.9604644775390625e-8 * cond;
 
     /* S5: which calorimeter tower receives the deposit.  e/gamma go to ECAL,
      * or to HCAL where ECAL does not cover; hadrons to HCAL; mu/nu to none. */
     int calo = -1, ring = -1;
     if (cls == OR_CLS_E || cls == OR_CLS_GAMMA) {
-      ring = ring_decide(d, i, OR_ECAL, &grid[OR_ECAL], ep, cband);
+      ring = ring_decide(d, i, OR_ECAL, &grid[OR_ECAL], ep);
       if (ring >= 0) calo = OR_ECAL;
       else {
-        ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep, cband);
+        ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep);
         if (ring >= 0) calo = OR_HCAL;
       }
     } else if (cls == OR_CLS_CHAD || cls == OR_CLS_NHAD) {
-      ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep, cband);
+      ring = ring_decide(d, i, OR_HCAL, &grid[OR_HCAL], ep);
       if (ring >= 0) calo = OR_HCAL;
     }
     uint32_t key = OR_NO_KEY;

@@ -259,7 +259,8 @@ def exported_symbols():
 
 
 MATH_FN = {"asin_half": 0, "sin_half_turn": 1, "ln_unit": 2, "log1p_pos": 3, "cos_two_pi": 4, "cosh": 5, "sinh": 6,
-           "asinh": 7, "u01": 8, "normal": 9, "rcp": 10, "sqrt": 11}
+           "asinh": 7, "u01": 8, "normal": 9, "rcp": 10, "sqrt": 11, "exp_ff_hi": 12, "exp_ff_lo": 13,
+           "sinh_ff_hi": 14, "sinh_ff_lo": 15}
 
 
 def math_eval(name: str, x, x2=None, stream=None):

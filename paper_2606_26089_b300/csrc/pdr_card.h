@@ -138,7 +138,10 @@ inline int expand_card(const pdr_card* c, DevCard& D) {
   }
   D.R = (float)c->R;
   D.L = (float)c->L;
-  D.kB = (float)(0.299792458 * std::fabs(c->B));
+  D.L_lo = (float)(c->L - (double)D.L);
+  const double kB = 0.299792458 * std::fabs(c->B);
+  D.kB = (float)kB;
+  D.kB_lo = (float)(kB - (double)D.kB);
   D.Bsign = c->B > 0.0 ? 1 : -1;
   D.has_field = c->B != 0.0;
   for (int q = 1; q <= PDR_MAXQ; ++q) {

@@ -1,11 +1,13 @@
 // Diagnostic entry point: the library's single-precision function
 // approximations (pdr_math.cuh and the cosh / sinh / asinh / smearing helpers
-// of the response kernel), evaluated element-wise on device arrays so a test
+// of the response kernel, and the float-float exponential and sinh of
+// pdr_ff.cuh as their hi and lo parts), evaluated element-wise on device arrays so a test
 // can hold each to its stated error bound over its whole input range.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "pdr.h"
+#include "pdr_ff.cuh"
 #include "pdr_internal.h"
 #include "pdr_math.cuh"
 
@@ -35,6 +37,10 @@ __global__ void math_eval_kernel(int fn, const float* __restrict__ x, const floa
       case PDR_FN_NORMAL: r = normal(__float_as_uint(v), __float_as_uint(x2[k])); break;
       case PDR_FN_RCP: r = rcp_approx(v); break;
       case PDR_FN_SQRT: r = sqrt_approx(v); break;
+      case PDR_FN_EXP_FF_HI: r = exp_ff(v).hi; break;
+      case PDR_FN_EXP_FF_LO: r = exp_ff(v).lo; break;
+      case PDR_FN_SINH_FF_HI: r = sinh_ff(v).hi; break;
+      case PDR_FN_SINH_FF_LO: r = sinh_ff(v).lo; break;
       default: break;
     }
     y[k] = r;

@@ -70,7 +70,7 @@ inline size_t build_hot_card(const DevCard& D, unsigned char* out, size_t cap) {
       std::memcpy(&data[nf++], &packed, sizeof(float));
     }
   }
-  H.R = D.R; H.L = D.L; H.kB = D.kB;
+  H.R = D.R; H.L = D.L; H.kB = D.kB; H.L_lo = D.L_lo; H.kB_lo = D.kB_lo;
   H.Bsign = D.Bsign; H.has_field = D.has_field;
   H.trk_npt = D.trk_npt; H.trk_neta = D.trk_neta; H.id_n = D.id_n;
   for (int k = 0; k < 4; ++k) H.res_n[k] = D.res_n[k];

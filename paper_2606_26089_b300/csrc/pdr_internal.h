@@ -53,7 +53,8 @@ struct DevCard {
   float phi_pool[PDR_PHIPOOL];
   // propagation
   float R, L;                    // float32 of the card values
-  float kB;                      // 0.299792458 |B|
+  float L_lo;                    // L - float32(L)
+  float kB, kB_lo;               // 0.299792458 |B|, split hi + lo
   int32_t Bsign, has_field, pad0;
   float cR_hi[PDR_MAXQ + 1], cR_lo[PDR_MAXQ + 1];  // c = 0.299792458 |q| |B| R, split hi + lo
   // tracking efficiency: pass iff (u64) w < T
@@ -101,7 +102,7 @@ struct HotCalo {
 
 struct alignas(16) HotCard {
   HotCalo calo[2];
-  float R, L, kB;
+  float R, L, kB, L_lo, kB_lo;    // L and 0.299792458 |B| as float32, and their float32 remainders
   int32_t Bsign, has_field, trk_npt, trk_neta, id_n;
   int32_t res_n[4];
   alignas(16) float trk_pt_edges[PDR_MAXEDGE];

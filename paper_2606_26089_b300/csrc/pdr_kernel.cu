@@ -32,6 +32,7 @@
 
 #include <mutex>
 
+#include "pdr_ff.cuh"
 #include "pdr_internal.h"
 #include "pdr_ip.cuh"
 #include "pdr_math.cuh"
@@ -125,7 +126,11 @@ struct Prop {
 // reached iff 2 pT >= c = 0.299792458 |q| |B| R, at turning angle
 // 2 asin(c / 2pT); otherwise the endcap after psi = s_z / r < 2 pi.  Both
 // crossings are computed for every particle and the valid one is selected
-// (one path for the warp instead of four).
+// (one path for the warp instead of four).  UNIFORM: the near-loop
+// recomputation below runs as a warp-uniform branch over the lanes that need
+// it (one-warp teams, whose warps run apart); otherwise as a divergent branch
+// around an out-of-line call.
+template <bool UNIFORM>
 __device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta, float sh, float phi,
                                           int q, float vz) {
   const bool charged = q != 0 && K.has_field;
@@ -149,18 +154,44 @@ __device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta,
   const float zb = fmaf(charged ? 2.0f * r * a : K.R, sh, vz);
   const bool barrel = (!charged || twopt >= cR) && fabsf(zb) <= K.L;
   // endcap: the transverse distance rho at z = +-L is s_z = (z_e - vz) / sinh(eta)
-  // for a straight line, 2 r sin(psi / 2) for the helix (psi = s_z / r)
+  // for a straight line, 2 r sin(psi / 2) for the helix, psi = s_z / r taken as
+  // (z_e - vz) kq / (pT sinh(eta)) (relative error below 7.5e-7: the card's L
+  // to float32 and its remainder, six roundings, sinh's 4e-7 and the
+  // reciprocal's 2^-23)
   const float ze = sh > 0.0f ? K.L : -K.L;
   const float sz = fdiv(ze - vz, sh);
-  const float psi = fdiv(sz, r);
-  const float rho = charged ? 2.0f * r * sin_half_turn(fminf(0.5f * psi, PI_F)) : sz;
-  const bool endcap = sh != 0.0f && (!charged || psi < TWO_PI_F);  // else pz = 0, or a looper
-  Prop P;
-  P.reach = (fabsf(vz) <= K.L) && (barrel || endcap);
+  const float psi = ((ze - vz) + (sh > 0.0f ? K.L_lo : -K.L_lo)) * kq * rcp_approx(pt * sh);
+  const float yh = 0.5f * psi;
+  const float sy = sin_half_turn(fminf(yh, PI_F));
+  bool endcap = sh != 0.0f && (!charged || psi < TWO_PI_F);  // else pz = 0, or a looper
   // a straight line from the axis origin keeps its direction
   const bool origin = !charged && vz == 0.0f;
+  float eta_s = origin ? eta : asinh_fast(barrel ? fdiv(zb, K.R) : fdiv(ze, charged ? 2.0f * r * sy : sz));
+  // A helix that has nearly closed (psi / 2 -> pi): eta_pos carries psi's
+  // relative error times |(psi/2) cot(psi/2)| = (psi/2) cos(d) / sin(d),
+  // d = pi - psi/2, on top of the endcap path's other roundings (below
+  // 6e-7 + 2.5e-7 max(|eta_pos|, 1)).  Where that sum could pass
+  // 2e-6 max(|eta_pos|, 1), pi - psi/2 is recomputed in float-float
+  // (half_turn_gap) and the loop decision taken on it.
+  const bool near_loop = charged && !barrel && yh >= 1.6f && yh <= 3.1417f &&
+                         !(7.5e-7f * yh * sqrt_approx(fmaf(-sy, sy, 1.0f)) <=
+                           fmaf(1.75e-6f, fmaxf(fabsf(eta_s), 1.0f), -6e-7f) * sy);
+  if constexpr (UNIFORM) {
+    if (__any_sync(__activemask(), near_loop)) {
+      const float g = half_turn_gap(pt, eta, vz, aq, K.L, K.L_lo, K.kB, K.kB_lo);
+      const float es = asinh_fast(fdiv(ze, 2.0f * r * sin_quarter(fmaxf(g, 0.0f))));
+      endcap = near_loop ? g > 0.0f : endcap;
+      eta_s = near_loop ? es : eta_s;
+    }
+  } else if (near_loop) {
+    const float g = half_turn_gap_call(pt, eta, vz, aq, K.L, K.L_lo, K.kB, K.kB_lo);
+    endcap = g > 0.0f;
+    eta_s = asinh_fast(fdiv(ze, 2.0f * r * sin_quarter(fmaxf(g, 0.0f))));
+  }
+  Prop P;
+  P.reach = (fabsf(vz) <= K.L) && (barrel || endcap);
   P.barrel = P.reach && (origin ? fabsf(K.R * sh) <= K.L : barrel);
-  P.eta_pos = P.reach ? (origin ? eta : asinh_fast(barrel ? fdiv(zb, K.R) : fdiv(ze, rho))) : 0.0f;
+  P.eta_pos = P.reach ? eta_s : 0.0f;
   const float turn = charged ? h * (barrel ? a : 0.5f * psi) : 0.0f;
   float pphi = phi - turn;
   pphi = pphi < -PI_F ? pphi + TWO_PI_F : (pphi >= PI_F ? pphi - TWO_PI_F : pphi);
@@ -289,6 +320,7 @@ struct PartA {
 // tracking-efficiency table (0 hadron, 1 electron, 2 muon) << 24 | photon << 28.
 #define PDR_JOB_PHOTON (1u << 28)
 
+template <int TEAM>
 __device__ __forceinline__ void particle_stage_a(const KSeg& S, const HotCard& K, const float* KD,
                                                  uint64_t g, uint32_t i, PartA& o) {
   g = PDR_B(S, g);
@@ -306,7 +338,7 @@ __device__ __forceinline__ void particle_stage_a(const KSeg& S, const HotCard& K
   o.E = sqrt_approx(fmaf(pc, pc, M * M));
   if (cls == CLS_INVIS) return;
   // S1
-  const Prop P = propagate(K, PT, ETA, sh, PHI, Q, VZ);
+  const Prop P = propagate<TEAM == 32>(K, PT, ETA, sh, PHI, Q, VZ);
   if (!P.reach) return;
   o.flags = PDR_F_REACH | (P.barrel ? PDR_F_BARREL : 0u);
   o.eta_pos = P.eta_pos;
@@ -581,7 +613,7 @@ __device__ __forceinline__ bool process_event(const KSeg& S, uint32_t* err, cons
     const bool valid = i < n;
     PartA o;
     o.key = PDR_NO_KEY; o.E = 0.0f; o.job = PDR_EMPTY;
-    if (valid) particle_stage_a(S, K, KD, a + i, i, o);
+    if (valid) particle_stage_a<TEAM>(S, K, KD, a + i, i, o);
     uint32_t slot = PDR_EMPTY;
     bool claimed = false;
     const unsigned long long e_fp = to_fp(o.E);

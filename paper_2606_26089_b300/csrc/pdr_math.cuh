@@ -33,8 +33,9 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return make_uint4(c0, c1, c2, c3);
 }
 
-// Reciprocal to 1 ulp (the hardware approximation; relative error below
-// 2^-22 over 1e-20 ... 1e20); used where the result only needs a few ulp:
+// Reciprocal to 1 ulp (the hardware approximation, 1 ulp at most by the PTX
+// ISA: relative error below 2^-23 over 1e-20 ... 1e20); used where the result
+// only needs a few ulp:
 // every such quotient feeds either an output compared at 2e-6 relative or a
 // decision taken with the 1e-5 marginal band.
 __device__ __forceinline__ float rcp_approx(float x) {

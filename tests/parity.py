@@ -16,11 +16,10 @@ Comparison protocol
   not marginal is a failure.
 * Floats: smeared kinematics and tower energies within REL = 2e-6 relative;
   the energy-flow excess dE (a cancellation) within REL * max(E', E_track);
-  propagated positions within REL * max(|eta|, 1) + 16 * 2^-24 * cond and
-  REL * pi, where cond = |d eta_pos / d ln psi| is the oracle's conditioning of
-  eta_pos on the helix turning angle psi (large only for endcap helices that
-  have nearly closed, psi -> 2 pi); the same term widens the marginal band of
-  that particle's eta-ring decisions.
+  propagated positions within REL * max(|eta|, 1) and REL * pi, also for
+  endcap helices that have nearly closed (turning angle psi -> 2 pi), whose
+  eta_pos is ill-conditioned in psi: the kernel takes pi - psi/2 in
+  float-float there.
 * Records come in particle order (towers and EFlow neutrals in the order of
   their lowest depositing particle), so sequences are compared exactly.
 """
@@ -36,7 +35,6 @@ import oracle
 
 REL = 2e-6
 G_BAND = 1e-5
-COND_ULPS = 16.0
 
 
 @dataclass
@@ -219,12 +217,13 @@ def compare_event(card, ev: dict, g: dict, seed: int, event: int, stats: Stats, 
         assert np.array_equal(gf, p["flags"].astype(np.uint32)), \
             f"flags differ at {np.flatnonzero(gf != p['flags'])[:5]}"
         reach = (p["flags"] & oracle.F_REACH) != 0
-        # eta_pos of an endcap helix that has nearly closed is ill-conditioned in
-        # the turning angle: allow float32's error on psi times that conditioning
-        tol_e = REL * np.maximum(np.abs(p["eta_pos"][reach]), 1.0) + COND_ULPS * 2.0**-24 * p["cond"][reach]
+        tol_e = REL * np.maximum(np.abs(p["eta_pos"][reach]), 1.0)
         e_err = np.abs(d["eta_pos"][reach] - p["eta_pos"][reach]) / tol_e * REL
         p_err = _dphi(d["phi_pos"][reach], p["phi_pos"][reach]) / math.pi
         if reach.any():
+            # (the largest conditioning of eta_pos on the turning angle seen:
+            # context for the eta_pos error, not an error itself)
+            stats.upd("eta_pos_cond", p["cond"][reach].max())
             stats.upd("eta_pos", e_err.max())
             stats.upd("phi_pos", p_err.max())
             assert e_err.max() <= REL, f"eta_pos error {e_err.max()}"

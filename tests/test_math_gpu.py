@@ -137,7 +137,32 @@ def test_reciprocal_and_square_root(B):
     rr = np.abs(r * x64 - 1)
     rq = np.abs(q / np.sqrt(x64) - 1)
     print("rcp max rel", rr.max(), "sqrt max rel", rq.max())
-    assert rr.max() <= 2.0**-22 and rq.max() <= 2.0**-22
+    assert rr.max() <= 2.0**-23 and rq.max() <= 2.0**-22
+
+
+def _ff(B, name, x):
+    hi = _ev(B, name + "_hi", x).astype(np.longdouble)
+    lo = _ev(B, name + "_lo", x).astype(np.longdouble)
+    return hi + lo
+
+
+def test_float_float_exponential(B):
+    x = np.concatenate([_grid(0.0, 88.0, 1 << 23), _grid(0.0, 1.0, 1 << 21)])
+    ref = np.exp(x.astype(np.longdouble))
+    rel = (np.abs(_ff(B, "exp_ff", x) - ref) / ref).astype(np.float64)
+    print("exp_ff max rel", rel.max(), "= 2^", np.log2(rel.max()))
+    assert rel.max() <= 2.0**-42
+
+
+def test_float_float_sinh(B):
+    x = np.concatenate([_grid(0.0, 88.0, 1 << 23), _grid(0.0, 1.0, 1 << 21), _grid(0.0, 1.0 / 32, 1 << 20),
+                        np.geomspace(1e-30, 1e-2, 1 << 16).astype(np.float32)])
+    ref = np.sinh(x.astype(np.longdouble))
+    err = np.abs(_ff(B, "sinh_ff", x) - ref)
+    rel = np.where(ref > 0, err / np.where(ref > 0, ref, 1), err).astype(np.float64)
+    print("sinh_ff max rel", rel.max(), "= 2^", np.log2(rel.max()),
+          "from 1/4 up", rel[x >= 0.25].max(), "= 2^", np.log2(rel[x >= 0.25].max()))
+    assert rel.max() <= 2.0**-36 and rel[x >= 0.25].max() <= 2.0**-41
 
 
 def test_unknown_function_is_rejected(B):
