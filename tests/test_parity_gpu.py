@@ -179,6 +179,50 @@ def test_charges_and_field_directions(B, ctx, synth):
         _check_all(ctx, ctx_card, f"B{field}", b, seed=17)
 
 
+def _near_loop_events(card: dict, rng):
+    """Charged helices that reach the endcap having nearly closed: for each
+    gap d = pi - psi/2 from 1.2 down to 1e-5, pT solved from
+    psi = (L - sign(eta) vz) kq / (pT sinh|eta|) = 2 (pi - d), over |eta|,
+    both signs, vertices and charges; plus |eta| < 1/4 ones, which need a
+    vertex near the endcap, down to d = 1e-4."""
+    L, B = card["L"], card["B"]
+    rows = []
+    for d in np.geomspace(1e-5, 1.2, 14):
+        for aeta in (0.3, 0.8, 1.5, 2.5, 4.0):
+            for sgn in (1.0, -1.0):
+                for vz in (0.0, 0.12, -0.12):
+                    for q in (1, -1, 2):
+                        kq = 0.299792458 * abs(q) * abs(B)
+                        pt = (L - sgn * vz) * kq / (2.0 * (np.pi - d) * np.sinh(aeta))
+                        pdg = {1: 211, -1: -211, 2: 1000020040}[q]
+                        mass = 0.13957039 if abs(q) == 1 else 3.727
+                        rows.append((pt, sgn * aeta, float(rng.uniform(-np.pi, np.pi)), mass, pdg, q, vz))
+    for d in np.geomspace(1e-4, 1.0, 8):
+        for aeta in (0.05, 0.12, 0.2):
+            for sgn in (1.0, -1.0):
+                vz = sgn * (L - 0.04)
+                kq = 0.299792458 * abs(B)
+                pt = (L - sgn * vz) * kq / (2.0 * (np.pi - d) * np.sinh(aeta))
+                rows.append((pt, sgn * aeta, float(rng.uniform(-np.pi, np.pi)), 0.13957039, 211, 1, vz))
+    return [rows[k:k + 60] for k in range(0, len(rows), 60)]
+
+
+def test_nearly_closed_endcap_helices(B, ctx, synth):
+    """eta_pos of helices that nearly close before the endcap is
+    ill-conditioned in the turning angle (up to 3e5 here); the kernel takes
+    pi - psi/2 in float-float there, so these positions must meet the same
+    2e-6 max(|eta|, 1) as every other, under the usual flip protocol."""
+    import json
+    for name in ("cms_like", "atlas_like", "ee_like"):
+        card = json.load(open(B.card_path(name)))
+        b = synth.from_particles(_near_loop_events(card, np.random.default_rng(41)))
+        cid, ocard = ctx.card_load(name), oracle.load_card(name)
+        host, stats = _check_all(ctx, {name: (cid, ocard)}, name, b, seed=23)
+        print(name, b.n_particles, "particles; max cond", stats.max_rel.get("eta_pos_cond"),
+              "eta_pos error / tolerance x 2e-6", stats.max_rel.get("eta_pos"))
+        assert stats.max_rel.get("eta_pos_cond", 0.0) > 1e5   # the cases do reach deep into the ill-conditioned range
+
+
 def test_event_larger_than_shared_table(B, ctx, cards, synth):
     # one 12k-particle event (beyond the 8192-slot shared-memory table) next to normal ones
     big = synth.make("pileup", n_events=3)
