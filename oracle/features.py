@@ -129,11 +129,12 @@ def condition(obj: dict, cond: dict, g: float):
     return m, marg
 
 
-def keep_mask(obj: dict, conds: Sequence[dict], combine: str = "all", g: float = 1e-5):
-    """(keep mask, number of marginal decisions) of a filter on one collection."""
+def keep_and_marginal(obj: dict, conds: Sequence[dict], combine: str = "all", g: float = 1e-5):
+    """(keep mask, marginal mask) of a filter on one collection: an object is
+    marginal when any of its float conditions is."""
     n = len(obj["pt"])
     if not conds:
-        return np.ones(n, bool), 0
+        return np.ones(n, bool), np.zeros(n, bool)
     if combine not in ("all", "any"):
         raise ValueError(combine)
     keep = np.ones(n, bool) if combine == "all" else np.zeros(n, bool)
@@ -142,18 +143,29 @@ def keep_mask(obj: dict, conds: Sequence[dict], combine: str = "all", g: float =
         m, mg = condition(obj, c, g)
         keep = keep & m if combine == "all" else keep | m
         marg |= mg
+    return keep, marg
+
+
+def keep_mask(obj: dict, conds: Sequence[dict], combine: str = "all", g: float = 1e-5):
+    """(keep mask, number of marginal decisions) of a filter on one collection."""
+    keep, marg = keep_and_marginal(obj, conds, combine, g)
     return keep, int(marg.sum())
 
 
-def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5) -> dict:
+def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5, flips: Optional[dict] = None) -> dict:
     """Filter one event's collections and compute H_T, missing E_T.
 
     ``filt`` = {"collection": one of COLLECTIONS, "combine": "all"|"any",
     "conditions": [...], "update_event_features": bool} or None (no filter).
+    ``flips`` = {collection: object positions} takes those objects' filter
+    decisions the other way; each must be marginal (ValueError otherwise),
+    as the response oracle refuses to flip a decision that is not.
     Returns the surviving records' positions per collection ("keep"), the
-    features and the number of marginal decisions."""
+    features, the number of marginal decisions and their positions
+    ("marginal_at")."""
     obj = objects(ref, ev)
     keep = {k: np.ones(len(v["pt"]), bool) for k, v in obj.items()}
+    marginal_at = {k: np.zeros(0, np.int64) for k in obj}
     n_marg = 0
     coll = None
     if filt is not None:
@@ -162,8 +174,16 @@ def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5) -> dic
             raise ValueError(coll)
         targets = ("track", "neutral") if coll == "pflow" else (coll,)
         for k in targets:
-            keep[k], m = keep_mask(obj[k], filt.get("conditions", []), filt.get("combine", "all"), g)
-            n_marg += m
+            keep[k], mg = keep_and_marginal(obj[k], filt.get("conditions", []), filt.get("combine", "all"), g)
+            marginal_at[k] = np.flatnonzero(mg)
+            n_marg += int(mg.sum())
+            f = np.asarray((flips or {}).get(k, ()), np.int64)
+            if len(f):
+                if not np.all(mg[f]):
+                    raise ValueError(f"flip of a {k} filter decision that is not marginal")
+                keep[k][f] = ~keep[k][f]
+    if flips and any(len(v) for k, v in flips.items() if k not in marginal_at or not len(marginal_at[k])):
+        raise ValueError("flip of a decision the filter did not take")
     from_survivors = filt is None or bool(filt.get("update_event_features", True))
     ht = mx = my = 0.0
     scale = 0.0  # sum of the terms' rounding scales (the pT, or a neutral's scale_pt if larger)
@@ -179,7 +199,7 @@ def event_features(ref, ev, filt: Optional[dict] = None, g: float = 1e-5) -> dic
         scale += float(np.maximum(np.abs(pt), sc[sel]).sum() if sc is not None else np.abs(pt).sum())
         n_terms += int(sel.sum())
     return {"keep": keep, "objects": obj, "ht": ht, "met_x": mx, "met_y": my, "met": float(np.hypot(mx, my)),
-            "marginal": n_marg, "scale": scale, "n_terms": n_terms}
+            "marginal": n_marg, "marginal_at": marginal_at, "scale": scale, "n_terms": n_terms}
 
 
 def pflow_four_momenta(ref, ev):

@@ -23,7 +23,6 @@ namespace pdr {
 namespace {
 
 constexpr float PDR_FEAT_Q = 16777216.0f;   // 2^24 per GeV
-constexpr double PDR_FEAT_INV_Q = 1.0 / 16777216.0;
 
 // One record's fields (the float ones; pdg and charge separately).
 struct Obj {
@@ -119,6 +118,17 @@ __device__ __forceinline__ long long to_q(float x) {
   return x < 0.0f ? -(long long)u : (long long)u;
 }
 
+// A fixed-point sum v (|v| < 2^55) in GeV as float32, with 32-bit conversions
+// only (64-bit integer and double conversions run on the FP64 pipe, of which
+// B300 has little): v = h 2^32 + l with h the signed high word (exact in
+// float32 below 2^24) and l the unsigned low word; relative error below one
+// float32 ulp plus 2^7 / |v|.
+__device__ __forceinline__ float from_q(long long v) {
+  const float h = (float)(int32_t)(v >> 32);
+  const float l = __uint2float_rn((uint32_t)(unsigned long long)v);
+  return fmaf(h, 4294967296.0f, l) * (1.0f / PDR_FEAT_Q);
+}
+
 // Slot of a surviving lane's record among this chunk's survivors.
 __device__ __forceinline__ uint32_t rank_in(uint32_t mask, uint32_t lane) {
   return __popc(mask & ((1u << lane) - 1u));
@@ -133,7 +143,7 @@ __device__ __forceinline__ void add_term(float pt, float phi, long long& ht, lon
   my -= to_q(pt * sn);
 }
 
-__global__ void __launch_bounds__(256) postprocess_kernel(const __grid_constant__ PostParams p) {
+__global__ void __launch_bounds__(256, 5) postprocess_kernel(const __grid_constant__ PostParams p) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t w0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -278,9 +288,8 @@ __global__ void __launch_bounds__(256) postprocess_kernel(const __grid_constant_
         p.counts[4 * e + 3] = wc;
       }
       if (p.features) {
-        const double x = (double)mx * PDR_FEAT_INV_Q, y = (double)my * PDR_FEAT_INV_Q;
-        p.features[e] = pdr_features{(float)((double)ht * PDR_FEAT_INV_Q), (float)x, (float)y,
-                                     (float)sqrt(x * x + y * y)};
+        const float x = from_q(mx), y = from_q(my);
+        p.features[e] = pdr_features{from_q(ht), x, y, sqrtf(fmaf(x, x, y * y))};
       }
     }
   }

@@ -180,3 +180,26 @@ def test_track_energy_is_the_mass_shell(real_event):
     n = F.objects(ref, ev)["neutral"]
     assert np.array_equal(n["pdg"] == 22, (n["key"] >> 24) == 0)
     assert np.allclose(n["pt"] * np.cosh(n["eta"]), n["e"], rtol=1e-12)
+
+
+def test_marginal_filter_decisions_flip_and_others_refuse():
+    """A threshold within the band g of a track's pT makes that decision
+    marginal; taking it the other way drops (or keeps) exactly that track and
+    moves H_T and the missing E_T by its own terms.  Flipping a decision that
+    is not marginal, or one on a collection the filter does not target, is
+    refused, as for the response's decisions."""
+    ref, ev = _hand_event()
+    spec = {"collection": "track", "conditions": [{"field": "pt", "op": ">", "value": 20.0 * (1 - 1e-6)}]}
+    f = F.event_features(ref, ev, spec)
+    # the 20 GeV track passes (20 > 19.99998) but sits within 1e-5 of the threshold
+    assert list(f["keep"]["track"]) == [False, True, False] and list(f["marginal_at"]["track"]) == [1]
+    assert f["ht"] == pytest.approx(20.0 + 3.0 + 4.0)
+    g = F.event_features(ref, ev, spec, flips={"track": [1]})
+    assert list(g["keep"]["track"]) == [False, False, False]
+    assert g["ht"] == pytest.approx(f["ht"] - 20.0)
+    # the 20 GeV track at phi = pi contributed +20 to the missing E_x
+    assert g["met_x"] == pytest.approx(f["met_x"] - 20.0) and g["met_y"] == pytest.approx(f["met_y"])
+    with pytest.raises(ValueError):
+        F.event_features(ref, ev, spec, flips={"track": [0]})
+    with pytest.raises(ValueError):
+        F.event_features(ref, ev, spec, flips={"neutral": [0]})

@@ -12,10 +12,16 @@ components must agree within 3e-6 of the sum of the terms' magnitudes plus
 the fixed-point quantum per term: each term carries the response's 2e-6
 relative error, the hardware sine/cosine's 4e-7 absolute error on |phi| <=
 pi, 2e-7 from a tower centre's float32 azimuth and a rounding of the
-product.  Events where a filter decision lies within rounding of
-its threshold are counted and skipped (the two sides may take it either
-way).
+product.  A filter decision whose value lies within the band g of its
+threshold is marginal: where the GPU took one the other way (seen in the
+surviving records), the oracle is re-run with that decision flipped, and it
+refuses to flip one that is not marginal; without compaction, where the
+survivors are not visible, the features must match the oracle's with some
+combination of the event's marginal decisions flipped.  No event is skipped;
+the marginal and flip counts are printed.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -75,17 +81,56 @@ def _run(B, ctx, setup, spec, compact=True):
     return host, feats.cpu().numpy()
 
 
+def _gpu_keep(o, ref, g):
+    """The GPU's filter decisions on the oracle's objects, from its surviving records."""
+    return {"track": np.isin(ref.tracks["idx"], g["tracks"]["idx"]),
+            "neutral": np.isin(o["objects"]["neutral"]["key"], g["eflow"]["key"]),
+            "tower": np.isin(o["objects"]["tower"]["key"], g["towers"]["key"]),
+            "cand": np.isin(ref.cands["idx"], g["cands"]["info"] & 0x0FFFFFFF)}
+
+
+def _features_ok(o, f):
+    tol = 3e-6 * o["scale"] + o["n_terms"] * 2.0**-25 + 1e-6
+    return (abs(f[0] - o["ht"]) <= tol + 6e-8 * o["ht"] and abs(f[1] - o["met_x"]) <= tol + 6e-8 * abs(o["met_x"])
+            and abs(f[2] - o["met_y"]) <= tol + 6e-8 * abs(o["met_y"])
+            and abs(f[3] - o["met"]) <= 1.5 * tol + 6e-8 * o["met"])
+
+
 def _check(B, ctx, setup, spec, compact=True):
     batch, cid, dev, refs = setup
     host, feats = _run(B, ctx, setup, spec, compact)
-    skipped = 0
+    n_marg = n_flip = 0
     for e in range(batch.n_events):
         ev = batch.event(e)
         o = OF.event_features(refs[e], ev, spec)
-        if o["marginal"]:
-            skipped += 1
-            continue
         g = B.event_records(host, host["counts"], batch.offsets, e)
+        n_marg += o["marginal"]
+        if o["marginal"] and spec is not None:
+            if compact:
+                # the decisions the GPU took the other way (the oracle refuses non-marginal ones)
+                gk = _gpu_keep(o, refs[e], g)
+                flips = {k: np.flatnonzero(gk[k] != o["keep"][k]) for k in o["marginal_at"]}
+                flips = {k: v for k, v in flips.items() if len(v)}
+                if flips:
+                    o = OF.event_features(refs[e], ev, spec, flips=flips)
+                    n_flip += sum(len(v) for v in flips.values())
+            elif spec.get("update_event_features", True):
+                # survivors not visible: some combination of marginal flips must give the GPU's features
+                at = [(k, int(j)) for k, v in o["marginal_at"].items() for j in v]
+                assert len(at) <= 10, (e, len(at))
+                for r in range(len(at) + 1):
+                    for sub in itertools.combinations(at, r):
+                        fl = {}
+                        for k, j in sub:
+                            fl.setdefault(k, []).append(j)
+                        oc = OF.event_features(refs[e], ev, spec, flips=fl) if fl else o
+                        if _features_ok(oc, feats[e]):
+                            o = oc
+                            n_flip += r
+                            break
+                    else:
+                        continue
+                    break
         keep = o["keep"] if compact or spec is None else {k: np.ones_like(v) for k, v in o["keep"].items()}
         assert np.array_equal(g["tracks"]["idx"], refs[e].tracks["idx"][keep["track"]]), (e, "tracks")
         assert np.array_equal(g["eflow"]["key"], o["objects"]["neutral"]["key"][keep["neutral"]]), (e, "neutrals")
@@ -100,7 +145,8 @@ def _check(B, ctx, setup, spec, compact=True):
         assert abs(feats[e, 1] - o["met_x"]) <= tol + 6e-8 * abs(o["met_x"]), (e, feats[e, 1], o["met_x"])
         assert abs(feats[e, 2] - o["met_y"]) <= tol + 6e-8 * abs(o["met_y"]), (e, feats[e, 2], o["met_y"])
         assert abs(feats[e, 3] - o["met"]) <= 1.5 * tol + 6e-8 * o["met"], (e, feats[e, 3], o["met"])
-    assert skipped <= max(2, batch.n_events // 20), f"{skipped} events with marginal filter decisions"
+    print(f"filter {spec and spec.get('collection')}: {batch.n_events} events, marginal filter decisions "
+          f"{n_marg}, flipped {n_flip}")
     return host, feats
 
 
@@ -167,3 +213,18 @@ def test_bad_filters_are_rejected(B, ctx, setup):
     f.n_conditions = 9
     with pytest.raises(B.PdrError):
         ctx.postprocess(b, B.make_outputs(outs), f, None)
+
+
+def test_decisions_at_the_threshold_go_through_the_flip_protocol(B, ctx, setup):
+    """Thresholds equal to the oracle's own float32 pT of chosen tracks: those
+    decisions are marginal by construction, the GPU's smeared pT (within 2e-6)
+    may fall on either side, and every decision it takes the other way must be
+    one the oracle accepts flipped; compacted and not."""
+    batch, cid, dev, refs = setup
+    picks = [(e, j) for e in range(0, batch.n_events, 17) for j in (0, 3) if len(refs[e].tracks) > j][:8]
+    conds = [{"field": "pt", "op": "==", "value": float(np.float32(refs[e].tracks["pt"][j]))} for e, j in picks]
+    spec = {"collection": "track", "combine": "any", "conditions": conds}
+    for compact in (True, False):
+        host, feats = _check(B, ctx, setup, spec, compact=compact)
+    n_marg = sum(OF.event_features(refs[e], batch.event(e), spec)["marginal"] for e in range(batch.n_events))
+    assert n_marg >= len(picks)
