@@ -218,7 +218,10 @@ def compare_event(card, ev: dict, g: dict, seed: int, event: int, stats: Stats, 
             f"flags differ at {np.flatnonzero(gf != p['flags'])[:5]}"
         reach = (p["flags"] & oracle.F_REACH) != 0
         tol_e = REL * np.maximum(np.abs(p["eta_pos"][reach]), 1.0)
-        e_err = np.abs(d["eta_pos"][reach] - p["eta_pos"][reach]) / tol_e * REL
+        ge, oe = d["eta_pos"][reach].astype(np.float64), p["eta_pos"][reach]
+        # (a helix that ends on the axis at the endcap has eta_pos = +-inf on both sides)
+        with np.errstate(invalid="ignore"):
+            e_err = np.where(ge == oe, 0.0, np.abs(ge - oe) / tol_e * REL)
         p_err = _dphi(d["phi_pos"][reach], p["phi_pos"][reach]) / math.pi
         if reach.any():
             # (the largest conditioning of eta_pos on the turning angle seen:

@@ -153,6 +153,28 @@ def test_empty_and_degenerate_events(B, ctx, cards, synth):
     assert h["counts"].shape[0] == 0
 
 
+def test_extreme_kinematics(B, ctx, cards, synth):
+    """Inputs at the edges of the method's domain, each against the oracle:
+    azimuth exactly +-pi in float32, photons from the origin exactly on
+    calorimeter ring edges, vertices exactly at and just beyond the endcap
+    (a helix that ends on the axis: eta_pos = +-inf on both sides), pT of
+    1e-30 (a looper) and 1e4 GeV, |eta| up to 15, and both charges."""
+    cid, ocard = cards["cms_like"]
+    M = 0.13957039
+    pi32 = float(np.float32(np.pi))
+    edges = [0.0, 0.0174, 0.087, 1.4964, 3.0, -1.4964, 4.959]
+    ev1 = [(5.0, 0.7, pi32, M, 211, 1), (5.0, -0.7, -pi32, M, -211, -1), (8.0, 0.2, pi32, 0.0, 22, 0),
+           (8.0, 0.2, -pi32, 0.0, 22, 0)]
+    ev1 += [(12.0, float(np.float32(x)), 0.3, 0.0, 22, 0) for x in edges]
+    ev1 += [(12.0, float(np.float32(x)), 0.3, 0.497611, 130, 0) for x in edges]
+    ev2 = [(2.0, 1.0, 0.5, M, 211, 1, 3.0), (2.0, -1.0, 0.5, M, -211, -1, -3.0), (2.0, 1.0, 0.5, M, 211, 1, 3.0001),
+           (4.0, 0.5, 0.5, 0.0, 22, 0, 3.0), (4.0, -0.5, 0.5, 0.0, 22, 0, -3.0), (1e-30, 2.0, 0.0, M, 211, 1, 0.0),
+           (1e4, 0.1, 1.0, M, -211, -1, 0.0), (1e4, 2.9, -1.0, 0.000511, 11, -1, 0.02),
+           (30.0, 15.0, 0.0, M, 211, 1, 0.0), (30.0, -15.0, 0.0, 0.0, 22, 0, 0.05), (30.0, 8.0, 2.0, 0.0, 22, 0, 0.0)]
+    b = synth.from_particles([ev1, ev2, [p[:6] for p in ev2]])
+    _check_all(ctx, cards, "cms_like", b, seed=19)
+
+
 def test_charges_and_field_directions(B, ctx, synth):
     """Multiply charged particles (|q| = 2, and |q| = 10 beyond the table of
     precomputed reach constants), vertices off the origin, and the CMS-like
