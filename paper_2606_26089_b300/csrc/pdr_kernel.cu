@@ -159,14 +159,16 @@ __device__ __forceinline__ Prop propagate(const HotCard& K, float pt, float eta,
   // to float32 and its remainder, six roundings, sinh's 4e-7 and the
   // reciprocal's 2^-23)
   const float ze = sh > 0.0f ? K.L : -K.L;
-  const float sz = fdiv(ze - vz, sh);
-  const float psi = ((ze - vz) + (sh > 0.0f ? K.L_lo : -K.L_lo)) * kq * rcp_approx(pt * sh);
+  const float dz = (ze - vz) + (sh > 0.0f ? K.L_lo : -K.L_lo);   // z_e - vz with the card's L to 2^-48
+  const float sz = fdiv(dz, sh);
+  const float psi = dz * kq * rcp_approx(pt * sh);
   const float yh = 0.5f * psi;
   const float sy = sin_half_turn(fminf(yh, PI_F));
   bool endcap = sh != 0.0f && (!charged || psi < TWO_PI_F);  // else pz = 0, or a looper
   // a straight line from the axis origin keeps its direction
   const bool origin = !charged && vz == 0.0f;
-  float eta_s = origin ? eta : asinh_fast(barrel ? fdiv(zb, K.R) : fdiv(ze, charged ? 2.0f * r * sy : sz));
+  // (rho = 2 r |sin(psi / 2)|: psi < 0 for a vertex just beyond the endcap plane)
+  float eta_s = origin ? eta : asinh_fast(barrel ? fdiv(zb, K.R) : fdiv(ze, charged ? 2.0f * r * fabsf(sy) : sz));
   // A helix that has nearly closed (psi / 2 -> pi): eta_pos carries psi's
   // relative error times |(psi/2) cot(psi/2)| = (psi/2) cos(d) / sin(d),
   // d = pi - psi/2, on top of the endcap path's other roundings (below

@@ -159,20 +159,28 @@ def test_extreme_kinematics(B, ctx, cards, synth):
     calorimeter ring edges, vertices exactly at and just beyond the endcap
     (a helix that ends on the axis: eta_pos = +-inf on both sides), pT of
     1e-30 (a looper) and 1e4 GeV, |eta| up to 15, and both charges."""
-    cid, ocard = cards["cms_like"]
+    import json
+    for name in ("cms_like", "atlas_like", "ee_like"):
+        L = float(json.load(open(B.card_path(name)))["L"])
+        b = _extreme_events(synth, L)
+        _check_all(ctx, cards, name, b, seed=19)
+
+
+def _extreme_events(synth, L):
     M = 0.13957039
     pi32 = float(np.float32(np.pi))
+    # ring edges of the CMS-like card (ordinary values on the others)
     edges = [0.0, 0.0174, 0.087, 1.4964, 3.0, -1.4964, 4.959]
     ev1 = [(5.0, 0.7, pi32, M, 211, 1), (5.0, -0.7, -pi32, M, -211, -1), (8.0, 0.2, pi32, 0.0, 22, 0),
            (8.0, 0.2, -pi32, 0.0, 22, 0)]
     ev1 += [(12.0, float(np.float32(x)), 0.3, 0.0, 22, 0) for x in edges]
     ev1 += [(12.0, float(np.float32(x)), 0.3, 0.497611, 130, 0) for x in edges]
-    ev2 = [(2.0, 1.0, 0.5, M, 211, 1, 3.0), (2.0, -1.0, 0.5, M, -211, -1, -3.0), (2.0, 1.0, 0.5, M, 211, 1, 3.0001),
-           (4.0, 0.5, 0.5, 0.0, 22, 0, 3.0), (4.0, -0.5, 0.5, 0.0, 22, 0, -3.0), (1e-30, 2.0, 0.0, M, 211, 1, 0.0),
+    above = float(np.nextafter(np.float32(L), np.float32(np.inf)))
+    ev2 = [(2.0, 1.0, 0.5, M, 211, 1, L), (2.0, -1.0, 0.5, M, -211, -1, -L), (2.0, 1.0, 0.5, M, 211, 1, above),
+           (4.0, 0.5, 0.5, 0.0, 22, 0, L), (4.0, -0.5, 0.5, 0.0, 22, 0, -L), (1e-30, 2.0, 0.0, M, 211, 1, 0.0),
            (1e4, 0.1, 1.0, M, -211, -1, 0.0), (1e4, 2.9, -1.0, 0.000511, 11, -1, 0.02),
            (30.0, 15.0, 0.0, M, 211, 1, 0.0), (30.0, -15.0, 0.0, 0.0, 22, 0, 0.05), (30.0, 8.0, 2.0, 0.0, 22, 0, 0.0)]
-    b = synth.from_particles([ev1, ev2, [p[:6] for p in ev2]])
-    _check_all(ctx, cards, "cms_like", b, seed=19)
+    return synth.from_particles([ev1, ev2, [p[:6] for p in ev2]])
 
 
 def test_charges_and_field_directions(B, ctx, synth):
