@@ -183,6 +183,44 @@ def _extreme_events(synth, L):
     return synth.from_particles([ev1, ev2, [p[:6] for p in ev2]])
 
 
+def test_stage_boundaries(B, ctx, cards, synth):
+    """Inputs exactly on the CMS-like card's decision boundaries, against the
+    oracle (marginal decisions through the flip protocol): tracking and
+    identification efficiency bins (pT 0.1 and 1 GeV, |eta| 1.5 and 2.5),
+    resolution rows, the candidate pT floor (10 GeV, strict), the isolation
+    object floor (0.5 GeV) and cone edges (dR = 0.3 and 0.01 from a
+    candidate), a track exactly tangent to the barrel (2 pT = c), and every
+    class rule, unphysical pairings of pdg and charge included."""
+    cid, ocard = cards["cms_like"]
+    M, ME, MMU = 0.13957039, 0.000511, 0.1056583755
+    f32 = lambda x: float(np.float32(x))
+    ev_a = []
+    for pt in (f32(0.1), 1.0, f32(0.0999999), f32(1.0000001)):
+        for eta in (0.0, 1.5, -1.5, 2.5, -2.5):
+            ev_a.append((pt, eta, 0.7 * len(ev_a) % 6.28 - 3.14, M, 211, 1))
+    for pdg, q, m in ((11, -1, ME), (13, -1, MMU), (22, 0, 0.0)):
+        for pt in (10.0, f32(10.000001)):
+            for eta in (0.5, 1.5, -2.5):
+                ev_a.append((pt, eta, 0.9 * len(ev_a) % 6.28 - 3.14, m, pdg, q))
+    # isolation: candidate electron at (0, 0); tracks on the cone edges and the object floor
+    ev_b = [(50.0, 0.0, 0.0, ME, 11, -1), (5.0, 0.3, 0.0, M, 211, 1), (5.0, -0.3, 0.0, M, -211, -1),
+            (5.0, 0.01, 0.0, M, 211, 1), (5.0, 0.0, 0.3, M, 211, 1), (0.5, 0.1, 0.1, M, 211, 1),
+            (f32(0.5000001), -0.1, 0.1, M, 211, 1), (3.0, 0.0, f32(0.2999999), M, 211, 1)]
+    # a track exactly tangent to the barrel: 2 pT = c = 0.299792458 |q| |B| R in float32
+    c = f32(0.299792458 * 3.8 * 1.29)
+    ev_b += [(c / 2, 0.3, 1.0, M, 211, 1), (c / 2, -0.8, 2.0, M, -211, -1), (f32(c / 2 * 0.9999999), 0.3, 1.5, M, 211, 1)]
+    # classes: charge and pdg disagree, neutrinos, baryons, kaons
+    ev_c = [(7.0, 0.2, 0.1, M, 211, 0), (7.0, 0.3, 0.2, 0.0, 22, 1), (7.0, 0.4, 0.3, 0.0, 12, 0),
+            (7.0, 0.5, 0.4, 0.0, -14, 0), (7.0, 0.6, 0.5, 0.0, 16, 0), (7.0, 0.7, 0.6, 0.938272, 2212, 1),
+            (7.0, 0.8, 0.7, 0.939565, 2112, 0), (7.0, 0.9, 0.8, 0.497611, 130, 0), (7.0, 1.0, 0.9, 0.493677, -321, -1),
+            (7.0, 1.1, 1.0, ME, -11, 1), (7.0, 1.2, 1.1, MMU, -13, 1), (7.0, 1.3, 1.2, 0.0, 0, 0),
+            (7.0, 1.4, 1.3, ME, 11, 0), (7.0, 1.45, 1.4, 5.0, 1000020040, 2)]
+    b = synth.from_particles([ev_a, ev_b, ev_c])
+    host, st = _check_all(ctx, cards, "cms_like", b, seed=29)
+    print("stage boundaries: marginal", st.marginal, "flipped", st.flips)
+    assert st.marginal > 0
+
+
 def test_charges_and_field_directions(B, ctx, synth):
     """Multiply charged particles (|q| = 2, and |q| = 10 beyond the table of
     precomputed reach constants), vertices off the origin, and the CMS-like
