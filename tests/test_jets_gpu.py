@@ -235,6 +235,38 @@ def test_many_coincident_objects(B, ctx):
         assert int(g[:gc[0], 5].view(np.uint32).max()) >= 200
 
 
+def test_clustering_boundaries(B, ctx):
+    """Truth events on the clustering's boundaries, against the oracle under
+    the forced-step protocol: an empty event, a single object, pairs exactly
+    R apart in rapidity (merge or beam is a tie), pairs straddling phi = +-pi,
+    objects far forward (|eta| = 8), massive objects (y != eta), a jet of
+    exactly pt_min, for anti-kT, C/A and kT."""
+    from paper_2606_26089_b300 import synth
+    f32 = lambda x: float(np.float32(x))
+    M = 0.13957039
+    events = [
+        [],
+        [(20.0, 0.5, 1.0, 0.0, 22, 0)],
+        [(20.0, 0.0, 0.0, 0.0, 22, 0), (15.0, 0.5, 0.0, 0.0, 22, 0), (12.0, -2.0, 1.0, 0.0, 22, 0),
+         (12.0, -2.0, f32(1.0 + 0.5), 0.0, 22, 0)],
+        [(25.0, 1.0, f32(3.1), 0.0, 22, 0), (18.0, 1.05, f32(-3.1), 0.0, 22, 0),
+         (11.0, -1.0, f32(np.pi), 0.0, 22, 0), (9.0, -1.0, f32(-np.pi), 0.0, 22, 0)],
+        [(30.0, 8.0, 0.2, 0.0, 22, 0), (30.0, -8.0, 0.2, 0.0, 22, 0), (14.0, 7.8, 0.3, M, 211, 1)],
+        [(40.0, 0.3, 0.5, 5.0, 211, 1), (40.0, 0.4, 0.6, 20.0, 211, 1), (10.0, -1.5, -2.0, 0.0, 22, 0),
+         (f32(9.999999), 2.0, 2.0, 0.0, 22, 0)],
+    ]
+    batch = synth.from_particles(events)
+    cid = ctx.card_load("cms_like")
+    dev = B.batch_to_device(batch)
+    for algorithm, p_ in (("antikt", -1.0), ("cambridge", 0.0), ("kt", 1.0)):
+        params = B.make_jet_params("truth", algorithm, 0.5, 10.0, 1)
+        g, gc = _gpu_jets(B, ctx, batch, dev, cid, None, params)
+        assert gc[0] == 0 and gc[1] == 1
+        for e in range(batch.n_events):
+            a = int(batch.offsets[e])
+            _match(g[a:a + gc[e]], OF.truth_four_momenta(batch.event(e)), p=p_, R=0.5, pt_min=10.0, nconst_min=1)
+
+
 def test_event_beyond_the_shared_memory_workspace_is_refused(B, ctx):
     """An event with more clustering objects than one warp's shared-memory
     workspace holds is refused on the host (no launch)."""
