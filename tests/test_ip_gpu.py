@@ -117,6 +117,33 @@ def test_vertices_on_the_axis_ee_like(B, ctx):
     _check(B, ctx, "ee_like", batch, z, z, v0_zero=True)
 
 
+def test_wide_displacements_and_momenta(B, ctx):
+    """Charged pions and doubly charged ions with pT from 0.12 GeV to 1 TeV
+    (helix radii from 0.1 m to about 1 km), vertices from 1 um to 0.5 m off
+    the axis in every direction (inside and outside the helix), |vz| up to
+    0.3 m, on the CMS-like card: the closed form's cancellations at both ends
+    of the range against the oracle."""
+    from paper_2606_26089_b300 import synth
+    rng = np.random.default_rng(71)
+    events, vxs, vys = [], [], []
+    for e in range(40):
+        ev = []
+        for k in range(80):
+            q = int(rng.choice([1, -1, 2, -2]))
+            pdg = {1: 211, -1: -211, 2: 1000020040, -2: -1000020040}[q]
+            m = 0.13957039 if abs(q) == 1 else 3.727
+            pt = float(np.exp(rng.uniform(np.log(0.12), np.log(1000.0))))
+            rad, ang = float(np.exp(rng.uniform(np.log(1e-6), np.log(0.5)))), float(rng.uniform(-np.pi, np.pi))
+            ev.append((pt, float(rng.uniform(-2.4, 2.4)), float(rng.uniform(-np.pi, np.pi)), m, pdg, q,
+                       float(rng.uniform(-0.3, 0.3))))
+            vxs.append(rad * np.cos(ang))
+            vys.append(rad * np.sin(ang))
+        events.append(ev)
+    batch = synth.from_particles(events)
+    worst = _check(B, ctx, "cms_like", batch, np.asarray(vxs, np.float32), np.asarray(vys, np.float32))
+    print("wide displacements: worst d0, z0, errors (fractions of tolerance)", worst)
+
+
 def test_bad_resolutions_are_rejected(B, ctx):
     from paper_2606_26089_b300 import synth
     batch = synth.make_batched(2, seed=1)
