@@ -135,6 +135,22 @@ def test_vertex_times_are_optional(B, ctx, synth):
     _compare(g, rerun(), rerun=rerun)
 
 
+def test_empty_and_single_particle_events(B, ctx, synth):
+    """Hard events that are empty or hold one particle, a minimum-bias pool
+    whose events are empty or hold one particle, and a pool of a single
+    event: every draw and copy against the oracle."""
+    M = 0.13957039
+    hard = synth.from_particles([[], [(5.0, 0.1, 0.2, M, 211, 1)], [], [(7.0, -1.0, 3.0, 0.0, 22, 0)] * 3, []])
+    pool = synth.from_particles([[], [(0.4, 2.0, -1.0, M, -211, -1)], [], [(0.3, 0.5, 0.5, M, 211, 1)] * 2])
+    one = synth.from_particles([[(0.6, -0.4, 1.0, M, 211, 1)]])
+    for p_ in (pool, one):
+        for mean in (0.5, 8.0):
+            g = _gpu_merge(B, ctx, hard, p_, mean)
+            rerun = lambda fl=None, p_=p_, mean=mean: oracle.pileup_merge(hard, p_, mean, SIGMA, ZMAX, True, SEED,
+                                                                         flips=fl)
+            _compare(g, rerun(), rerun=rerun)
+
+
 def test_no_pileup_returns_the_hard_events(B, ctx, synth):
     pool = synth.make_minbias_pool(20)
     hard = synth.make_hard(10)
